@@ -1,0 +1,207 @@
+"""Seeded synthetic inputs for the NSSG build and search.
+
+This module holds no arithmetic of the method itself: it only draws base vectors,
+queries and navigating-node ids.  Both the CUDA path and the CPU oracle consume
+what it produces, so it is the one piece of code the two share.
+
+The paper evaluates on SIFT1M, GIST1M and Deep100M (Sec. 5.1, Table 2), none of
+which ship with this project.  The generators below stand in for them with the
+same shapes, sizes and value ranges:
+
+* ``small``      -- 10,000 x 32 float32, a mixture of 16 isotropic Gaussians
+                    (centres ~ N(0, 4I), unit spread); 1,000 queries.  Sized
+                    like the SIFT10K pre-experiment of Sec. 4.1.
+* ``sift_like``  -- 1,000,000 x 128 float32 holding integers 0..255: 1,000
+                    anisotropic Gaussians (per-cluster random orthonormal basis,
+                    log-uniform per-axis spread 2..30, centre coordinates
+                    N(mu, 40^2)), rounded and clipped, with mu bisected so that
+                    about 30% of all coordinates are zero; 10,000 queries.
+                    Shaped like SIFT1M (Table 2).
+* ``gist_like``  -- 1,000,000 x 960 float32 in [0, 1]: 500 Gaussians passed
+                    through a softplus and divided by the global maximum;
+                    1,000 queries.  Shaped like GIST1M (Table 2).
+* ``deep_like``  -- N x 96 float32, 2,000 Gaussians, L2-normalised rows.
+                    Shaped like Deep100M (Table 2) at a smaller N.
+
+All draws use numpy's PCG64 with a fixed seed, so a configuration is fully
+determined by its name, its sizes and its seed.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+SEED_SMALL = 190706141
+SEED_SIFT = 190706142
+SEED_GIST = 190706143
+SEED_BATCH = 190706144
+SEED_DEEP = 190706145
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    base: np.ndarray      # float32 [n][d], C-contiguous
+    queries: np.ndarray   # float32 [nq][d], C-contiguous
+    K: int                # kNN-graph degree
+    L: int                # candidate pool size (paper's l)
+    R: int                # maximum out-degree (paper's r)
+    alpha: float          # minimum angle in degrees
+    n_nav: int            # navigating nodes (paper's s, or m in Sec. 5.3)
+    info: dict
+
+    @property
+    def n(self) -> int:
+        return self.base.shape[0]
+
+    @property
+    def d(self) -> int:
+        return self.base.shape[1]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def small(n: int = 10_000, d: int = 32, nq: int = 1_000, n_centres: int = 16,
+          seed: int = SEED_SMALL) -> Workload:
+    """Isotropic Gaussian mixture: centres ~ N(0, 4I), points = centre + N(0, I)."""
+    rng = _rng(seed)
+    centres = rng.normal(0.0, 2.0, size=(n_centres, d))
+    lab = rng.integers(0, n_centres, size=n)
+    base = centres[lab] + rng.normal(0.0, 1.0, size=(n, d))
+    qlab = rng.integers(0, n_centres, size=nq)
+    queries = centres[qlab] + rng.normal(0.0, 1.0, size=(nq, d))
+    return Workload("small", np.ascontiguousarray(base, dtype=np.float32),
+                    np.ascontiguousarray(queries, dtype=np.float32),
+                    K=20, L=100, R=32, alpha=60.0, n_nav=3,
+                    info={"seed": seed, "n_centres": n_centres})
+
+
+def _random_orthonormal(rng: np.random.Generator, d: int) -> np.ndarray:
+    a = rng.normal(size=(d, d))
+    q, r = np.linalg.qr(a)
+    return q * np.sign(np.diag(r))[None, :]
+
+
+def sift_like(n: int = 1_000_000, d: int = 128, nq: int = 10_000, n_clusters: int = 1_000,
+              zero_frac: float = 0.30, seed: int = SEED_SIFT) -> Workload:
+    """Integer-valued (0..255) anisotropic Gaussian mixture with ~30% zeros."""
+    rng = _rng(seed)
+    n_clusters = min(n_clusters, max(1, (n + nq) // 8))
+    offsets = rng.normal(0.0, 40.0, size=(n_clusters, d))
+    spreads = np.exp(rng.uniform(np.log(2.0), np.log(30.0), size=(n_clusters, d)))
+    lab = rng.integers(0, n_clusters, size=n + nq)
+    z = rng.normal(size=(n + nq, d))
+    y = np.empty((n + nq, d), dtype=np.float64)
+    order = np.argsort(lab, kind="stable")
+    bounds = np.searchsorted(lab[order], np.arange(n_clusters + 1))
+    for c in range(n_clusters):
+        basis = _random_orthonormal(rng, d)
+        idx = order[bounds[c]:bounds[c + 1]]
+        y[idx] = offsets[c] + (z[idx] * spreads[c]) @ basis.T
+    # Bisect the common shift mu so that the rounded, clipped data holds the requested
+    # fraction of zeros; evaluated on a fixed subsample of coordinates.
+    flat = y.reshape(-1)
+    sub = flat[rng.integers(0, flat.size, size=min(flat.size, 2_000_000))]
+    lo, hi = -200.0, 400.0
+    for _ in range(60):
+        mu = 0.5 * (lo + hi)
+        frac = np.mean(np.rint(sub + mu) <= 0.0)
+        if frac > zero_frac:
+            lo = mu
+        else:
+            hi = mu
+    mu = 0.5 * (lo + hi)
+    x = np.clip(np.rint(y + mu), 0.0, 255.0).astype(np.float32)
+    perm = rng.permutation(n + nq)
+    x = x[perm]
+    base = np.ascontiguousarray(x[:n])
+    queries = np.ascontiguousarray(x[n:])
+    return Workload("sift_like", base, queries, K=200, L=100, R=50, alpha=60.0, n_nav=10,
+                    info={"seed": seed, "n_clusters": n_clusters, "mu": float(mu),
+                          "zero_frac": float(np.mean(base == 0.0))})
+
+
+def gist_like(n: int = 1_000_000, d: int = 960, nq: int = 1_000, n_clusters: int = 500,
+              seed: int = SEED_GIST, chunk: int = 65_536) -> Workload:
+    """Non-negative data in [0, 1]: softplus of a Gaussian mixture, divided by the global max."""
+    rng = _rng(seed)
+    centres = rng.normal(0.0, 1.0, size=(n_clusters, d)).astype(np.float32)
+    lab = rng.integers(0, n_clusters, size=n + nq)
+    x = np.empty((n + nq, d), dtype=np.float32)
+    for s in range(0, n + nq, chunk):
+        e = min(n + nq, s + chunk)
+        v = centres[lab[s:e]] + rng.normal(0.0, 0.5, size=(e - s, d)).astype(np.float32)
+        x[s:e] = np.logaddexp(np.float32(0.0), v)
+    x /= x.max()
+    return Workload("gist_like", np.ascontiguousarray(x[:n]), np.ascontiguousarray(x[n:]),
+                    K=100, L=500, R=70, alpha=60.0, n_nav=10,
+                    info={"seed": seed, "n_clusters": n_clusters})
+
+
+def deep_like(n: int = 10_000_000, d: int = 96, nq: int = 10_000, n_clusters: int = 2_000,
+              seed: int = SEED_DEEP, chunk: int = 262_144) -> Workload:
+    """L2-normalised Gaussian mixture (unit-norm rows)."""
+    rng = _rng(seed)
+    centres = rng.normal(0.0, 1.0, size=(n_clusters, d)).astype(np.float32)
+    lab = rng.integers(0, n_clusters, size=n + nq)
+    x = np.empty((n + nq, d), dtype=np.float32)
+    for s in range(0, n + nq, chunk):
+        e = min(n + nq, s + chunk)
+        v = centres[lab[s:e]] + rng.normal(0.0, 0.35, size=(e - s, d)).astype(np.float32)
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        x[s:e] = v
+    return Workload("deep_like", np.ascontiguousarray(x[:n]), np.ascontiguousarray(x[n:]),
+                    K=100, L=100, R=32, alpha=60.0, n_nav=10,
+                    info={"seed": seed, "n_clusters": n_clusters})
+
+
+def uniform_points(n: int, d: int, seed: int, integer: bool = False, hi: int = 255) -> np.ndarray:
+    """Uniform points for tiny test cases: [0,1)^d floats, or integers 0..hi."""
+    rng = _rng(seed)
+    if integer:
+        return rng.integers(0, hi + 1, size=(n, d)).astype(np.float32)
+    return rng.random(size=(n, d)).astype(np.float32)
+
+
+# --- navigating-node ids -------------------------------------------------------------
+# SplitMix64 (G. Steele, D. Lea, C. Flood, "Fast splittable pseudorandom number
+# generators", OOPSLA 2014; the constants are those of the published finaliser).
+_M64 = (1 << 64) - 1
+
+
+def splitmix64_stream(seed: int):
+    state = seed & _M64
+    while True:
+        state = (state + 0x9E3779B97F4A7C15) & _M64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        yield z ^ (z >> 31)
+
+
+def nav_ids(n: int, s: int, seed: int) -> np.ndarray:
+    """s distinct node ids in draw order: successive SplitMix64 outputs modulo n,
+    repeats skipped.  The library draws the same ids when it is given only a seed."""
+    if s > n:
+        raise ValueError("more navigating nodes than points")
+    out: list[int] = []
+    seen: set[int] = set()
+    for z in splitmix64_stream(seed):
+        v = int(z % n)
+        if v not in seen:
+            seen.add(v)
+            out.append(v)
+            if len(out) == s:
+                break
+    return np.asarray(out, dtype=np.int32)
+
+
+CONFIGS = {
+    "small": small,
+    "sift_like": sift_like,
+    "gist_like": gist_like,
+    "deep_like": deep_like,
+}
