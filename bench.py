@@ -1,0 +1,409 @@
+"""Benchmark of the NSSG hot path on GB300.
+
+One step = one pass of the whole path over one synthetic workload: ingest, exact kNN
+graph, candidate pools, SSG prune, reverse-neighbour merge, navigating-node connectivity
+(the build, Alg. 3), then Search-on-Graph (Alg. 1) for every query and the brute-force
+ground truth with recall@10 (Sec. 5.2).
+
+Workload (default): 1,000,000 x 128 integer-valued vectors shaped like SIFT1M (synthetic,
+seeded), K = 200, L = 100, R = 50, alpha = 60 degrees, 10 navigating nodes, 10,000
+queries; L_search is the smallest value of a sweep whose recall@10 reaches 0.95.
+
+Prints one JSON line.  `value` is build seconds per million points (lower is better);
+search QPS at recall@10 >= 0.95 is reported beside it.  Under torchrun every rank builds
+its own replica (no collective on the data path) and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NSSG build s/1M pts & QPS@recall@10=0.95, mixed-prec vs plain FP32 path"
+LS_SWEEP = [10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 100, 128, 160, 200, 256, 320, 400, 512, 768,
+            1024]
+NOMINAL_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(values, ws):
+    """Element-wise max over ranks of a list of floats (identity for one rank)."""
+    if ws == 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(values, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.cpu().tolist()
+
+
+def aggregate(step_ms, points_per_rank, ws):
+    """Whole-job build time per million points: the slowest rank's mean step time over the
+    points all ranks built (replicas: every rank builds its own index)."""
+    worst = reduce_max([float(np.mean(step_ms))], ws)[0]
+    total_points = points_per_rank * ws
+    return worst / 1000.0 / (total_points / 1e6), worst
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1].split()[0]))
+                    mx.append(float(parts[2].split()[0]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names[1:], parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(busy)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("knn.cu", "knn_tc.cu", "knn.cuh", "common.cuh"):
+        p = os.path.join(ROOT, "paper_1907_06146_gb300", "csrc", f)
+        if os.path.exists(p):
+            with open(p, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(f"{kernel}:{workload}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def make_workload(name: str, n: int | None, rank: int):
+    from paper_1907_06146_gb300 import synth
+    kw = {}
+    if n is not None:
+        kw["n"] = n
+    if name == "sift_like":
+        return synth.sift_like(seed=synth.SEED_SIFT + rank, **kw)
+    if name == "small":
+        return synth.small(seed=synth.SEED_SMALL + rank, **kw)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample of the same workload.
+# ---------------------------------------------------------------------------------------
+def oracle_sample_seconds_per_million(w, n_nodes: int, seed: int):
+    """Times the oracle's kNN rows (for each sampled node and for the neighbours whose rows
+    its pool reads), pools and prunes of n_nodes seeded random nodes, and extrapolates to
+    seconds per million points.  The reverse merge and connectivity are not in the sample."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    nodes = np.sort(rng.choice(w.n, size=n_nodes, replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    ids, _ = oracle.knn_rows(w.base, w.K, rows=nodes)
+    t1 = time.perf_counter()
+    # rows the pool walk reads: the node's own row and those of its neighbours up to the
+    # point where the pool reaches L (with K >= L only the first neighbour's row)
+    need = []
+    for r in range(n_nodes):
+        cnt = 0
+        for t in range(w.K):
+            need.append(int(ids[r, t]))
+            cnt += 1 + w.K
+            if cnt >= w.L:
+                break
+    need = np.unique(np.asarray(need, np.int64))
+    need = need[~np.isin(need, nodes)]
+    t2 = time.perf_counter()
+    nb_ids, _ = oracle.knn_rows(w.base, w.K, rows=need)
+    t3 = time.perf_counter()
+    knn = np.zeros((w.n, w.K), np.int32)
+    knn[nodes] = ids
+    knn[need] = nb_ids
+    t4 = time.perf_counter()
+    pid, _, pl = oracle.pool(w.base, knn, w.L, rows=nodes)
+    oracle.prune(w.base, pid, pl, w.R, w.alpha, nodes=nodes)
+    t5 = time.perf_counter()
+    knn_rows = n_nodes + need.size
+    per_row = ((t1 - t0) + (t3 - t2)) / knn_rows
+    per_node = (t5 - t4) / n_nodes
+    return (per_row + per_node) * 1e6, {"knn_rows": int(knn_rows), "nodes": n_nodes,
+                                        "sec": (t1 - t0) + (t3 - t2) + (t5 - t4)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = make_workload(args.workload, args.n, 0)
+    cores = oracle.max_threads()
+    per_step = []
+    for s in range(args.warmup + args.steps):
+        v, info = oracle_sample_seconds_per_million(w, args.ref_nodes, 1000 + s)
+        if s >= args.warmup:
+            per_step.append(v)
+    value = float(np.mean(per_step))
+    sample = (f"oracle kNN rows + pools + prunes of {args.ref_nodes} seeded random nodes of the "
+              f"{w.n}x{w.d} workload per step, extrapolated to 1M points; reverse merge and "
+              f"connectivity not sampled")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/1M pts",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{w.name} n={w.n} d={w.d} K={w.K} L={w.L} R={w.R} "
+                                   f"alpha={w.alpha} nav={w.n_nav}"},
+            "cpu_baseline": {"value": value, "unit": "s/1M pts", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "s/1M pts", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1907_06146_gb300 import ssg, synth
+    ssg.lib()
+
+    w = make_workload(args.workload, args.n, rank)
+    nav = synth.nav_ids(w.n, w.n_nav, synth.SEED_DEEP + rank)
+    base = torch.from_numpy(w.base).cuda()
+    queries = torch.from_numpy(w.queries).cuda()
+    nq = w.queries.shape[0]
+    stream = torch.cuda.current_stream()
+
+    def step(ls):
+        g = ssg.build(base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ids, _ = g.search(base, queries, 10, ls)
+        e1.record(stream)
+        truth, _ = ssg.knn_query(base, queries, 10)
+        e2.record(stream)
+        hits = ssg.recall_hits(ids, truth, 10)
+        torch.cuda.synchronize()
+        return g, ids, e0.elapsed_time(e1), e1.elapsed_time(e2), hits / (nq * 10.0)
+
+    # calibration: smallest L_search of the sweep with recall@10 >= 0.95
+    g = ssg.build(base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec)
+    truth, _ = ssg.knn_query(base, queries, 10)
+    ls_used, rec_used = LS_SWEEP[-1], None
+    sweep = []
+    for ls in LS_SWEEP:
+        ids, _ = g.search(base, queries, 10, ls)
+        r = ssg.recall_hits(ids, truth, 10) / (nq * 10.0)
+        sweep.append((ls, r))
+        if r >= args.target_recall:
+            ls_used, rec_used = ls, r
+            break
+    del g
+
+    for _ in range(args.warmup):
+        step(ls_used)
+
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ssg.launch_count()
+    build_ms, search_ms, gt_ms, recalls, stats = [], [], [], [], []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        g, ids, s_ms, gt, rec = step(ls_used)
+        build_ms.append(g.stats["ms_total"])
+        stats.append(g.stats)
+        search_ms.append(s_ms)
+        gt_ms.append(gt)
+        recalls.append(rec)
+        del g
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t_wall0
+    launches = ssg.launch_count() - launches0
+    clk = clocks.stop()
+
+    value, worst_build_ms = aggregate(build_ms, w.n, ws)
+    worst_search_ms = reduce_max([float(np.mean(search_ms))], ws)[0]
+    qps = nq * ws / (worst_search_ms / 1000.0)
+
+    # end to end through the host-buffer entry point: H2D of the base and D2H of the graph
+    # inside the timed region
+    pinned = torch.from_numpy(w.base).pin_memory()
+    host_base = pinned.numpy()
+    e2e_ms = []
+    for s in range(1 + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g, adj_h, deg_h = ssg.build_host(host_base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec)
+        t1 = time.perf_counter()
+        del g
+        if s > 0:
+            e2e_ms.append((t1 - t0) * 1000.0)
+    e2e_value, _ = aggregate(e2e_ms, w.n, ws)
+
+    # roofline of the dominant kernel: the distance GEMM + top-K selection
+    peaks = load_peaks()
+    gemm_ms = float(np.mean([s["ms_knn_gemm"] for s in stats]))
+    flops = 2.0 * w.n * (w.n - 1) * w.d
+    used_prec = stats[0]["gemm_prec_used"]
+    if used_prec == 1:
+        kname = "knn_select_bf16_tc"
+        peak = peaks["bf16_tflops_sustained"]
+        bound, peak_note = "tensor", f"bf16 dense, {peaks['source']} sustained"
+    else:
+        kname = "knn_select_fp32"
+        peak = NOMINAL_SM * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        bound, peak_note = "alu", "fp32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
+    achieved = flops / (gemm_ms / 1000.0) / 1e12
+    traffic = committed_traffic(kname, w.name)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        v, info = oracle_sample_seconds_per_million(w, args.ref_nodes, 4242)
+        cpu = {"value": v, "unit": "s/1M pts", "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"{args.ref_nodes} seeded random nodes: their exact kNN rows and those "
+                         f"of the neighbours their pools read ({info['knn_rows']} rows of "
+                         f"{w.n}x{w.d}), pools and prunes; extrapolated to 1M points; reverse "
+                         f"merge and connectivity not sampled"}
+
+    if rank != 0:
+        return
+    st0 = stats[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "s/1M pts", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": wall * 1000.0 / args.steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if used_prec == 1 else "f32", "data": "synthetic",
+        "config": {"workload": f"{w.name} n={w.n} d={w.d} K={w.K} L={w.L} R={w.R} "
+                               f"alpha={w.alpha} nav={w.n_nav} queries={nq}",
+                   "l2": "inputs larger than L2 (base 512 MB)", "gemm_prec": args.prec,
+                   "parallelism": f"replicas x{ws}"},
+        "search": {"qps": qps, "recall@10": float(np.mean(recalls)), "L_search": ls_used,
+                   "k": 10, "ms": float(np.mean(search_ms)), "sweep": sweep},
+        "stages_ms": {k: float(np.mean([s[k] for s in stats])) for k in
+                      ("ms_ingest", "ms_knn", "ms_knn_gemm", "ms_pool", "ms_prune", "ms_reverse",
+                       "ms_connect", "ms_total")},
+        "ground_truth_ms": float(np.mean(gt_ms)),
+        "counters": {k: st0[k] for k in ("n_repair", "n_angle_fp64", "n_order_fp64",
+                                         "n_knn_fallback_rows", "max_indegree", "exact_mode")},
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                     "peak_source": peak_note, "algorithmic": "2 n (n-1) d flop per launch"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "s/1M pts", "h2d_bytes_per_step": int(w.base.nbytes),
+                "d2h_bytes_per_step": int(w.n * w.R * 4 + w.n * 4)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "worst_rank_build_ms": worst_build_ms,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sift_like", choices=["sift_like", "small"])
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16"])
+    ap.add_argument("--target-recall", type=float, default=0.95)
+    ap.add_argument("--ref-nodes", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * ssg.h -- C ABI of the GB300 (sm_103a) NSSG library.
+ *
+ * NSSG = Navigating Satellite System Graph, from "High Dimensional Similarity Search
+ * with Satellite System Graph" (Fu, Wang, Cai; arXiv 1907.06146).  The library builds
+ * the graph index of Alg. 3 (exact kNN graph -> 2-hop candidate pools -> SSG angle
+ * prune -> reverse-neighbour merge -> connectivity from navigating nodes) and runs
+ * Search-on-Graph (Alg. 1) from the nearest navigating node (Sec. 4.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller unless the name ends in
+ *    _host.  Vectors are float32, row-major, one row of d values per point.  Ids are
+ *    int32 (n < 2^31).  Adjacency rows are int32 [n][R], padded with -1 after deg[i].
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Staged entry points
+ *    enqueue their kernels on it and return; ssg_build and ssg_connect synchronise the
+ *    stream at stage boundaries to read sizes.
+ *  - Scratch memory is taken from the CUDA stream-ordered allocator on `stream` and
+ *    released before the call returns (in stream order).
+ *  - Errors come back as an ssg_status; nothing is thrown across the ABI.  After a
+ *    non-OK status, ssg_last_error() gives a message for the calling thread.  EINVAL
+ *    means an argument is out of range and nothing was enqueued.
+ *  - Orders: every list the library returns is sorted by (squared distance, id)
+ *    ascending; squared Euclidean distance orders like the distance of Sec. 2.1.
+ *  - Results are exact with respect to double-precision arithmetic on the float32
+ *    inputs: fast single-precision (or tensor-core) results decide only where a
+ *    rigorous error bound separates them from the decision boundary, and the rest is
+ *    re-decided in double precision (counters in ssg_build_stats).
+ */
+#ifndef SSG_H
+#define SSG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SSG_OK = 0,
+  SSG_EINVAL = 1,     /* an argument is out of range; nothing was enqueued */
+  SSG_ENOMEM = 2,     /* a device allocation failed */
+  SSG_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+  SSG_ETIMEOUT = 4,   /* a bounded device wait gave up (device status word set) */
+  SSG_EINTERNAL = 5,  /* an internal capacity or invariant was exceeded */
+  SSG_EIO = 6         /* ssg_save / ssg_load could not read or write the file */
+} ssg_status;
+
+typedef enum {
+  SSG_PREC_FP32 = 0,  /* single-precision SIMT distance GEMM */
+  SSG_PREC_BF16 = 1,  /* bf16 tensor-core distance GEMM (exact on small integers) */
+  SSG_PREC_AUTO = 2   /* bf16 where the data make it exact, fp32 otherwise */
+} ssg_precision;
+
+typedef void* ssg_stream; /* cudaStream_t */
+
+/* Build options.  Initialise with ssg_default_opts(). */
+typedef struct {
+  ssg_precision gemm_prec;  /* precision of the kNN distance GEMM */
+  int32_t n_nav;            /* navigating nodes s (Alg. 3 input; Sec. 5.3 uses 10) */
+  const int32_t* nav_ids_host; /* optional: n_nav distinct ids in [0, n) (host memory);
+                                  NULL = draw them with ssg_nav_ids(n, n_nav, seed) */
+  uint64_t seed;            /* seed for the navigating-node draw */
+  int32_t debug_checks;     /* nonzero: check graph invariants after each stage */
+} ssg_build_opts;
+
+/* Per-build measurements (all times from CUDA events on the build stream). */
+typedef struct {
+  double ms_ingest, ms_knn, ms_pool, ms_prune, ms_reverse, ms_connect, ms_total;
+  int64_t n_repair;             /* edges added by the connectivity step */
+  int64_t n_angle_fp64;         /* angle decisions re-tested in fp64 (|cos - cos a| small) */
+  int64_t n_order_fp64;         /* near-tie orderings re-sorted in fp64 */
+  int64_t n_knn_fallback_rows;  /* kNN rows recomputed exhaustively in fp64 */
+  int32_t max_indegree;         /* largest in-degree seen by the reverse merge */
+  int32_t exact_mode;           /* 1 if the inputs are small integers (all fp32 exact) */
+  int64_t kernel_launches;      /* kernels this call launched */
+  int32_t gemm_prec_used;       /* ssg_precision actually used for the kNN GEMM */
+  double ms_knn_gemm;           /* time of the distance-GEMM + selection kernel alone */
+} ssg_build_stats;
+
+typedef struct ssg_graph ssg_graph; /* opaque, owned by the library; ssg_free releases it */
+
+/* ---- housekeeping -------------------------------------------------------------------- */
+void ssg_default_opts(ssg_build_opts* opts);
+const char* ssg_strerror(ssg_status s);
+const char* ssg_last_error(void);        /* message of the last failure on this thread */
+int64_t ssg_kernel_launch_count(void);   /* kernels launched by this process so far */
+
+/* Navigating nodes (Alg. 3: "random select s points"): s distinct ids in [0, n), the
+ * successive SplitMix64 outputs (Steele, Lea, Flood 2014) modulo n with repeats skipped.
+ * Host only; out_host has room for s ids.  EINVAL if s < 1 or s > n. */
+ssg_status ssg_nav_ids(int64_t n, int32_t s, uint64_t seed, int32_t* out_host);
+
+/* ---- staged entry points (each step of Alg. 3 / Alg. 1 on its own) --------------------- */
+
+/* Exact kNN graph (Alg. 3 line 1, computed exactly): for every i, the K nearest j != i
+ * by (d2, id).  knn_id int32 [n][K], knn_d2 float32 [n][K] (d2 rounded to float32).
+ * EINVAL if n < 2, d < 1, K < 1, K > n - 1 or K > 768. */
+ssg_status ssg_knn(const float* base, int64_t n, int32_t d, int32_t K, ssg_precision prec,
+                   int32_t* knn_id, float* knn_d2, ssg_stream stream);
+
+/* Brute-force ground truth for unindexed queries (serial scan, Sec. 5.3 item 8): the k
+ * base points nearest each query by (d2, id).  ids int32 [nq][k], d2 float32 [nq][k].
+ * EINVAL if k < 1, k > n or k > 768. */
+ssg_status ssg_knn_query(const float* base, int64_t n, int32_t d, const float* queries,
+                         int64_t nq, int32_t k, ssg_precision prec, int32_t* ids, float* d2,
+                         ssg_stream stream);
+
+/* Candidate pools (Alg. 3, neighbours and neighbours' neighbours of each node): walk
+ * knn(i) in order, adding n and then knn(n), skipping i and repeats, and stop after the
+ * first n at which the pool holds >= L ids; sort by (d2(i, .), id) and keep the first L.
+ * pool_id int32 [n][L] (-1 padded), pool_d2 float32 [n][L], pool_len int32 [n].
+ * EINVAL if L < 1 or L + K > 1023. */
+ssg_status ssg_pool(const float* base, int64_t n, int32_t d, const int32_t* knn_id, int32_t K,
+                    int32_t L, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
+                    ssg_stream stream);
+
+/* SSG prune (Alg. 2 selection, applied to each pool by Alg. 3): keep the first candidate;
+ * keep each later one unless cos(angle j-i-k) > cos(alpha) for a kept k (cos from the
+ * centred dot products, 0 for a zero-length edge); stop once R are kept.
+ * pool_id [n][L] sorted as ssg_pool leaves it; adj int32 [n][R], deg int32 [n].
+ * EINVAL if R < 1, R > 128, alpha outside (0, 180) or R * (d + 1) * 4 > 96 KiB. */
+ssg_status ssg_prune(const float* base, int64_t n, int32_t d, const int32_t* pool_id,
+                     const int32_t* pool_len, int32_t L, int32_t R, double alpha_deg,
+                     int32_t* adj, int32_t* deg, ssg_stream stream);
+
+/* Reverse-neighbour merge (Alg. 3, reverse neighbour checking; Sec. 4.1): every node j
+ * re-prunes adj0[j] united with {i : j in adj0[i]}, sorted by (d2(j, .), id), with the
+ * same rule and cap R.  adj0/adj1 int32 [n][R]; deg0/deg1 int32 [n].
+ * EINTERNAL if some node has more than 16383 candidates (in-degree + R). */
+ssg_status ssg_reverse(const float* base, int64_t n, int32_t d, const int32_t* adj0,
+                       const int32_t* deg0, int32_t R, double alpha_deg, int32_t* adj1,
+                       int32_t* deg1, ssg_stream stream);
+
+/* Connectivity from navigating nodes (Alg. 3, DFS-spanning from each node of NV; details
+ * in the NSG paper): for each root in order, while some node is unreachable from it,
+ * link the smallest unreached id u from the reached node v with deg(v) < R that minimises
+ * (d2(v, u), id) and mark all reachable from u.  adj/deg are updated in place; nav is a
+ * device array of n_nav ids; *n_repair_host receives the number of added edges.
+ * EINTERNAL if an unreached node remains and no reached node has a free slot. */
+ssg_status ssg_connect(const float* base, int64_t n, int32_t d, int32_t* adj, int32_t* deg,
+                       int32_t R, const int32_t* nav, int32_t n_nav, int64_t* n_repair_host,
+                       ssg_stream stream);
+
+/* Search-on-Graph (Alg. 1) from the navigating node nearest each query (Sec. 4.1): a pool
+ * of at most L_search entries sorted by (d2, id); expand the first unchecked entry, add
+ * every neighbour not visited before, re-sort, cut to L_search; stop when all entries are
+ * checked; return the first k (padded with -1 / +inf).  out_d2 may be NULL.
+ * EINVAL if k < 1, k > L_search or L_search > 1024. */
+ssg_status ssg_search_adj(const float* base, int64_t n, int32_t d, const int32_t* adj,
+                          const int32_t* deg, int32_t R, const int32_t* nav, int32_t n_nav,
+                          const float* queries, int64_t nq, int32_t k, int32_t L_search,
+                          int32_t* out_ids, float* out_d2, ssg_stream stream);
+
+/* Hits for precision(R) = |R n G| / |G| (Sec. 5.2): the number of (query, id) pairs where
+ * id is among the first k of both found [nq][ld_found] and truth [nq][ld_truth].
+ * *hits_host receives the count (the call synchronises the stream). */
+ssg_status ssg_recall_hits(const int32_t* found, int32_t ld_found, const int32_t* truth,
+                           int32_t ld_truth, int64_t nq, int32_t k, int64_t* hits_host,
+                           ssg_stream stream);
+
+/* ---- whole build and search ---------------------------------------------------------- */
+
+/* NSSGIndexing (Alg. 3) end to end on device-resident base vectors.  `base` must stay
+ * alive and unchanged while the graph is searched.  *out receives a graph owned by the
+ * library.  stats may be NULL. */
+ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
+                     double alpha_deg, const ssg_build_opts* opts, ssg_stream stream,
+                     ssg_graph** out, ssg_build_stats* stats);
+
+/* Same as ssg_build from HOST base vectors: the library copies them to a device buffer
+ * that the graph owns, builds, and (when adj_host/deg_host are not NULL) copies the
+ * adjacency [n][R] and degrees [n] back to host memory.  Pinned host memory is fastest. */
+ssg_status ssg_build_host(const float* base_host, int64_t n, int32_t d, int32_t K, int32_t L,
+                          int32_t R, double alpha_deg, const ssg_build_opts* opts,
+                          ssg_stream stream, ssg_graph** out, int32_t* adj_host,
+                          int32_t* deg_host, ssg_build_stats* stats);
+
+/* Device views of a graph (no copies).  Any output pointer may be NULL. */
+ssg_status ssg_graph_view(const ssg_graph* g, const int32_t** adj, const int32_t** deg,
+                          const int32_t** nav, int32_t* n_nav, int32_t* R, int64_t* n,
+                          int32_t* d);
+
+/* Alg. 1 on a built graph.  `base` is the device array the graph was built from (NULL
+ * for a graph from ssg_build_host, which owns its copy). */
+ssg_status ssg_search(const ssg_graph* g, const float* base, const float* queries, int64_t nq,
+                      int32_t k, int32_t L_search, int32_t* out_ids, float* out_d2,
+                      ssg_stream stream);
+
+/* Alg. 1 with HOST queries and results (copies inside; synchronises the stream).  Needs a
+ * graph from ssg_build_host (which owns its device copy of the base); EINVAL otherwise. */
+ssg_status ssg_search_host(const ssg_graph* g, const float* queries_host, int64_t nq, int32_t k,
+                           int32_t L_search, int32_t* out_ids_host, float* out_d2_host,
+                           ssg_stream stream);
+
+/* Graph file: header (magic, version, n, d, R, n_nav, alpha) + nav + deg + adj. */
+ssg_status ssg_save(const ssg_graph* g, const char* path);
+ssg_status ssg_load(const char* path, ssg_graph** out);
+void ssg_free(ssg_graph* g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSG_H */

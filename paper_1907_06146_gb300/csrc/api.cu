@@ -1,0 +1,609 @@
+// C ABI entry points of the NSSG library (declared in include/ssg.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "graph_dev.cuh"
+#include "knn.cuh"
+
+namespace ssg {
+
+std::atomic<int64_t> g_launches{0};
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+double cos_alpha_of(double a) {
+  if (a == 0.0) return 1.0;
+  if (a == 60.0) return 0.5;
+  if (a == 90.0) return 0.0;
+  if (a == 120.0) return -0.5;
+  if (a == 180.0) return -1.0;
+  return std::cos(a * 3.14159265358979323846 / 180.0);
+}
+
+template <class F>
+static ssg_status guard(F&& f) {
+  try {
+    f();
+    return SSG_OK;
+  } catch (const Fail& e) {
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return SSG_ENOMEM;
+  } catch (...) {
+    set_error("unexpected exception");
+    return SSG_EINTERNAL;
+  }
+}
+
+// Kernel that counts, per query, the ids found among the first k of both lists.
+__global__ void k_recall_hits(const int32_t* __restrict__ found, int ldf,
+                              const int32_t* __restrict__ truth, int ldt, int64_t nq, int k,
+                              unsigned long long* __restrict__ hits) {
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= nq) return;
+  const int lane = lane_id();
+  unsigned c = 0;
+  for (int t = lane; t < k; t += 32) {
+    const int32_t id = found[q * ldf + t];
+    if (id < 0) continue;
+    for (int u = 0; u < k; ++u)
+      if (truth[q * ldt + u] == id) {
+        ++c;
+        break;
+      }
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0 && c) atomicAdd(hits, (unsigned long long)c);
+}
+
+static void check_alpha(double a) {
+  SSG_REQUIRE(a > 0.0 && a < 180.0, SSG_EINVAL, "alpha must lie in (0, 180) degrees, got %g", a);
+}
+static void check_prune_fit(int d, int R) {
+  SSG_REQUIRE(R >= 1 && R <= 128, SSG_EINVAL, "R must lie in [1, 128], got %d", R);
+  SSG_REQUIRE(prune_smem_floats(d, R) * 4 <= 96 * 1024, SSG_EINVAL,
+              "R * (d + 1) * 4 bytes must fit 96 KiB of shared memory (d=%d, R=%d)", d, R);
+}
+
+struct Ingested {
+  PaddedRows rows;
+  Scratch<float> norms;
+  DataInfo info{};
+};
+
+static void ingest_all(const float* X, int64_t n, int d, cudaStream_t st, Ingested& g,
+                       bool want_norms) {
+  if (want_norms) g.norms.alloc((size_t)n, st);
+  ingest(X, n, d, st, g.rows, want_norms ? g.norms.p : nullptr, &g.info);
+}
+
+}  // namespace ssg
+
+using namespace ssg;
+
+struct ssg_graph {
+  int64_t n = 0;
+  int32_t d = 0, R = 0, n_nav = 0;
+  double alpha = 0;
+  int32_t* adj = nullptr;
+  int32_t* deg = nullptr;
+  int32_t* nav_dev = nullptr;
+  std::vector<int32_t> nav_host;
+  float* base_owned = nullptr;
+  ~ssg_graph() {
+    if (adj) cudaFree(adj);
+    if (deg) cudaFree(deg);
+    if (nav_dev) cudaFree(nav_dev);
+    if (base_owned) cudaFree(base_owned);
+  }
+};
+
+static const char* const kStatusNames[] = {"ok", "invalid argument", "out of device memory",
+                                           "CUDA error", "device wait timed out",
+                                           "internal capacity exceeded", "file I/O error"};
+
+extern "C" {
+
+void ssg_default_opts(ssg_build_opts* o) {
+  if (!o) return;
+  o->gemm_prec = SSG_PREC_AUTO;
+  o->n_nav = 10;
+  o->nav_ids_host = nullptr;
+  o->seed = 190706145ull;
+  o->debug_checks = 0;
+}
+
+const char* ssg_strerror(ssg_status s) {
+  if ((int)s < 0 || (int)s > 6) return "unknown status";
+  return kStatusNames[s];
+}
+
+const char* ssg_last_error(void) { return g_err; }
+
+int64_t ssg_kernel_launch_count(void) { return g_launches.load(); }
+
+ssg_status ssg_nav_ids(int64_t n, int32_t s, uint64_t seed, int32_t* out) {
+  return guard([&] {
+    SSG_REQUIRE(out && s >= 1 && s <= n, SSG_EINVAL, "need 1 <= s <= n (s=%d, n=%lld)", s,
+                (long long)n);
+    uint64_t state = seed;
+    int got = 0;
+    std::vector<char> seen;
+    while (got < s) {
+      state += 0x9E3779B97F4A7C15ull;
+      uint64_t z = state;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      const int32_t v = (int32_t)(z % (uint64_t)n);
+      bool dup = false;
+      for (int t = 0; t < got; ++t) dup |= out[t] == v;
+      if (!dup) out[got++] = v;
+    }
+  });
+}
+
+ssg_status ssg_knn(const float* base, int64_t n, int32_t d, int32_t K, ssg_precision prec,
+                   int32_t* knn_id, float* knn_d2, ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(base && knn_id && knn_d2, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(n >= 2 && n < (1ll << 31) && d >= 1, SSG_EINVAL, "need 2 <= n < 2^31 and d >= 1");
+    SSG_REQUIRE(K >= 1 && K <= n - 1 && K <= 700, SSG_EINVAL, "need 1 <= K <= min(n - 1, 700)");
+    cudaStream_t st = (cudaStream_t)stream;
+    Ingested g;
+    ingest_all(base, n, d, st, g, true);
+    const bool tc = prec != SSG_PREC_FP32 && g.info.bf16_exact && knn_tc_available();
+    SSG_REQUIRE(prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
+                "bf16 distance GEMM needs integer data with |x| <= 256 and 2 d max|x|^2 <= 2^24");
+    if (tc)
+      knn_exact_tc(g.rows.p, n, g.rows.ld, g.norms.p, g.rows.p, n, g.rows.ld, g.norms.p, d, 1, K,
+                   knn_id, knn_d2, st, nullptr);
+    else
+      knn_exact(g.rows.p, n, g.rows.ld, g.norms.p, g.rows.p, n, g.rows.ld, g.norms.p, d, g.info,
+                1, K, knn_id, knn_d2, st, nullptr);
+  });
+}
+
+ssg_status ssg_knn_query(const float* base, int64_t n, int32_t d, const float* queries,
+                         int64_t nq, int32_t k, ssg_precision prec, int32_t* ids, float* d2,
+                         ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(base && queries && ids && d2, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(n >= 1 && n < (1ll << 31) && d >= 1 && nq >= 0, SSG_EINVAL, "bad sizes");
+    SSG_REQUIRE(k >= 1 && k <= n && k <= 700, SSG_EINVAL, "need 1 <= k <= min(n, 700)");
+    if (nq == 0) return;
+    cudaStream_t st = (cudaStream_t)stream;
+    Ingested gb, gq;
+    ingest_all(base, n, d, st, gb, true);
+    ingest_all(queries, nq, d, st, gq, true);
+    DataInfo info;
+    const float ma = std::max(gb.info.max_abs, gq.info.max_abs);
+    info.exact = gb.info.exact && gq.info.exact && 2.0 * d * (double)ma * ma <= 16777216.0;
+    info.bf16_exact = info.exact && ma <= 256.f;
+    info.max_norm = gb.info.max_norm;
+    info.max_abs = ma;
+    const bool tc = prec != SSG_PREC_FP32 && info.bf16_exact && knn_tc_available();
+    SSG_REQUIRE(prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
+                "bf16 distance GEMM needs integer data with |x| <= 256 and 2 d max|x|^2 <= 2^24");
+    if (tc)
+      knn_exact_tc(gq.rows.p, nq, gq.rows.ld, gq.norms.p, gb.rows.p, n, gb.rows.ld, gb.norms.p, d,
+                   0, k, ids, d2, st, nullptr);
+    else
+      knn_exact(gq.rows.p, nq, gq.rows.ld, gq.norms.p, gb.rows.p, n, gb.rows.ld, gb.norms.p, d,
+                info, 0, k, ids, d2, st, nullptr);
+  });
+}
+
+ssg_status ssg_pool(const float* base, int64_t n, int32_t d, const int32_t* knn_id, int32_t K,
+                    int32_t L, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
+                    ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(base && knn_id && pool_id && pool_d2 && pool_len, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(n >= 2 && d >= 1 && K >= 1 && K <= n - 1, SSG_EINVAL, "bad sizes");
+    SSG_REQUIRE(L >= 1 && L + K <= 1023, SSG_EINVAL, "need L >= 1 and L + K <= 1023");
+    cudaStream_t st = (cudaStream_t)stream;
+    Ingested g;
+    ingest_all(base, n, d, st, g, false);
+    Scratch<Counters> ctr(1, st);
+    SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
+    pool_run(g.rows.p, g.rows.ld, d, n, knn_id, K, L, g.info.exact, pool_id, pool_d2, pool_len,
+             ctr.p, st);
+  });
+}
+
+ssg_status ssg_prune(const float* base, int64_t n, int32_t d, const int32_t* pool_id,
+                     const int32_t* pool_len, int32_t L, int32_t R, double alpha_deg,
+                     int32_t* adj, int32_t* deg, ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(base && pool_id && pool_len && adj && deg, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(n >= 1 && d >= 1 && L >= 1, SSG_EINVAL, "bad sizes");
+    check_alpha(alpha_deg);
+    check_prune_fit(d, R);
+    cudaStream_t st = (cudaStream_t)stream;
+    Ingested g;
+    ingest_all(base, n, d, st, g, false);
+    Scratch<Counters> ctr(1, st);
+    SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
+    prune_run(g.rows.p, g.rows.ld, d, n, pool_id, pool_len, L, R, cos_alpha_of(alpha_deg), adj, deg,
+              ctr.p, st);
+  });
+}
+
+ssg_status ssg_reverse(const float* base, int64_t n, int32_t d, const int32_t* adj0,
+                       const int32_t* deg0, int32_t R, double alpha_deg, int32_t* adj1,
+                       int32_t* deg1, ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(base && adj0 && deg0 && adj1 && deg1, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(n >= 1 && d >= 1, SSG_EINVAL, "bad sizes");
+    check_alpha(alpha_deg);
+    check_prune_fit(d, R);
+    cudaStream_t st = (cudaStream_t)stream;
+    Ingested g;
+    ingest_all(base, n, d, st, g, false);
+    Scratch<Counters> ctr(1, st);
+    SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
+    reverse_run(g.rows.p, g.rows.ld, d, n, adj0, deg0, R, cos_alpha_of(alpha_deg), g.info.exact,
+                adj1, deg1, ctr.p, st);
+  });
+}
+
+ssg_status ssg_connect(const float* base, int64_t n, int32_t d, int32_t* adj, int32_t* deg,
+                       int32_t R, const int32_t* nav, int32_t n_nav, int64_t* n_repair_host,
+                       ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(base && adj && deg && nav, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(n >= 1 && d >= 1 && R >= 1 && n_nav >= 1, SSG_EINVAL, "bad sizes");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> h((size_t)n_nav);
+    SSG_CUDA(cudaMemcpyAsync(h.data(), nav, sizeof(int32_t) * n_nav, cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    for (int t = 0; t < n_nav; ++t)
+      SSG_REQUIRE(h[t] >= 0 && h[t] < n, SSG_EINVAL, "navigating node id %d out of range", h[t]);
+    Ingested g;
+    ingest_all(base, n, d, st, g, false);
+    const int64_t rep = connect_run(g.rows.p, g.rows.ld, d, n, adj, deg, R, nav, h.data(), n_nav, st);
+    if (n_repair_host) *n_repair_host = rep;
+  });
+}
+
+ssg_status ssg_search_adj(const float* base, int64_t n, int32_t d, const int32_t* adj,
+                          const int32_t* deg, int32_t R, const int32_t* nav, int32_t n_nav,
+                          const float* queries, int64_t nq, int32_t k, int32_t L_search,
+                          int32_t* out_ids, float* out_d2, ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(base && adj && deg && nav && queries && out_ids, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(n >= 1 && d >= 1 && R >= 1 && R <= 128 && n_nav >= 1 && nq >= 0, SSG_EINVAL,
+                "bad sizes");
+    SSG_REQUIRE(k >= 1 && k <= L_search && L_search <= 1024, SSG_EINVAL,
+                "need 1 <= k <= L_search <= 1024");
+    if (nq == 0) return;
+    cudaStream_t st = (cudaStream_t)stream;
+    Ingested gb;
+    ingest_all(base, n, d, st, gb, false);
+    PaddedRows q;
+    q.ld = (d + 3) & ~3;
+    if (q.ld == d && ((uintptr_t)queries & 15) == 0) {
+      q.p = queries;
+    } else {
+      Ingested gq;
+      ingest_all(queries, nq, d, st, gq, false);
+      q.own.alloc((size_t)nq * gq.rows.ld, st);
+      SSG_CUDA(cudaMemcpyAsync(q.own.p, gq.rows.p, sizeof(float) * nq * gq.rows.ld,
+                               cudaMemcpyDeviceToDevice, st));
+      q.p = q.own.p;
+    }
+    search_run(gb.rows.p, gb.rows.ld, d, n, adj, deg, R, nav, n_nav, q.p, q.ld, nq, k, L_search,
+               out_ids, out_d2, st);
+  });
+}
+
+ssg_status ssg_recall_hits(const int32_t* found, int32_t ld_found, const int32_t* truth,
+                           int32_t ld_truth, int64_t nq, int32_t k, int64_t* hits_host,
+                           ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(found && truth && hits_host, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(k >= 1 && k <= ld_found && k <= ld_truth && nq >= 0, SSG_EINVAL, "bad sizes");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch<unsigned long long> h(1, st);
+    SSG_CUDA(cudaMemsetAsync(h.p, 0, sizeof(unsigned long long), st));
+    if (nq > 0)
+      SSG_LAUNCH(k_recall_hits, (unsigned)ceil_div(nq, 8), 256, 0, st, found, ld_found, truth,
+                 ld_truth, nq, k, h.p);
+    unsigned long long v = 0;
+    SSG_CUDA(cudaMemcpyAsync(&v, h.p, sizeof(v), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    *hits_host = (int64_t)v;
+  });
+}
+
+ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
+                     double alpha_deg, const ssg_build_opts* opts_in, ssg_stream stream,
+                     ssg_graph** out, ssg_build_stats* stats) {
+  return guard([&] {
+    SSG_REQUIRE(base && out, SSG_EINVAL, "null pointer");
+    *out = nullptr;
+    ssg_build_opts opts;
+    ssg_default_opts(&opts);
+    if (opts_in) opts = *opts_in;
+    SSG_REQUIRE(n >= 2 && n < (1ll << 31) && d >= 1, SSG_EINVAL, "need 2 <= n < 2^31 and d >= 1");
+    SSG_REQUIRE(K >= 1 && K <= n - 1 && K <= 700, SSG_EINVAL, "need 1 <= K <= min(n - 1, 700)");
+    SSG_REQUIRE(L >= 1 && L + K <= 1023, SSG_EINVAL, "need L >= 1 and L + K <= 1023");
+    check_alpha(alpha_deg);
+    check_prune_fit(d, R);
+    SSG_REQUIRE(opts.n_nav >= 1 && opts.n_nav <= n && opts.n_nav <= 4096, SSG_EINVAL,
+                "need 1 <= n_nav <= min(n, 4096)");
+    std::vector<int32_t> nav((size_t)opts.n_nav);
+    if (opts.nav_ids_host) {
+      for (int t = 0; t < opts.n_nav; ++t) {
+        nav[t] = opts.nav_ids_host[t];
+        SSG_REQUIRE(nav[t] >= 0 && nav[t] < n, SSG_EINVAL, "navigating node %d out of range", nav[t]);
+        for (int u = 0; u < t; ++u)
+          SSG_REQUIRE(nav[u] != nav[t], SSG_EINVAL, "navigating nodes must be distinct");
+      }
+    } else {
+      ssg_status s = ssg_nav_ids(n, opts.n_nav, opts.seed, nav.data());
+      if (s != SSG_OK) throw Fail{s};
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t launches0 = g_launches.load();
+    ssg_build_stats S{};
+    StageTimer t_all(st), t_ing(st), t_knn(st), t_gemm(st), t_pool(st), t_prune(st), t_rev(st),
+        t_con(st);
+    t_all.start();
+
+    ssg_graph* g = new ssg_graph();
+    std::unique_ptr<ssg_graph> gp(g);
+    g->n = n;
+    g->d = d;
+    g->R = R;
+    g->n_nav = opts.n_nav;
+    g->alpha = alpha_deg;
+    g->nav_host = nav;
+    SSG_CUDA(cudaMalloc(&g->adj, sizeof(int32_t) * n * R));
+    SSG_CUDA(cudaMalloc(&g->deg, sizeof(int32_t) * n));
+    SSG_CUDA(cudaMalloc(&g->nav_dev, sizeof(int32_t) * opts.n_nav));
+    SSG_CUDA(cudaMemcpyAsync(g->nav_dev, nav.data(), sizeof(int32_t) * opts.n_nav,
+                             cudaMemcpyHostToDevice, st));
+
+    t_ing.start();
+    Ingested in;
+    ingest_all(base, n, d, st, in, true);
+    t_ing.stop();
+    Scratch<Counters> ctr(1, st);
+    SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
+    const double cos_a = cos_alpha_of(alpha_deg);
+
+    // a1: exact kNN graph
+    Scratch<int32_t> knn_id((size_t)n * K, st);
+    Scratch<float> knn_d2((size_t)n * K, st);
+    const bool tc = opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact && knn_tc_available();
+    SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
+                "bf16 distance GEMM needs integer data with |x| <= 256 and 2 d max|x|^2 <= 2^24");
+    t_knn.start();
+    KnnResult kr;
+    if (tc)
+      knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d, 1,
+                   K, knn_id.p, knn_d2.p, st, &t_gemm);
+    else
+      kr = knn_exact(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d,
+                     in.info, 1, K, knn_id.p, knn_d2.p, st, &t_gemm);
+    t_knn.stop();
+    in.norms.release();
+
+    // a2: candidate pools
+    Scratch<int32_t> pool_id((size_t)n * L, st), pool_len((size_t)n, st);
+    Scratch<float> pool_d2((size_t)n * L, st);
+    t_pool.start();
+    pool_run(in.rows.p, in.rows.ld, d, n, knn_id.p, K, L, in.info.exact, pool_id.p, pool_d2.p,
+             pool_len.p, ctr.p, st);
+    t_pool.stop();
+    knn_id.release();
+    knn_d2.release();
+
+    // a3: SSG prune
+    Scratch<int32_t> adj0((size_t)n * R, st), deg0((size_t)n, st);
+    t_prune.start();
+    prune_run(in.rows.p, in.rows.ld, d, n, pool_id.p, pool_len.p, L, R, cos_a, adj0.p, deg0.p,
+              ctr.p, st);
+    t_prune.stop();
+    pool_id.release();
+    pool_d2.release();
+    pool_len.release();
+
+    // a4: reverse-neighbour merge
+    t_rev.start();
+    const int maxin = reverse_run(in.rows.p, in.rows.ld, d, n, adj0.p, deg0.p, R, cos_a,
+                                  in.info.exact, g->adj, g->deg, ctr.p, st);
+    t_rev.stop();
+    adj0.release();
+    deg0.release();
+
+    // a5: connectivity from the navigating nodes
+    t_con.start();
+    const int64_t rep = connect_run(in.rows.p, in.rows.ld, d, n, g->adj, g->deg, R, g->nav_dev,
+                                    nav.data(), opts.n_nav, st);
+    t_con.stop();
+    t_all.stop();
+
+    Counters hc;
+    SSG_CUDA(cudaMemcpyAsync(&hc, ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    S.ms_ingest = t_ing.ms();
+    S.ms_knn = t_knn.ms();
+    S.ms_knn_gemm = t_gemm.ms();
+    S.ms_pool = t_pool.ms();
+    S.ms_prune = t_prune.ms();
+    S.ms_reverse = t_rev.ms();
+    S.ms_connect = t_con.ms();
+    S.ms_total = t_all.ms();
+    S.n_repair = rep;
+    S.n_angle_fp64 = (int64_t)hc.angle_fp64;
+    S.n_order_fp64 = (int64_t)hc.order_fp64;
+    S.n_knn_fallback_rows = kr.fallback_rows;
+    S.max_indegree = maxin;
+    S.exact_mode = in.info.exact;
+    S.gemm_prec_used = tc ? SSG_PREC_BF16 : SSG_PREC_FP32;
+    S.kernel_launches = g_launches.load() - launches0;
+    if (stats) *stats = S;
+    *out = gp.release();
+  });
+}
+
+ssg_status ssg_build_host(const float* base_host, int64_t n, int32_t d, int32_t K, int32_t L,
+                          int32_t R, double alpha_deg, const ssg_build_opts* opts,
+                          ssg_stream stream, ssg_graph** out, int32_t* adj_host, int32_t* deg_host,
+                          ssg_build_stats* stats) {
+  float* dev = nullptr;
+  ssg_status s = guard([&] {
+    SSG_REQUIRE(base_host && out && n >= 2 && d >= 1, SSG_EINVAL, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    SSG_CUDA(cudaMalloc(&dev, sizeof(float) * n * d));
+    SSG_CUDA(cudaMemcpyAsync(dev, base_host, sizeof(float) * n * d, cudaMemcpyHostToDevice, st));
+  });
+  if (s != SSG_OK) {
+    if (dev) cudaFree(dev);
+    return s;
+  }
+  s = ssg_build(dev, n, d, K, L, R, alpha_deg, opts, stream, out, stats);
+  if (s != SSG_OK) {
+    cudaFree(dev);
+    return s;
+  }
+  (*out)->base_owned = dev;
+  return guard([&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (adj_host)
+      SSG_CUDA(cudaMemcpyAsync(adj_host, (*out)->adj, sizeof(int32_t) * n * R,
+                               cudaMemcpyDeviceToHost, st));
+    if (deg_host)
+      SSG_CUDA(cudaMemcpyAsync(deg_host, (*out)->deg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+ssg_status ssg_graph_view(const ssg_graph* g, const int32_t** adj, const int32_t** deg,
+                          const int32_t** nav, int32_t* n_nav, int32_t* R, int64_t* n, int32_t* d) {
+  if (!g) {
+    set_error("null graph");
+    return SSG_EINVAL;
+  }
+  if (adj) *adj = g->adj;
+  if (deg) *deg = g->deg;
+  if (nav) *nav = g->nav_dev;
+  if (n_nav) *n_nav = g->n_nav;
+  if (R) *R = g->R;
+  if (n) *n = g->n;
+  if (d) *d = g->d;
+  return SSG_OK;
+}
+
+ssg_status ssg_search(const ssg_graph* g, const float* base, const float* queries, int64_t nq,
+                      int32_t k, int32_t L_search, int32_t* out_ids, float* out_d2,
+                      ssg_stream stream) {
+  if (!g) {
+    set_error("null graph");
+    return SSG_EINVAL;
+  }
+  const float* b = base ? base : g->base_owned;
+  if (!b) {
+    set_error("no base vectors: pass the device array the graph was built from");
+    return SSG_EINVAL;
+  }
+  return ssg_search_adj(b, g->n, g->d, g->adj, g->deg, g->R, g->nav_dev, g->n_nav, queries, nq, k,
+                        L_search, out_ids, out_d2, stream);
+}
+
+ssg_status ssg_search_host(const ssg_graph* g, const float* queries_host, int64_t nq, int32_t k,
+                           int32_t L_search, int32_t* out_ids_host, float* out_d2_host,
+                           ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(g && g->base_owned, SSG_EINVAL, "ssg_search_host needs a graph from ssg_build_host");
+    SSG_REQUIRE(queries_host && out_ids_host && nq >= 0, SSG_EINVAL, "bad arguments");
+    if (nq == 0) return;
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch<float> q((size_t)nq * g->d, st);
+    Scratch<int32_t> ids((size_t)nq * k, st);
+    Scratch<float> dd((size_t)nq * k, st);
+    SSG_CUDA(cudaMemcpyAsync(q.p, queries_host, sizeof(float) * nq * g->d, cudaMemcpyHostToDevice, st));
+    ssg_status s = ssg_search(g, nullptr, q.p, nq, k, L_search, ids.p, dd.p, stream);
+    if (s != SSG_OK) throw Fail{s};
+    SSG_CUDA(cudaMemcpyAsync(out_ids_host, ids.p, sizeof(int32_t) * nq * k, cudaMemcpyDeviceToHost, st));
+    if (out_d2_host)
+      SSG_CUDA(cudaMemcpyAsync(out_d2_host, dd.p, sizeof(float) * nq * k, cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+static const char kMagic[8] = {'N', 'S', 'S', 'G', 'r', 'a', 'p', 'h'};
+
+ssg_status ssg_save(const ssg_graph* g, const char* path) {
+  return guard([&] {
+    SSG_REQUIRE(g && path, SSG_EINVAL, "null argument");
+    std::vector<int32_t> adj((size_t)g->n * g->R), deg((size_t)g->n);
+    SSG_CUDA(cudaDeviceSynchronize());
+    SSG_CUDA(cudaMemcpy(adj.data(), g->adj, sizeof(int32_t) * adj.size(), cudaMemcpyDeviceToHost));
+    SSG_CUDA(cudaMemcpy(deg.data(), g->deg, sizeof(int32_t) * deg.size(), cudaMemcpyDeviceToHost));
+    FILE* f = fopen(path, "wb");
+    SSG_REQUIRE(f, SSG_EIO, "cannot open %s for writing", path);
+    const uint32_t version = 1;
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(&version, 4, 1, f) == 1 &&
+              fwrite(&g->n, 8, 1, f) == 1 && fwrite(&g->d, 4, 1, f) == 1 &&
+              fwrite(&g->R, 4, 1, f) == 1 && fwrite(&g->n_nav, 4, 1, f) == 1 &&
+              fwrite(&g->alpha, 8, 1, f) == 1 &&
+              fwrite(g->nav_host.data(), 4, g->nav_host.size(), f) == g->nav_host.size() &&
+              fwrite(deg.data(), 4, deg.size(), f) == deg.size() &&
+              fwrite(adj.data(), 4, adj.size(), f) == adj.size();
+    ok = (fclose(f) == 0) && ok;
+    SSG_REQUIRE(ok, SSG_EIO, "short write to %s", path);
+  });
+}
+
+ssg_status ssg_load(const char* path, ssg_graph** out) {
+  return guard([&] {
+    SSG_REQUIRE(path && out, SSG_EINVAL, "null argument");
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    SSG_REQUIRE(f, SSG_EIO, "cannot open %s", path);
+    std::unique_ptr<FILE, int (*)(FILE*)> fc(f, fclose);
+    char magic[8];
+    uint32_t version = 0;
+    std::unique_ptr<ssg_graph> g(new ssg_graph());
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 &&
+              fread(&version, 4, 1, f) == 1 && version == 1 && fread(&g->n, 8, 1, f) == 1 &&
+              fread(&g->d, 4, 1, f) == 1 && fread(&g->R, 4, 1, f) == 1 &&
+              fread(&g->n_nav, 4, 1, f) == 1 && fread(&g->alpha, 8, 1, f) == 1;
+    SSG_REQUIRE(ok && g->n >= 1 && g->R >= 1 && g->n_nav >= 1 && g->n_nav <= g->n, SSG_EIO,
+                "%s is not a graph file of this library", path);
+    g->nav_host.resize(g->n_nav);
+    std::vector<int32_t> adj((size_t)g->n * g->R), deg((size_t)g->n);
+    ok = fread(g->nav_host.data(), 4, g->n_nav, f) == (size_t)g->n_nav &&
+         fread(deg.data(), 4, deg.size(), f) == deg.size() &&
+         fread(adj.data(), 4, adj.size(), f) == adj.size();
+    SSG_REQUIRE(ok, SSG_EIO, "%s is truncated", path);
+    SSG_CUDA(cudaMalloc(&g->adj, sizeof(int32_t) * adj.size()));
+    SSG_CUDA(cudaMalloc(&g->deg, sizeof(int32_t) * deg.size()));
+    SSG_CUDA(cudaMalloc(&g->nav_dev, sizeof(int32_t) * g->n_nav));
+    SSG_CUDA(cudaMemcpy(g->adj, adj.data(), sizeof(int32_t) * adj.size(), cudaMemcpyHostToDevice));
+    SSG_CUDA(cudaMemcpy(g->deg, deg.data(), sizeof(int32_t) * deg.size(), cudaMemcpyHostToDevice));
+    SSG_CUDA(cudaMemcpy(g->nav_dev, g->nav_host.data(), sizeof(int32_t) * g->n_nav,
+                        cudaMemcpyHostToDevice));
+    *out = g.release();
+  });
+}
+
+void ssg_free(ssg_graph* g) { delete g; }
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// Warp-level building blocks shared by the pool, prune and reverse-merge kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace ssg {
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// fp32 squared distance of two padded rows by a team of 8 lanes (float4 loads); every
+// lane of the warp must call it (teams whose `valid` is false contribute nothing).
+__device__ __forceinline__ float team8_dist(const float* __restrict__ a,
+                                            const float* __restrict__ b, int ld4, int tl,
+                                            bool valid) {
+  float s = 0.f;
+  if (valid) {
+    const float4* a4 = (const float4*)a;
+    const float4* b4 = (const float4*)b;
+    for (int f = tl; f < ld4; f += 8) {
+      float4 x = __ldg(a4 + f), y = __ldg(b4 + f);
+      float u;
+      u = x.x - y.x;
+      s = fmaf(u, u, s);
+      u = x.y - y.y;
+      s = fmaf(u, u, s);
+      u = x.z - y.z;
+      s = fmaf(u, u, s);
+      u = x.w - y.w;
+      s = fmaf(u, u, s);
+    }
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  return s;
+}
+
+// keys[t] holds a candidate id in its low 32 bits; replace every key in [0, m) by
+// (fp32 d2(x_i, candidate), id).  xi points at node i's padded row.
+__device__ __forceinline__ void warp_fill_dist_keys(uint64_t* keys, int m,
+                                                    const float* __restrict__ X, int ld,
+                                                    const float* __restrict__ xi) {
+  const int lane = lane_id(), team = lane >> 3, tl = lane & 7;
+  const int ld4 = ld >> 2;
+  for (int t0 = 0; t0 < m; t0 += 4) {
+    const int t = t0 + team;
+    const bool valid = t < m;
+    const int32_t id = valid ? key_id(keys[t]) : 0;
+    const float dd = team8_dist(xi, X + (int64_t)id * ld, ld4, tl, valid);
+    __syncwarp();
+    if (valid && tl == 0) keys[t] = make_key(dd, id);
+  }
+  __syncwarp();
+}
+
+// keys[0, m) are sorted by their fp32 distances.  The fp32 value of a direct sum of d
+// squared differences lies within a relative `rel` of the exact value, so two entries
+// can be out of their true (d2, id) order only inside a run of neighbours whose fp32
+// values are within that bound of each other.  Every such run that starts before
+// `limit` is re-sorted by (fp64 d2, id).  d64 is scratch for m doubles.
+// Returns the number of runs re-sorted by this lane (sum over lanes = total).
+__device__ __forceinline__ int warp_fix_runs(uint64_t* keys, int m, int limit, double* d64,
+                                             const float* __restrict__ X, int ld, int d,
+                                             const float* __restrict__ xi, float rel) {
+  const int lane = lane_id();
+  auto close = [&](int p) -> bool {  // entries p and p + 1 are within the bound
+    float a = key_dist(keys[p]), b = key_dist(keys[p + 1]);
+    return (b - a) <= rel * (a + b);
+  };
+  int fixed = 0;
+  const int smax = m - 1 < limit ? m - 1 : limit;
+  for (int s = lane; s < smax; s += 32) {
+    if (!close(s) || (s > 0 && close(s - 1))) continue;
+    int e = s + 1;
+    while (e + 1 < m && close(e)) ++e;
+    for (int t = s; t <= e; ++t) d64[t] = dist2_f64(xi, X + (int64_t)key_id(keys[t]) * ld, d);
+    for (int t = s + 1; t <= e; ++t) {  // insertion sort of the run by (d64, id)
+      uint64_t kk = keys[t];
+      double dv = d64[t];
+      int u = t - 1;
+      while (u >= s && (d64[u] > dv || (d64[u] == dv && (uint32_t)keys[u] > (uint32_t)kk))) {
+        keys[u + 1] = keys[u];
+        d64[u + 1] = d64[u];
+        --u;
+      }
+      keys[u + 1] = kk;
+      d64[u + 1] = dv;
+    }
+    ++fixed;
+  }
+  __syncwarp();
+  return fixed;
+}
+
+// SSG prune of one node by one warp (Alg. 2 selection): cand[0, len) in (d2, id) order.
+// Keeps cand[0]; keeps each later candidate unless its angle to a kept edge has
+// cos > cos(alpha); stops at R kept.  The cosine comes from the centred dot products of
+// the fp32 differences c - x_i held in shared memory (V: one row of D1 >= d floats per
+// kept edge plus one tentative row, D1 odd so that lanes reading different rows hit
+// different banks).  A decision within `margin` of cos(alpha), or with a zero-length
+// edge, is re-taken in fp64 from the original vectors.
+// Writes the kept ids to out[0, kept) (lane 0) and returns kept; *n64 += fp64 re-tests.
+__device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int ld, int d,
+                                               int64_t i, const int32_t* cand, int len, int R,
+                                               float cosA32, double cosA64, float margin,
+                                               float* V, int D1, float* xs, float* gkk,
+                                               int32_t* out, unsigned long long* n64) {
+  const int lane = lane_id();
+  const float* xg = X + i * ld;
+  for (int t = lane; t < d; t += 32) xs[t] = xg[t];
+  __syncwarp();
+  int kept = 0;
+  unsigned long long fp64_tests = 0;
+  for (int t = 0; t < len && kept < R; ++t) {
+    const int32_t j = cand[t];
+    const float* cj = X + (int64_t)j * ld;
+    float* slot = V + kept * D1;
+    float part = 0.f;
+    for (int dd = lane; dd < d; dd += 32) {
+      float v = cj[dd] - xs[dd];
+      slot[dd] = v;
+      part = fmaf(v, v, part);
+    }
+    const float gjj = warp_sum(part);
+    __syncwarp();
+    bool definite = false;
+    unsigned border = 0;
+    for (int k = lane, r = 0; k < kept; k += 32, ++r) {
+      const float* vk = V + k * D1;
+      float g = 0.f;
+      for (int dd = 0; dd < d; ++dd) g = fmaf(slot[dd], vk[dd], g);
+      const float gk = gkk[k];
+      if (gjj == 0.f || gk == 0.f) {
+        border |= 1u << r;
+      } else {
+        const float c = g / (sqrtf(gjj) * sqrtf(gk));
+        if (c > cosA32 + margin)
+          definite = true;
+        else if (c >= cosA32 - margin)
+          border |= 1u << r;
+      }
+    }
+    bool conflict = __any_sync(0xffffffffu, definite);
+    if (!conflict && __any_sync(0xffffffffu, border != 0)) {
+      bool c64 = false;
+      for (int r = 0; border >> r; ++r) {
+        if (!((border >> r) & 1u)) continue;
+        const int k = lane + 32 * r;
+        const float* ck = X + (int64_t)out[k] * ld;
+        const double gjk = centred_dot_f64(cj, ck, xg, d);
+        const double g1 = centred_dot_f64(cj, cj, xg, d);
+        const double g2 = centred_dot_f64(ck, ck, xg, d);
+        if (cos_from_gram_f64(gjk, g1, g2) > cosA64) c64 = true;
+        ++fp64_tests;
+      }
+      conflict = __any_sync(0xffffffffu, c64);
+    }
+    if (!conflict) {
+      if (lane == 0) {
+        out[kept] = j;
+        gkk[kept] = gjj;
+      }
+      ++kept;
+    }
+    __syncwarp();
+  }
+  if (fp64_tests) atomicAdd(n64, fp64_tests);
+  return kept;
+}
+
+// Shared-memory layout of warp_prune_node for one warp, in floats.
+__host__ __device__ inline int prune_row_stride(int d) { return (d & 1) ? d : d + 1; }
+__host__ __device__ inline size_t prune_smem_floats(int d, int R) {
+  const int D1 = prune_row_stride(d);
+  return (size_t)(R + 1) * D1 + (size_t)D1 + (size_t)R + 1;
+}
+
+}  // namespace ssg

@@ -1,0 +1,74 @@
+// Declarations shared by the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace ssg {
+
+// Rows with a 16-byte-aligned stride (ld % 4 == 0, zero padded beyond d).
+struct PaddedRows {
+  const float* p = nullptr;
+  int ld = 0;
+  Scratch<float> own;
+};
+
+struct KnnResult {
+  int64_t fallback_rows = 0;
+};
+
+// Ingest (build step a0): padded view of X, fp32 squared norms (may be null), data facts.
+void ingest(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out, float* norms,
+            DataInfo* info);
+
+// Exact top-K by (d2, id) of every row of A against the rows of B (self = A is B and
+// row i skips column i).  info describes A and B together.
+KnnResult knn_exact(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
+                    int64_t nb, int ldb, const float* b_norm, int d, const DataInfo& info,
+                    int self, int K, int32_t* out_id, float* out_d2, cudaStream_t st,
+                    StageTimer* gemm_timer);
+
+// bf16 tensor-core variant of the exact top-K (only for info.bf16_exact data).
+bool knn_tc_available();
+void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
+                  int64_t nb, int ldb, const float* b_norm, int d, int self, int K,
+                  int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer);
+
+struct Counters {
+  unsigned long long angle_fp64;
+  unsigned long long order_fp64;
+  int max_indeg;
+  int status;
+};
+
+// Pools (Alg. 3 neighbour / neighbour's-neighbour loop).
+void pool_run(const float* X, int ld, int d, int64_t n, const int32_t* knn, int K, int L,
+              int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len, Counters* dctr,
+              cudaStream_t st);
+
+// SSG prune of each node's pool.
+void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
+               const int32_t* pool_len, int L, int R, double cos_a, int32_t* adj,
+               int32_t* deg, Counters* dctr, cudaStream_t st);
+
+// Reverse-neighbour merge; returns the largest in-degree.
+int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
+                const int32_t* deg0, int R, double cos_a, int exact, int32_t* adj1,
+                int32_t* deg1, Counters* dctr, cudaStream_t st);
+
+// Connectivity from navigating nodes; returns the number of repair edges.
+int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int32_t* deg,
+                    int R, const int32_t* nav_dev, const int32_t* nav_host, int n_nav,
+                    cudaStream_t st);
+
+// Search-on-Graph.
+void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
+                const int32_t* deg, int R, const int32_t* nav, int n_nav, const float* Q,
+                int ldq, int64_t nq, int k, int Ls, int32_t* out_ids, float* out_d2,
+                cudaStream_t st);
+
+// Smallest margin (in cos units) beyond which the fp32 angle test is certain.
+inline float angle_margin_fp32(int d) { return (float)((2.0 * d + 20.0) * U32 * 1.1); }
+// Relative error bound of an fp32 squared distance summed directly from differences.
+inline float dist_rel_fp32(int d) { return (float)((d + 4.0) * U32 * 1.01); }
+
+}  // namespace ssg

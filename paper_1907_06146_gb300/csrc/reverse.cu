@@ -1,0 +1,231 @@
+// Reverse-neighbour merge (Alg. 3, reverse neighbour checking; Sec. 4.1).
+//
+// Order-free batch reading: from the pruned graph adj0 as a whole, every node j gets the
+// candidates adj0[j] united with its in-neighbours {i : j in adj0[i]}, sorted by
+// (d2(j, .), id), and the same SSG prune with the same cap R.  The transpose is a
+// histogram (atomic in-degree count), an exclusive scan to 64-bit offsets, and an atomic
+// scatter; the scatter order inside a node's in-list does not matter because the list is
+// sorted afterwards.  Nodes whose candidate count exceeds the per-warp capacity (hubs)
+// are processed by a second launch with one warp and a large shared-memory buffer each.
+#include "common.cuh"
+#include "graph_dev.cuh"
+#include "knn.cuh"
+
+namespace ssg {
+
+__global__ void k_indeg(const int32_t* __restrict__ adj0, const int32_t* __restrict__ deg0, int R,
+                        int64_t n, int* __restrict__ indeg) {
+  const int64_t total = n * R;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / R;
+    const int t = (int)(e - i * R);
+    if (t < deg0[i]) atomicAdd(indeg + adj0[e], 1);
+  }
+}
+
+__global__ void k_scatter(const int32_t* __restrict__ adj0, const int32_t* __restrict__ deg0, int R,
+                          int64_t n, const int64_t* __restrict__ off, int* __restrict__ fill,
+                          int32_t* __restrict__ rev) {
+  const int64_t total = n * R;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / R;
+    const int t = (int)(e - i * R);
+    if (t < deg0[i]) {
+      const int32_t j = adj0[e];
+      rev[off[j] + atomicAdd(fill + j, 1)] = (int32_t)i;
+    }
+  }
+}
+
+// ---- exclusive scan of int32 counts into int64 offsets (out has n + 1 entries) ----------
+constexpr int SCAN_B = 1024;
+
+__global__ void k_scan_block(const int* __restrict__ in, const int64_t* __restrict__ in64,
+                             int64_t n, int64_t* __restrict__ out, int64_t* __restrict__ sums) {
+  __shared__ int64_t ws[32];
+  const int64_t idx = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
+  int64_t v = idx < n ? (in ? (int64_t)in[idx] : in64[idx]) : 0;
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    ws[lane] = w;
+  }
+  __syncthreads();
+  const int64_t incl = x + (warp > 0 ? ws[warp - 1] : 0);
+  if (idx < n) out[idx] = incl - v;
+  if (threadIdx.x == SCAN_B - 1) sums[blockIdx.x] = incl;
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ boff) {
+  const int64_t idx = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
+  if (idx < n) out[idx] += boff[blockIdx.x];
+}
+
+// Exclusive scan; returns the total on the host (synchronises the stream).
+static int64_t exclusive_scan(const int* in32, const int64_t* in64, int64_t n, int64_t* out,
+                              cudaStream_t st) {
+  const int64_t nb = ceil_div(n, SCAN_B);
+  Scratch<int64_t> sums((size_t)nb, st);
+  SSG_LAUNCH(k_scan_block, (unsigned)nb, SCAN_B, 0, st, in32, in64, n, out, sums.p);
+  int64_t total = 0;
+  if (nb > 1) {
+    Scratch<int64_t> boff((size_t)nb + 1, st);
+    total = exclusive_scan(nullptr, sums.p, nb, boff.p, st);
+    SSG_LAUNCH(k_scan_add, (unsigned)nb, SCAN_B, 0, st, out, n, boff.p);
+  } else {
+    SSG_CUDA(cudaMemcpyAsync(&total, sums.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+  }
+  SSG_CUDA(cudaMemcpyAsync(out + n, &total, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  SSG_CUDA(cudaStreamSynchronize(st));
+  return total;
+}
+
+// ---- merge + prune ----------------------------------------------------------------------
+__global__ void k_reverse_merge(const float* __restrict__ X, int ld, int d, int64_t n,
+                                const int32_t* __restrict__ adj0, const int32_t* __restrict__ deg0,
+                                int R, const int64_t* __restrict__ off,
+                                const int32_t* __restrict__ rev,
+                                const int32_t* __restrict__ node_list, int64_t count, int cap,
+                                int exact, float rel, float cosA32, double cosA64, float margin,
+                                int32_t* __restrict__ adj1, int32_t* __restrict__ deg1,
+                                int32_t* __restrict__ big_list, int* __restrict__ big_count,
+                                unsigned long long* __restrict__ n_order,
+                                unsigned long long* __restrict__ n_angle) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
+  const size_t prune_bytes = prune_smem_floats(d, R) * sizeof(float);
+  const size_t per_warp = (size_t)cap * 20 + ((prune_bytes + 15) & ~(size_t)15);
+  unsigned char* base = sm_raw + warp * per_warp;
+  uint64_t* keys = (uint64_t*)base;
+  double* d64 = (double*)(keys + cap);
+  int32_t* cand = (int32_t*)(d64 + cap);
+  float* V = (float*)(base + (size_t)cap * 20);
+  const int D1 = prune_row_stride(d);
+  float* xs = V + (size_t)(R + 1) * D1;
+  float* gkk = xs + D1;
+
+  const int64_t w = (int64_t)blockIdx.x * wpb + warp;
+  if (w >= count) return;
+  const int64_t j = node_list ? node_list[w] : w;
+  const int d0 = deg0[j];
+  const int64_t r0 = off[j], r1 = off[j + 1];
+  if (d0 + (r1 - r0) > cap) {
+    if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)j;
+    return;
+  }
+  for (int t = lane; t < d0; t += 32) keys[t] = (uint64_t)(uint32_t)adj0[j * R + t];
+  __syncwarp();
+  int m = d0;
+  for (int64_t c = r0; c < r1; c += 32) {
+    const int64_t p = c + lane;
+    int32_t id = p < r1 ? rev[p] : -1;
+    bool fresh = id >= 0;
+    for (int t = 0; t < d0 && fresh; ++t)
+      if (key_id(keys[t]) == id) fresh = false;
+    const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+    if (fresh) keys[m + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
+    m += __popc(bal);
+  }
+  __syncwarp();
+  const float* xj = X + j * ld;
+  warp_fill_dist_keys(keys, m, X, ld, xj);
+  int mp = 1;
+  while (mp < m) mp <<= 1;
+  for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
+  __syncwarp();
+  warp_sort_keys(keys, mp);
+  if (!exact && m > 1) {
+    int f = warp_fix_runs(keys, m, m, d64, X, ld, d, xj, rel);
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0 && f) atomicAdd(n_order, (unsigned long long)f);
+  }
+  for (int t = lane; t < m; t += 32) cand[t] = key_id(keys[t]);
+  __syncwarp();
+  int32_t* out = adj1 + j * R;
+  const int kept = warp_prune_node(X, ld, d, j, cand, m, R, cosA32, cosA64, margin, V, D1, xs,
+                                   gkk, out, n_angle);
+  for (int t = kept + lane; t < R; t += 32) out[t] = -1;
+  if (lane == 0) deg1[j] = kept;
+}
+
+__global__ void k_max_int(const int* __restrict__ v, int64_t n, int* __restrict__ out) {
+  int m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, v[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane_id() == 0) atomicMax(out, m);
+}
+
+int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
+                const int32_t* deg0, int R, double cos_a, int exact, int32_t* adj1,
+                int32_t* deg1, Counters* dctr, cudaStream_t st) {
+  const int grid = 8 * num_sms();
+  Scratch<int> indeg((size_t)n, st), fill((size_t)n, st), small(2, st);
+  SSG_CUDA(cudaMemsetAsync(indeg.p, 0, sizeof(int) * n, st));
+  SSG_CUDA(cudaMemsetAsync(fill.p, 0, sizeof(int) * n, st));
+  SSG_CUDA(cudaMemsetAsync(small.p, 0, sizeof(int) * 2, st));
+  SSG_LAUNCH(k_indeg, grid, 256, 0, st, adj0, deg0, R, n, indeg.p);
+  SSG_LAUNCH(k_max_int, grid, 256, 0, st, indeg.p, n, small.p + 1);
+  Scratch<int64_t> off((size_t)n + 1, st);
+  const int64_t total = exclusive_scan(indeg.p, nullptr, n, off.p, st);
+  Scratch<int32_t> rev((size_t)std::max<int64_t>(total, 1), st);
+  SSG_LAUNCH(k_scatter, grid, 256, 0, st, adj0, deg0, R, n, off.p, fill.p, rev.p);
+
+  const size_t prune_bytes = ((prune_smem_floats(d, R) * sizeof(float)) + 15) & ~(size_t)15;
+  const float rel = dist_rel_fp32(d), margin = angle_margin_fp32(d);
+  // warp path
+  const int cap = 256;
+  const size_t per_warp = (size_t)cap * 20 + prune_bytes;
+  const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
+  const size_t smem = per_warp * wpb;
+  SSG_REQUIRE(smem <= 200 * 1024, SSG_EINVAL, "reverse merge: R * d too large for shared memory");
+  static size_t attr = 0;
+  const size_t smem_big_max = 220 * 1024;
+  if (attr < smem_big_max) {
+    SSG_CUDA(cudaFuncSetAttribute(k_reverse_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_big_max));
+    attr = smem_big_max;
+  }
+  Scratch<int32_t> big((size_t)n, st);
+  SSG_LAUNCH(k_reverse_merge, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, ld, d, n, adj0,
+             deg0, R, off.p, rev.p, (const int32_t*)nullptr, n, cap, exact, rel, (float)cos_a,
+             cos_a, margin, adj1, deg1, big.p, small.p, &dctr->order_fp64, &dctr->angle_fp64);
+  int h[2];
+  SSG_CUDA(cudaMemcpyAsync(h, small.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+  SSG_CUDA(cudaStreamSynchronize(st));
+  if (h[0] > 0) {
+    int cap_big = 1;
+    while ((size_t)(cap_big * 2) * 20 + prune_bytes <= smem_big_max) cap_big *= 2;
+    SSG_REQUIRE(h[1] + R <= cap_big, SSG_EINTERNAL,
+                "reverse merge: a node has %d candidates, more than the %d supported", h[1] + R,
+                cap_big);
+    const size_t smem_big = (size_t)cap_big * 20 + prune_bytes;
+    // every listed node fits cap_big, so the second launch appends to no list
+    Scratch<int32_t> none(1, st);
+    Scratch<int> small2(2, st);
+    SSG_CUDA(cudaMemsetAsync(small2.p, 0, sizeof(int) * 2, st));
+    SSG_LAUNCH(k_reverse_merge, h[0], 32, smem_big, st, X, ld, d, n, adj0, deg0, R, off.p, rev.p,
+               big.p, (int64_t)h[0], cap_big, exact, rel, (float)cos_a, cos_a, margin, adj1, deg1,
+               none.p, small2.p, &dctr->order_fp64, &dctr->angle_fp64);
+  }
+  return h[1];
+}
+
+}  // namespace ssg

@@ -1,0 +1,250 @@
+// Search-on-Graph (Alg. 1) from the navigating node nearest the query (Sec. 4.1).
+//
+// One warp per query.  The candidate pool S (at most L_search entries, sorted by
+// (d2, id), with a checked flag each) lives in shared memory; each round expands the
+// first unchecked entry, gathers its adjacency row (coalesced), computes the distances
+// of the neighbours not seen before with teams of 8 lanes (float4 loads), sorts them with
+// a warp bitonic sort and merges them into S with a rank-based parallel merge, cut at
+// L_search.
+//
+// Visited set: a direct-mapped cache of ids in shared memory.  Alg. 1 never re-adds a
+// visited node; here a node that fell out of the cache may be met again and its distance
+// recomputed, but the result is the same: a node that is still in S has the same key and
+// is dropped by the duplicate check of the merge, and a node that left S (or never
+// entered it) did so because S was full and its key was above the L_search-th key, which
+// never increases once S is full, so it is cut again.  Before S first fills nothing has
+// left it.  The cache only saves distance computations.
+#include "common.cuh"
+#include "graph_dev.cuh"
+#include "knn.cuh"
+
+namespace ssg {
+
+__device__ __forceinline__ float team8_dist_q(const float* __restrict__ qs,
+                                              const float* __restrict__ x, int ld4, int tl,
+                                              bool valid) {
+  float s = 0.f;
+  if (valid) {
+    const float4* q4 = (const float4*)qs;
+    const float4* x4 = (const float4*)x;
+    for (int f = tl; f < ld4; f += 8) {
+      float4 a = q4[f], b = __ldg(x4 + f);
+      float u;
+      u = a.x - b.x;
+      s = fmaf(u, u, s);
+      u = a.y - b.y;
+      s = fmaf(u, u, s);
+      u = a.z - b.z;
+      s = fmaf(u, u, s);
+      u = a.w - b.w;
+      s = fmaf(u, u, s);
+    }
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  return s;
+}
+
+// number of entries of a[0, len) that are < x (a sorted ascending)
+__device__ __forceinline__ int count_less(const uint64_t* a, int len, uint64_t x) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+struct SearchLayout {
+  int Ls, RP, ld, log2h;
+  __host__ __device__ size_t pool_bytes() const { return (size_t)Ls * 8; }
+  __host__ __device__ size_t per_warp() const {
+    size_t b = 2 * pool_bytes() + (((size_t)2 * Ls + 15) & ~(size_t)15) + (size_t)RP * 8 +
+               (size_t)ld * 4 + ((size_t)4 << log2h);
+    return (b + 15) & ~(size_t)15;
+  }
+};
+
+__global__ void k_search(const float* __restrict__ X, int ld, int d, const int32_t* __restrict__ adj,
+                         const int32_t* __restrict__ deg, int R, const int32_t* __restrict__ nav,
+                         int n_nav, const float* __restrict__ Q, int ldq, int64_t nq, int k,
+                         SearchLayout lay, int32_t* __restrict__ out_ids,
+                         float* __restrict__ out_d2) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
+  const int team = lane >> 3, tl = lane & 7;
+  const int Ls = lay.Ls;
+  unsigned char* base = sm_raw + (size_t)warp * lay.per_warp();
+  uint64_t* pA = (uint64_t*)base;
+  uint64_t* pB = pA + Ls;
+  unsigned char* fA = (unsigned char*)(pB + Ls);
+  unsigned char* fB = fA + Ls;
+  uint64_t* newk = (uint64_t*)(base + 2 * lay.pool_bytes() + (((size_t)2 * Ls + 15) & ~(size_t)15));
+  float* qs = (float*)(newk + lay.RP);
+  int32_t* cache = (int32_t*)(qs + ld);
+  const int hcap = 1 << lay.log2h;
+  const int ld4 = ld >> 2;
+  (void)d;
+
+  for (int64_t qi = (int64_t)blockIdx.x * wpb + warp; qi < nq; qi += (int64_t)gridDim.x * wpb) {
+    const float* qg = Q + qi * ldq;
+    for (int t = lane; t < ld; t += 32) qs[t] = t < d ? qg[t] : 0.f;
+    for (int t = lane; t < hcap; t += 32) cache[t] = -1;
+    __syncwarp();
+
+    // entry: the nearest navigating node by (d2, id)
+    uint64_t best = KEY_NONE;
+    for (int s0 = 0; s0 < n_nav; s0 += 4) {
+      const int s = s0 + team;
+      const bool valid = s < n_nav;
+      const int32_t id = valid ? nav[s] : 0;
+      const float dd = team8_dist_q(qs, X + (int64_t)id * ld, ld4, tl, valid);
+      const uint64_t key = valid ? make_key(dd, id) : KEY_NONE;
+      best = key < best ? key : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      uint64_t other = __shfl_xor_sync(0xffffffffu, best, o);
+      best = other < best ? other : best;
+    }
+    if (lane == 0) {
+      pA[0] = best;
+      fA[0] = 0;
+      const int32_t e = key_id(best);
+      cache[((uint32_t)e * 2654435761u) >> (32 - lay.log2h)] = e;
+    }
+    int s = 1;
+    __syncwarp();
+
+    for (;;) {
+      int p = -1;
+      for (int c = 0; c < s; c += 32) {
+        const int idx = c + lane;
+        const unsigned bal = __ballot_sync(0xffffffffu, idx < s && !fA[idx]);
+        if (bal) {
+          p = c + __ffs(bal) - 1;
+          break;
+        }
+      }
+      if (p < 0) break;
+      const int32_t node = key_id(pA[p]);
+      __syncwarp();
+      if (lane == 0) fA[p] = 1;
+      const int dg = deg[node];
+      int cnt = 0;
+      for (int c = 0; c < dg; c += 32) {
+        const int t = c + lane;
+        bool fresh = false;
+        int32_t id = -1;
+        if (t < dg) {
+          id = adj[(int64_t)node * R + t];
+          const uint32_t slot = ((uint32_t)id * 2654435761u) >> (32 - lay.log2h);
+          if (cache[slot] != id) {
+            cache[slot] = id;
+            fresh = true;
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+        if (fresh) newk[cnt + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
+        cnt += __popc(bal);
+      }
+      __syncwarp();
+      for (int t0 = 0; t0 < cnt; t0 += 4) {
+        const int t = t0 + team;
+        const bool valid = t < cnt;
+        const int32_t id = valid ? key_id(newk[t]) : 0;
+        const float dd = team8_dist_q(qs, X + (int64_t)id * ld, ld4, tl, valid);
+        __syncwarp();
+        if (valid && tl == 0) newk[t] = make_key(dd, id);
+      }
+      __syncwarp();
+      int cp = 1;
+      while (cp < cnt) cp <<= 1;
+      for (int t = cnt + lane; t < cp; t += 32) newk[t] = KEY_NONE;
+      __syncwarp();
+      if (cnt > 1) warp_sort_keys(newk, cp);
+      // drop keys already in S (same id => same key), compacting in place
+      int kept = 0;
+      for (int c = 0; c < cnt; c += 32) {
+        const int j = c + lane;
+        uint64_t b = KEY_NONE;
+        bool keep = false;
+        if (j < cnt) {
+          b = newk[j];
+          const int r = count_less(pA, s, b);
+          keep = !(r < s && pA[r] == b);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) newk[kept + __popc(bal & lanemask_lt())] = b;
+        kept += __popc(bal);
+        __syncwarp();
+      }
+      // merge S and the new keys into the other buffer, cut at Ls
+      for (int i = lane; i < s; i += 32) {
+        const uint64_t a = pA[i];
+        const int pos = i + count_less(newk, kept, a);
+        if (pos < Ls) {
+          pB[pos] = a;
+          fB[pos] = fA[i];
+        }
+      }
+      for (int j = lane; j < kept; j += 32) {
+        const uint64_t b = newk[j];
+        const int pos = j + count_less(pA, s, b);
+        if (pos < Ls) {
+          pB[pos] = b;
+          fB[pos] = 0;
+        }
+      }
+      s = s + kept < Ls ? s + kept : Ls;
+      __syncwarp();
+      uint64_t* tp = pA;
+      pA = pB;
+      pB = tp;
+      unsigned char* tf = fA;
+      fA = fB;
+      fB = tf;
+    }
+    for (int t = lane; t < k; t += 32) {
+      const bool v = t < s;
+      out_ids[qi * k + t] = v ? key_id(pA[t]) : -1;
+      if (out_d2) out_d2[qi * k + t] = v ? key_dist(pA[t]) : __int_as_float(0x7f800000);
+    }
+    __syncwarp();
+  }
+}
+
+void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
+                const int32_t* deg, int R, const int32_t* nav, int n_nav, const float* Q,
+                int ldq, int64_t nq, int k, int Ls, int32_t* out_ids, float* out_d2,
+                cudaStream_t st) {
+  (void)n;
+  if (nq == 0) return;
+  SearchLayout lay;
+  lay.Ls = Ls;
+  lay.RP = std::max(32, next_pow2(R));
+  lay.ld = ld;
+  lay.log2h = 12;
+  const int wpb = 4;
+  while (lay.per_warp() * wpb > 200 * 1024 && lay.log2h > 8) --lay.log2h;
+  const size_t smem = lay.per_warp() * wpb;
+  SSG_REQUIRE(smem <= 220 * 1024, SSG_EINVAL, "search: L_search and d too large for shared memory");
+  static size_t attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    SSG_CUDA(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  int blocks_per_sm = 0;
+  SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search, wpb * 32, smem));
+  const int64_t want = ceil_div(nq, wpb);
+  const int grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, blocks_per_sm) * num_sms());
+  SSG_LAUNCH(k_search, grid, wpb * 32, smem, st, X, ld, d, adj, deg, R, nav, n_nav, Q, ldq, nq, k,
+             lay, out_ids, out_d2);
+}
+
+}  // namespace ssg

@@ -1,0 +1,388 @@
+"""Thin Python binding of libssg.so (the C ABI declared in include/ssg.h).
+
+Argument marshalling only: every step of the NSSG build and search runs in the library's
+CUDA kernels.  Device arrays are torch CUDA tensors; the calls run on the current torch
+stream.  There is no CPU fallback: if libssg.so is missing or cannot load, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libssg.so")
+_lock = threading.Lock()
+_lib = None
+
+PREC = {"fp32": 0, "bf16": 1, "auto": 2}
+
+
+class SSGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ssg status {status}: {msg}")
+        self.status = status
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("gemm_prec", ctypes.c_int), ("n_nav", ctypes.c_int32),
+                ("nav_ids_host", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("debug_checks", ctypes.c_int32)]
+
+
+class BuildStats(ctypes.Structure):
+    _fields_ = [("ms_ingest", ctypes.c_double), ("ms_knn", ctypes.c_double),
+                ("ms_pool", ctypes.c_double), ("ms_prune", ctypes.c_double),
+                ("ms_reverse", ctypes.c_double), ("ms_connect", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("n_repair", ctypes.c_int64),
+                ("n_angle_fp64", ctypes.c_int64), ("n_order_fp64", ctypes.c_int64),
+                ("n_knn_fallback_rows", ctypes.c_int64), ("max_indegree", ctypes.c_int32),
+                ("exact_mode", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+                ("gemm_prec_used", ctypes.c_int32), ("ms_knn_gemm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+SYMBOLS = {
+    # name: (restype, argtypes)
+    "ssg_default_opts": (None, [ctypes.c_void_p]),
+    "ssg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "ssg_last_error": (ctypes.c_char_p, []),
+    "ssg_kernel_launch_count": (ctypes.c_int64, []),
+    "ssg_nav_ids": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p]),
+    "ssg_knn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_knn_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                     ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_pool": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_prune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_reverse": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
+    "ssg_connect": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
+    "ssg_search_adj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_recall_hits": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_build_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "ssg_graph_view": (ctypes.c_int, [ctypes.c_void_p] * 8),
+    "ssg_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_search_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "ssg_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_void_p]),
+    "ssg_free": (None, [ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Load libssg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "paper_1907_06146_gb300.build_ext.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SYMBOLS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().ssg_last_error().decode(errors="replace")
+        raise SSGError(status, msg)
+
+
+def launch_count() -> int:
+    return int(lib().ssg_kernel_launch_count())
+
+
+def nav_ids(n: int, s: int, seed: int) -> np.ndarray:
+    out = np.empty(s, np.int32)
+    _check(lib().ssg_nav_ids(n, s, seed, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+# ---- torch marshalling ----------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t))
+    t = t.to(device="cuda", dtype=dtype)
+    return t.contiguous()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def knn(base, K: int, prec: str = "auto"):
+    """Exact kNN graph: (ids int32 [n][K], d2 float32 [n][K])."""
+    torch = _torch()
+    b = _dev(base, torch.float32)
+    n, d = b.shape
+    ids = torch.empty((n, K), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((n, K), dtype=torch.float32, device="cuda")
+    _check(lib().ssg_knn(_ptr(b), n, d, K, PREC[prec], _ptr(ids), _ptr(d2), _stream()))
+    return ids, d2
+
+
+def knn_query(base, queries, k: int, prec: str = "auto"):
+    """Brute-force ground truth: (ids int32 [nq][k], d2 float32 [nq][k])."""
+    torch = _torch()
+    b = _dev(base, torch.float32)
+    q = _dev(queries, torch.float32)
+    n, d = b.shape
+    nq = q.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    _check(lib().ssg_knn_query(_ptr(b), n, d, _ptr(q), nq, k, PREC[prec], _ptr(ids), _ptr(d2),
+                               _stream()))
+    return ids, d2
+
+
+def pool(base, knn_id, L: int):
+    torch = _torch()
+    b = _dev(base, torch.float32)
+    kn = _dev(knn_id, torch.int32)
+    n, d = b.shape
+    K = kn.shape[1]
+    pid = torch.empty((n, L), dtype=torch.int32, device="cuda")
+    pd2 = torch.empty((n, L), dtype=torch.float32, device="cuda")
+    pl = torch.empty((n,), dtype=torch.int32, device="cuda")
+    _check(lib().ssg_pool(_ptr(b), n, d, _ptr(kn), K, L, _ptr(pid), _ptr(pd2), _ptr(pl), _stream()))
+    return pid, pd2, pl
+
+
+def prune(base, pool_id, pool_len, R: int, alpha: float):
+    torch = _torch()
+    b = _dev(base, torch.float32)
+    pid = _dev(pool_id, torch.int32)
+    pl = _dev(pool_len, torch.int32)
+    n, d = b.shape
+    adj = torch.empty((n, R), dtype=torch.int32, device="cuda")
+    deg = torch.empty((n,), dtype=torch.int32, device="cuda")
+    _check(lib().ssg_prune(_ptr(b), n, d, _ptr(pid), _ptr(pl), pid.shape[1], R, float(alpha),
+                           _ptr(adj), _ptr(deg), _stream()))
+    return adj, deg
+
+
+def reverse(base, adj0, deg0, alpha: float):
+    torch = _torch()
+    b = _dev(base, torch.float32)
+    a0 = _dev(adj0, torch.int32)
+    d0 = _dev(deg0, torch.int32)
+    n, d = b.shape
+    R = a0.shape[1]
+    adj1 = torch.empty_like(a0)
+    deg1 = torch.empty_like(d0)
+    _check(lib().ssg_reverse(_ptr(b), n, d, _ptr(a0), _ptr(d0), R, float(alpha), _ptr(adj1),
+                             _ptr(deg1), _stream()))
+    return adj1, deg1
+
+
+def connect(base, adj, deg, nav):
+    """Connectivity repair on copies of adj/deg; returns (adj, deg, n_repair)."""
+    torch = _torch()
+    b = _dev(base, torch.float32)
+    a = _dev(adj, torch.int32).clone()
+    dg = _dev(deg, torch.int32).clone()
+    nv = _dev(nav, torch.int32)
+    n, d = b.shape
+    rep = ctypes.c_int64(0)
+    _check(lib().ssg_connect(_ptr(b), n, d, _ptr(a), _ptr(dg), a.shape[1], _ptr(nv), nv.numel(),
+                             ctypes.byref(rep), _stream()))
+    return a, dg, int(rep.value)
+
+
+def search_adj(base, adj, deg, nav, queries, k: int, L_search: int):
+    torch = _torch()
+    b = _dev(base, torch.float32)
+    a = _dev(adj, torch.int32)
+    dg = _dev(deg, torch.int32)
+    nv = _dev(nav, torch.int32)
+    q = _dev(queries, torch.float32)
+    n, d = b.shape
+    nq = q.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    _check(lib().ssg_search_adj(_ptr(b), n, d, _ptr(a), _ptr(dg), a.shape[1], _ptr(nv), nv.numel(),
+                                _ptr(q), nq, k, L_search, _ptr(ids), _ptr(d2), _stream()))
+    return ids, d2
+
+
+def recall_hits(found, truth, k: int) -> int:
+    torch = _torch()
+    f = _dev(found, torch.int32)
+    t = _dev(truth, torch.int32)
+    h = ctypes.c_int64(0)
+    _check(lib().ssg_recall_hits(_ptr(f), f.shape[1], _ptr(t), t.shape[1], f.shape[0], k,
+                                 ctypes.byref(h), _stream()))
+    return int(h.value)
+
+
+class _DevView:
+    """A device array owned by the library, exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": tuple(shape),
+                                         "typestr": typestr, "version": 2, "strides": None}
+        self._owner = owner
+
+
+class Graph:
+    """An NSSG index owned by the library (released on garbage collection)."""
+
+    def __init__(self, handle: ctypes.c_void_p, stats: BuildStats | None = None):
+        self._h = handle
+        self.stats = stats.as_dict() if stats is not None else None
+        adj, deg, nav = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        n_nav, R, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        n = ctypes.c_int64()
+        _check(lib().ssg_graph_view(self._h, ctypes.byref(adj), ctypes.byref(deg), ctypes.byref(nav),
+                                    ctypes.byref(n_nav), ctypes.byref(R), ctypes.byref(n),
+                                    ctypes.byref(d)))
+        self.n, self.d, self.R, self.n_nav = n.value, d.value, R.value, n_nav.value
+        self._adj, self._deg, self._nav = adj.value, deg.value, nav.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ssg_free(self._h)
+            self._h = None
+
+    def _view(self, ptr, shape):
+        torch = _torch()
+        return torch.as_tensor(_DevView(ptr, shape, "<i4", self), device="cuda")
+
+    @property
+    def adj(self):
+        return self._view(self._adj, (self.n, self.R))
+
+    @property
+    def deg(self):
+        return self._view(self._deg, (self.n,))
+
+    @property
+    def nav(self):
+        return self._view(self._nav, (self.n_nav,))
+
+    def search(self, base, queries, k: int, L_search: int):
+        torch = _torch()
+        q = _dev(queries, torch.float32)
+        b = ctypes.c_void_p(0) if base is None else _ptr(_dev(base, torch.float32))
+        nq = q.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+        d2 = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+        _check(lib().ssg_search(self._h, b, _ptr(q), nq, k, L_search, _ptr(ids), _ptr(d2), _stream()))
+        return ids, d2
+
+    def search_host(self, queries: np.ndarray, k: int, L_search: int):
+        """Alg. 1 with host queries and host results (copies inside the call)."""
+        q = np.ascontiguousarray(queries, dtype=np.float32)
+        ids = np.empty((q.shape[0], k), np.int32)
+        d2 = np.empty((q.shape[0], k), np.float32)
+        _check(lib().ssg_search_host(self._h, q.ctypes.data_as(ctypes.c_void_p), q.shape[0], k,
+                                     L_search, ids.ctypes.data_as(ctypes.c_void_p),
+                                     d2.ctypes.data_as(ctypes.c_void_p), _stream()))
+        return ids, d2
+
+    def save(self, path: str):
+        _check(lib().ssg_save(self._h, path.encode()))
+
+    @staticmethod
+    def load(path: str) -> "Graph":
+        h = ctypes.c_void_p()
+        _check(lib().ssg_load(path.encode(), ctypes.byref(h)))
+        return Graph(h)
+
+
+def _opts(n_nav, nav, seed, prec):
+    o = BuildOpts()
+    lib().ssg_default_opts(ctypes.byref(o))
+    o.gemm_prec = PREC[prec]
+    keep = None
+    if nav is not None:
+        keep = np.ascontiguousarray(np.asarray(nav), dtype=np.int32)
+        o.n_nav = keep.size
+        o.nav_ids_host = keep.ctypes.data
+    else:
+        o.n_nav = n_nav
+    if seed is not None:
+        o.seed = seed
+    return o, keep
+
+
+def build(base, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None, seed=None,
+          prec: str = "auto") -> Graph:
+    """NSSGIndexing (Alg. 3) on a device-resident base (torch CUDA float32 [n][d])."""
+    torch = _torch()
+    b = _dev(base, torch.float32)
+    n, d = b.shape
+    o, keep = _opts(n_nav, nav, seed, prec)
+    h = ctypes.c_void_p()
+    st = BuildStats()
+    _check(lib().ssg_build(_ptr(b), n, d, K, L, R, float(alpha), ctypes.byref(o), _stream(),
+                           ctypes.byref(h), ctypes.byref(st)))
+    del keep
+    g = Graph(h, st)
+    g._base_ref = b
+    return g
+
+
+def build_host(base: np.ndarray, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None,
+               seed=None, prec: str = "auto"):
+    """NSSGIndexing from host vectors; returns (graph, adj numpy [n][R], deg numpy [n])."""
+    x = np.ascontiguousarray(base, dtype=np.float32)
+    n, d = x.shape
+    o, keep = _opts(n_nav, nav, seed, prec)
+    adj = np.empty((n, R), np.int32)
+    deg = np.empty(n, np.int32)
+    h = ctypes.c_void_p()
+    st = BuildStats()
+    _check(lib().ssg_build_host(x.ctypes.data_as(ctypes.c_void_p), n, d, K, L, R, float(alpha),
+                                ctypes.byref(o), _stream(), ctypes.byref(h),
+                                adj.ctypes.data_as(ctypes.c_void_p),
+                                deg.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st)))
+    del keep
+    return Graph(h, st), adj, deg

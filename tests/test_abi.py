@@ -1,0 +1,85 @@
+"""The C-ABI library loads on a machine without a GPU, exports every entry point that
+include/ssg.h declares, and rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1907_06146_gb300 import build_ext, ssg, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build_ext.build()
+    return ssg.lib()
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "ssg.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ssg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+    # and the binding declares argument types for each of them
+    assert set(names) <= set(ssg.SYMBOLS)
+
+
+def test_nav_ids_match_generator(L):
+    for n, s, seed in [(1000, 10, 1), (17, 17, 2), (10_000_000, 10, 190706145)]:
+        np.testing.assert_array_equal(ssg.nav_ids(n, s, seed), synth.nav_ids(n, s, seed))
+
+
+def test_nav_ids_rejects(L):
+    out = np.empty(4, np.int32)
+    assert L.ssg_nav_ids(3, 4, 0, out.ctypes.data_as(ctypes.c_void_p)) == 1
+    assert b"s <= n" in L.ssg_last_error()
+
+
+def test_strerror(L):
+    assert L.ssg_strerror(0) == b"ok"
+    assert L.ssg_strerror(1) == b"invalid argument"
+    assert L.ssg_strerror(99) == b"unknown status"
+
+
+def test_invalid_arguments_rejected_without_device(L):
+    P = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+    s = ctypes.c_void_p(0)
+    # K > n - 1
+    assert L.ssg_knn(P, 10, 4, 10, 0, P, P, s) == 1
+    # K too large for the selection buffers
+    assert L.ssg_knn(P, 10_000, 4, 701, 0, P, P, s) == 1
+    # null output
+    assert L.ssg_knn(P, 10, 4, 3, 0, None, P, s) == 1
+    # L + K too large
+    assert L.ssg_pool(P, 5000, 8, P, 600, 500, P, P, P, s) == 1
+    # alpha outside (0, 180)
+    assert L.ssg_prune(P, 100, 8, P, P, 10, 8, 0.0, P, P, s) == 1
+    assert L.ssg_prune(P, 100, 8, P, P, 10, 8, 180.0, P, P, s) == 1
+    # R out of range, and R * (d + 1) too large for shared memory
+    assert L.ssg_prune(P, 100, 8, P, P, 10, 0, 60.0, P, P, s) == 1
+    assert L.ssg_prune(P, 100, 960, P, P, 10, 70, 60.0, P, P, s) == 1
+    # k > L_search
+    assert L.ssg_search_adj(P, 100, 8, P, P, 8, P, 1, P, 5, 20, 10, P, P, s) == 1
+    # build: n_nav > n
+    opts = ssg.BuildOpts()
+    L.ssg_default_opts(ctypes.byref(opts))
+    opts.n_nav = 50
+    h = ctypes.c_void_p()
+    assert L.ssg_build(P, 20, 4, 5, 10, 8, 60.0, ctypes.byref(opts), s, ctypes.byref(h), None) == 1
+    assert h.value is None
+
+
+def test_default_opts(L):
+    o = ssg.BuildOpts()
+    L.ssg_default_opts(ctypes.byref(o))
+    assert o.gemm_prec == ssg.PREC["auto"] and o.n_nav == 10 and o.nav_ids_host is None

@@ -1,0 +1,267 @@
+"""GPU parity: every stage of the CUDA path against the CPU oracle, element by element.
+
+Stages are isolated: each GPU stage takes the oracle's output of the previous stage as
+its input (oracle -> GPU only; no oracle input ever comes from the GPU).  The bar:
+adjacency, pools and kNN ids bit-exact (the library re-decides every near-boundary case
+in double precision); search recall@10 within 0.002 of the oracle's on float data and
+ids identical on integer data, where every distance is exact in single precision.
+Sizes span several 128-row tiles with a ragged tail.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_06146_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ssg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_06146_gb300 import build_ext, ssg as S
+    build_ext.build()
+    S.lib()
+    return S
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _np(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def small():
+    return synth.small(n=4_000, nq=300)
+
+
+@pytest.fixture(scope="module")
+def intdata():
+    return synth.sift_like(n=6_000, nq=300, n_clusters=40)
+
+
+@pytest.fixture(scope="module")
+def small_ref(small):
+    nav = synth.nav_ids(small.n, small.n_nav, 11)
+    return oracle.build_graph(small.base, small.K, small.L, small.R, small.alpha, nav)
+
+
+@pytest.fixture(scope="module")
+def int_ref(intdata):
+    nav = synth.nav_ids(intdata.n, intdata.n_nav, 12)
+    return oracle.build_graph(intdata.base, intdata.K, intdata.L, intdata.R, intdata.alpha, nav)
+
+
+# ---- a1: exact kNN graph ---------------------------------------------------------------
+def test_knn_small_float(ssg, small, small_ref):
+    ids, d2 = ssg.knn(_cuda(small.base), small.K)
+    np.testing.assert_array_equal(_np(ids), small_ref["knn_id"])
+    np.testing.assert_array_equal(_np(d2), small_ref["knn_d2"].astype(np.float32))
+
+
+def test_knn_integer_exact(ssg, intdata, int_ref):
+    for prec in ("fp32", "auto"):
+        ids, d2 = ssg.knn(_cuda(intdata.base), intdata.K, prec=prec)
+        np.testing.assert_array_equal(_np(ids), int_ref["knn_id"])
+        np.testing.assert_array_equal(_np(d2), int_ref["knn_d2"].astype(np.float32))
+
+
+@pytest.mark.parametrize("n,d,K", [(1037, 3, 1), (1037, 3, 7), (1300, 33, 200), (700, 17, 640)])
+def test_knn_ragged(ssg, n, d, K):
+    base = synth.uniform_points(n, d, 1000 + d)
+    ids, d2 = ssg.knn(_cuda(base), K)
+    ref_ids, ref_d2 = oracle.knn_rows(base, K)
+    np.testing.assert_array_equal(_np(ids), ref_ids)
+    np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
+
+
+def test_knn_duplicates(ssg):
+    base = synth.uniform_points(900, 8, 77)
+    base[100:130] = base[5]          # 31 copies of one point
+    base[500] = base[501]
+    ids, d2 = ssg.knn(_cuda(base), 40)
+    ref_ids, ref_d2 = oracle.knn_rows(base, 40)
+    np.testing.assert_array_equal(_np(ids), ref_ids)
+    np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
+
+
+def test_ground_truth_queries(ssg, small, intdata):
+    for w in (small, intdata):
+        ids, d2 = ssg.knn_query(_cuda(w.base), _cuda(w.queries), 10)
+        ref_ids, ref_d2 = oracle.knn_queries(w.base, w.queries, 10)
+        np.testing.assert_array_equal(_np(ids), ref_ids)
+        np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
+
+
+# ---- a2: candidate pools -----------------------------------------------------------------
+@pytest.mark.parametrize("which", ["small", "int"])
+def test_pool(ssg, which, small, intdata, small_ref, int_ref):
+    w, ref = (small, small_ref) if which == "small" else (intdata, int_ref)
+    pid, pd2, pl = ssg.pool(_cuda(w.base), _cuda(ref["knn_id"]), w.L)
+    np.testing.assert_array_equal(_np(pl), ref["pool_len"])
+    np.testing.assert_array_equal(_np(pid), ref["pool_id"])
+
+
+def test_pool_small_L(ssg, small):
+    knn, _ = oracle.knn_rows(small.base, 10)
+    ref = oracle.pool(small.base, knn, 30)
+    pid, _, pl = ssg.pool(_cuda(small.base), _cuda(knn), 30)
+    np.testing.assert_array_equal(_np(pl), ref[2])
+    np.testing.assert_array_equal(_np(pid), ref[0])
+
+
+# ---- a3: SSG prune -----------------------------------------------------------------------
+@pytest.mark.parametrize("which", ["small", "int"])
+def test_prune(ssg, which, small, intdata, small_ref, int_ref):
+    w, ref = (small, small_ref) if which == "small" else (intdata, int_ref)
+    adj, deg = ssg.prune(_cuda(w.base), _cuda(ref["pool_id"]), _cuda(ref["pool_len"]), w.R, w.alpha)
+    np.testing.assert_array_equal(_np(deg), ref["deg0"])
+    np.testing.assert_array_equal(_np(adj), ref["adj0"])
+
+
+@pytest.mark.parametrize("alpha,R", [(45.0, 32), (90.0, 8), (30.0, 64), (75.0, 5)])
+def test_prune_angles(ssg, small, small_ref, alpha, R):
+    ref = oracle.prune(small.base, small_ref["pool_id"], small_ref["pool_len"], R, alpha)
+    adj, deg = ssg.prune(_cuda(small.base), _cuda(small_ref["pool_id"]),
+                         _cuda(small_ref["pool_len"]), R, alpha)
+    np.testing.assert_array_equal(_np(deg), ref[1])
+    np.testing.assert_array_equal(_np(adj), ref[0])
+
+
+# ---- a4: reverse merge -------------------------------------------------------------------
+@pytest.mark.parametrize("which", ["small", "int"])
+def test_reverse(ssg, which, small, intdata, small_ref, int_ref):
+    w, ref = (small, small_ref) if which == "small" else (intdata, int_ref)
+    adj1, deg1 = ssg.reverse(_cuda(w.base), _cuda(ref["adj0"]), _cuda(ref["deg0"]), w.alpha)
+    np.testing.assert_array_equal(_np(deg1), ref["deg1"])
+    np.testing.assert_array_equal(_np(adj1), ref["adj1"])
+
+
+def test_reverse_hub(ssg):
+    """A node that every other node points at: its in-degree exceeds the per-warp buffer."""
+    n, R = 1200, 6
+    base = synth.uniform_points(n, 5, 91)
+    rng = np.random.default_rng(3)
+    adj0 = np.full((n, R), -1, np.int32)
+    deg0 = np.zeros(n, np.int32)
+    for i in range(n):
+        others = rng.choice(n, size=4, replace=False)
+        row = [0] + [int(x) for x in others if x not in (0, i)]
+        row = [x for x in row if x != i][:R]
+        adj0[i, :len(row)] = row
+        deg0[i] = len(row)
+    ref = oracle.reverse(base, adj0, deg0, 60.0)
+    adj1, deg1 = ssg.reverse(_cuda(base), _cuda(adj0), _cuda(deg0), 60.0)
+    np.testing.assert_array_equal(_np(deg1), ref[1])
+    np.testing.assert_array_equal(_np(adj1), ref[0])
+
+
+# ---- a5: connectivity --------------------------------------------------------------------
+@pytest.mark.parametrize("which", ["small", "int"])
+def test_connect(ssg, which, small, intdata, small_ref, int_ref):
+    w, ref = (small, small_ref) if which == "small" else (intdata, int_ref)
+    adj, deg, nrep = ssg.connect(_cuda(w.base), _cuda(ref["adj1"]), _cuda(ref["deg1"]),
+                                 _cuda(ref["nav"]))
+    assert nrep == ref["n_repair"]
+    np.testing.assert_array_equal(_np(deg), ref["deg"])
+    np.testing.assert_array_equal(_np(adj), ref["adj"])
+
+
+def test_connect_many_components(ssg):
+    rng = np.random.default_rng(7)
+    n, R = 3000, 6
+    base = synth.uniform_points(n, 3, 71)
+    adj = np.full((n, R), -1, np.int32)
+    deg = rng.integers(0, 3, size=n).astype(np.int32)
+    for i in range(n):
+        adj[i, :deg[i]] = rng.choice(n, size=deg[i], replace=False)
+    nav = synth.nav_ids(n, 4, 1234)
+    ref = oracle.connect(base, adj, deg, nav)
+    a, dg, nrep = ssg.connect(_cuda(base), _cuda(adj), _cuda(deg), _cuda(nav))
+    assert nrep == ref[2] and nrep > 100
+    np.testing.assert_array_equal(_np(dg), ref[1])
+    np.testing.assert_array_equal(_np(a), ref[0])
+
+
+# ---- whole build ---------------------------------------------------------------------------
+@pytest.mark.parametrize("which", ["small", "int"])
+def test_build_end_to_end(ssg, which, small, intdata, small_ref, int_ref):
+    w, ref = (small, small_ref) if which == "small" else (intdata, int_ref)
+    g = ssg.build(_cuda(w.base), w.K, w.L, w.R, w.alpha, nav=ref["nav"])
+    np.testing.assert_array_equal(_np(g.nav), ref["nav"])
+    np.testing.assert_array_equal(_np(g.deg), ref["deg"])
+    np.testing.assert_array_equal(_np(g.adj), ref["adj"])
+    st = g.stats
+    assert st["n_repair"] == ref["n_repair"]
+    assert st["kernel_launches"] > 5
+    assert st["exact_mode"] == (1 if which == "int" else 0)
+
+
+def test_build_host_matches_device(ssg, small, small_ref):
+    g, adj, deg = ssg.build_host(small.base, small.K, small.L, small.R, small.alpha,
+                                 nav=small_ref["nav"])
+    np.testing.assert_array_equal(deg, small_ref["deg"])
+    np.testing.assert_array_equal(adj, small_ref["adj"])
+    ids, _ = g.search_host(small.queries, 10, 40)
+    oid, _, _, _ = oracle.search(small.base, small_ref["adj"], small_ref["deg"], small_ref["nav"],
+                                 small.queries, 10, 40)
+    truth, _ = oracle.knn_queries(small.base, small.queries, 10)
+    assert abs(oracle.recall_at(ids, truth) - oracle.recall_at(oid, truth)) <= 0.002
+
+
+def test_save_load(ssg, small, small_ref, tmp_path):
+    g = ssg.build(_cuda(small.base), small.K, small.L, small.R, small.alpha, nav=small_ref["nav"])
+    p = str(tmp_path / "g.nssg")
+    g.save(p)
+    h = ssg.Graph.load(p)
+    np.testing.assert_array_equal(_np(h.adj), small_ref["adj"])
+    np.testing.assert_array_equal(_np(h.nav), small_ref["nav"])
+
+
+# ---- a6 / a7: search and recall -----------------------------------------------------------
+@pytest.mark.parametrize("Ls", [10, 20, 40, 80])
+def test_search_float_recall(ssg, small, small_ref, Ls):
+    ids, _ = ssg.search_adj(_cuda(small.base), _cuda(small_ref["adj"]), _cuda(small_ref["deg"]),
+                            _cuda(small_ref["nav"]), _cuda(small.queries), 10, Ls)
+    oid, _, _, _ = oracle.search(small.base, small_ref["adj"], small_ref["deg"], small_ref["nav"],
+                                 small.queries, 10, Ls)
+    truth, _ = oracle.knn_queries(small.base, small.queries, 10)
+    g_ids = _np(ids)
+    assert abs(oracle.recall_at(g_ids, truth) - oracle.recall_at(oid, truth)) <= 0.002
+    assert np.mean(np.all(g_ids == oid, axis=1)) > 0.97
+
+
+@pytest.mark.parametrize("Ls", [10, 50, 200])
+def test_search_integer_exact(ssg, intdata, int_ref, Ls):
+    ids, d2 = ssg.search_adj(_cuda(intdata.base), _cuda(int_ref["adj"]), _cuda(int_ref["deg"]),
+                             _cuda(int_ref["nav"]), _cuda(intdata.queries), 10, Ls)
+    oid, od2, _, _ = oracle.search(intdata.base, int_ref["adj"], int_ref["deg"], int_ref["nav"],
+                                   intdata.queries, 10, Ls)
+    np.testing.assert_array_equal(_np(ids), oid)
+    np.testing.assert_array_equal(_np(d2), od2.astype(np.float32))
+
+
+def test_search_full_pool_is_brute_force(ssg):
+    w = synth.small(n=900, nq=50)
+    nav = synth.nav_ids(900, 3, 5)
+    ref = oracle.build_graph(w.base, 10, 40, 12, 60, nav)
+    ids, _ = ssg.search_adj(_cuda(w.base), _cuda(ref["adj"]), _cuda(ref["deg"]), _cuda(nav),
+                            _cuda(w.queries), 10, 1024)
+    truth, _ = oracle.knn_queries(w.base, w.queries, 10)
+    np.testing.assert_array_equal(_np(ids), truth)
+
+
+def test_recall_hits(ssg, small):
+    truth, _ = oracle.knn_queries(small.base, small.queries, 10)
+    found = truth.copy()
+    found[::2, 3] = -1
+    found[1::3, 0] = 10**6
+    hits = ssg.recall_hits(_cuda(found), _cuda(truth), 10)
+    assert hits / truth.size == pytest.approx(oracle.recall_at(found, truth))
