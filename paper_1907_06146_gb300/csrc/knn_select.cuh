@@ -1,0 +1,81 @@
+// Streaming top-K selection helpers shared by the kNN kernels: per-row buffers of
+// (distance, id) keys in global scratch, compacted by a warp-wide bitonic sort.
+#pragma once
+
+#include "common.cuh"
+
+namespace ssg {
+
+// Register bitonic sort of C keys held by a warp: element index e * 32 + lane.
+template <int C>
+__device__ __forceinline__ void warp_sort_regs(uint64_t (&v)[C / 32]) {
+  constexpr int E = C / 32;
+  const int lane = lane_id();
+#pragma unroll
+  for (int k = 2; k <= C; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int p = e ^ (j >> 5);
+          if (p > e) {
+            const bool up = (((e << 5) | lane) & k) == 0;
+            uint64_t a = v[e], b = v[p];
+            if ((a > b) == up) {
+              v[e] = b;
+              v[p] = a;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = (e << 5) | lane;
+          const bool up = (i & k) == 0;
+          const bool lower = (lane & j) == 0;
+          uint64_t o = __shfl_xor_sync(0xffffffffu, v[e], j);
+          uint64_t mn = v[e] < o ? v[e] : o;
+          uint64_t mx = v[e] < o ? o : v[e];
+          v[e] = (lower == up) ? mn : mx;
+        }
+      }
+    }
+  }
+}
+
+// Compact one row's buffer: sort its cnt keys, keep the KS smallest at the front.
+// Returns the new count; *tau receives the KS-th distance (or +inf while fewer).
+template <int C>
+__device__ __forceinline__ int compact_row(uint64_t* __restrict__ buf, int cnt, int KS,
+                                           float* tau) {
+  constexpr int E = C / 32;
+  const int lane = lane_id();
+  uint64_t v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    int i = (e << 5) | lane;
+    v[e] = i < cnt ? buf[i] : KEY_NONE;
+  }
+  __syncwarp();
+  warp_sort_regs<C>(v);
+  const int keep = cnt < KS ? cnt : KS;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    int i = (e << 5) | lane;
+    if (i < keep) buf[i] = v[e];
+  }
+  uint64_t last = KEY_NONE;
+  if (keep == KS) {
+    const int ei = (KS - 1) >> 5;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e == ei) last = v[e];
+    last = __shfl_sync(0xffffffffu, last, (KS - 1) & 31);
+  }
+  __syncwarp();
+  *tau = (keep == KS) ? key_dist(last) : __int_as_float(0x7f800000);
+  return keep;
+}
+
+}  // namespace ssg

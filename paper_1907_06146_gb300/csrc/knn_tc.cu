@@ -1,15 +1,505 @@
-// bf16 tensor-core (tcgen05) distance GEMM with fused top-K: not built yet.
+// Exact kNN graph on the 5th-generation tensor cores (tcgen05, sm_103a) for inputs that
+// bf16 holds exactly (integers with |x| <= 256 and 2 d max|x|^2 <= 2^24: every product
+// and every partial sum of the fp32 accumulation is an integer below 2^24, so the
+// distance |x|^2 + |y|^2 - 2 x.y comes out exact, whatever the summation order).
+//
+// Persistent kernel, one CTA per SM, 10 warps:
+//   warp 0      TMA producer: the CTA's 256 query rows (A, resident per row block) and a
+//               pipeline of 128-column base tiles (B), both bf16 with 128-byte swizzle;
+//   warp 1      allocates 512 TMEM columns and issues tcgen05.mma: for every B tile two
+//               128x128 accumulators (the two 128-row halves of A) into one of two TMEM
+//               buffers, so the epilogue drains one buffer while the MMAs fill the other;
+//   warps 2..9  epilogue, one thread per query row (TMEM lane): tcgen05.ld 32 columns at
+//               a time, d2 = |x|^2 + |y|^2 - 2 acc, and every value below the row's
+//               threshold is appended to the row's buffer in global scratch (L2); a warp
+//               compacts a full buffer with a register bitonic sort (top-KS, new
+//               threshold).  Columns arrive in increasing id order, so "d2 < threshold"
+//               also settles equal distances by id.  The row's own column (self) takes
+//               one extra slot and is dropped at output.
+// Every wait on an mbarrier is bounded (about 2 s); a wait that runs out sets an error
+// word, tells the other roles to stop, and the CTA releases its TMEM and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 #include "knn.cuh"
+#include "knn_select.cuh"
 
 namespace ssg {
+namespace {
 
-bool knn_tc_available() { return false; }
+constexpr int BM = 256;               // query rows per CTA (two UMMA_M = 128 halves)
+constexpr int BN = 128;               // base columns per pipeline stage (UMMA_N)
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + EPI_WARPS * 32;
+constexpr int TMEM_COLS = 512;        // 2 buffers x 2 halves x 128 fp32 columns
+constexpr int MAX_STAGES = 6;
+// tcgen05 instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, N = 128, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+constexpr uint64_t WAIT_NS = 2000000000ull;
 
-void knn_exact_tc(const float*, int64_t, int, const float*, const float*, int64_t, int,
-                  const float*, int, int, int, int32_t*, float*, cudaStream_t, StageTimer*) {
-  set_error("bf16 tensor-core kNN is not available");
-  throw Fail{SSG_EINTERNAL};
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: false on timeout (about 2 s) or when another role has aborted.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > WAIT_NS) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups of
+// 128 bytes 1024 bytes apart.  The leading-byte offset is unused by this layout.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+struct TcArgs {
+  const float* a_norm;
+  const float* b_norm;
+  int64_t na, nb;
+  int kchunks;  // padded d / 64
+  int stages;
+  int self;
+  int KS, K;
+  uint64_t* rowbuf;
+  int32_t* out_id;
+  float* out_d2;
+  int* err;
+};
+
+template <int C>
+__global__ void __launch_bounds__(THREADS, 1)
+k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+         TcArgs p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = p.stages;
+  const uint32_t a_bytes = (uint32_t)p.kchunks * BM * 128;
+  const uint32_t b_bytes = (uint32_t)p.kchunks * BN * 128;
+  unsigned char* sA = sm;
+  unsigned char* sB = sA + a_bytes;
+  float* nyw = (float*)(sB + (size_t)S * b_bytes);
+  uint64_t* bars = (uint64_t*)(nyw + EPI_WARPS * BN);
+  uint64_t* a_full = bars;
+  uint64_t* a_empty = bars + 1;
+  uint64_t* b_full = bars + 2;
+  uint64_t* b_empty = b_full + MAX_STAGES;
+  uint64_t* t_full = b_empty + MAX_STAGES;
+  uint64_t* t_empty = t_full + 2;
+  uint32_t* tmem_slot = (uint32_t*)(t_empty + 2);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(a_full), 1);
+    mbar_init(smem_u32(a_empty), 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(b_full + s), 1);
+      mbar_init(smem_u32(b_empty + s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(t_full + b), 1);
+      mbar_init(smem_u32(t_empty + b), EPI_WARPS);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int64_t nrb = (p.na + BM - 1) / BM;
+  const int64_t nct = (p.nb + BN - 1) / BN;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int64_t it = 0;
+      int rbi = 0;
+      bool ok = true;
+      for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++rbi) {
+        ok = mbar_wait(smem_u32(a_empty), (rbi & 1) ^ 1, abort_flag);
+        if (!ok) break;
+        mbar_expect_tx(smem_u32(a_full), a_bytes);
+        for (int kc = 0; kc < p.kchunks; ++kc)
+          tma_load_2d(smem_u32(sA + (size_t)kc * BM * 128), &tmA, smem_u32(a_full), kc * 64,
+                      (int)(rb * BM));
+        for (int64_t ct = 0; ct < nct; ++ct, ++it) {
+          const int s = (int)(it % S);
+          const uint32_t ph = (uint32_t)((it / S) & 1);
+          ok = mbar_wait(smem_u32(b_empty + s), ph ^ 1, abort_flag);
+          if (!ok) break;
+          mbar_expect_tx(smem_u32(b_full + s), b_bytes);
+          unsigned char* dst = sB + (size_t)s * b_bytes;
+          for (int kc = 0; kc < p.kchunks; ++kc)
+            tma_load_2d(smem_u32(dst + (size_t)kc * BN * 128), &tmB, smem_u32(b_full + s), kc * 64,
+                        (int)(ct * BN));
+        }
+      }
+      if (!ok) {
+        atomicOr(p.err, 1);
+        *abort_flag = 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int64_t it = 0;
+      int rbi = 0;
+      bool ok = true;
+      const int ksteps = p.kchunks * 4;
+      for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++rbi) {
+        ok = mbar_wait(smem_u32(a_full), rbi & 1, abort_flag);
+        if (!ok) break;
+        for (int64_t ct = 0; ct < nct; ++ct, ++it) {
+          const int s = (int)(it % S);
+          const uint32_t ph = (uint32_t)((it / S) & 1);
+          const int b = (int)(it & 1);
+          const uint32_t tph = (uint32_t)((it >> 1) & 1);
+          ok = mbar_wait(smem_u32(t_empty + b), tph ^ 1, abort_flag) &&
+               mbar_wait(smem_u32(b_full + s), ph, abort_flag);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t bbase = smem_u32(sB + (size_t)s * b_bytes);
+          const uint32_t abase = smem_u32(sA);
+#pragma unroll 1
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t d_tmem = tmem_base + (uint32_t)((b * 2 + h) * BN);
+#pragma unroll 1
+            for (int ks = 0; ks < ksteps; ++ks) {
+              const int kc = ks >> 2, kk = ks & 3;
+              const uint64_t ad =
+                  sdesc_sw128(abase + (uint32_t)(kc * BM * 128 + h * 128 * 128 + kk * 32));
+              const uint64_t bd = sdesc_sw128(bbase + (uint32_t)(kc * BN * 128 + kk * 32));
+              umma_bf16(d_tmem, ad, bd, ks > 0 ? 1u : 0u);
+            }
+          }
+          umma_commit(smem_u32(b_empty + s));
+          umma_commit(smem_u32(t_full + b));
+        }
+        if (ok) umma_commit(smem_u32(a_empty));
+      }
+      if (!ok) {
+        atomicOr(p.err, 2);
+        *abort_flag = 1;
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: one thread per query row ----------------
+    const int ew = warp - 2;
+    const int h = ew >> 2;          // which 128-row half
+    const int q = warp & 3;         // TMEM lane quadrant this warp may access
+    const int row_in_cta = h * 128 + q * 32 + lane;
+    float* ny = nyw + ew * BN;
+    int64_t it = 0;
+    bool ok = true;
+    const float INF = __int_as_float(0x7f800000);
+    for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
+      const int64_t row = rb * BM + row_in_cta;
+      const float nx = row < p.na ? p.a_norm[row] : 0.f;
+      float tau = INF;
+      int cnt = 0;
+      uint64_t* buf = p.rowbuf + ((size_t)blockIdx.x * BM + row_in_cta) * C;
+      for (int64_t ct = 0; ct < nct; ++ct, ++it) {
+        const int b = (int)(it & 1);
+        const uint32_t tph = (uint32_t)((it >> 1) & 1);
+        const int64_t j0 = ct * BN;
+#pragma unroll
+        for (int c = 0; c < BN / 32; ++c) {
+          const int64_t jj = j0 + c * 32 + lane;
+          ny[c * 32 + lane] = jj < p.nb ? p.b_norm[jj] : INF;
+        }
+        __syncwarp();
+        ok = mbar_wait(smem_u32(t_full + b), tph, abort_flag);
+        if (!__all_sync(0xffffffffu, ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)((b * 2 + h) * BN);
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+          uint32_t v[32];
+          tmem_ld32(taddr + c * 32, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const float dd = fmaf(-2.f, __uint_as_float(v[e]), nx + ny[c * 32 + e]);
+            if (dd < tau) buf[cnt++] = make_key(dd, (int32_t)(j0 + c * 32 + e));
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(t_empty + b));
+        unsigned need = __ballot_sync(0xffffffffu, cnt > C - BN);
+        while (need) {
+          const int l = __ffs(need) - 1;
+          need &= need - 1;
+          uint64_t* lb = p.rowbuf + ((size_t)blockIdx.x * BM + h * 128 + q * 32 + l) * C;
+          float t2;
+          const int c2 = compact_row<C>(lb, __shfl_sync(0xffffffffu, cnt, l), p.KS, &t2);
+          if (lane == l) {
+            cnt = c2;
+            tau = t2;
+          }
+        }
+      }
+      if (!ok) break;
+      // final compaction of each row of this warp, then output (dropping the row itself)
+      for (int l = 0; l < 32; ++l) {
+        const int rin = h * 128 + q * 32 + l;
+        const int64_t r = rb * BM + rin;
+        uint64_t* lb = p.rowbuf + ((size_t)blockIdx.x * BM + rin) * C;
+        float t2;
+        const int c2 = compact_row<C>(lb, __shfl_sync(0xffffffffu, cnt, l), p.KS, &t2);
+        if (r >= p.na) continue;
+        int selfpos = c2;
+        if (p.self) {
+          for (int e0 = 0; e0 < c2; e0 += 32) {
+            const int e = e0 + lane;
+            const unsigned m = __ballot_sync(0xffffffffu, e < c2 && key_id(lb[e]) == (int32_t)r);
+            if (m) {
+              selfpos = e0 + __ffs(m) - 1;
+              break;
+            }
+          }
+        }
+        for (int t = lane; t < p.K; t += 32) {
+          const int src = t < selfpos ? t : t + 1;
+          const uint64_t key = src < c2 ? lb[src] : KEY_NONE;
+          p.out_id[r * p.K + t] = key == KEY_NONE ? -1 : key_id(key);
+          p.out_d2[r * p.K + t] = key == KEY_NONE ? INF : key_dist(key);
+        }
+        __syncwarp();
+      }
+    }
+    if (!ok && lane == 0) {
+      atomicOr(p.err, 4);
+      *abort_flag = 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int d, int ld,
+                          __nv_bfloat16* __restrict__ Y, int dp) {
+  const int64_t total = n * (int64_t)dp;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / dp;
+    const int c = (int)(i - r * dp);
+    Y[i] = __float2bfloat16_rn(c < d ? X[r * ld + c] : 0.f);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+CUtensorMap make_map(const __nv_bfloat16* ptr, int64_t rows, int dp, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ptr, dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  SSG_REQUIRE(r == CUDA_SUCCESS, SSG_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return m;
+}
+
+size_t tc_smem_bytes(int kchunks, int stages) {
+  return 1024 + (size_t)kchunks * BM * 128 + (size_t)stages * kchunks * BN * 128 +
+         EPI_WARPS * BN * sizeof(float) + sizeof(uint64_t) * (2 + 2 * MAX_STAGES + 4) + 16;
+}
+
+template <int C>
+void launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, TcArgs& a, int grid, size_t smem,
+               cudaStream_t st) {
+  static size_t attr = 0;
+  if (smem > attr) {
+    SSG_CUDA(cudaFuncSetAttribute(k_knn_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  SSG_LAUNCH(k_knn_tc<C>, grid, THREADS, smem, st, ma, mb, a);
+}
+
+}  // namespace
+
+bool knn_tc_available() {
+  static int avail = -1;
+  if (avail < 0) {
+    int dev = 0, major = 0, minor = 0;
+    avail = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
+      avail = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
+  }
+  return avail == 1;
+}
+
+void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
+                  int64_t nb, int ldb, const float* b_norm, int d, int self, int K,
+                  int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer) {
+  const int dp = (d + 63) & ~63;
+  const int kchunks = dp / 64;
+  int stages = MAX_STAGES;
+  while (stages > 2 && tc_smem_bytes(kchunks, stages) > 225 * 1024) --stages;
+  SSG_REQUIRE(tc_smem_bytes(kchunks, stages) <= 225 * 1024, SSG_EINVAL,
+              "tensor-core kNN: d = %d is too large for the shared-memory pipeline", d);
+  const int KS = self ? K + 1 : K;
+  Scratch<__nv_bfloat16> ab((size_t)na * dp, st);
+  Scratch<__nv_bfloat16> bb;
+  const int cgrid = 8 * num_sms();
+  SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, A, na, d, lda, ab.p, dp);
+  const __nv_bfloat16* bptr = ab.p;
+  if (!self) {
+    bb.alloc((size_t)nb * dp, st);
+    SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, B, nb, d, ldb, bb.p, dp);
+    bptr = bb.p;
+  }
+  const CUtensorMap ma = make_map(ab.p, na, dp, BM);
+  const CUtensorMap mb = make_map(bptr, nb, dp, BN);
+  const int64_t nrb = ceil_div(na, BM);
+  const int grid = (int)std::min<int64_t>(nrb, num_sms());
+  const int C = KS + BN <= 256 ? 256 : (KS + BN <= 512 ? 512 : 1024);
+  Scratch<uint64_t> rowbuf((size_t)grid * BM * C, st);
+  Scratch<int> err(1, st);
+  SSG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+  TcArgs a{a_norm, b_norm, na, nb, kchunks, stages, self, KS, K, rowbuf.p, out_id, out_d2, err.p};
+  const size_t smem = tc_smem_bytes(kchunks, stages);
+  if (gemm_timer) gemm_timer->start();
+  if (C == 256)
+    launch_tc<256>(ma, mb, a, grid, smem, st);
+  else if (C == 512)
+    launch_tc<512>(ma, mb, a, grid, smem, st);
+  else
+    launch_tc<1024>(ma, mb, a, grid, smem, st);
+  if (gemm_timer) gemm_timer->stop();
+  int h = 0;
+  SSG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SSG_CUDA(cudaStreamSynchronize(st));
+  SSG_REQUIRE(h == 0, SSG_ETIMEOUT, "tensor-core kNN: a pipeline wait timed out (code %d)", h);
 }
 
 }  // namespace ssg

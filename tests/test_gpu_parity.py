@@ -73,6 +73,41 @@ def test_knn_integer_exact(ssg, intdata, int_ref):
         np.testing.assert_array_equal(_np(d2), int_ref["knn_d2"].astype(np.float32))
 
 
+def _tc(ssg):
+    return ssg.lib() is not None and _has_tc(ssg)
+
+
+def _has_tc(ssg):
+    # the bf16 path is taken only on sm_103 with exact (small-integer) data
+    base = np.arange(64 * 8, dtype=np.float32).reshape(64, 8) % 7
+    try:
+        ssg.knn(_cuda(base), 3, prec="bf16")
+        return True
+    except ssg.SSGError:
+        return False
+
+
+@pytest.mark.parametrize("n,d,K", [(1037, 7, 1), (1037, 7, 20), (3001, 64, 200), (900, 130, 600),
+                                   (6000, 128, 200)])
+def test_knn_bf16_tensor_cores(ssg, n, d, K):
+    if not _tc(ssg):
+        pytest.skip("bf16 tensor-core kNN needs sm_103")
+    base = synth.uniform_points(n, d, 2000 + d, integer=True, hi=255 if d <= 128 else 100)
+    ids, d2 = ssg.knn(_cuda(base), K, prec="bf16")
+    ref_ids, ref_d2 = oracle.knn_rows(base, K)
+    np.testing.assert_array_equal(_np(ids), ref_ids)
+    np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
+
+
+def test_ground_truth_bf16(ssg, intdata):
+    if not _tc(ssg):
+        pytest.skip("bf16 tensor-core kNN needs sm_103")
+    ids, d2 = ssg.knn_query(_cuda(intdata.base), _cuda(intdata.queries), 10, prec="bf16")
+    ref_ids, ref_d2 = oracle.knn_queries(intdata.base, intdata.queries, 10)
+    np.testing.assert_array_equal(_np(ids), ref_ids)
+    np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
+
+
 @pytest.mark.parametrize("n,d,K", [(1037, 3, 1), (1037, 3, 7), (1300, 33, 200), (700, 17, 640)])
 def test_knn_ragged(ssg, n, d, K):
     base = synth.uniform_points(n, d, 1000 + d)
