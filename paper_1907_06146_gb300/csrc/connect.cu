@@ -12,6 +12,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "graph_dev.cuh"
 #include "knn.cuh"
 
 namespace ssg {
@@ -65,6 +66,7 @@ __global__ void k_first_unreached(const uint32_t* __restrict__ bm, int64_t nw, i
   }
 }
 
+// Exhaustive fp64 argmin (used only when the fp32 band below overflows its list).
 __global__ void k_repair_dist(const float* __restrict__ X, int ld, int d, int64_t n,
                               const uint32_t* __restrict__ bm, const int32_t* __restrict__ deg,
                               int R, int64_t u, double* __restrict__ dv,
@@ -82,9 +84,9 @@ __global__ void k_repair_dist(const float* __restrict__ X, int ld, int d, int64_
   }
 }
 
-__global__ void k_repair_pick(const double* __restrict__ dv, int64_t n,
-                              const unsigned long long* __restrict__ best_bits,
-                              int* __restrict__ best_id) {
+__global__ void k_repair_pick_all(const double* __restrict__ dv, int64_t n,
+                                  const unsigned long long* __restrict__ best_bits,
+                                  int* __restrict__ best_id) {
   const unsigned long long b = *best_bits;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
@@ -93,36 +95,196 @@ __global__ void k_repair_pick(const double* __restrict__ dv, int64_t n,
   }
 }
 
-__global__ void k_add_edge(int32_t* __restrict__ adj, int32_t* __restrict__ deg, int R,
-                           const int* __restrict__ best_id, int32_t u, uint32_t* __restrict__ bm,
-                           int32_t* __restrict__ frontier, int* __restrict__ fcount) {
-  const int v = *best_id;
-  if (v == INT_MAX) return;
-  adj[(int64_t)v * R + deg[v]] = u;
-  deg[v] += 1;
-  atomicOr(bm + (u >> 5), 1u << (u & 31));
-  frontier[0] = u;
-  *fcount = 1;
+// Device-side state of one repair step.
+struct RepairState {
+  unsigned long long u;  // smallest unreached id (n if none)
+  unsigned hi_bits;      // smallest fp32 upper bound of d2(v, u) over the candidates
+  int band;              // candidates whose fp32 lower bound reaches that upper bound
+  int best;              // chosen v (INT_MAX: none; -2: band overflow)
+  int fcnt[2];           // frontier sizes
+  int bfs_state;         // -1 traversal finished, else index of the frontier still to expand
+};
+
+__global__ void k_repair_init(RepairState* __restrict__ s, int64_t n) {
+  s->u = (unsigned long long)n;
+  s->hi_bits = 0x7f800000u;
+  s->band = 0;
+  s->best = INT_MAX;
+  s->fcnt[0] = 0;
 }
 
-namespace {
-struct Bfs {
-  int32_t* f[2];
-  int* cnt;  // [2]
-};
-}  // namespace
+// Pass 1: fp32 distance of every reached node with a free slot to u, by teams of 8 lanes;
+// the smallest upper bound d32 (1 + 2 rel) over them.
+__global__ void k_repair_fp32(const float* __restrict__ X, int ld, int64_t n,
+                              const uint32_t* __restrict__ bm, const int32_t* __restrict__ deg,
+                              int R, float rel, float* __restrict__ d32,
+                              RepairState* __restrict__ s) {
+  const int64_t u = (int64_t)s->u;
+  if (u >= n) return;
+  const int lane = lane_id(), team = lane >> 3, tl = lane & 7;
+  const float* xu = X + u * ld;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float best = __int_as_float(0x7f800000);
+  for (int64_t v0 = gw * 4; v0 < n; v0 += nwarp * 4) {
+    const int64_t v = v0 + team;
+    const bool cand = v < n && ((bm[v >> 5] >> (v & 31)) & 1u) && deg[v] < R;
+    const float e = team8_dist(X + (cand ? v : 0) * ld, xu, ld >> 2, tl, cand);
+    if (tl == 0 && v < n) d32[v] = cand ? e : -1.f;
+    if (cand) best = fminf(best, e);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (lane == 0 && best < __int_as_float(0x7f800000))
+    atomicMin(&s->hi_bits, __float_as_uint(best * (1.f + 2.f * rel) + 1e-30f));
+}
 
-// Level-synchronous traversal from the frontier already in f[0] / cnt[0].
-static void bfs_run(const int32_t* adj, const int32_t* deg, int R, uint32_t* bm, Bfs& b,
-                    cudaStream_t st) {
-  const int grid = 4 * num_sms();
+// Pass 2: every candidate whose fp32 lower bound does not exceed that upper bound is
+// recomputed in fp64 (coordinate-order sum) into a short list.
+__global__ void k_repair_band(const float* __restrict__ X, int ld, int d, int64_t n,
+                              const float* __restrict__ d32, float rel, int cap,
+                              int32_t* __restrict__ ids, double* __restrict__ dv,
+                              RepairState* __restrict__ s) {
+  const int64_t u = (int64_t)s->u;
+  if (u >= n) return;
+  const float hi = __uint_as_float(s->hi_bits);
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const float e = d32[v];
+    if (e >= 0.f && e * (1.f - 2.f * rel) <= hi) {
+      const double x = dist2_f64(X + v * ld, X + u * ld, d);
+      const int p = atomicAdd(&s->band, 1);
+      if (p < cap) {
+        ids[p] = (int32_t)v;
+        dv[p] = x;
+      }
+    }
+  }
+}
+
+// Pass 3 (one block): the (d2, id)-smallest entry of the list; link it to u and make u the
+// frontier of the next traversal.
+__global__ void k_repair_pick(const int32_t* __restrict__ ids, const double* __restrict__ dv,
+                              int cap, int32_t* __restrict__ adj, int32_t* __restrict__ deg, int R,
+                              uint32_t* __restrict__ bm, int32_t* __restrict__ frontier,
+                              int64_t n, RepairState* __restrict__ s) {
+  __shared__ double bd[32];
+  __shared__ int bi[32];
+  const int64_t u = (int64_t)s->u;
+  if (u >= n) return;
+  const int m = s->band;
+  if (m > cap) {
+    if (threadIdx.x == 0) s->best = -2;
+    return;
+  }
+  double best = __longlong_as_double(0x7ff0000000000000ll);
+  int bid = INT_MAX;
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    const double x = dv[t];
+    const int v = ids[t];
+    if (x < best || (x == best && v < bid)) {
+      best = x;
+      bid = v;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bid, o);
+    if (ob < best || (ob == best && oi < bid)) {
+      best = ob;
+      bid = oi;
+    }
+  }
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  if (lane == 0) {
+    bd[w] = best;
+    bi[w] = bid;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 1; t < (int)(blockDim.x >> 5); ++t)
+      if (bd[t] < best || (bd[t] == best && bi[t] < bid)) {
+        best = bd[t];
+        bid = bi[t];
+      }
+    s->best = bid;
+    if (bid != INT_MAX) {
+      adj[(int64_t)bid * R + deg[bid]] = (int32_t)u;
+      deg[bid] += 1;
+      atomicOr(bm + (u >> 5), 1u << (u & 31));
+      frontier[0] = (int32_t)u;
+      s->fcnt[0] = 1;
+    }
+  }
+}
+
+// Link v = *best (exhaustive path) and make u the next frontier.
+__global__ void k_add_edge(int32_t* __restrict__ adj, int32_t* __restrict__ deg, int R,
+                           const int* __restrict__ best_id, uint32_t* __restrict__ bm,
+                           int32_t* __restrict__ frontier, RepairState* __restrict__ s) {
+  const int v = *best_id;
+  s->best = v;
+  if (v == INT_MAX) return;
+  const int64_t u = (int64_t)s->u;
+  adj[(int64_t)v * R + deg[v]] = (int32_t)u;
+  deg[v] += 1;
+  atomicOr(bm + (u >> 5), 1u << (u & 31));
+  frontier[0] = (int32_t)u;
+  s->fcnt[0] = 1;
+}
+
+// Traversal by one block while the frontier stays small (no host round trip per level);
+// leaves bfs_state = -1 when done, or the index of the frontier buffer still to expand.
+__global__ void k_bfs_small(const int32_t* __restrict__ adj, const int32_t* __restrict__ deg, int R,
+                            uint32_t* __restrict__ bm, int32_t* __restrict__ f0,
+                            int32_t* __restrict__ f1, int limit, RepairState* __restrict__ s) {
+  const int lane = lane_id();
+  const int nwarps = blockDim.x >> 5;
   int cur = 0;
   for (;;) {
-    SSG_CUDA(cudaMemsetAsync(b.cnt + (cur ^ 1), 0, sizeof(int), st));
-    SSG_LAUNCH(k_bfs_level, grid, 256, 0, st, adj, deg, R, bm, b.f[cur], b.cnt + cur,
-               b.f[cur ^ 1], b.cnt + (cur ^ 1));
+    __syncthreads();
+    const int fc = s->fcnt[cur];
+    if (fc == 0 || fc > limit) {
+      if (threadIdx.x == 0) s->bfs_state = fc == 0 ? -1 : cur;
+      return;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s->fcnt[cur ^ 1] = 0;
+    __syncthreads();
+    const int32_t* fr = cur ? f1 : f0;
+    int32_t* nx = cur ? f0 : f1;
+    for (int w = threadIdx.x >> 5; w < fc; w += nwarps) {
+      const int32_t node = fr[w];
+      const int dg = deg[node];
+      for (int c = 0; c < dg; c += 32) {
+        const int t = c + lane;
+        bool fresh = false;
+        int32_t v = 0;
+        if (t < dg) {
+          v = adj[(int64_t)node * R + t];
+          const uint32_t bit = 1u << (v & 31);
+          fresh = !(atomicOr(bm + (v >> 5), bit) & bit);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+        int basep = 0;
+        if (lane == 0 && bal) basep = atomicAdd(&s->fcnt[cur ^ 1], __popc(bal));
+        basep = __shfl_sync(0xffffffffu, basep, 0);
+        if (fresh) nx[basep + __popc(bal & lanemask_lt())] = v;
+      }
+    }
+    cur ^= 1;
+  }
+}
+
+// Level-synchronous traversal by the whole grid, starting from frontier buffer `cur`.
+static void bfs_levels(const int32_t* adj, const int32_t* deg, int R, uint32_t* bm, int32_t* f[2],
+                       RepairState* s, int cur, cudaStream_t st) {
+  const int grid = 4 * num_sms();
+  for (;;) {
+    SSG_CUDA(cudaMemsetAsync(&s->fcnt[cur ^ 1], 0, sizeof(int), st));
+    SSG_LAUNCH(k_bfs_level, grid, 256, 0, st, adj, deg, R, bm, f[cur], &s->fcnt[cur], f[cur ^ 1],
+               &s->fcnt[cur ^ 1]);
     int h = 0;
-    SSG_CUDA(cudaMemcpyAsync(&h, b.cnt + (cur ^ 1), sizeof(int), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaMemcpyAsync(&h, &s->fcnt[cur ^ 1], sizeof(int), cudaMemcpyDeviceToHost, st));
     SSG_CUDA(cudaStreamSynchronize(st));
     cur ^= 1;
     if (h == 0) break;
@@ -134,42 +296,64 @@ int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int3
                     cudaStream_t st) {
   (void)nav_dev;
   const int64_t nw = ceil_div(n, 32);
+  const int cap = 1 << 16;
   Scratch<uint32_t> bm((size_t)nw, st);
-  Scratch<int32_t> f0((size_t)n, st), f1((size_t)n, st);
-  Scratch<int> cnt(4, st);
-  Scratch<unsigned long long> ull(2, st);
-  Scratch<double> dv((size_t)n, st);
-  Bfs b{{f0.p, f1.p}, cnt.p};
+  Scratch<int32_t> f0((size_t)n, st), f1((size_t)n, st), band_ids((size_t)cap, st);
+  Scratch<double> band_d((size_t)cap, st);
+  Scratch<float> d32((size_t)n, st);
+  Scratch<RepairState> state(1, st);
+  Scratch<unsigned long long> ull(1, st);
+  Scratch<double> dv;
+  int32_t* f[2] = {f0.p, f1.p};
+  RepairState* S = state.p;
   const int grid = 8 * num_sms();
+  const float rel = dist_rel_fp32(d);
+  const int small_limit = 4096;
   int64_t repairs = 0;
-  for (int s = 0; s < n_nav; ++s) {
+  for (int r = 0; r < n_nav; ++r) {
     SSG_CUDA(cudaMemsetAsync(bm.p, 0, sizeof(uint32_t) * nw, st));
-    SSG_LAUNCH(k_mark, 1, 1, 0, st, bm.p, b.f[0], b.cnt, nav_host[s]);
-    bfs_run(adj, deg, R, bm.p, b, st);
+    SSG_LAUNCH(k_mark, 1, 1, 0, st, bm.p, f[0], &S->fcnt[0], nav_host[r]);
     int64_t start = 0;
+    bool first = true;
     for (;;) {
-      const unsigned long long init[2] = {(unsigned long long)n, ~0ull};
-      SSG_CUDA(cudaMemcpyAsync(ull.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
-      SSG_LAUNCH(k_first_unreached, grid, 256, 0, st, bm.p, nw, n, start, ull.p);
-      unsigned long long u = 0;
-      SSG_CUDA(cudaMemcpyAsync(&u, ull.p, sizeof(u), cudaMemcpyDeviceToHost, st));
+      if (!first) {
+        SSG_LAUNCH(k_repair_init, 1, 1, 0, st, S, n);
+        SSG_LAUNCH(k_first_unreached, grid, 256, 0, st, bm.p, nw, n, start, &S->u);
+        SSG_LAUNCH(k_repair_fp32, grid, 256, 0, st, X, ld, n, bm.p, deg, R, rel, d32.p, S);
+        SSG_LAUNCH(k_repair_band, grid, 256, 0, st, X, ld, d, n, d32.p, rel, cap, band_ids.p,
+                   band_d.p, S);
+        SSG_LAUNCH(k_repair_pick, 1, 256, 0, st, band_ids.p, band_d.p, cap, adj, deg, R, bm.p, f[0],
+                   n, S);
+      }
+      SSG_LAUNCH(k_bfs_small, 1, 1024, 0, st, adj, deg, R, bm.p, f[0], f[1], small_limit, S);
+      RepairState h;
+      SSG_CUDA(cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st));
       SSG_CUDA(cudaStreamSynchronize(st));
-      if ((int64_t)u >= n) break;
-      start = (int64_t)u >> 5;
-      const int imax = INT_MAX;
-      SSG_CUDA(cudaMemcpyAsync(cnt.p + 2, &imax, sizeof(int), cudaMemcpyHostToDevice, st));
-      SSG_LAUNCH(k_repair_dist, grid, 256, 0, st, X, ld, d, n, bm.p, deg, R, (int64_t)u, dv.p,
-                 ull.p + 1);
-      SSG_LAUNCH(k_repair_pick, grid, 256, 0, st, dv.p, n, ull.p + 1, cnt.p + 2);
-      int best = 0;
-      SSG_CUDA(cudaMemcpyAsync(&best, cnt.p + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
-      SSG_CUDA(cudaStreamSynchronize(st));
-      SSG_REQUIRE(best != INT_MAX, SSG_EINTERNAL,
-                  "connectivity: node %lld is unreached and no reached node has a free slot",
-                  (long long)u);
-      SSG_LAUNCH(k_add_edge, 1, 1, 0, st, adj, deg, R, cnt.p + 2, (int32_t)u, bm.p, b.f[0], b.cnt);
-      bfs_run(adj, deg, R, bm.p, b, st);
-      ++repairs;
+      if (!first) {
+        if ((int64_t)h.u >= n) break;
+        if (h.best == -2) {
+          // the band list overflowed (many exact ties): exhaustive fp64 argmin instead
+          if (!dv.p) dv.alloc((size_t)n, st);
+          const unsigned long long init = ~0ull;
+          const int imax = INT_MAX;
+          SSG_CUDA(cudaMemcpyAsync(ull.p, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+          SSG_CUDA(cudaMemcpyAsync(&S->best, &imax, sizeof(int), cudaMemcpyHostToDevice, st));
+          SSG_LAUNCH(k_repair_dist, grid, 256, 0, st, X, ld, d, n, bm.p, deg, R, (int64_t)h.u,
+                     dv.p, ull.p);
+          SSG_LAUNCH(k_repair_pick_all, grid, 256, 0, st, dv.p, n, ull.p, &S->best);
+          SSG_LAUNCH(k_add_edge, 1, 1, 0, st, adj, deg, R, &S->best, bm.p, f[0], S);
+          SSG_LAUNCH(k_bfs_small, 1, 1024, 0, st, adj, deg, R, bm.p, f[0], f[1], small_limit, S);
+          SSG_CUDA(cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st));
+          SSG_CUDA(cudaStreamSynchronize(st));
+        }
+        SSG_REQUIRE(h.best != INT_MAX, SSG_EINTERNAL,
+                    "connectivity: node %lld is unreached and no reached node has a free slot",
+                    (long long)h.u);
+        start = (int64_t)h.u >> 5;
+        ++repairs;
+      }
+      if (h.bfs_state >= 0) bfs_levels(adj, deg, R, bm.p, f, S, h.bfs_state, st);
+      first = false;
     }
   }
   return repairs;

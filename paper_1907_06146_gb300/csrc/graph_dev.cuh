@@ -99,10 +99,12 @@ __device__ __forceinline__ int warp_fix_runs(uint64_t* keys, int m, int limit, d
 // SSG prune of one node by one warp (Alg. 2 selection): cand[0, len) in (d2, id) order.
 // Keeps cand[0]; keeps each later candidate unless its angle to a kept edge has
 // cos > cos(alpha); stops at R kept.  The cosine comes from the centred dot products of
-// the fp32 differences c - x_i held in shared memory (V: one row of D1 >= d floats per
-// kept edge plus one tentative row, D1 odd so that lanes reading different rows hit
-// different banks).  A decision within `margin` of cos(alpha), or with a zero-length
-// edge, is re-taken in fp64 from the original vectors.
+// the fp32 differences c - x_i held in shared memory (V: one row of D1 floats per kept
+// edge plus one tentative row; D1 is a multiple of 4 with D1 % 32 == 4, so that the
+// float4 reads of 8 lanes from 8 different rows fall in 8 different 16-byte bank groups).
+// A decision within `margin` of cos(alpha), or with a zero-length edge, is re-taken in
+// fp64 from the original vectors.  Rows are read up to d rounded to 4 (the padding of X
+// is zero).
 // Writes the kept ids to out[0, kept) (lane 0) and returns kept; *n64 += fp64 re-tests.
 __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int ld, int d,
                                                int64_t i, const int32_t* cand, int len, int R,
@@ -111,7 +113,8 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
                                                int32_t* out, unsigned long long* n64) {
   const int lane = lane_id();
   const float* xg = X + i * ld;
-  for (int t = lane; t < d; t += 32) xs[t] = xg[t];
+  const int d4 = (d + 3) & ~3;
+  for (int t = lane; t < d4; t += 32) xs[t] = xg[t];
   __syncwarp();
   int kept = 0;
   unsigned long long fp64_tests = 0;
@@ -120,7 +123,7 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
     const float* cj = X + (int64_t)j * ld;
     float* slot = V + kept * D1;
     float part = 0.f;
-    for (int dd = lane; dd < d; dd += 32) {
+    for (int dd = lane; dd < d4; dd += 32) {
       float v = cj[dd] - xs[dd];
       slot[dd] = v;
       part = fmaf(v, v, part);
@@ -130,9 +133,16 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
     bool definite = false;
     unsigned border = 0;
     for (int k = lane, r = 0; k < kept; k += 32, ++r) {
-      const float* vk = V + k * D1;
+      const float4* vk = (const float4*)(V + k * D1);
+      const float4* sl = (const float4*)slot;
       float g = 0.f;
-      for (int dd = 0; dd < d; ++dd) g = fmaf(slot[dd], vk[dd], g);
+      for (int q = 0; q < (d4 >> 2); ++q) {
+        const float4 a = sl[q], b = vk[q];
+        g = fmaf(a.x, b.x, g);
+        g = fmaf(a.y, b.y, g);
+        g = fmaf(a.z, b.z, g);
+        g = fmaf(a.w, b.w, g);
+      }
       const float gk = gkk[k];
       if (gjj == 0.f || gk == 0.f) {
         border |= 1u << r;
@@ -173,10 +183,14 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
 }
 
 // Shared-memory layout of warp_prune_node for one warp, in floats.
-__host__ __device__ inline int prune_row_stride(int d) { return (d & 1) ? d : d + 1; }
+__host__ __device__ inline int prune_row_stride(int d) {
+  int D1 = (d + 3) & ~3;
+  while ((D1 & 31) != 4) D1 += 4;
+  return D1;
+}
 __host__ __device__ inline size_t prune_smem_floats(int d, int R) {
   const int D1 = prune_row_stride(d);
-  return (size_t)(R + 1) * D1 + (size_t)D1 + (size_t)R + 1;
+  return (((size_t)(R + 1) * D1 + (size_t)D1 + (size_t)R + 1) + 3) & ~(size_t)3;
 }
 
 }  // namespace ssg

@@ -12,11 +12,10 @@ same shapes, sizes and value ranges:
                     (centres ~ N(0, 4I), unit spread); 1,000 queries.  Sized
                     like the SIFT10K pre-experiment of Sec. 4.1.
 * ``sift_like``  -- 1,000,000 x 128 float32 holding integers 0..255: 1,000
-                    anisotropic Gaussians (per-cluster random orthonormal basis,
-                    log-uniform per-axis spread 2..30, centre coordinates
-                    N(mu, 40^2)), rounded and clipped, with mu bisected so that
-                    about 30% of all coordinates are zero; 10,000 queries.
-                    Shaped like SIFT1M (Table 2).
+                    overlapping anisotropic Gaussians in a shared basis (power-law
+                    spectrum, local intrinsic dimension about 13), rounded and
+                    clipped, shifted so that about 30% of all coordinates are zero;
+                    10,000 queries.  Shaped like SIFT1M (Table 2: d = 128, LID 12.9).
 * ``gist_like``  -- 1,000,000 x 960 float32 in [0, 1]: 500 Gaussians passed
                     through a softplus and divided by the global maximum;
                     1,000 queries.  Shaped like GIST1M (Table 2).
@@ -86,37 +85,42 @@ def _random_orthonormal(rng: np.random.Generator, d: int) -> np.ndarray:
 
 
 def sift_like(n: int = 1_000_000, d: int = 128, nq: int = 10_000, n_clusters: int = 1_000,
-              zero_frac: float = 0.30, seed: int = SEED_SIFT) -> Workload:
-    """Integer-valued (0..255) anisotropic Gaussian mixture with ~30% zeros."""
+              zero_frac: float = 0.30, seed: int = SEED_SIFT, gamma: float = 1.0,
+              top: float = 70.0, jitter: float = 0.3, chunk: int = 131_072) -> Workload:
+    """Integer-valued (0..255) mixture of anisotropic Gaussians with ~30% zeros.
+
+    All clusters share one random orthonormal basis Q.  Along its k-th axis the cluster
+    centres spread with standard deviation top * k^-gamma and each cluster's own spread is
+    top * k^-gamma times a per-cluster log-normal factor (sigma = jitter), so the clusters
+    overlap into one continuous, anisotropic cloud whose local intrinsic dimension is
+    about 13 for the defaults (SIFT1M: 12.9, Table 2).  A common shift is bisected so that
+    the rounded, clipped data hold the requested fraction of zeros."""
     rng = _rng(seed)
-    n_clusters = min(n_clusters, max(1, (n + nq) // 8))
-    offsets = rng.normal(0.0, 40.0, size=(n_clusters, d))
-    spreads = np.exp(rng.uniform(np.log(2.0), np.log(30.0), size=(n_clusters, d)))
+    Q = _random_orthonormal(rng, d)
+    k = np.arange(1, d + 1, dtype=np.float64)
+    spec = top * k ** (-gamma)
+    centres = (rng.normal(size=(n_clusters, d)) * spec) @ Q.T
+    spreads = spec * np.exp(rng.normal(0.0, jitter, size=(n_clusters, d)))
     lab = rng.integers(0, n_clusters, size=n + nq)
-    z = rng.normal(size=(n + nq, d))
-    y = np.empty((n + nq, d), dtype=np.float64)
-    order = np.argsort(lab, kind="stable")
-    bounds = np.searchsorted(lab[order], np.arange(n_clusters + 1))
-    for c in range(n_clusters):
-        basis = _random_orthonormal(rng, d)
-        idx = order[bounds[c]:bounds[c + 1]]
-        y[idx] = offsets[c] + (z[idx] * spreads[c]) @ basis.T
-    # Bisect the common shift mu so that the rounded, clipped data holds the requested
-    # fraction of zeros; evaluated on a fixed subsample of coordinates.
+    y = np.empty((n + nq, d), dtype=np.float32)
+    for s in range(0, n + nq, chunk):
+        e = min(n + nq, s + chunk)
+        w = rng.normal(size=(e - s, d)) * spreads[lab[s:e]]
+        y[s:e] = centres[lab[s:e]] + w @ Q.T
     flat = y.reshape(-1)
-    sub = flat[rng.integers(0, flat.size, size=min(flat.size, 2_000_000))]
-    lo, hi = -200.0, 400.0
+    sub = flat[rng.integers(0, flat.size, size=min(flat.size, 2_000_000))].astype(np.float64)
+    lo, hi = -1000.0, 1000.0
     for _ in range(60):
         mu = 0.5 * (lo + hi)
-        frac = np.mean(np.rint(sub + mu) <= 0.0)
-        if frac > zero_frac:
+        if np.mean(np.rint(sub + mu) <= 0.0) > zero_frac:
             lo = mu
         else:
             hi = mu
     mu = 0.5 * (lo + hi)
-    x = np.clip(np.rint(y + mu), 0.0, 255.0).astype(np.float32)
-    perm = rng.permutation(n + nq)
-    x = x[perm]
+    for s in range(0, n + nq, chunk):
+        e = min(n + nq, s + chunk)
+        y[s:e] = np.clip(np.rint(y[s:e].astype(np.float64) + mu), 0.0, 255.0)
+    x = y[rng.permutation(n + nq)]
     base = np.ascontiguousarray(x[:n])
     queries = np.ascontiguousarray(x[n:])
     return Workload("sift_like", base, queries, K=200, L=100, R=50, alpha=60.0, n_nav=10,
