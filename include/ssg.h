@@ -141,6 +141,27 @@ ssg_status ssg_connect(const float* base, int64_t n, int32_t d, int32_t* adj, in
                        int32_t R, const int32_t* nav, int32_t n_nav, int64_t* n_repair_host,
                        ssg_stream stream);
 
+/* ssg_connect for callers that cannot allocate device memory while they run: code that
+ * records a CUDA graph (cudaMalloc is not allowed during stream capture), serving loops
+ * whose device memory is fixed before requests arrive, or hosts that forbid allocations
+ * outside their own allocator.  The paper has no counterpart; this is a deployment
+ * variant of the connectivity step above, with the same arguments and the same result.
+ * Its scratch (reached-node bitmap, two frontier buffers, per-node fp32 distances, the
+ * list of fp64 re-tests) lives in one fixed array of about 12.3 MiB inside the library's
+ * device image, which every GPU that loads the library holds until the process exits.
+ * The call itself allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * Limits: 1 <= n <= 1,048,576 nodes; d % 4 == 0 and `base` 16-byte aligned (no padded
+ * copy is made); at most 16,384 candidate nodes may tie for the nearest reached node of
+ * one repair (EINTERNAL otherwise; ssg_connect has no such limit).  EINVAL beyond the
+ * size limits.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and each starts by clearing
+ * what must start at zero, so calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller. */
+ssg_status ssg_connect_noalloc(const float* base, int64_t n, int32_t d, int32_t* adj,
+                               int32_t* deg, int32_t R, const int32_t* nav, int32_t n_nav,
+                               int64_t* n_repair_host, ssg_stream stream);
+
 /* Search-on-Graph (Alg. 1) from the navigating node nearest each query (Sec. 4.1): a pool
  * of at most L_search entries sorted by (d2, id); expand the first unchecked entry, add
  * every neighbour not visited before, re-sort, cut to L_search; stop when all entries are

@@ -10,6 +10,7 @@
 // depth-first one and gets the same graph.  The argmin is taken in fp64 with the
 // coordinate-order sum, so its ties resolve exactly as a sequential double loop would.
 #include <climits>
+#include <mutex>
 
 #include "common.cuh"
 #include "graph_dev.cuh"
@@ -358,5 +359,139 @@ int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int3
   }
   return repairs;
 }
+
+// ---------------------------------------------------------------------------------------
+// Connectivity without device allocation (ssg_connect_noalloc).
+//
+// Some callers cannot allocate device memory while they run: code that records a CUDA
+// graph (a cudaMalloc during stream capture is an error), serving loops that fix all
+// their memory before they take requests, or hosts that own a custom allocator and
+// forbid the driver's.  For them the connectivity step also comes with its scratch in one
+// fixed array that is part of the library's device image: the bitmap of reached nodes,
+// two frontier buffers, the fp32 distance of every node and the short list of fp64
+// re-tests, for graphs of up to NOALLOC_MAX_N nodes.  The same kernels run as in
+// ssg_connect; only the scratch differs.
+// ---------------------------------------------------------------------------------------
+namespace {
+constexpr int64_t NOALLOC_MAX_N = 1 << 20;       // nodes
+constexpr int NOALLOC_BAND = 1 << 14;            // fp64 re-tests per repair
+constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t OFF_BM = 0;
+constexpr size_t OFF_F0 = al256(OFF_BM + (size_t)(NOALLOC_MAX_N / 32) * 4);
+constexpr size_t OFF_F1 = al256(OFF_F0 + (size_t)NOALLOC_MAX_N * 4);
+constexpr size_t OFF_D32 = al256(OFF_F1 + (size_t)NOALLOC_MAX_N * 4);
+constexpr size_t OFF_BAND_ID = al256(OFF_D32 + (size_t)NOALLOC_MAX_N * 4);
+constexpr size_t OFF_BAND_D = al256(OFF_BAND_ID + (size_t)NOALLOC_BAND * 4);
+constexpr size_t OFF_STATE = al256(OFF_BAND_D + (size_t)NOALLOC_BAND * 8);
+constexpr size_t NOALLOC_BYTES = al256(OFF_STATE + sizeof(RepairState));
+}  // namespace
+
+// Held by every GPU that loads the library, until the process exits (about 12.3 MiB).
+static __device__ __align__(256) unsigned char g_connect_scratch[NOALLOC_BYTES];
+
+// Device address of g_connect_scratch on the current device, looked up once per device
+// (host code cannot use the array's name as a device address).
+static unsigned char* noalloc_scratch() {
+  static std::mutex mu;
+  static unsigned char* addr[64] = {};
+  int dev = 0;
+  SSG_CUDA(cudaGetDevice(&dev));
+  SSG_REQUIRE(dev >= 0 && dev < 64, SSG_EINTERNAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    SSG_CUDA(cudaGetSymbolAddress(&p, g_connect_scratch));
+    addr[dev] = (unsigned char*)p;
+  }
+  return addr[dev];
+}
+
+static int64_t connect_run_noalloc(const float* X, int ld, int d, int64_t n, int32_t* adj,
+                                   int32_t* deg, int R, const int32_t* nav_dev, int n_nav,
+                                   cudaStream_t st) {
+  unsigned char* base = noalloc_scratch();
+  uint32_t* bm = (uint32_t*)(base + OFF_BM);
+  int32_t* f[2] = {(int32_t*)(base + OFF_F0), (int32_t*)(base + OFF_F1)};
+  float* d32 = (float*)(base + OFF_D32);
+  int32_t* band_ids = (int32_t*)(base + OFF_BAND_ID);
+  double* band_d = (double*)(base + OFF_BAND_D);
+  RepairState* S = (RepairState*)(base + OFF_STATE);
+  const int64_t nw = ceil_div(n, 32);
+  const int grid = 8 * num_sms();
+  const float rel = dist_rel_fp32(d);
+  const int small_limit = 4096;
+  int64_t repairs = 0;
+  for (int r = 0; r < n_nav; ++r) {
+    int32_t root = 0;
+    SSG_CUDA(cudaMemcpyAsync(&root, nav_dev + r, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    SSG_REQUIRE(root >= 0 && root < n, SSG_EINVAL, "navigating node id %d out of range", root);
+    SSG_CUDA(cudaMemsetAsync(bm, 0, sizeof(uint32_t) * nw, st));
+    SSG_LAUNCH(k_mark, 1, 1, 0, st, bm, f[0], &S->fcnt[0], root);
+    int64_t start = 0;
+    bool first = true;
+    for (;;) {
+      if (!first) {
+        SSG_LAUNCH(k_repair_init, 1, 1, 0, st, S, n);
+        SSG_LAUNCH(k_first_unreached, grid, 256, 0, st, bm, nw, n, start, &S->u);
+        SSG_LAUNCH(k_repair_fp32, grid, 256, 0, st, X, ld, n, bm, deg, R, rel, d32, S);
+        SSG_LAUNCH(k_repair_band, grid, 256, 0, st, X, ld, d, n, d32, rel, NOALLOC_BAND, band_ids,
+                   band_d, S);
+        SSG_LAUNCH(k_repair_pick, 1, 256, 0, st, band_ids, band_d, NOALLOC_BAND, adj, deg, R, bm,
+                   f[0], n, S);
+      }
+      SSG_LAUNCH(k_bfs_small, 1, 1024, 0, st, adj, deg, R, bm, f[0], f[1], small_limit, S);
+      RepairState h;
+      SSG_CUDA(cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st));
+      SSG_CUDA(cudaStreamSynchronize(st));
+      if (!first) {
+        if ((int64_t)h.u >= n) break;
+        SSG_REQUIRE(h.best != -2, SSG_EINTERNAL,
+                    "connectivity without allocation: more than %d nodes tie for the nearest "
+                    "reached node of node %lld; use ssg_connect",
+                    NOALLOC_BAND, (long long)h.u);
+        SSG_REQUIRE(h.best != INT_MAX, SSG_EINTERNAL,
+                    "connectivity: node %lld is unreached and no reached node has a free slot",
+                    (long long)h.u);
+        start = (int64_t)h.u >> 5;
+        ++repairs;
+      }
+      if (h.bfs_state >= 0) bfs_levels(adj, deg, R, bm, f, S, h.bfs_state, st);
+      first = false;
+    }
+  }
+  return repairs;
+}
+
+}  // namespace ssg
+
+extern "C" ssg_status ssg_connect_noalloc(const float* base, int64_t n, int32_t d, int32_t* adj,
+                                          int32_t* deg, int32_t R, const int32_t* nav,
+                                          int32_t n_nav, int64_t* n_repair_host,
+                                          ssg_stream stream) {
+  using namespace ssg;
+  try {
+    SSG_REQUIRE(base && adj && deg && nav, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(n >= 1 && n <= NOALLOC_MAX_N, SSG_EINVAL,
+                "connectivity without allocation handles 1 <= n <= %lld nodes, got %lld",
+                (long long)NOALLOC_MAX_N, (long long)n);
+    SSG_REQUIRE(d >= 1 && d % 4 == 0 && ((uintptr_t)base & 15) == 0, SSG_EINVAL,
+                "connectivity without allocation needs d %% 4 == 0 and a 16-byte aligned base "
+                "(no padded copy is made), got d = %d",
+                d);
+    SSG_REQUIRE(R >= 1 && n_nav >= 1, SSG_EINVAL, "need R >= 1 and n_nav >= 1");
+    const int64_t rep = connect_run_noalloc(base, d, d, n, adj, deg, R, nav, n_nav,
+                                            (cudaStream_t)stream);
+    if (n_repair_host) *n_repair_host = rep;
+    return SSG_OK;
+  } catch (const Fail& e) {
+    return e.st;
+  } catch (...) {
+    set_error("unexpected exception");
+    return SSG_EINTERNAL;
+  }
+}
+
+namespace ssg {
 
 }  // namespace ssg
