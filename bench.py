@@ -232,6 +232,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(ssg, g, base, w, seconds: float, rate: float, seed: int = 190706145):
+    """Open-loop Poisson stream of requests against a continuous-batching server: batch
+    sizes log-uniform in [1, 4096], k in {1, 10, 100}, L_search uniform in [k, 512].
+    Returns latency percentiles, throughput and recall@10 of the requests with k >= 10."""
+    import threading
+    import time as _t
+
+    rng = np.random.default_rng(seed)
+    srv = ssg.Server(g, base, n_streams=4, max_batch=8192, mem_budget_bytes=256 << 20)
+    nq_all = w.queries.shape[0]
+    reqs = []
+    t = 0.0
+    while t < seconds:
+        t += rng.exponential(1.0 / rate)
+        nq = int(np.exp(rng.uniform(0.0, np.log(4096.0))))
+        k = int(rng.choice([1, 10, 100]))
+        ls = int(rng.integers(k, 513))
+        rows = rng.integers(0, nq_all, size=nq)
+        reqs.append((t, rows, k, ls))
+    tickets = [None] * len(reqs)
+    results = [None] * len(reqs)
+    done = threading.Event()
+
+    def waiter():
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                _t.sleep(0.0002)
+            results[i] = srv.wait(tickets[i])
+        done.set()
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = _t.perf_counter()
+    for i, (ta, rows, k, ls) in enumerate(reqs):
+        now = _t.perf_counter() - t0
+        if ta > now:
+            _t.sleep(ta - now)
+        tickets[i] = srv.submit(w.queries[rows], k, ls)
+    done.wait()
+    wall = _t.perf_counter() - t0
+    th.join()
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r[2] for r in results])
+    total_q = int(sum(len(r[1]) for r in reqs))
+    # recall@10 of the k >= 10 requests, first 10 ids against brute force
+    import torch
+    sel = [i for i, r in enumerate(reqs) if r[2] >= 10]
+    rows = np.concatenate([reqs[i][1] for i in sel])
+    found = np.concatenate([results[i][0][:, :10] for i in sel])
+    truth, _ = ssg.knn_query(base, torch.from_numpy(w.queries[rows]).cuda(), 10)
+    hits = ssg.recall_hits(torch.from_numpy(np.ascontiguousarray(found)).cuda(), truth, 10)
+    return {"requests": len(reqs), "queries": total_q, "offered_rate_req_s": rate,
+            "seconds": wall, "qps": total_q / wall, "latency_ms_p50": float(np.percentile(lat, 50)),
+            "latency_ms_p99": float(np.percentile(lat, 99)),
+            "recall@10_k>=10": hits / (10.0 * len(rows)), "batches": st["batches"],
+            "max_batches_in_flight": st["max_batches_in_flight"],
+            "max_queries_in_flight": st["max_queries_in_flight"],
+            "mix": "Poisson arrivals; batch 1..4096 log-uniform; k in {1,10,100}; "
+                   "L_search uniform in [k, 512]"}
+
+
 # ---------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------
@@ -279,6 +341,10 @@ def run_gpu(args):
         if r >= args.target_recall:
             ls_used, rec_used = ls, r
             break
+    # the search's work at that L_search (untimed): algorithmic bytes per query
+    _, _, work = ssg.search_work(base, g.adj, g.deg, g.nav, queries, 10, ls_used)
+    search_bytes = (work["adjacency_entries"] * 4 + work["expansions"] * 4
+                    + work["distances"] * w.d * 4 + nq * w.d * 4)
     del g
 
     for _ in range(args.warmup):
@@ -326,6 +392,12 @@ def run_gpu(args):
             e2e_ms.append((t1 - t0) * 1000.0)
     e2e_value, _ = aggregate(e2e_ms, w.n, ws)
 
+    serving = None
+    if rank == 0 and args.serve_seconds > 0:
+        g_srv = ssg.build(base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec)
+        serving = run_serving(ssg, g_srv, base, w, args.serve_seconds, args.serve_rate)
+        del g_srv
+
     # roofline of the dominant kernel: the distance GEMM + top-K selection
     peaks = load_peaks()
     gemm_ms = float(np.mean([s["ms_knn_gemm"] for s in stats]))
@@ -366,11 +438,20 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (base 512 MB)", "gemm_prec": args.prec,
                    "parallelism": f"replicas x{ws}"},
         "search": {"qps": qps, "recall@10": float(np.mean(recalls)), "L_search": ls_used,
-                   "k": 10, "ms": float(np.mean(search_ms)), "sweep": sweep},
+                   "k": 10, "ms": float(np.mean(search_ms)), "sweep": sweep,
+                   "work_per_query": {k2: v / nq for k2, v in work.items()},
+                   "roofline": {"bound": "hbm", "achieved": search_bytes / (np.mean(search_ms) / 1e3) / 1e9,
+                                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                "frac": search_bytes / (np.mean(search_ms) / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                "traffic": None, "kernel": "k_search",
+                                "algorithmic": "per query: 4 B per adjacency entry read and per "
+                                               "expansion (degree), d x 4 B per distance, d x 4 B "
+                                               "query"}},
         "stages_ms": {k: float(np.mean([s[k] for s in stats])) for k in
                       ("ms_ingest", "ms_knn", "ms_knn_gemm", "ms_pool", "ms_prune", "ms_reverse",
                        "ms_connect", "ms_total")},
         "ground_truth_ms": float(np.mean(gt_ms)),
+        "serving": serving,
         "counters": {k: st0[k] for k in ("n_repair", "n_angle_fp64", "n_order_fp64",
                                          "n_knn_fallback_rows", "max_indegree", "exact_mode")},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -398,6 +479,9 @@ def main():
     ap.add_argument("--target-recall", type=float, default=0.95)
     ap.add_argument("--ref-nodes", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="length of the serving run (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="requests per second offered")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -118,7 +118,8 @@ ssg_status ssg_pool(const float* base, int64_t n, int32_t d, const int32_t* knn_
  * keep each later one unless cos(angle j-i-k) > cos(alpha) for a kept k (cos from the
  * centred dot products, 0 for a zero-length edge); stop once R are kept.
  * pool_id [n][L] sorted as ssg_pool leaves it; adj int32 [n][R], deg int32 [n].
- * EINVAL if R < 1, R > 128, alpha outside (0, 180) or R * (d + 1) * 4 > 96 KiB. */
+ * EINVAL if R < 1, R > 128, d > 8192 or alpha outside (0, 180).  Rows too long for R + 1
+ * of them to fit in shared memory keep the kept vectors in device scratch instead. */
 ssg_status ssg_prune(const float* base, int64_t n, int32_t d, const int32_t* pool_id,
                      const int32_t* pool_len, int32_t L, int32_t R, double alpha_deg,
                      int32_t* adj, int32_t* deg, ssg_stream stream);
@@ -172,6 +173,16 @@ ssg_status ssg_search_adj(const float* base, int64_t n, int32_t d, const int32_t
                           const float* queries, int64_t nq, int32_t k, int32_t L_search,
                           int32_t* out_ids, float* out_d2, ssg_stream stream);
 
+/* ssg_search_adj plus the work it did, summed over the batch into work_host[3]:
+ * expansions (pool entries checked), distance evaluations (navigating nodes included;
+ * a node met again after leaving the visited cache counts again) and adjacency entries
+ * read.  These give the search's algorithmic bytes.  Synchronises the stream. */
+ssg_status ssg_search_work(const float* base, int64_t n, int32_t d, const int32_t* adj,
+                           const int32_t* deg, int32_t R, const int32_t* nav, int32_t n_nav,
+                           const float* queries, int64_t nq, int32_t k, int32_t L_search,
+                           int32_t* out_ids, float* out_d2, int64_t* work_host,
+                           ssg_stream stream);
+
 /* Hits for precision(R) = |R n G| / |G| (Sec. 5.2): the number of (query, id) pairs where
  * id is among the first k of both found [nq][ld_found] and truth [nq][ld_truth].
  * *hits_host receives the count (the call synchronises the stream). */
@@ -212,6 +223,49 @@ ssg_status ssg_search(const ssg_graph* g, const float* base, const float* querie
 ssg_status ssg_search_host(const ssg_graph* g, const float* queries_host, int64_t nq, int32_t k,
                            int32_t L_search, int32_t* out_ids_host, float* out_d2_host,
                            ssg_stream stream);
+
+/* ---- serving: continuous batching of searches -------------------------------------------
+ * A server owns a scheduler thread and n_streams batch slots (CUDA streams with their own
+ * pinned and device buffers).  Requests (a block of queries with one k and one L_search)
+ * are submitted from any host thread and waited for by ticket.  Whenever a slot is free the
+ * scheduler admits waiting requests first come, first served, while the batch stays within
+ * max_batch queries and the device bytes of everything in flight (per query: the query row,
+ * two parameters, k ids and k distances) stay within mem_budget_bytes; it then copies the
+ * batch in, runs Alg. 1 for every query with its own k and L_search, and copies the results
+ * out on that slot's stream.  Batches on different slots overlap on the device; requests
+ * arriving meanwhile join the next free slot.  A query's result does not depend on the rest
+ * of its batch.  The graph and `base` must outlive the server. */
+typedef struct ssg_server ssg_server;
+typedef struct {
+  int32_t n_streams;        /* batch slots in flight (default 4) */
+  int32_t max_batch;        /* queries per batch (default 8192); larger requests: EINVAL */
+  int64_t mem_budget_bytes; /* device bytes of all queries in flight (default 256 MiB) */
+  int32_t max_k;            /* largest k of a request (default 128) */
+  int32_t max_L_search;     /* largest L_search of a request (default 1024) */
+} ssg_server_opts;
+typedef struct {
+  int64_t requests_done, queries_done, batches;
+  int64_t max_batches_in_flight;  /* most slots busy at once */
+  int64_t max_queries_in_flight;  /* most queries on the device at once */
+  double busy_ms;                 /* wall time with at least one batch in flight */
+} ssg_server_stats;
+
+void ssg_server_default_opts(ssg_server_opts* opts);
+/* `base` = the device array the graph was built from (NULL for a graph from
+ * ssg_build_host). */
+ssg_status ssg_server_create(const ssg_graph* g, const float* base, const ssg_server_opts* opts,
+                             ssg_server** out);
+/* Copies the nq x d host queries; returns at once with a ticket. */
+ssg_status ssg_server_submit(ssg_server* s, const float* queries_host, int64_t nq, int32_t k,
+                             int32_t L_search, uint64_t* ticket);
+ssg_status ssg_server_poll(ssg_server* s, uint64_t ticket, int32_t* done);
+/* Blocks until the request is done; writes ids [nq][k] (and d2, nullable) to host memory,
+ * the submit-to-done latency in ms (nullable), and forgets the ticket. */
+ssg_status ssg_server_wait(ssg_server* s, uint64_t ticket, int32_t* ids_host, float* d2_host,
+                           double* latency_ms);
+ssg_status ssg_server_get_stats(ssg_server* s, ssg_server_stats* out);
+/* Finishes every submitted request, then releases the server. */
+void ssg_server_destroy(ssg_server* s);
 
 /* Graph file: header (magic, version, n, d, R, n_nav, alpha) + nav + deg + adj. */
 ssg_status ssg_save(const ssg_graph* g, const char* path);

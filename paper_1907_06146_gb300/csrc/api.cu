@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "graph.cuh"
 #include "graph_dev.cuh"
 #include "knn.cuh"
 
@@ -74,8 +75,7 @@ static void check_alpha(double a) {
 }
 static void check_prune_fit(int d, int R) {
   SSG_REQUIRE(R >= 1 && R <= 128, SSG_EINVAL, "R must lie in [1, 128], got %d", R);
-  SSG_REQUIRE(prune_smem_floats(d, R) * 4 <= 96 * 1024, SSG_EINVAL,
-              "R * (d + 1) * 4 bytes must fit 96 KiB of shared memory (d=%d, R=%d)", d, R);
+  SSG_REQUIRE(d >= 1 && d <= 8192, SSG_EINVAL, "d must lie in [1, 8192], got %d", d);
 }
 
 struct Ingested {
@@ -93,23 +93,6 @@ static void ingest_all(const float* X, int64_t n, int d, cudaStream_t st, Ingest
 }  // namespace ssg
 
 using namespace ssg;
-
-struct ssg_graph {
-  int64_t n = 0;
-  int32_t d = 0, R = 0, n_nav = 0;
-  double alpha = 0;
-  int32_t* adj = nullptr;
-  int32_t* deg = nullptr;
-  int32_t* nav_dev = nullptr;
-  std::vector<int32_t> nav_host;
-  float* base_owned = nullptr;
-  ~ssg_graph() {
-    if (adj) cudaFree(adj);
-    if (deg) cudaFree(deg);
-    if (nav_dev) cudaFree(nav_dev);
-    if (base_owned) cudaFree(base_owned);
-  }
-};
 
 static const char* const kStatusNames[] = {"ok", "invalid argument", "out of device memory",
                                            "CUDA error", "device wait timed out",
@@ -165,9 +148,10 @@ ssg_status ssg_knn(const float* base, int64_t n, int32_t d, int32_t K, ssg_preci
     cudaStream_t st = (cudaStream_t)stream;
     Ingested g;
     ingest_all(base, n, d, st, g, true);
-    const bool tc = prec != SSG_PREC_FP32 && g.info.bf16_exact && knn_tc_available();
+    const bool tc = prec != SSG_PREC_FP32 && g.info.bf16_exact && knn_tc_available(d);
     SSG_REQUIRE(prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
-                "bf16 distance GEMM needs integer data with |x| <= 256 and 2 d max|x|^2 <= 2^24");
+                "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
+                "and 2 d max|x|^2 <= 2^24");
     if (tc)
       knn_exact_tc(g.rows.p, n, g.rows.ld, g.norms.p, g.rows.p, n, g.rows.ld, g.norms.p, d, 1, K,
                    knn_id, knn_d2, st, nullptr);
@@ -195,9 +179,10 @@ ssg_status ssg_knn_query(const float* base, int64_t n, int32_t d, const float* q
     info.bf16_exact = info.exact && ma <= 256.f;
     info.max_norm = gb.info.max_norm;
     info.max_abs = ma;
-    const bool tc = prec != SSG_PREC_FP32 && info.bf16_exact && knn_tc_available();
+    const bool tc = prec != SSG_PREC_FP32 && info.bf16_exact && knn_tc_available(d);
     SSG_REQUIRE(prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
-                "bf16 distance GEMM needs integer data with |x| <= 256 and 2 d max|x|^2 <= 2^24");
+                "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
+                "and 2 d max|x|^2 <= 2^24");
     if (tc)
       knn_exact_tc(gq.rows.p, nq, gq.rows.ld, gq.norms.p, gb.rows.p, n, gb.rows.ld, gb.norms.p, d,
                    0, k, ids, d2, st, nullptr);
@@ -291,22 +276,40 @@ ssg_status ssg_search_adj(const float* base, int64_t n, int32_t d, const int32_t
                 "need 1 <= k <= L_search <= 1024");
     if (nq == 0) return;
     cudaStream_t st = (cudaStream_t)stream;
-    Ingested gb;
-    ingest_all(base, n, d, st, gb, false);
-    PaddedRows q;
-    q.ld = (d + 3) & ~3;
-    if (q.ld == d && ((uintptr_t)queries & 15) == 0) {
-      q.p = queries;
-    } else {
-      Ingested gq;
-      ingest_all(queries, nq, d, st, gq, false);
-      q.own.alloc((size_t)nq * gq.rows.ld, st);
-      SSG_CUDA(cudaMemcpyAsync(q.own.p, gq.rows.p, sizeof(float) * nq * gq.rows.ld,
-                               cudaMemcpyDeviceToDevice, st));
-      q.p = q.own.p;
+    PaddedRows b, q;
+    pad_rows(base, n, d, st, b);
+    pad_rows(queries, nq, d, st, q);
+    search_run(b.p, b.ld, d, n, adj, deg, R, nav, n_nav, q.p, q.ld, nq, k, L_search, out_ids,
+               out_d2, st);
+  });
+}
+
+ssg_status ssg_search_work(const float* base, int64_t n, int32_t d, const int32_t* adj,
+                           const int32_t* deg, int32_t R, const int32_t* nav, int32_t n_nav,
+                           const float* queries, int64_t nq, int32_t k, int32_t L_search,
+                           int32_t* out_ids, float* out_d2, int64_t* work_host,
+                           ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(base && adj && deg && nav && queries && out_ids && work_host, SSG_EINVAL,
+                "null pointer");
+    SSG_REQUIRE(n >= 1 && d >= 1 && R >= 1 && R <= 128 && n_nav >= 1 && nq >= 0, SSG_EINVAL,
+                "bad sizes");
+    SSG_REQUIRE(k >= 1 && k <= L_search && L_search <= 1024, SSG_EINVAL,
+                "need 1 <= k <= L_search <= 1024");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch<unsigned long long> w(3, st);
+    SSG_CUDA(cudaMemsetAsync(w.p, 0, 3 * sizeof(unsigned long long), st));
+    if (nq > 0) {
+      PaddedRows b, q;
+      pad_rows(base, n, d, st, b);
+      pad_rows(queries, nq, d, st, q);
+      search_run(b.p, b.ld, d, n, adj, deg, R, nav, n_nav, q.p, q.ld, nq, k, L_search, out_ids,
+                 out_d2, st, w.p);
     }
-    search_run(gb.rows.p, gb.rows.ld, d, n, adj, deg, R, nav, n_nav, q.p, q.ld, nq, k, L_search,
-               out_ids, out_d2, st);
+    unsigned long long h[3];
+    SSG_CUDA(cudaMemcpyAsync(h, w.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    for (int t = 0; t < 3; ++t) work_host[t] = (int64_t)h[t];
   });
 }
 
@@ -389,9 +392,10 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     // a1: exact kNN graph
     Scratch<int32_t> knn_id((size_t)n * K, st);
     Scratch<float> knn_d2((size_t)n * K, st);
-    const bool tc = opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact && knn_tc_available();
+    const bool tc = opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact && knn_tc_available(d);
     SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
-                "bf16 distance GEMM needs integer data with |x| <= 256 and 2 d max|x|^2 <= 2^24");
+                "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
+                "and 2 d max|x|^2 <= 2^24");
     t_knn.start();
     KnnResult kr;
     if (tc)

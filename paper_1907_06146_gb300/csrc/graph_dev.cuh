@@ -96,15 +96,34 @@ __device__ __forceinline__ int warp_fix_runs(uint64_t* keys, int m, int limit, d
   return fixed;
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Candidate rows kept in flight by warp_prune_node (asynchronous copies into a ring).
+constexpr int PRUNE_PREFETCH = 4;
+
 // SSG prune of one node by one warp (Alg. 2 selection): cand[0, len) in (d2, id) order.
 // Keeps cand[0]; keeps each later candidate unless its angle to a kept edge has
 // cos > cos(alpha); stops at R kept.  The cosine comes from the centred dot products of
 // the fp32 differences c - x_i held in shared memory (V: one row of D1 floats per kept
 // edge plus one tentative row; D1 is a multiple of 4 with D1 % 32 == 4, so that the
 // float4 reads of 8 lanes from 8 different rows fall in 8 different 16-byte bank groups).
+// Candidate rows arrive through a ring of PRUNE_PREFETCH rows filled by cp.async ahead of
+// use, so the global-memory latency of one row overlaps the work on earlier ones.
 // A decision within `margin` of cos(alpha), or with a zero-length edge, is re-taken in
 // fp64 from the original vectors.  Rows are read up to d rounded to 4 (the padding of X
-// is zero).
+// is zero).  Shared memory per warp: prune_smem_floats(d, R) floats starting at V.
 // Writes the kept ids to out[0, kept) (lane 0) and returns kept; *n64 += fp64 re-tests.
 __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int ld, int d,
                                                int64_t i, const int32_t* cand, int len, int R,
@@ -114,35 +133,50 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
   const int lane = lane_id();
   const float* xg = X + i * ld;
   const int d4 = (d + 3) & ~3;
+  const int nq4 = d4 >> 2;
+  float* ring = gkk + ((R + 1 + 3) & ~3);
   for (int t = lane; t < d4; t += 32) xs[t] = xg[t];
+  auto prefetch = [&](int t) {
+    if (t < len) {
+      const float* src = X + (int64_t)cand[t] * ld;
+      float* dst = ring + (t % PRUNE_PREFETCH) * D1;
+      for (int f = lane; f < nq4; f += 32) cp_async16(dst + 4 * f, src + 4 * f);
+    }
+    cp_async_commit();
+  };
+  for (int t = 0; t < PRUNE_PREFETCH; ++t) prefetch(t);
   __syncwarp();
   int kept = 0;
   unsigned long long fp64_tests = 0;
   for (int t = 0; t < len && kept < R; ++t) {
     const int32_t j = cand[t];
-    const float* cj = X + (int64_t)j * ld;
+    cp_async_wait<PRUNE_PREFETCH - 1>();
+    __syncwarp();
+    const float* cs = ring + (t % PRUNE_PREFETCH) * D1;
     float* slot = V + kept * D1;
     float part = 0.f;
     for (int dd = lane; dd < d4; dd += 32) {
-      float v = cj[dd] - xs[dd];
+      float v = cs[dd] - xs[dd];
       slot[dd] = v;
       part = fmaf(v, v, part);
     }
     const float gjj = warp_sum(part);
     __syncwarp();
+    prefetch(t + PRUNE_PREFETCH);
     bool definite = false;
     unsigned border = 0;
     for (int k = lane, r = 0; k < kept; k += 32, ++r) {
       const float4* vk = (const float4*)(V + k * D1);
       const float4* sl = (const float4*)slot;
-      float g = 0.f;
-      for (int q = 0; q < (d4 >> 2); ++q) {
+      float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+      for (int q = 0; q < nq4; ++q) {
         const float4 a = sl[q], b = vk[q];
-        g = fmaf(a.x, b.x, g);
-        g = fmaf(a.y, b.y, g);
-        g = fmaf(a.z, b.z, g);
-        g = fmaf(a.w, b.w, g);
+        g0 = fmaf(a.x, b.x, g0);
+        g1 = fmaf(a.y, b.y, g1);
+        g2 = fmaf(a.z, b.z, g2);
+        g3 = fmaf(a.w, b.w, g3);
       }
+      const float g = (g0 + g1) + (g2 + g3);
       const float gk = gkk[k];
       if (gjj == 0.f || gk == 0.f) {
         border |= 1u << r;
@@ -157,6 +191,7 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
     bool conflict = __any_sync(0xffffffffu, definite);
     if (!conflict && __any_sync(0xffffffffu, border != 0)) {
       bool c64 = false;
+      const float* cj = X + (int64_t)j * ld;
       for (int r = 0; border >> r; ++r) {
         if (!((border >> r) & 1u)) continue;
         const int k = lane + 32 * r;
@@ -178,11 +213,14 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
     }
     __syncwarp();
   }
+  cp_async_wait<0>();
+  __syncwarp();
   if (fp64_tests) atomicAdd(n64, fp64_tests);
   return kept;
 }
 
-// Shared-memory layout of warp_prune_node for one warp, in floats.
+// Shared-memory layout of warp_prune_node for one warp, in floats: V [(R + 1) D1],
+// xs [D1], gkk [R + 1 rounded to 4], ring [PRUNE_PREFETCH D1].
 __host__ __device__ inline int prune_row_stride(int d) {
   int D1 = (d + 3) & ~3;
   while ((D1 & 31) != 4) D1 += 4;
@@ -190,7 +228,98 @@ __host__ __device__ inline int prune_row_stride(int d) {
 }
 __host__ __device__ inline size_t prune_smem_floats(int d, int R) {
   const int D1 = prune_row_stride(d);
-  return (((size_t)(R + 1) * D1 + (size_t)D1 + (size_t)R + 1) + 3) & ~(size_t)3;
+  return (size_t)(R + 1) * D1 + (size_t)D1 + (size_t)((R + 1 + 3) & ~3) +
+         (size_t)PRUNE_PREFETCH * D1;
+}
+
+// Rows too long for R + 1 of them to sit in shared memory (wide rows, e.g. d = 960):
+// the kept centred vectors live in a global-memory slot of the warp, Vg [(R + 1)][d4],
+// and each dot product is a warp-wide sum over coordinates (coalesced float4 reads).
+// Same decisions and the same fp32 bound (any summation order), same fp64 re-test.
+// Shared memory per warp: xs [d4], cs [d4], gkk [R + 1 rounded to 4].
+__host__ __device__ inline size_t prune_wide_smem_floats(int d, int R) {
+  const int d4 = (d + 3) & ~3;
+  return 2 * (size_t)d4 + (size_t)((R + 1 + 3) & ~3);
+}
+__host__ __device__ inline bool prune_is_wide(int d, int R) {
+  return prune_smem_floats(d, R) * sizeof(float) > 96 * 1024;
+}
+
+__device__ __forceinline__ int warp_prune_node_wide(const float* __restrict__ X, int ld, int d,
+                                                    int64_t i, const int32_t* cand, int len,
+                                                    int R, float cosA32, double cosA64,
+                                                    float margin, float* __restrict__ Vg,
+                                                    float* xs, float* cs, float* gkk,
+                                                    int32_t* out, unsigned long long* n64) {
+  const int lane = lane_id();
+  const float* xg = X + i * ld;
+  const int d4 = (d + 3) & ~3;
+  const int nq4 = d4 >> 2;
+  for (int t = lane; t < d4; t += 32) xs[t] = xg[t];
+  __syncwarp();
+  int kept = 0;
+  unsigned long long fp64_tests = 0;
+  for (int t = 0; t < len && kept < R; ++t) {
+    const int32_t j = cand[t];
+    const float4* cj4 = (const float4*)(X + (int64_t)j * ld);
+    float4* slot4 = (float4*)(Vg + (size_t)kept * d4);
+    float part = 0.f;
+    for (int f = lane; f < nq4; f += 32) {
+      const float4 c = __ldg(cj4 + f);
+      const float4 x = ((const float4*)xs)[f];
+      const float4 v = make_float4(c.x - x.x, c.y - x.y, c.z - x.z, c.w - x.w);
+      ((float4*)cs)[f] = v;
+      slot4[f] = v;
+      part = fmaf(v.x, v.x, part);
+      part = fmaf(v.y, v.y, part);
+      part = fmaf(v.z, v.z, part);
+      part = fmaf(v.w, v.w, part);
+    }
+    const float gjj = warp_sum(part);
+    __syncwarp();
+    bool conflict = false;
+    for (int k = 0; k < kept && !conflict; ++k) {
+      const float4* vk = (const float4*)(Vg + (size_t)k * d4);
+      float g = 0.f;
+      for (int f = lane; f < nq4; f += 32) {
+        const float4 a = ((const float4*)cs)[f], b = vk[f];
+        g = fmaf(a.x, b.x, g);
+        g = fmaf(a.y, b.y, g);
+        g = fmaf(a.z, b.z, g);
+        g = fmaf(a.w, b.w, g);
+      }
+      g = warp_sum(g);
+      const float gk = gkk[k];
+      bool border = gjj == 0.f || gk == 0.f;
+      if (!border) {
+        const float c = g / (sqrtf(gjj) * sqrtf(gk));
+        if (c > cosA32 + margin)
+          conflict = true;
+        else if (c >= cosA32 - margin)
+          border = true;
+      }
+      if (border) {
+        // every lane takes the same fp64 decision from the same sequential sums
+        const float* ck = X + (int64_t)out[k] * ld;
+        const float* cjp = X + (int64_t)j * ld;
+        const double gjk = centred_dot_f64(cjp, ck, xg, d);
+        const double g1 = centred_dot_f64(cjp, cjp, xg, d);
+        const double g2 = centred_dot_f64(ck, ck, xg, d);
+        conflict = cos_from_gram_f64(gjk, g1, g2) > cosA64;
+        ++fp64_tests;
+      }
+    }
+    if (!conflict) {
+      if (lane == 0) {
+        out[kept] = j;
+        gkk[kept] = gjj;
+      }
+      ++kept;
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && fp64_tests) atomicAdd(n64, fp64_tests);
+  return kept;
 }
 
 }  // namespace ssg

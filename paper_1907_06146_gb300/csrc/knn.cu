@@ -409,8 +409,7 @@ __global__ void k_knn_fallback(const float* __restrict__ A, int lda, const float
 // ---------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------
-void ingest(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out, float* norms,
-            DataInfo* info) {
+void pad_rows(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out) {
   out.ld = (d + 3) & ~3;
   const bool aligned = ((uintptr_t)X & 15) == 0;
   if (out.ld == d && aligned) {
@@ -422,6 +421,11 @@ void ingest(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out, 
     SSG_LAUNCH(k_pad_copy, grid, 256, 0, st, X, n, d, out.own.p, out.ld);
     out.p = out.own.p;
   }
+}
+
+void ingest(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out, float* norms,
+            DataInfo* info) {
+  pad_rows(X, n, d, st, out);
   Scratch<unsigned> facts(3, st);
   SSG_CUDA(cudaMemsetAsync(facts.p, 0, 3 * sizeof(unsigned), st));
   SSG_LAUNCH(k_row_stats, (unsigned)ceil_div(n, 8), 256, 0, st, out.p, n, d, out.ld, norms,

@@ -28,7 +28,8 @@ KnnResult knn_exact(const float* A, int64_t na, int lda, const float* a_norm, co
                     StageTimer* gemm_timer);
 
 // bf16 tensor-core variant of the exact top-K (only for info.bf16_exact data).
-bool knn_tc_available();
+// True on sm_103 when the shared-memory pipeline fits rows of d values (d <= 128).
+bool knn_tc_available(int d);
 void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
                   int64_t nb, int ldb, const float* b_norm, int d, int self, int K,
                   int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer);
@@ -61,10 +62,20 @@ int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int3
                     cudaStream_t st);
 
 // Search-on-Graph.
+// work (nullable, device): totals of expansions, distance evaluations, adjacency entries.
 void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
                 const int32_t* deg, int R, const int32_t* nav, int n_nav, const float* Q,
                 int ldq, int64_t nq, int k, int Ls, int32_t* out_ids, float* out_d2,
-                cudaStream_t st);
+                cudaStream_t st, unsigned long long* work = nullptr);
+
+// Search with a per-query k (qk) and pool size (qls <= ls_max); results at stride ldo.
+void search_run_mixed(const float* X, int ld, int d, const int32_t* adj, const int32_t* deg, int R,
+                      const int32_t* nav, int n_nav, const float* Q, int ldq, int64_t nq,
+                      const int32_t* qk, const int32_t* qls, int ls_max, int ldo,
+                      int32_t* out_ids, float* out_d2, cudaStream_t st);
+
+// Padded view of X only (no statistics, no synchronisation).
+void pad_rows(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out);
 
 // Smallest margin (in cos units) beyond which the fp32 angle test is certain.
 inline float angle_margin_fp32(int d) { return (float)((2.0 * d + 20.0) * U32 * 1.1); }

@@ -46,9 +46,11 @@ __device__ __forceinline__ void warp_sort_regs(uint64_t (&v)[C / 32]) {
 
 // Compact one row's buffer: sort its cnt keys, keep the KS smallest at the front.
 // Returns the new count; *tau receives the KS-th distance (or +inf while fewer).
+// Not inlined: the unrolled sort is large and runs rarely, so one copy of it keeps the
+// hot loops of the callers small in the instruction cache.
 template <int C>
-__device__ __forceinline__ int compact_row(uint64_t* __restrict__ buf, int cnt, int KS,
-                                           float* tau) {
+__device__ __noinline__ int compact_row(uint64_t* __restrict__ buf, int cnt, int KS,
+                                        float* tau) {
   constexpr int E = C / 32;
   const int lane = lane_id();
   uint64_t v[E];

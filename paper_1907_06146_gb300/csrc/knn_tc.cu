@@ -138,6 +138,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// Wait for the outstanding TMEM loads and mark v as written by the wait, so that the
+// compiler cannot move a use of v (filled asynchronously by tcgen05.ld) above it.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]),
+                 "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]),
+                 "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]),
+                 "+r"(v[30]), "+r"(v[31])
+               :
+               : "memory");
+}
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups of
 // 128 bytes 1024 bytes apart.  The leading-byte offset is unused by this layout.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
@@ -176,7 +189,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   unsigned char* sA = sm;
   unsigned char* sB = sA + a_bytes;
   float* nyw = (float*)(sB + (size_t)S * b_bytes);
-  uint64_t* bars = (uint64_t*)(nyw + EPI_WARPS * BN);
+  float* stash = nyw + EPI_WARPS * BN;  // 32 floats per epilogue thread
+  uint64_t* bars = (uint64_t*)(stash + EPI_WARPS * 32 * 32);
   uint64_t* a_full = bars;
   uint64_t* a_empty = bars + 1;
   uint64_t* b_full = bars + 2;
@@ -304,16 +318,25 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       float tau = INF;
       int cnt = 0;
       uint64_t* buf = p.rowbuf + ((size_t)blockIdx.x * BM + row_in_cta) * C;
+      // column norms of the next tile, loaded one tile ahead
+      float nyr[BN / 32];
+#pragma unroll
+      for (int c = 0; c < BN / 32; ++c) {
+        const int64_t jj = c * 32 + lane;
+        nyr[c] = jj < p.nb ? p.b_norm[jj] : INF;
+      }
       for (int64_t ct = 0; ct < nct; ++ct, ++it) {
         const int b = (int)(it & 1);
         const uint32_t tph = (uint32_t)((it >> 1) & 1);
         const int64_t j0 = ct * BN;
 #pragma unroll
-        for (int c = 0; c < BN / 32; ++c) {
-          const int64_t jj = j0 + c * 32 + lane;
-          ny[c * 32 + lane] = jj < p.nb ? p.b_norm[jj] : INF;
-        }
+        for (int c = 0; c < BN / 32; ++c) ny[c * 32 + lane] = nyr[c];
         __syncwarp();
+#pragma unroll
+        for (int c = 0; c < BN / 32; ++c) {
+          const int64_t jj = j0 + BN + c * 32 + lane;
+          nyr[c] = jj < p.nb ? p.b_norm[jj] : INF;
+        }
         ok = mbar_wait(smem_u32(t_full + b), tph, abort_flag);
         if (!__all_sync(0xffffffffu, ok)) {
           ok = false;
@@ -321,20 +344,53 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         }
         tc_fence_after();
         const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)((b * 2 + h) * BN);
-#pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
-          uint32_t v[32];
-          tmem_ld32(taddr + c * 32, v);
-          tmem_wait_ld();
+        // d2 < tau  <=>  |y|^2 - 2 acc < tau - |x|^2, all exact integers here: per value
+        // one multiply-add, one compare and one bit of a pass mask.  A thread with passing
+        // values parks the chunk in its shared-memory stash (float4 slots XOR-swizzled by
+        // lane, so 8 lanes store to 8 different bank groups) and appends only the set bits.
+        const float tp = tau - nx;
+        float* st = stash + (size_t)(ew * 32 + lane) * 32;
+        const int sw = lane & 7;
+        auto scan32 = [&](const uint32_t(&v)[32], int c) {
+          float x[32];
+          uint32_t m = 0;
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
-            const float dd = fmaf(-2.f, __uint_as_float(v[e]), nx + ny[c * 32 + e]);
-            if (dd < tau) buf[cnt++] = make_key(dd, (int32_t)(j0 + c * 32 + e));
+            x[e] = fmaf(-2.f, __uint_as_float(v[e]), ny[c * 32 + e]);
+            m |= (x[e] < tp ? 1u : 0u) << e;
           }
-        }
+          if (m) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              *(float4*)(st + ((k ^ sw) << 2)) =
+                  make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
+            const int32_t jc = (int32_t)(j0 + c * 32);
+            do {
+              const int e = __ffs(m) - 1;
+              m &= m - 1;
+              const float xv = st[(((e >> 2) ^ sw) << 2) | (e & 3)];
+              buf[cnt++] = make_key(xv + nx, jc + e);
+            } while (m);
+          }
+        };
+        // The load of chunk c + 1 is in flight while chunk c is scanned; the accumulator
+        // buffer is handed back to the MMA warp as soon as the last chunk is in registers.
+        uint32_t v0[32], v1[32];
+        tmem_ld32(taddr, v0);
+        tmem_wait_ld(v0);
+        tmem_ld32(taddr + 32, v1);
+        scan32(v0, 0);
+        tmem_wait_ld(v1);
+        tmem_ld32(taddr + 64, v0);
+        scan32(v1, 1);
+        tmem_wait_ld(v0);
+        tmem_ld32(taddr + 96, v1);
+        scan32(v0, 2);
+        tmem_wait_ld(v1);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(t_empty + b));
+        scan32(v1, 3);
         unsigned need = __ballot_sync(0xffffffffu, cnt > C - BN);
         while (need) {
           const int l = __ffs(need) - 1;
@@ -429,7 +485,7 @@ CUtensorMap make_map(const __nv_bfloat16* ptr, int64_t rows, int dp, int box_row
 
 size_t tc_smem_bytes(int kchunks, int stages) {
   return 1024 + (size_t)kchunks * BM * 128 + (size_t)stages * kchunks * BN * 128 +
-         EPI_WARPS * BN * sizeof(float) + sizeof(uint64_t) * (2 + 2 * MAX_STAGES + 4) + 16;
+         EPI_WARPS * BN * sizeof(float) + EPI_WARPS * 32 * 32 * sizeof(float) + sizeof(uint64_t) * (2 + 2 * MAX_STAGES + 4) + 16;
 }
 
 template <int C>
@@ -445,7 +501,7 @@ void launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, TcArgs& a, int grid
 
 }  // namespace
 
-bool knn_tc_available() {
+bool knn_tc_available(int d) {
   static int avail = -1;
   if (avail < 0) {
     int dev = 0, major = 0, minor = 0;
@@ -455,7 +511,8 @@ bool knn_tc_available() {
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
       avail = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
   }
-  return avail == 1;
+  const int kchunks = ((d + 63) & ~63) / 64;
+  return avail == 1 && d >= 1 && tc_smem_bytes(kchunks, 2) <= 225 * 1024;
 }
 
 void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,

@@ -103,30 +103,45 @@ void pool_run(const float* X, int ld, int d, int64_t n, const int32_t* knn, int 
 // ---------------------------------------------------------------------------------------
 // Prune (Alg. 2 selection on each pool, Alg. 3).
 // ---------------------------------------------------------------------------------------
+// One warp per node.  Vg == nullptr: the kept vectors sit in shared memory
+// (warp_prune_node); otherwise each warp of the (persistent) grid owns the global slot
+// Vg + warp_index * (R + 1) * d4 for wide rows (warp_prune_node_wide).
 __global__ void k_prune(const float* __restrict__ X, int ld, int d, int64_t n,
                         const int32_t* __restrict__ pool_id, const int32_t* __restrict__ pool_len,
                         int L, int R, float cosA32, double cosA64, float margin,
                         int32_t* __restrict__ adj, int32_t* __restrict__ deg,
-                        unsigned long long* __restrict__ n64) {
+                        unsigned long long* __restrict__ n64, float* __restrict__ Vg) {
   extern __shared__ __align__(16) float smf[];
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
+  const int64_t gwarp = (int64_t)blockIdx.x * wpb + warp;
+  const int64_t nwarps = (int64_t)gridDim.x * wpb;
+  const int d4 = (d + 3) & ~3;
   const int D1 = prune_row_stride(d);
-  float* V = smf + (size_t)warp * prune_smem_floats(d, R);
-  float* xs = V + (size_t)(R + 1) * D1;
-  float* gkk = xs + D1;
-  const int64_t i = (int64_t)blockIdx.x * wpb + warp;
-  if (i >= n) return;
-  int32_t* out = adj + i * R;
-  const int kept = warp_prune_node(X, ld, d, i, pool_id + i * L, pool_len[i], R, cosA32, cosA64,
-                                   margin, V, D1, xs, gkk, out, n64);
-  for (int t = kept + lane; t < R; t += 32) out[t] = -1;
-  if (lane == 0) deg[i] = kept;
+  float* base = smf + (size_t)warp * (Vg ? prune_wide_smem_floats(d, R) : prune_smem_floats(d, R));
+  for (int64_t i = gwarp; i < n; i += nwarps) {
+    int32_t* out = adj + i * R;
+    int kept;
+    if (Vg) {
+      kept = warp_prune_node_wide(X, ld, d, i, pool_id + i * L, pool_len[i], R, cosA32, cosA64,
+                                  margin, Vg + (size_t)gwarp * (R + 1) * d4, base, base + d4,
+                                  base + 2 * d4, out, n64);
+    } else {
+      float* xs = base + (size_t)(R + 1) * D1;
+      kept = warp_prune_node(X, ld, d, i, pool_id + i * L, pool_len[i], R, cosA32, cosA64, margin,
+                             base, D1, xs, xs + D1, out, n64);
+    }
+    for (int t = kept + lane; t < R; t += 32) out[t] = -1;
+    if (lane == 0) deg[i] = kept;
+    __syncwarp();
+  }
 }
 
 void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
                const int32_t* pool_len, int L, int R, double cos_a, int32_t* adj, int32_t* deg,
                Counters* dctr, cudaStream_t st) {
-  const size_t per_warp = prune_smem_floats(d, R) * sizeof(float);
+  const bool wide = prune_is_wide(d, R);
+  const size_t per_warp =
+      (wide ? prune_wide_smem_floats(d, R) : prune_smem_floats(d, R)) * sizeof(float);
   int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
   const size_t smem = per_warp * wpb;
   static size_t attr = 0;
@@ -134,9 +149,14 @@ void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
     SSG_CUDA(cudaFuncSetAttribute(k_prune, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }
-  SSG_LAUNCH(k_prune, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, ld, d, n, pool_id,
-             pool_len, L, R, (float)cos_a, cos_a, angle_margin_fp32(d), adj, deg,
-             &dctr->angle_fp64);
+  int blocks_per_sm = 0;
+  SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_prune, wpb * 32, smem));
+  const int64_t grid =
+      std::min<int64_t>(ceil_div(n, wpb), (int64_t)std::max(1, blocks_per_sm) * num_sms());
+  Scratch<float> Vg;
+  if (wide) Vg.alloc((size_t)grid * wpb * (R + 1) * ((d + 3) & ~3), st);
+  SSG_LAUNCH(k_prune, (unsigned)grid, wpb * 32, smem, st, X, ld, d, n, pool_id, pool_len, L, R,
+             (float)cos_a, cos_a, angle_margin_fp32(d), adj, deg, &dctr->angle_fp64, Vg.p);
 }
 
 }  // namespace ssg

@@ -97,6 +97,14 @@ static int64_t exclusive_scan(const int* in32, const int64_t* in64, int64_t n, i
 }
 
 // ---- merge + prune ----------------------------------------------------------------------
+// One warp per node, persistent over count nodes.  Vg == nullptr: the prune keeps its
+// vectors in shared memory; otherwise each warp owns the global slot
+// Vg + warp_index * (R + 1) * d4 for wide rows.
+__host__ __device__ inline size_t merge_prune_bytes(int d, int R, bool wide) {
+  const size_t f = wide ? prune_wide_smem_floats(d, R) : prune_smem_floats(d, R);
+  return (f * sizeof(float) + 15) & ~(size_t)15;
+}
+
 __global__ void k_reverse_merge(const float* __restrict__ X, int ld, int d, int64_t n,
                                 const int32_t* __restrict__ adj0, const int32_t* __restrict__ deg0,
                                 int R, const int64_t* __restrict__ off,
@@ -106,62 +114,71 @@ __global__ void k_reverse_merge(const float* __restrict__ X, int ld, int d, int6
                                 int32_t* __restrict__ adj1, int32_t* __restrict__ deg1,
                                 int32_t* __restrict__ big_list, int* __restrict__ big_count,
                                 unsigned long long* __restrict__ n_order,
-                                unsigned long long* __restrict__ n_angle) {
+                                unsigned long long* __restrict__ n_angle, float* __restrict__ Vg) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
-  const size_t prune_bytes = prune_smem_floats(d, R) * sizeof(float);
-  const size_t per_warp = (size_t)cap * 20 + ((prune_bytes + 15) & ~(size_t)15);
+  const size_t per_warp = (size_t)cap * 20 + merge_prune_bytes(d, R, Vg != nullptr);
   unsigned char* base = sm_raw + warp * per_warp;
   uint64_t* keys = (uint64_t*)base;
   double* d64 = (double*)(keys + cap);
   int32_t* cand = (int32_t*)(d64 + cap);
-  float* V = (float*)(base + (size_t)cap * 20);
+  float* P = (float*)(base + (size_t)cap * 20);
   const int D1 = prune_row_stride(d);
-  float* xs = V + (size_t)(R + 1) * D1;
-  float* gkk = xs + D1;
+  const int d4 = (d + 3) & ~3;
+  const int64_t gwarp = (int64_t)blockIdx.x * wpb + warp;
+  const int64_t nwarps = (int64_t)gridDim.x * wpb;
 
-  const int64_t w = (int64_t)blockIdx.x * wpb + warp;
-  if (w >= count) return;
-  const int64_t j = node_list ? node_list[w] : w;
-  const int d0 = deg0[j];
-  const int64_t r0 = off[j], r1 = off[j + 1];
-  if (d0 + (r1 - r0) > cap) {
-    if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)j;
-    return;
+  for (int64_t w = gwarp; w < count; w += nwarps) {
+    const int64_t j = node_list ? node_list[w] : w;
+    const int d0 = deg0[j];
+    const int64_t r0 = off[j], r1 = off[j + 1];
+    if (d0 + (r1 - r0) > cap) {
+      if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)j;
+      continue;
+    }
+    for (int t = lane; t < d0; t += 32) keys[t] = (uint64_t)(uint32_t)adj0[j * R + t];
+    __syncwarp();
+    int m = d0;
+    for (int64_t c = r0; c < r1; c += 32) {
+      const int64_t p = c + lane;
+      int32_t id = p < r1 ? rev[p] : -1;
+      bool fresh = id >= 0;
+      for (int t = 0; t < d0 && fresh; ++t)
+        if (key_id(keys[t]) == id) fresh = false;
+      const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+      if (fresh) keys[m + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
+      m += __popc(bal);
+    }
+    __syncwarp();
+    const float* xj = X + j * ld;
+    warp_fill_dist_keys(keys, m, X, ld, xj);
+    int mp = 1;
+    while (mp < m) mp <<= 1;
+    for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
+    __syncwarp();
+    warp_sort_keys(keys, mp);
+    if (!exact && m > 1) {
+      int f = warp_fix_runs(keys, m, m, d64, X, ld, d, xj, rel);
+      for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+      if (lane == 0 && f) atomicAdd(n_order, (unsigned long long)f);
+    }
+    for (int t = lane; t < m; t += 32) cand[t] = key_id(keys[t]);
+    __syncwarp();
+    int32_t* out = adj1 + j * R;
+    int kept;
+    if (Vg) {
+      kept = warp_prune_node_wide(X, ld, d, j, cand, m, R, cosA32, cosA64, margin,
+                                  Vg + (size_t)gwarp * (R + 1) * d4, P, P + d4, P + 2 * d4, out,
+                                  n_angle);
+    } else {
+      float* xs = P + (size_t)(R + 1) * D1;
+      kept = warp_prune_node(X, ld, d, j, cand, m, R, cosA32, cosA64, margin, P, D1, xs, xs + D1,
+                             out, n_angle);
+    }
+    for (int t = kept + lane; t < R; t += 32) out[t] = -1;
+    if (lane == 0) deg1[j] = kept;
+    __syncwarp();
   }
-  for (int t = lane; t < d0; t += 32) keys[t] = (uint64_t)(uint32_t)adj0[j * R + t];
-  __syncwarp();
-  int m = d0;
-  for (int64_t c = r0; c < r1; c += 32) {
-    const int64_t p = c + lane;
-    int32_t id = p < r1 ? rev[p] : -1;
-    bool fresh = id >= 0;
-    for (int t = 0; t < d0 && fresh; ++t)
-      if (key_id(keys[t]) == id) fresh = false;
-    const unsigned bal = __ballot_sync(0xffffffffu, fresh);
-    if (fresh) keys[m + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
-    m += __popc(bal);
-  }
-  __syncwarp();
-  const float* xj = X + j * ld;
-  warp_fill_dist_keys(keys, m, X, ld, xj);
-  int mp = 1;
-  while (mp < m) mp <<= 1;
-  for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
-  __syncwarp();
-  warp_sort_keys(keys, mp);
-  if (!exact && m > 1) {
-    int f = warp_fix_runs(keys, m, m, d64, X, ld, d, xj, rel);
-    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-    if (lane == 0 && f) atomicAdd(n_order, (unsigned long long)f);
-  }
-  for (int t = lane; t < m; t += 32) cand[t] = key_id(keys[t]);
-  __syncwarp();
-  int32_t* out = adj1 + j * R;
-  const int kept = warp_prune_node(X, ld, d, j, cand, m, R, cosA32, cosA64, margin, V, D1, xs,
-                                   gkk, out, n_angle);
-  for (int t = kept + lane; t < R; t += 32) out[t] = -1;
-  if (lane == 0) deg1[j] = kept;
 }
 
 __global__ void k_max_int(const int* __restrict__ v, int64_t n, int* __restrict__ out) {
@@ -188,14 +205,15 @@ int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
   Scratch<int32_t> rev((size_t)std::max<int64_t>(total, 1), st);
   SSG_LAUNCH(k_scatter, grid, 256, 0, st, adj0, deg0, R, n, off.p, fill.p, rev.p);
 
-  const size_t prune_bytes = ((prune_smem_floats(d, R) * sizeof(float)) + 15) & ~(size_t)15;
+  const bool wide = prune_is_wide(d, R);
+  const size_t prune_bytes = merge_prune_bytes(d, R, wide);
   const float rel = dist_rel_fp32(d), margin = angle_margin_fp32(d);
+  const int d4 = (d + 3) & ~3;
   // warp path
   const int cap = 256;
   const size_t per_warp = (size_t)cap * 20 + prune_bytes;
   const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
   const size_t smem = per_warp * wpb;
-  SSG_REQUIRE(smem <= 200 * 1024, SSG_EINVAL, "reverse merge: R * d too large for shared memory");
   static size_t attr = 0;
   const size_t smem_big_max = 220 * 1024;
   if (attr < smem_big_max) {
@@ -203,10 +221,17 @@ int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
                                   (int)smem_big_max));
     attr = smem_big_max;
   }
+  int blocks_per_sm = 0;
+  SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_reverse_merge, wpb * 32,
+                                                         smem));
+  const int64_t mgrid =
+      std::min<int64_t>(ceil_div(n, wpb), (int64_t)std::max(1, blocks_per_sm) * num_sms());
+  Scratch<float> Vg;
+  if (wide) Vg.alloc((size_t)mgrid * wpb * (R + 1) * d4, st);
   Scratch<int32_t> big((size_t)n, st);
-  SSG_LAUNCH(k_reverse_merge, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, ld, d, n, adj0,
-             deg0, R, off.p, rev.p, (const int32_t*)nullptr, n, cap, exact, rel, (float)cos_a,
-             cos_a, margin, adj1, deg1, big.p, small.p, &dctr->order_fp64, &dctr->angle_fp64);
+  SSG_LAUNCH(k_reverse_merge, (unsigned)mgrid, wpb * 32, smem, st, X, ld, d, n, adj0, deg0, R, off.p,
+             rev.p, (const int32_t*)nullptr, n, cap, exact, rel, (float)cos_a, cos_a, margin, adj1,
+             deg1, big.p, small.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p);
   int h[2];
   SSG_CUDA(cudaMemcpyAsync(h, small.p, sizeof(h), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
@@ -217,13 +242,15 @@ int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
                 "reverse merge: a node has %d candidates, more than the %d supported", h[1] + R,
                 cap_big);
     const size_t smem_big = (size_t)cap_big * 20 + prune_bytes;
-    // every listed node fits cap_big, so the second launch appends to no list
+    // every listed node fits cap_big, so the second launch appends to no list; one warp per
+    // block, so the wide slots of the first launch (>= this many warps) are reused
+    const int grid_big = (int)std::min<int64_t>(h[0], mgrid * wpb);
     Scratch<int32_t> none(1, st);
     Scratch<int> small2(2, st);
     SSG_CUDA(cudaMemsetAsync(small2.p, 0, sizeof(int) * 2, st));
-    SSG_LAUNCH(k_reverse_merge, h[0], 32, smem_big, st, X, ld, d, n, adj0, deg0, R, off.p, rev.p,
+    SSG_LAUNCH(k_reverse_merge, grid_big, 32, smem_big, st, X, ld, d, n, adj0, deg0, R, off.p, rev.p,
                big.p, (int64_t)h[0], cap_big, exact, rel, (float)cos_a, cos_a, margin, adj1, deg1,
-               none.p, small2.p, &dctr->order_fp64, &dctr->angle_fp64);
+               none.p, small2.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p);
   }
   return h[1];
 }

@@ -72,18 +72,19 @@ struct SearchLayout {
 __global__ void k_search(const float* __restrict__ X, int ld, int d, const int32_t* __restrict__ adj,
                          const int32_t* __restrict__ deg, int R, const int32_t* __restrict__ nav,
                          int n_nav, const float* __restrict__ Q, int ldq, int64_t nq, int k,
+                         const int32_t* __restrict__ qk, const int32_t* __restrict__ qls, int ldo,
                          SearchLayout lay, int32_t* __restrict__ out_ids,
-                         float* __restrict__ out_d2) {
+                         float* __restrict__ out_d2, unsigned long long* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
   const int team = lane >> 3, tl = lane & 7;
-  const int Ls = lay.Ls;
+  const int LsCap = lay.Ls;
   unsigned char* base = sm_raw + (size_t)warp * lay.per_warp();
-  uint64_t* pA = (uint64_t*)base;
-  uint64_t* pB = pA + Ls;
-  unsigned char* fA = (unsigned char*)(pB + Ls);
-  unsigned char* fB = fA + Ls;
-  uint64_t* newk = (uint64_t*)(base + 2 * lay.pool_bytes() + (((size_t)2 * Ls + 15) & ~(size_t)15));
+  uint64_t* pA0 = (uint64_t*)base;
+  uint64_t* pB0 = pA0 + LsCap;
+  unsigned char* fA0 = (unsigned char*)(pB0 + LsCap);
+  unsigned char* fB0 = fA0 + LsCap;
+  uint64_t* newk = (uint64_t*)(base + 2 * lay.pool_bytes() + (((size_t)2 * LsCap + 15) & ~(size_t)15));
   float* qs = (float*)(newk + lay.RP);
   int32_t* cache = (int32_t*)(qs + ld);
   const int hcap = 1 << lay.log2h;
@@ -91,6 +92,14 @@ __global__ void k_search(const float* __restrict__ X, int ld, int d, const int32
   (void)d;
 
   for (int64_t qi = (int64_t)blockIdx.x * wpb + warp; qi < nq; qi += (int64_t)gridDim.x * wpb) {
+    // per-query pool size and result count (a batch may mix them; the layout is sized for
+    // the largest pool)
+    const int Ls = qls ? qls[qi] : LsCap;
+    const int kq = qk ? qk[qi] : k;
+    uint64_t* pA = pA0;
+    uint64_t* pB = pB0;
+    unsigned char* fA = fA0;
+    unsigned char* fB = fB0;
     const float* qg = Q + qi * ldq;
     for (int t = lane; t < ld; t += 32) qs[t] = t < d ? qg[t] : 0.f;
     for (int t = lane; t < hcap; t += 32) cache[t] = -1;
@@ -118,6 +127,7 @@ __global__ void k_search(const float* __restrict__ X, int ld, int d, const int32
       cache[((uint32_t)e * 2654435761u) >> (32 - lay.log2h)] = e;
     }
     int s = 1;
+    unsigned long long w_exp = 0, w_dist = (unsigned long long)n_nav, w_adj = 0;
     __syncwarp();
 
     for (;;) {
@@ -152,6 +162,9 @@ __global__ void k_search(const float* __restrict__ X, int ld, int d, const int32
         if (fresh) newk[cnt + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
         cnt += __popc(bal);
       }
+      ++w_exp;
+      w_adj += (unsigned long long)dg;
+      w_dist += (unsigned long long)cnt;
       __syncwarp();
       for (int t0 = 0; t0 < cnt; t0 += 4) {
         const int t = t0 + team;
@@ -210,19 +223,56 @@ __global__ void k_search(const float* __restrict__ X, int ld, int d, const int32
       fA = fB;
       fB = tf;
     }
-    for (int t = lane; t < k; t += 32) {
-      const bool v = t < s;
-      out_ids[qi * k + t] = v ? key_id(pA[t]) : -1;
-      if (out_d2) out_d2[qi * k + t] = v ? key_dist(pA[t]) : __int_as_float(0x7f800000);
+    for (int t = lane; t < ldo; t += 32) {
+      const bool v = t < s && t < kq;
+      out_ids[qi * ldo + t] = v ? key_id(pA[t]) : -1;
+      if (out_d2) out_d2[qi * ldo + t] = v ? key_dist(pA[t]) : __int_as_float(0x7f800000);
+    }
+    if (work && lane == 0) {
+      atomicAdd(work, w_exp);
+      atomicAdd(work + 1, w_dist);
+      atomicAdd(work + 2, w_adj);
     }
     __syncwarp();
   }
 }
 
+static size_t search_smem_setup(SearchLayout& lay, int wpb) {
+  while (lay.per_warp() * wpb > 200 * 1024 && lay.log2h > 8) --lay.log2h;
+  const size_t smem = lay.per_warp() * wpb;
+  SSG_REQUIRE(smem <= 220 * 1024, SSG_EINVAL, "search: L_search and d too large for shared memory");
+  static size_t attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    SSG_CUDA(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  return smem;
+}
+
+void search_run_mixed(const float* X, int ld, int d, const int32_t* adj, const int32_t* deg, int R,
+                      const int32_t* nav, int n_nav, const float* Q, int ldq, int64_t nq,
+                      const int32_t* qk, const int32_t* qls, int ls_max, int ldo,
+                      int32_t* out_ids, float* out_d2, cudaStream_t st) {
+  if (nq == 0) return;
+  SearchLayout lay;
+  lay.Ls = ls_max;
+  lay.RP = std::max(32, next_pow2(R));
+  lay.ld = ld;
+  lay.log2h = 12;
+  const int wpb = 4;
+  const size_t smem = search_smem_setup(lay, wpb);
+  int blocks_per_sm = 0;
+  SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search, wpb * 32, smem));
+  const int64_t want = ceil_div(nq, wpb);
+  const int grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, blocks_per_sm) * num_sms());
+  SSG_LAUNCH(k_search, grid, wpb * 32, smem, st, X, ld, d, adj, deg, R, nav, n_nav, Q, ldq, nq, 0,
+             qk, qls, ldo, lay, out_ids, out_d2, (unsigned long long*)nullptr);
+}
+
 void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
                 const int32_t* deg, int R, const int32_t* nav, int n_nav, const float* Q,
                 int ldq, int64_t nq, int k, int Ls, int32_t* out_ids, float* out_d2,
-                cudaStream_t st) {
+                cudaStream_t st, unsigned long long* work) {
   (void)n;
   if (nq == 0) return;
   SearchLayout lay;
@@ -244,7 +294,7 @@ void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
   const int64_t want = ceil_div(nq, wpb);
   const int grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, blocks_per_sm) * num_sms());
   SSG_LAUNCH(k_search, grid, wpb * 32, smem, st, X, ld, d, adj, deg, R, nav, n_nav, Q, ldq, nq, k,
-             lay, out_ids, out_d2);
+             (const int32_t*)nullptr, (const int32_t*)nullptr, k, lay, out_ids, out_d2, work);
 }
 
 }  // namespace ssg

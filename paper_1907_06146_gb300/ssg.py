@@ -82,6 +82,12 @@ SYMBOLS = {
                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_search_work": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
     "ssg_recall_hits": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_void_p]),
@@ -100,6 +106,16 @@ SYMBOLS = {
     "ssg_search_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_server_default_opts": (None, [ctypes.c_void_p]),
+    "ssg_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "ssg_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "ssg_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "ssg_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_server_destroy": (None, [ctypes.c_void_p]),
     "ssg_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "ssg_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_void_p]),
     "ssg_free": (None, [ctypes.c_void_p]),
@@ -256,6 +272,25 @@ def search_adj(base, adj, deg, nav, queries, k: int, L_search: int):
     return ids, d2
 
 
+def search_work(base, adj, deg, nav, queries, k: int, L_search: int):
+    """search_adj plus the batch's work: {expansions, distances, adjacency_entries}."""
+    torch = _torch()
+    b = _dev(base, torch.float32)
+    a = _dev(adj, torch.int32)
+    dg = _dev(deg, torch.int32)
+    nv = _dev(nav, torch.int32)
+    q = _dev(queries, torch.float32)
+    n, d = b.shape
+    nq = q.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    w = (ctypes.c_int64 * 3)()
+    _check(lib().ssg_search_work(_ptr(b), n, d, _ptr(a), _ptr(dg), a.shape[1], _ptr(nv),
+                                 nv.numel(), _ptr(q), nq, k, L_search, _ptr(ids), _ptr(d2), w,
+                                 _stream()))
+    return ids, d2, {"expansions": w[0], "distances": w[1], "adjacency_entries": w[2]}
+
+
 def recall_hits(found, truth, k: int) -> int:
     torch = _torch()
     f = _dev(found, torch.int32)
@@ -339,6 +374,73 @@ class Graph:
         h = ctypes.c_void_p()
         _check(lib().ssg_load(path.encode(), ctypes.byref(h)))
         return Graph(h)
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("mem_budget_bytes", ctypes.c_int64), ("max_k", ctypes.c_int32),
+                ("max_L_search", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests_done", ctypes.c_int64), ("queries_done", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("max_batches_in_flight", ctypes.c_int64),
+                ("max_queries_in_flight", ctypes.c_int64), ("busy_ms", ctypes.c_double)]
+
+
+class Server:
+    """Continuous-batching search server over a built graph (see ssg_server_* in ssg.h).
+    submit() returns a ticket at once; wait(ticket) blocks and returns (ids, d2, latency_ms).
+    Safe to call from several host threads."""
+
+    def __init__(self, graph: Graph, base=None, n_streams: int = 4, max_batch: int = 8192,
+                 mem_budget_bytes: int = 256 << 20, max_k: int = 128, max_L_search: int = 1024):
+        o = ServerOpts()
+        lib().ssg_server_default_opts(ctypes.byref(o))
+        o.n_streams, o.max_batch, o.mem_budget_bytes = n_streams, max_batch, mem_budget_bytes
+        o.max_k, o.max_L_search = max_k, max_L_search
+        self._graph = graph
+        self._base = None if base is None else _dev(base, _torch().float32)
+        bp = ctypes.c_void_p(0) if self._base is None else _ptr(self._base)
+        self._h = ctypes.c_void_p()
+        _check(lib().ssg_server_create(graph._h, bp, ctypes.byref(o), ctypes.byref(self._h)))
+        self._shape = {}
+        self._lock = __import__("threading").Lock()
+
+    def submit(self, queries: np.ndarray, k: int, L_search: int) -> int:
+        q = np.ascontiguousarray(queries, dtype=np.float32)
+        t = ctypes.c_uint64()
+        _check(lib().ssg_server_submit(self._h, q.ctypes.data_as(ctypes.c_void_p), q.shape[0], k,
+                                       L_search, ctypes.byref(t)))
+        with self._lock:
+            self._shape[t.value] = (q.shape[0], k)
+        return t.value
+
+    def wait(self, ticket: int):
+        with self._lock:
+            nq, k = self._shape.pop(ticket)
+        ids = np.empty((nq, k), np.int32)
+        d2 = np.empty((nq, k), np.float32)
+        lat = ctypes.c_double()
+        _check(lib().ssg_server_wait(self._h, ticket, ids.ctypes.data_as(ctypes.c_void_p),
+                                     d2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(lat)))
+        return ids, d2, lat.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().ssg_server_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().ssg_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _opts(n_nav, nav, seed, prec):

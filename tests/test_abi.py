@@ -65,9 +65,10 @@ def test_invalid_arguments_rejected_without_device(L):
     # alpha outside (0, 180)
     assert L.ssg_prune(P, 100, 8, P, P, 10, 8, 0.0, P, P, s) == 1
     assert L.ssg_prune(P, 100, 8, P, P, 10, 8, 180.0, P, P, s) == 1
-    # R out of range, and R * (d + 1) too large for shared memory
+    # R or d out of range
     assert L.ssg_prune(P, 100, 8, P, P, 10, 0, 60.0, P, P, s) == 1
-    assert L.ssg_prune(P, 100, 960, P, P, 10, 70, 60.0, P, P, s) == 1
+    assert L.ssg_prune(P, 100, 8, P, P, 10, 129, 60.0, P, P, s) == 1
+    assert L.ssg_prune(P, 100, 9000, P, P, 10, 70, 60.0, P, P, s) == 1
     # k > L_search
     assert L.ssg_search_adj(P, 100, 8, P, P, 8, P, 1, P, 5, 20, 10, P, P, s) == 1
     # build: n_nav > n

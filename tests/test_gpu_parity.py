@@ -87,7 +87,7 @@ def _has_tc(ssg):
         return False
 
 
-@pytest.mark.parametrize("n,d,K", [(1037, 7, 1), (1037, 7, 20), (3001, 64, 200), (900, 130, 600),
+@pytest.mark.parametrize("n,d,K", [(1037, 7, 1), (1037, 7, 20), (3001, 64, 200), (900, 96, 600),
                                    (6000, 128, 200)])
 def test_knn_bf16_tensor_cores(ssg, n, d, K):
     if not _tc(ssg):
@@ -97,6 +97,18 @@ def test_knn_bf16_tensor_cores(ssg, n, d, K):
     ref_ids, ref_d2 = oracle.knn_rows(base, K)
     np.testing.assert_array_equal(_np(ids), ref_ids)
     np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
+
+
+def test_knn_wide_integer_rows_use_fp32(ssg):
+    """d > 128 does not fit the tensor-core pipeline: auto falls back to the (exact) fp32
+    path and an explicit bf16 request is refused."""
+    base = synth.uniform_points(700, 130, 2130, integer=True, hi=100)
+    ids, d2 = ssg.knn(_cuda(base), 50, prec="auto")
+    ref_ids, ref_d2 = oracle.knn_rows(base, 50)
+    np.testing.assert_array_equal(_np(ids), ref_ids)
+    np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
+    with pytest.raises(ssg.SSGError):
+        ssg.knn(_cuda(base), 50, prec="bf16")
 
 
 def test_ground_truth_bf16(ssg, intdata):
@@ -237,6 +249,31 @@ def test_build_end_to_end(ssg, which, small, intdata, small_ref, int_ref):
     assert st["n_repair"] == ref["n_repair"]
     assert st["kernel_launches"] > 5
     assert st["exact_mode"] == (1 if which == "int" else 0)
+
+
+@pytest.fixture(scope="module")
+def wide():
+    """GIST-shaped rows (d = 960, values in [0, 1]) at a size the oracle builds quickly;
+    R = 70 rows of 960 floats do not fit in shared memory, so the prune and the reverse
+    merge take their wide-row path."""
+    w = synth.gist_like(n=1_200, nq=60, n_clusters=12)
+    nav = synth.nav_ids(w.n, w.n_nav, 13)
+    ref = oracle.build_graph(w.base, 50, 200, 70, 60.0, nav)
+    return w, ref
+
+
+def test_wide_rows_prune_reverse_build(ssg, wide):
+    w, ref = wide
+    b = _cuda(w.base)
+    adj0, deg0 = ssg.prune(b, _cuda(ref["pool_id"]), _cuda(ref["pool_len"]), 70, 60.0)
+    np.testing.assert_array_equal(_np(deg0), ref["deg0"])
+    np.testing.assert_array_equal(_np(adj0), ref["adj0"])
+    adj1, deg1 = ssg.reverse(b, _cuda(ref["adj0"]), _cuda(ref["deg0"]), 60.0)
+    np.testing.assert_array_equal(_np(deg1), ref["deg1"])
+    np.testing.assert_array_equal(_np(adj1), ref["adj1"])
+    g = ssg.build(b, 50, 200, 70, 60.0, nav=ref["nav"])
+    np.testing.assert_array_equal(_np(g.deg), ref["deg"])
+    np.testing.assert_array_equal(_np(g.adj), ref["adj"])
 
 
 def test_build_host_matches_device(ssg, small, small_ref):
