@@ -151,8 +151,10 @@ void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
   }
   int blocks_per_sm = 0;
   SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_prune, wpb * 32, smem));
+  // wide rows: a persistent grid (one device slot per warp); otherwise one warp per node
   const int64_t grid =
-      std::min<int64_t>(ceil_div(n, wpb), (int64_t)std::max(1, blocks_per_sm) * num_sms());
+      wide ? std::min<int64_t>(ceil_div(n, wpb), (int64_t)std::max(1, blocks_per_sm) * num_sms())
+           : ceil_div(n, wpb);
   Scratch<float> Vg;
   if (wide) Vg.alloc((size_t)grid * wpb * (R + 1) * ((d + 3) & ~3), st);
   SSG_LAUNCH(k_prune, (unsigned)grid, wpb * 32, smem, st, X, ld, d, n, pool_id, pool_len, L, R,

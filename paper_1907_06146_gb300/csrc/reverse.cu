@@ -224,8 +224,10 @@ int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
   int blocks_per_sm = 0;
   SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_reverse_merge, wpb * 32,
                                                          smem));
+  // wide rows: a persistent grid (one device slot per warp); otherwise one warp per node
   const int64_t mgrid =
-      std::min<int64_t>(ceil_div(n, wpb), (int64_t)std::max(1, blocks_per_sm) * num_sms());
+      wide ? std::min<int64_t>(ceil_div(n, wpb), (int64_t)std::max(1, blocks_per_sm) * num_sms())
+           : ceil_div(n, wpb);
   Scratch<float> Vg;
   if (wide) Vg.alloc((size_t)mgrid * wpb * (R + 1) * d4, st);
   Scratch<int32_t> big((size_t)n, st);
