@@ -398,6 +398,21 @@ def run_gpu(args):
         serving = run_serving(ssg, g_srv, base, w, args.serve_seconds, args.serve_rate)
         del g_srv
 
+    # the plain FP32 path on the same input, once (untimed in value): its build time, the
+    # recall of its graph at the same L_search, and whether its edge set equals this one's
+    fp32_arm = None
+    if rank == 0 and args.fp32_arm and args.prec != "fp32":
+        g_mp = ssg.build(base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec)
+        g32 = ssg.build(base, w.K, w.L, w.R, w.alpha, nav=nav, prec="fp32")
+        ids32, _ = g32.search(base, queries, 10, ls_used)
+        rec32 = ssg.recall_hits(ids32, truth, 10) / (nq * 10.0)
+        same = bool(torch.equal(g32.deg, g_mp.deg) and torch.equal(g32.adj, g_mp.adj))
+        fp32_arm = {"build_s_per_1M": g32.stats["ms_total"] / 1000.0 * 1e6 / w.n,
+                    "ms_knn": g32.stats["ms_knn"], "recall@10": rec32, "L_search": ls_used,
+                    "edge_sets_identical": same,
+                    "mixed_over_fp32_speedup": g32.stats["ms_total"] / float(np.mean(build_ms))}
+        del g32, g_mp, ids32
+
     # roofline of the dominant kernel: the distance GEMM + top-K selection
     peaks = load_peaks()
     gemm_ms = float(np.mean([s["ms_knn_gemm"] for s in stats]))
@@ -452,6 +467,7 @@ def run_gpu(args):
                        "ms_connect", "ms_total")},
         "ground_truth_ms": float(np.mean(gt_ms)),
         "serving": serving,
+        "fp32_path": fp32_arm,
         "counters": {k: st0[k] for k in ("n_repair", "n_angle_fp64", "n_order_fp64",
                                          "n_knn_fallback_rows", "max_indegree", "exact_mode")},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -479,6 +495,8 @@ def main():
     ap.add_argument("--target-recall", type=float, default=0.95)
     ap.add_argument("--ref-nodes", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-arm", dest="fp32_arm", action="store_false",
+                    help="skip the one plain-FP32 build reported beside the mixed-precision path")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="length of the serving run (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="requests per second offered")

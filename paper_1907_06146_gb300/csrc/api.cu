@@ -151,7 +151,7 @@ ssg_status ssg_knn(const float* base, int64_t n, int32_t d, int32_t K, ssg_preci
     const bool tc = prec != SSG_PREC_FP32 && g.info.bf16_exact && knn_tc_available(d);
     SSG_REQUIRE(prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
                 "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
-                "and 2 d max|x|^2 <= 2^24");
+                "and 2 d max|x|^2 <= 2^24 (4 d max|x|^2 with negative values)");
     if (tc)
       knn_exact_tc(g.rows.p, n, g.rows.ld, g.norms.p, g.rows.p, n, g.rows.ld, g.norms.p, d, 1, K,
                    knn_id, knn_d2, st, nullptr);
@@ -175,14 +175,15 @@ ssg_status ssg_knn_query(const float* base, int64_t n, int32_t d, const float* q
     ingest_all(queries, nq, d, st, gq, true);
     DataInfo info;
     const float ma = std::max(gb.info.max_abs, gq.info.max_abs);
-    info.exact = gb.info.exact && gq.info.exact && 2.0 * d * (double)ma * ma <= 16777216.0;
+    info.nonneg = gb.info.nonneg && gq.info.nonneg;
+    info.exact = gb.info.exact && gq.info.exact && exact_bound(d, ma, info.nonneg);
     info.bf16_exact = info.exact && ma <= 256.f;
     info.max_norm = gb.info.max_norm;
     info.max_abs = ma;
     const bool tc = prec != SSG_PREC_FP32 && info.bf16_exact && knn_tc_available(d);
     SSG_REQUIRE(prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
                 "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
-                "and 2 d max|x|^2 <= 2^24");
+                "and 2 d max|x|^2 <= 2^24 (4 d max|x|^2 with negative values)");
     if (tc)
       knn_exact_tc(gq.rows.p, nq, gq.rows.ld, gq.norms.p, gb.rows.p, n, gb.rows.ld, gb.norms.p, d,
                    0, k, ids, d2, st, nullptr);
@@ -395,7 +396,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     const bool tc = opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact && knn_tc_available(d);
     SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
                 "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
-                "and 2 d max|x|^2 <= 2^24");
+                "and 2 d max|x|^2 <= 2^24 (4 d max|x|^2 with negative values)");
     t_knn.start();
     KnnResult kr;
     if (tc)

@@ -249,10 +249,18 @@ constexpr double U32 = 5.9604644775390625e-08;  // 2^-24
 
 // Dataset facts gathered at ingest.
 struct DataInfo {
-  int exact;        // all values integers with 2 * d * max|x|^2 <= 2^24: fp32 sums exact
+  int exact;        // all values integers and every squared distance, norm and partial sum
+                    // an integer below 2^24 (2 d max|x|^2 <= 2^24 for non-negative data,
+                    // 4 d max|x|^2 <= 2^24 otherwise): fp32 sums are exact
   int bf16_exact;   // exact and max|x| <= 256: bf16 holds every value
+  int nonneg;       // no negative value
   float max_norm;   // max over rows of the Euclidean norm (fp32)
   float max_abs;
 };
+
+// Exactness of fp32 distance arithmetic on integer data (see DataInfo::exact).
+inline bool exact_bound(int d, double max_abs, bool nonneg) {
+  return (nonneg ? 2.0 : 4.0) * d * max_abs * max_abs <= 16777216.0;
+}
 
 }  // namespace ssg

@@ -28,29 +28,33 @@ namespace ssg {
 // ---------------------------------------------------------------------------------------
 __global__ void k_row_stats(const float* __restrict__ X, int64_t n, int d, int ld,
                             float* __restrict__ norms, unsigned* __restrict__ max_norm_bits,
-                            unsigned* __restrict__ max_abs_bits, int* __restrict__ non_integer) {
+                            unsigned* __restrict__ max_abs_bits, int* __restrict__ non_integer,
+                            int* __restrict__ negative) {
   int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
   const int lane = lane_id();
   const float* x = X + row * ld;
   float s = 0.f, mx = 0.f;
-  int bad = 0;
+  int bad = 0, neg = 0;
   for (int t = lane; t < d; t += 32) {
     float v = x[t];
     s = fmaf(v, v, s);
     mx = fmaxf(mx, fabsf(v));
     bad |= (v != rintf(v));
+    neg |= (v < 0.f);
   }
   for (int o = 16; o > 0; o >>= 1) {
     s += __shfl_xor_sync(0xffffffffu, s, o);
     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    neg |= __shfl_xor_sync(0xffffffffu, neg, o);
   }
   if (lane == 0) {
     if (norms) norms[row] = s;
     atomicMax(max_norm_bits, __float_as_uint(sqrtf(s)));
     atomicMax(max_abs_bits, __float_as_uint(mx));
     if (bad) atomicOr(non_integer, 1);
+    if (neg) atomicOr(negative, 1);
   }
 }
 
@@ -426,11 +430,11 @@ void pad_rows(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out
 void ingest(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out, float* norms,
             DataInfo* info) {
   pad_rows(X, n, d, st, out);
-  Scratch<unsigned> facts(3, st);
-  SSG_CUDA(cudaMemsetAsync(facts.p, 0, 3 * sizeof(unsigned), st));
+  Scratch<unsigned> facts(4, st);
+  SSG_CUDA(cudaMemsetAsync(facts.p, 0, 4 * sizeof(unsigned), st));
   SSG_LAUNCH(k_row_stats, (unsigned)ceil_div(n, 8), 256, 0, st, out.p, n, d, out.ld, norms,
-             facts.p, facts.p + 1, (int*)facts.p + 2);
-  unsigned h[3];
+             facts.p, facts.p + 1, (int*)facts.p + 2, (int*)facts.p + 3);
+  unsigned h[4];
   SSG_CUDA(cudaMemcpyAsync(h, facts.p, sizeof(h), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
   float mn, ma;
@@ -438,8 +442,8 @@ void ingest(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out, 
   memcpy(&ma, &h[1], 4);
   info->max_norm = mn;
   info->max_abs = ma;
-  const double bound = 2.0 * d * (double)ma * (double)ma;
-  info->exact = (h[2] == 0) && bound <= 16777216.0;
+  info->nonneg = h[3] == 0;
+  info->exact = (h[2] == 0) && exact_bound(d, ma, info->nonneg);
   info->bf16_exact = info->exact && ma <= 256.f;
 }
 

@@ -1,21 +1,29 @@
-// Exact kNN graph on the 5th-generation tensor cores (tcgen05, sm_103a) for inputs that
-// bf16 holds exactly (integers with |x| <= 256 and 2 d max|x|^2 <= 2^24: every product
-// and every partial sum of the fp32 accumulation is an integer below 2^24, so the
-// distance |x|^2 + |y|^2 - 2 x.y comes out exact, whatever the summation order).
+// Exact kNN graph on the 5th-generation tensor cores (tcgen05, sm_103a) for integer data
+// that bf16 holds exactly (|x| <= 256, and the bounds of DataInfo::exact).
+//
+// The GEMM is augmented so that the accumulator already holds what the threshold test
+// needs: A = [x | 1 1 1 1 0..], B = [y | -p1 -p2 -p3 -p4 0..] with p1 + .. + p4 = |y|^2 / 2
+// (bf16 parts of an integer or half-integer below 2^23), so acc = x.y - |y|^2 / 2 and
+// d2 = |x|^2 - 2 acc.  Every product and partial sum is a multiple of 1/2 below 2^23 in
+// magnitude (2 d max|x|^2 <= 2^24 for non-negative data, 4 d max|x|^2 <= 2^24 otherwise),
+// so the accumulation is exact in fp32 whatever its order, and so is d2.
 //
 // Persistent kernel, one CTA per SM, 10 warps:
 //   warp 0      TMA producer: the CTA's 256 query rows (A, resident per row block) and a
-//               pipeline of 128-column base tiles (B), both bf16 with 128-byte swizzle;
+//               pipeline of 128-column base tiles (B), bf16 with 128-byte swizzle, plus the
+//               16-element augmentation rows with 32-byte swizzle;
 //   warp 1      allocates 512 TMEM columns and issues tcgen05.mma: for every B tile two
 //               128x128 accumulators (the two 128-row halves of A) into one of two TMEM
 //               buffers, so the epilogue drains one buffer while the MMAs fill the other;
-//   warps 2..9  epilogue, one thread per query row (TMEM lane): tcgen05.ld 32 columns at
-//               a time, d2 = |x|^2 + |y|^2 - 2 acc, and every value below the row's
-//               threshold is appended to the row's buffer in global scratch (L2); a warp
-//               compacts a full buffer with a register bitonic sort (top-KS, new
-//               threshold).  Columns arrive in increasing id order, so "d2 < threshold"
-//               also settles equal distances by id.  The row's own column (self) takes
-//               one extra slot and is dropped at output.
+//   warps 2..9  epilogue, one thread per query row (TMEM lane): tcgen05.ld 64 columns at
+//               a time, their largest accumulator against the row's threshold (a tree of
+//               three-input maxes), and only where some lane passes, the passing values go
+//               to the row's buffer in global scratch (L2); a warp compacts a full buffer
+//               with a register bitonic sort (top-KS, new threshold).  The row's own column
+//               (self) takes one extra slot and is dropped at output.
+// Columns are visited in BN-wide tiles, in id order or (large self-joins) nearest cluster
+// first; in id order "d2 < threshold" also settles equal distances by id, otherwise ties
+// are admitted and settled by the compaction.
 // Every wait on an mbarrier is bounded (about 2 s); a wait that runs out sets an error
 // word, tells the other roles to stop, and the CTA releases its TMEM and exits.
 #include <cuda.h>
@@ -35,6 +43,8 @@ constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + EPI_WARPS * 32;
 constexpr int TMEM_COLS = 512;        // 2 buffers x 2 halves x 128 fp32 columns
 constexpr int MAX_STAGES = 6;
+constexpr int AUG = 16;               // augmentation K-step (bf16 elements)
+constexpr int AUG_BYTES = AUG * 2;    // one augmentation row: 32 bytes
 // tcgen05 instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
 // K-major, N = 128, M = 128.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -135,13 +145,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 // Wait for the outstanding TMEM loads and mark v as written by the wait, so that the
 // compiler cannot move a use of v (filled asynchronously by tcgen05.ld) above it.
 __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]),
+                 "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]),
+                 "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]),
+                 "+r"(v[30]), "+r"(v[31])
+               :
+               : "memory");
+}
+// Marks v as written here (after a preceding tcgen05.wait::ld), so that its uses stay
+// below the wait.
+__device__ __forceinline__ void tmem_dep(uint32_t (&v)[32]) {
+  asm volatile(""
                : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
                  "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
                  "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]),
@@ -163,11 +183,24 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// The same for the augmentation step: K-major, 32-byte swizzle (rows of 32 bytes, 8-row
+// groups 256 bytes apart).
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(256 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;
+  return d;
+}
+
 struct TcArgs {
-  const float* a_norm;
-  const float* b_norm;
-  int64_t na, nb;
-  int kchunks;  // padded d / 64
+  const float* a_norm;  // |x|^2 of the stored query rows (exact integers)
+  int64_t na;           // query rows
+  int64_t nb;           // base rows: stored column positions >= nb are padding
+  int64_t ntiles;       // BN-column tiles of the base
+  int kchunks;          // padded d / 64
   int stages;
   int self;
   int KS, K;
@@ -175,21 +208,82 @@ struct TcArgs {
   int32_t* out_id;
   float* out_d2;
   int* err;
+  const int32_t* perm;        // stored position -> original id (null: the identity)
+  const int32_t* tile_order;  // per cluster, the ntiles tile indices (null: in order)
+  const int32_t* rb_cluster;  // cluster of each block of BM stored query rows
 };
+
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// Largest of 32 accumulators: a depth-4 tree of three-input maxes.
+__device__ __forceinline__ float max32(const uint32_t (&v)[32]) {
+  float a[11];
+#pragma unroll
+  for (int i = 0; i < 10; ++i)
+    a[i] = fmax3(__uint_as_float(v[3 * i]), __uint_as_float(v[3 * i + 1]),
+                 __uint_as_float(v[3 * i + 2]));
+  a[10] = fmaxf(__uint_as_float(v[30]), __uint_as_float(v[31]));
+  const float b0 = fmax3(a[0], a[1], a[2]), b1 = fmax3(a[3], a[4], a[5]);
+  const float b2 = fmax3(a[6], a[7], a[8]), b3 = fmaxf(a[9], a[10]);
+  return fmaxf(fmax3(b0, b1, b2), b3);
+}
+
+// Parks 32 accumulators in a thread's stash: float4 slots XOR-swizzled by sw = lane & 7,
+// so 8 lanes store to 8 different bank groups.
+__device__ __forceinline__ void stash32(float* st, int sw, const uint32_t (&v)[32]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    *(float4*)(st + ((k ^ sw) << 2)) =
+        make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                    __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
+}
+
+// Appends the parked accumulators above ts to a row's buffer as (|x|^2 - 2 acc, column id)
+// keys; column e of the chunk is stored position jc + e (padding from nb on), mapped
+// through perm when the columns are stored in cluster order.  Out of line: once the
+// threshold has settled it runs for few chunks, and one copy keeps the scan loop small in
+// the instruction cache.
+__device__ __noinline__ int append_stash(const float* st, int sw, float ts, float nx, int32_t jc,
+                                         int64_t nb, const int32_t* __restrict__ perm,
+                                         uint64_t* buf, int cnt) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float4 q = *(const float4*)(st + ((k ^ sw) << 2));
+    m |= ((q.x > ts ? 1u : 0u) | (q.y > ts ? 2u : 0u) | (q.z > ts ? 4u : 0u) |
+          (q.w > ts ? 8u : 0u))
+         << (4 * k);
+  }
+  while (m) {
+    const int e = __ffs(m) - 1;
+    m &= m - 1;
+    const int32_t j = jc + e;
+    if (j >= nb) break;  // padding columns come last within a chunk
+    const float acc = st[(((e >> 2) ^ sw) << 2) | (e & 3)];
+    buf[cnt++] = make_key(fmaf(-2.f, acc, nx), perm ? perm[j] : j);
+  }
+  return cnt;
+}
 
 template <int C>
 __global__ void __launch_bounds__(THREADS, 1)
 k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+         const __grid_constant__ CUtensorMap tmAaug, const __grid_constant__ CUtensorMap tmBaug,
          TcArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = p.stages;
-  const uint32_t a_bytes = (uint32_t)p.kchunks * BM * 128;
-  const uint32_t b_bytes = (uint32_t)p.kchunks * BN * 128;
+  const uint32_t a_main = (uint32_t)p.kchunks * BM * 128;
+  const uint32_t a_bytes = a_main + BM * AUG_BYTES;
+  const uint32_t b_main = (uint32_t)p.kchunks * BN * 128;
+  const uint32_t b_bytes = b_main + BN * AUG_BYTES;
   unsigned char* sA = sm;
   unsigned char* sB = sA + a_bytes;
-  float* nyw = (float*)(sB + (size_t)S * b_bytes);
-  float* stash = nyw + EPI_WARPS * BN;  // 32 floats per epilogue thread
+  float* stash = (float*)(sB + (size_t)S * b_bytes);  // 32 floats per epilogue thread
   uint64_t* bars = (uint64_t*)(stash + EPI_WARPS * 32 * 32);
   uint64_t* a_full = bars;
   uint64_t* a_empty = bars + 1;
@@ -225,7 +319,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   const uint32_t tmem_base = *tmem_slot;
 
   const int64_t nrb = (p.na + BM - 1) / BM;
-  const int64_t nct = (p.nb + BN - 1) / BN;
+  const int64_t ntiles = p.ntiles;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -240,7 +334,12 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         for (int kc = 0; kc < p.kchunks; ++kc)
           tma_load_2d(smem_u32(sA + (size_t)kc * BM * 128), &tmA, smem_u32(a_full), kc * 64,
                       (int)(rb * BM));
-        for (int64_t ct = 0; ct < nct; ++ct, ++it) {
+        tma_load_2d(smem_u32(sA + a_main), &tmAaug, smem_u32(a_full), 0, 0);
+        const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * ntiles : nullptr;
+        int64_t tn = tl ? tl[0] : 0;  // tile index, read one tile ahead
+        for (int64_t i = 0; i < ntiles; ++i, ++it) {
+          const int j0 = (int)(tn * BN);
+          if (i + 1 < ntiles) tn = tl ? tl[i + 1] : i + 1;
           const int s = (int)(it % S);
           const uint32_t ph = (uint32_t)((it / S) & 1);
           ok = mbar_wait(smem_u32(b_empty + s), ph ^ 1, abort_flag);
@@ -249,7 +348,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           unsigned char* dst = sB + (size_t)s * b_bytes;
           for (int kc = 0; kc < p.kchunks; ++kc)
             tma_load_2d(smem_u32(dst + (size_t)kc * BN * 128), &tmB, smem_u32(b_full + s), kc * 64,
-                        (int)(ct * BN));
+                        j0);
+          tma_load_2d(smem_u32(dst + b_main), &tmBaug, smem_u32(b_full + s), 0, j0);
         }
       }
       if (!ok) {
@@ -264,11 +364,12 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       int64_t it = 0;
       int rbi = 0;
       bool ok = true;
-      const int ksteps = p.kchunks * 4;
+      const uint64_t adesc0 = sdesc_sw128(smem_u32(sA));
+      const uint64_t adesc_aug = sdesc_sw32(smem_u32(sA + a_main));
       for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++rbi) {
         ok = mbar_wait(smem_u32(a_full), rbi & 1, abort_flag);
         if (!ok) break;
-        for (int64_t ct = 0; ct < nct; ++ct, ++it) {
+        for (int64_t ct = 0; ct < ntiles; ++ct, ++it) {
           const int s = (int)(it % S);
           const uint32_t ph = (uint32_t)((it / S) & 1);
           const int b = (int)(it & 1);
@@ -277,19 +378,25 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
                mbar_wait(smem_u32(b_full + s), ph, abort_flag);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t bbase = smem_u32(sB + (size_t)s * b_bytes);
-          const uint32_t abase = smem_u32(sA);
-#pragma unroll 1
+          // descriptors of the K-steps: the 14-bit start-address field (bytes / 16) of the
+          // base descriptor plus the step's offset; shared addresses stay below 256 KB, so
+          // the sum never carries out of the field
+          const uint32_t bst = smem_u32(sB + (size_t)s * b_bytes);
+          const uint64_t bdesc0 = sdesc_sw128(bst);
+          const uint64_t bdesc_aug = sdesc_sw32(bst + b_main);
+#pragma unroll
           for (int h = 0; h < 2; ++h) {
             const uint32_t d_tmem = tmem_base + (uint32_t)((b * 2 + h) * BN);
-#pragma unroll 1
-            for (int ks = 0; ks < ksteps; ++ks) {
-              const int kc = ks >> 2, kk = ks & 3;
-              const uint64_t ad =
-                  sdesc_sw128(abase + (uint32_t)(kc * BM * 128 + h * 128 * 128 + kk * 32));
-              const uint64_t bd = sdesc_sw128(bbase + (uint32_t)(kc * BN * 128 + kk * 32));
-              umma_bf16(d_tmem, ad, bd, ks > 0 ? 1u : 0u);
+            for (int kc = 0; kc < p.kchunks; ++kc) {
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad =
+                    adesc0 + (uint64_t)((kc * BM * 128 + h * 128 * 128 + kk * 32) >> 4);
+                const uint64_t bd = bdesc0 + (uint64_t)((kc * BN * 128 + kk * 32) >> 4);
+                umma_bf16(d_tmem, ad, bd, (kc | kk) ? 1u : 0u);
+              }
             }
+            umma_bf16(d_tmem, adesc_aug + (uint64_t)((h * 128 * AUG_BYTES) >> 4), bdesc_aug, 1u);
           }
           umma_commit(smem_u32(b_empty + s));
           umma_commit(smem_u32(t_full + b));
@@ -308,7 +415,9 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     const int h = ew >> 2;          // which 128-row half
     const int q = warp & 3;         // TMEM lane quadrant this warp may access
     const int row_in_cta = h * 128 + q * 32 + lane;
-    float* ny = nyw + ew * BN;
+    float* st = stash + (size_t)(ew * 32 + lane) * 32;
+    const int sw = lane & 7;
+    const bool strict = p.tile_order == nullptr;
     int64_t it = 0;
     bool ok = true;
     const float INF = __int_as_float(0x7f800000);
@@ -318,25 +427,13 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       float tau = INF;
       int cnt = 0;
       uint64_t* buf = p.rowbuf + ((size_t)blockIdx.x * BM + row_in_cta) * C;
-      // column norms of the next tile, loaded one tile ahead
-      float nyr[BN / 32];
-#pragma unroll
-      for (int c = 0; c < BN / 32; ++c) {
-        const int64_t jj = c * 32 + lane;
-        nyr[c] = jj < p.nb ? p.b_norm[jj] : INF;
-      }
-      for (int64_t ct = 0; ct < nct; ++ct, ++it) {
+      const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * ntiles : nullptr;
+      int64_t tn = tl ? tl[0] : 0;  // tile index, read one tile ahead
+      for (int64_t i = 0; i < ntiles; ++i, ++it) {
+        const int32_t j0 = (int32_t)(tn * BN);
+        if (i + 1 < ntiles) tn = tl ? tl[i + 1] : i + 1;
         const int b = (int)(it & 1);
         const uint32_t tph = (uint32_t)((it >> 1) & 1);
-        const int64_t j0 = ct * BN;
-#pragma unroll
-        for (int c = 0; c < BN / 32; ++c) ny[c * 32 + lane] = nyr[c];
-        __syncwarp();
-#pragma unroll
-        for (int c = 0; c < BN / 32; ++c) {
-          const int64_t jj = j0 + BN + c * 32 + lane;
-          nyr[c] = jj < p.nb ? p.b_norm[jj] : INF;
-        }
         ok = mbar_wait(smem_u32(t_full + b), tph, abort_flag);
         if (!__all_sync(0xffffffffu, ok)) {
           ok = false;
@@ -344,53 +441,41 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         }
         tc_fence_after();
         const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)((b * 2 + h) * BN);
-        // d2 < tau  <=>  |y|^2 - 2 acc < tau - |x|^2, all exact integers here: per value
-        // one multiply-add, one compare and one bit of a pass mask.  A thread with passing
-        // values parks the chunk in its shared-memory stash (float4 slots XOR-swizzled by
-        // lane, so 8 lanes store to 8 different bank groups) and appends only the set bits.
-        const float tp = tau - nx;
-        float* st = stash + (size_t)(ew * 32 + lane) * 32;
-        const int sw = lane & 7;
-        auto scan32 = [&](const uint32_t(&v)[32], int c) {
-          float x[32];
-          uint32_t m = 0;
-#pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            x[e] = fmaf(-2.f, __uint_as_float(v[e]), ny[c * 32 + e]);
-            m |= (x[e] < tp ? 1u : 0u) << e;
-          }
-          if (m) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              *(float4*)(st + ((k ^ sw) << 2)) =
-                  make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
-            const int32_t jc = (int32_t)(j0 + c * 32);
-            do {
-              const int e = __ffs(m) - 1;
-              m &= m - 1;
-              const float xv = st[(((e >> 2) ^ sw) << 2) | (e & 3)];
-              buf[cnt++] = make_key(xv + nx, jc + e);
-            } while (m);
+        // d2 < tau  <=>  acc > (|x|^2 - tau) / 2 (exact); ties admitted (ts just below the
+        // bound) unless the columns arrive in id order.  tau = inf gives ts = -inf.
+        const float thr = 0.5f * (nx - tau);
+        const float ts = strict ? thr : nextafterf(thr, -INF);
+        auto scan64 = [&](const uint32_t(&va)[32], const uint32_t(&vb)[32], int c) {
+          const bool pa = max32(va) > ts;
+          const bool pb = max32(vb) > ts;
+          if (__any_sync(0xffffffffu, pa || pb)) {
+            if (pa) {
+              stash32(st, sw, va);
+              cnt = append_stash(st, sw, ts, nx, j0 + c * 32, p.nb, p.perm, buf, cnt);
+            }
+            if (pb) {
+              stash32(st, sw, vb);
+              cnt = append_stash(st, sw, ts, nx, j0 + c * 32 + 32, p.nb, p.perm, buf, cnt);
+            }
+            __syncwarp();
           }
         };
-        // The load of chunk c + 1 is in flight while chunk c is scanned; the accumulator
-        // buffer is handed back to the MMA warp as soon as the last chunk is in registers.
+        // two passes of 64 columns; the accumulator buffer goes back to the MMA warp as soon
+        // as the second pass is in registers
         uint32_t v0[32], v1[32];
-        tmem_ld32(taddr, v0);
-        tmem_wait_ld(v0);
-        tmem_ld32(taddr + 32, v1);
-        scan32(v0, 0);
-        tmem_wait_ld(v1);
-        tmem_ld32(taddr + 64, v0);
-        scan32(v1, 1);
-        tmem_wait_ld(v0);
-        tmem_ld32(taddr + 96, v1);
-        scan32(v0, 2);
-        tmem_wait_ld(v1);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(t_empty + b));
-        scan32(v1, 3);
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; c += 2) {
+          tmem_ld32(taddr + (uint32_t)c * 32, v0);
+          tmem_ld32(taddr + (uint32_t)c * 32 + 32, v1);
+          tmem_wait_ld(v0);
+          tmem_dep(v1);
+          if (c + 2 == BN / 32) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(t_empty + b));
+          }
+          scan64(v0, v1, c);
+        }
         unsigned need = __ballot_sync(0xffffffffu, cnt > C - BN);
         while (need) {
           const int l = __ffs(need) - 1;
@@ -413,11 +498,12 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         float t2;
         const int c2 = compact_row<C>(lb, __shfl_sync(0xffffffffu, cnt, l), p.KS, &t2);
         if (r >= p.na) continue;
+        const int64_t ro = p.perm ? (int64_t)p.perm[r] : r;  // the row's original id
         int selfpos = c2;
         if (p.self) {
           for (int e0 = 0; e0 < c2; e0 += 32) {
             const int e = e0 + lane;
-            const unsigned m = __ballot_sync(0xffffffffu, e < c2 && key_id(lb[e]) == (int32_t)r);
+            const unsigned m = __ballot_sync(0xffffffffu, e < c2 && key_id(lb[e]) == (int32_t)ro);
             if (m) {
               selfpos = e0 + __ffs(m) - 1;
               break;
@@ -427,8 +513,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         for (int t = lane; t < p.K; t += 32) {
           const int src = t < selfpos ? t : t + 1;
           const uint64_t key = src < c2 ? lb[src] : KEY_NONE;
-          p.out_id[r * p.K + t] = key == KEY_NONE ? -1 : key_id(key);
-          p.out_d2[r * p.K + t] = key == KEY_NONE ? INF : key_dist(key);
+          p.out_id[ro * p.K + t] = key == KEY_NONE ? -1 : key_id(key);
+          p.out_d2[ro * p.K + t] = key == KEY_NONE ? INF : key_dist(key);
         }
         __syncwarp();
       }
@@ -446,15 +532,46 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   }
 }
 
+// bf16 copy with rows padded to dp; with perm, stored row r holds row perm[r] (and its norm).
 __global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int d, int ld,
-                          __nv_bfloat16* __restrict__ Y, int dp) {
+                          __nv_bfloat16* __restrict__ Y, int dp, const int32_t* __restrict__ perm,
+                          const float* __restrict__ norm_in, float* __restrict__ norm_out) {
   const int64_t total = n * (int64_t)dp;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / dp;
     const int c = (int)(i - r * dp);
-    Y[i] = __float2bfloat16_rn(c < d ? X[r * ld + c] : 0.f);
+    const int64_t src = perm ? (int64_t)perm[r] : r;
+    Y[i] = __float2bfloat16_rn(c < d ? X[src * ld + c] : 0.f);
+    if (norm_out && c == 0) norm_out[r] = norm_in[src];
   }
+}
+
+// Augmentation rows of the base: -|y|^2 / 2 as four bf16 parts (each the bf16 rounding of
+// what the previous ones leave), then zeros.  err is set if a row's parts do not add up
+// to the value exactly.
+__global__ void k_aug_rows(const float* __restrict__ norm, int64_t n, __nv_bfloat16* __restrict__ aug,
+                           int* __restrict__ err) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    float rest = -0.5f * norm[r];
+    __nv_bfloat16 part[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      part[k] = __float2bfloat16_rn(rest);
+      rest -= __bfloat162float(part[k]);
+    }
+    if (rest != 0.f) atomicOr(err, 1);
+    __nv_bfloat16* o = aug + r * AUG;
+#pragma unroll
+    for (int k = 0; k < AUG; ++k) o[k] = k < 4 ? part[k] : __float2bfloat16_rn(0.f);
+  }
+}
+
+// Augmentation rows of the queries: four ones, then zeros (BM identical rows).
+__global__ void k_aug_ones(__nv_bfloat16* __restrict__ aug) {
+  for (int i = threadIdx.x; i < BM * AUG; i += blockDim.x)
+    aug[i] = __float2bfloat16_rn((i % AUG) < 4 ? 1.f : 0.f);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -470,33 +587,39 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-CUtensorMap make_map(const __nv_bfloat16* ptr, int64_t rows, int dp, int box_rows) {
+// 2-D bf16 tensor map over rows of width elements: boxes of box_w x box_rows.
+CUtensorMap make_map(const __nv_bfloat16* ptr, int64_t rows, int width, int box_w, int box_rows,
+                     CUtensorMapSwizzle swz) {
   CUtensorMap m;
-  cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)width * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ptr, dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   SSG_REQUIRE(r == CUDA_SUCCESS, SSG_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return m;
 }
 
 size_t tc_smem_bytes(int kchunks, int stages) {
-  return 1024 + (size_t)kchunks * BM * 128 + (size_t)stages * kchunks * BN * 128 +
-         EPI_WARPS * BN * sizeof(float) + EPI_WARPS * 32 * 32 * sizeof(float) + sizeof(uint64_t) * (2 + 2 * MAX_STAGES + 4) + 16;
+  return 1024 + (size_t)kchunks * BM * 128 + BM * AUG_BYTES +
+         (size_t)stages * (kchunks * BN * 128 + BN * AUG_BYTES) +
+         EPI_WARPS * 32 * 32 * sizeof(float) + sizeof(uint64_t) * (2 + 2 * MAX_STAGES + 4) + 16;
 }
 
+struct TcMaps {
+  CUtensorMap a, b, a_aug, b_aug;
+};
+
 template <int C>
-void launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, TcArgs& a, int grid, size_t smem,
-               cudaStream_t st) {
+void launch_tc(const TcMaps& m, TcArgs& a, int grid, size_t smem, cudaStream_t st) {
   static size_t attr = 0;
   if (smem > attr) {
     SSG_CUDA(cudaFuncSetAttribute(k_knn_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }
-  SSG_LAUNCH(k_knn_tc<C>, grid, THREADS, smem, st, ma, mb, a);
+  SSG_LAUNCH(k_knn_tc<C>, grid, THREADS, smem, st, m.a, m.b, m.a_aug, m.b_aug, a);
 }
 
 }  // namespace
@@ -525,37 +648,75 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   SSG_REQUIRE(tc_smem_bytes(kchunks, stages) <= 225 * 1024, SSG_EINVAL,
               "tensor-core kNN: d = %d is too large for the shared-memory pipeline", d);
   const int KS = self ? K + 1 : K;
+  // Near-first column order for large self-joins with a deep top-K (where the streaming
+  // threshold otherwise falls slowly and many candidates are appended).
+  KnnOrder ord;
+  Scratch<float> norm_p;
+  const bool ordered = self && na >= (1 << 16) && K >= 16 && knn_order_fits(na, BN);
+  if (ordered) {
+    knn_cluster_order(A, lda, d, na, BM, BN, st, ord);
+    norm_p.alloc((size_t)na, st);
+  }
   Scratch<__nv_bfloat16> ab((size_t)na * dp, st);
   Scratch<__nv_bfloat16> bb;
   const int cgrid = 8 * num_sms();
-  SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, A, na, d, lda, ab.p, dp);
+  SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, A, na, d, lda, ab.p, dp,
+             ordered ? (const int32_t*)ord.perm.p : nullptr, a_norm, ordered ? norm_p.p : nullptr);
+  if (ordered) a_norm = b_norm = norm_p.p;
   const __nv_bfloat16* bptr = ab.p;
   if (!self) {
     bb.alloc((size_t)nb * dp, st);
-    SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, B, nb, d, ldb, bb.p, dp);
+    SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, B, nb, d, ldb, bb.p, dp, (const int32_t*)nullptr,
+               (const float*)nullptr, (float*)nullptr);
     bptr = bb.p;
   }
-  const CUtensorMap ma = make_map(ab.p, na, dp, BM);
-  const CUtensorMap mb = make_map(bptr, nb, dp, BN);
+  Scratch<__nv_bfloat16> aug_b((size_t)nb * AUG, st), aug_a((size_t)BM * AUG, st);
+  Scratch<int> err(1, st);
+  SSG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+  SSG_LAUNCH(k_aug_rows, (unsigned)std::min<int64_t>(ceil_div(nb, 256), cgrid), 256, 0, st, b_norm,
+             nb, aug_b.p, err.p);
+  SSG_LAUNCH(k_aug_ones, 1, 256, 0, st, aug_a.p);
+  TcMaps maps;
+  maps.a = make_map(ab.p, na, dp, 64, BM, CU_TENSOR_MAP_SWIZZLE_128B);
+  maps.b = make_map(bptr, nb, dp, 64, BN, CU_TENSOR_MAP_SWIZZLE_128B);
+  maps.a_aug = make_map(aug_a.p, BM, AUG, AUG, BM, CU_TENSOR_MAP_SWIZZLE_32B);
+  maps.b_aug = make_map(aug_b.p, nb, AUG, AUG, BN, CU_TENSOR_MAP_SWIZZLE_32B);
   const int64_t nrb = ceil_div(na, BM);
   const int grid = (int)std::min<int64_t>(nrb, num_sms());
   const int C = KS + BN <= 256 ? 256 : (KS + BN <= 512 ? 512 : 1024);
   Scratch<uint64_t> rowbuf((size_t)grid * BM * C, st);
-  Scratch<int> err(1, st);
-  SSG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
-  TcArgs a{a_norm, b_norm, na, nb, kchunks, stages, self, KS, K, rowbuf.p, out_id, out_d2, err.p};
+  TcArgs a{};
+  a.a_norm = a_norm;
+  a.na = na;
+  a.nb = nb;
+  a.ntiles = ceil_div(nb, BN);
+  a.kchunks = kchunks;
+  a.stages = stages;
+  a.self = self;
+  a.KS = KS;
+  a.K = K;
+  a.rowbuf = rowbuf.p;
+  a.out_id = out_id;
+  a.out_d2 = out_d2;
+  a.err = err.p;
+  if (ordered) {
+    a.perm = ord.perm.p;
+    a.tile_order = ord.tile_order.p;
+    a.rb_cluster = ord.rb_cluster.p;
+  }
   const size_t smem = tc_smem_bytes(kchunks, stages);
   if (gemm_timer) gemm_timer->start();
   if (C == 256)
-    launch_tc<256>(ma, mb, a, grid, smem, st);
+    launch_tc<256>(maps, a, grid, smem, st);
   else if (C == 512)
-    launch_tc<512>(ma, mb, a, grid, smem, st);
+    launch_tc<512>(maps, a, grid, smem, st);
   else
-    launch_tc<1024>(ma, mb, a, grid, smem, st);
+    launch_tc<1024>(maps, a, grid, smem, st);
   if (gemm_timer) gemm_timer->stop();
   int h = 0;
   SSG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
+  SSG_REQUIRE(h != 1, SSG_EINTERNAL, "tensor-core kNN: a squared norm is not split exactly");
   SSG_REQUIRE(h == 0, SSG_ETIMEOUT, "tensor-core kNN: a pipeline wait timed out (code %d)", h);
 }
 

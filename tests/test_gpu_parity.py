@@ -99,6 +99,57 @@ def test_knn_bf16_tensor_cores(ssg, n, d, K):
     np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
 
 
+def test_knn_bf16_near_first_order(ssg):
+    """Self-joins of at least 65536 rows with K >= 16 visit the columns cluster by cluster,
+    nearest clusters first.  Sampled rows against the oracle (self dropped from its K+1
+    nearest), and every row sorted by (d2, id) with distinct ids and no self."""
+    if not _tc(ssg):
+        pytest.skip("bf16 tensor-core kNN needs sm_103")
+    w = synth.sift_like(n=70_001, nq=10)
+    K = 200
+    ids, d2 = ssg.knn(_cuda(w.base), K, prec="bf16")
+    ids, d2 = _np(ids), _np(d2)
+    rng = np.random.default_rng(5)
+    rows = np.sort(rng.choice(w.n, 160, replace=False))
+    rows[-1] = w.n - 1
+    ref_ids, ref_d2 = oracle.knn_queries(w.base, w.base[rows], K + 1)
+    for i, r in enumerate(rows):
+        keep = ref_ids[i] != r
+        np.testing.assert_array_equal(ids[r], ref_ids[i][keep][:K])
+        np.testing.assert_array_equal(d2[r], ref_d2[i][keep][:K].astype(np.float32))
+    assert (ids >= 0).all() and (ids < w.n).all()
+    assert not (ids == np.arange(w.n)[:, None]).any()
+    srt = np.sort(ids, axis=1)
+    assert not (srt[:, 1:] == srt[:, :-1]).any()
+    order_ok = (d2[:, 1:] > d2[:, :-1]) | ((d2[:, 1:] == d2[:, :-1]) & (ids[:, 1:] > ids[:, :-1]))
+    assert order_ok.all()
+    sel = rng.choice(w.n, 500, replace=False)
+    x = w.base[sel].astype(np.float64)
+    y = w.base[ids[sel]].astype(np.float64)
+    np.testing.assert_array_equal(d2[sel], ((x[:, None, :] - y) ** 2).sum(-1).astype(np.float32))
+
+
+def test_knn_bf16_signed_integers(ssg):
+    """Negative values: the tensor-core path needs 4 d max|x|^2 <= 2^24 (squared distances
+    up to 4 d max|x|^2 must stay exact); within it bf16 is taken and exact, beyond it auto
+    falls back to the fp32 path (still exact) and an explicit bf16 request is refused."""
+    if not _tc(ssg):
+        pytest.skip("bf16 tensor-core kNN needs sm_103")
+    rng = np.random.default_rng(31)
+    inside = rng.integers(-100, 101, size=(2100, 64)).astype(np.float32)   # 4*64*100^2 < 2^24
+    ids, d2 = ssg.knn(_cuda(inside), 30, prec="bf16")
+    ref_ids, ref_d2 = oracle.knn_rows(inside, 30)
+    np.testing.assert_array_equal(_np(ids), ref_ids)
+    np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
+    beyond = rng.integers(-200, 201, size=(1500, 128)).astype(np.float32)  # 4*128*200^2 > 2^24
+    ids, d2 = ssg.knn(_cuda(beyond), 30, prec="auto")
+    ref_ids, ref_d2 = oracle.knn_rows(beyond, 30)
+    np.testing.assert_array_equal(_np(ids), ref_ids)
+    np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
+    with pytest.raises(ssg.SSGError):
+        ssg.knn(_cuda(beyond), 30, prec="bf16")
+
+
 def test_knn_wide_integer_rows_use_fp32(ssg):
     """d > 128 does not fit the tensor-core pipeline: auto falls back to the (exact) fp32
     path and an explicit bf16 request is refused."""
