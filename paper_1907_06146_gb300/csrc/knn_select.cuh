@@ -80,4 +80,62 @@ __device__ __noinline__ int compact_row(uint64_t* __restrict__ buf, int cnt, int
   return keep;
 }
 
+// Threshold step of a row's buffer without sorting: finds the KS-th smallest distance t
+// by bisection over the 32-bit order keys (each step counts the entries at or below the
+// midpoint), then keeps, unsorted and in their old relative order, every entry with a
+// distance at most t (all ties at t stay).  Returns the new count with *tau = t, or -1 with
+// the buffer untouched when more than cap entries would stay.  Needs cnt >= KS.
+template <int C>
+__device__ __noinline__ int select_row(uint64_t* __restrict__ buf, int cnt, int KS, int cap,
+                                       float* tau) {
+  constexpr int E = C / 32;
+  const int lane = lane_id();
+  uint32_t k[E];
+  uint64_t v[E];
+  uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = (e << 5) | lane;
+    v[e] = i < cnt ? buf[i] : KEY_NONE;
+    k[e] = (uint32_t)(v[e] >> 32);  // KEY_NONE: above every real key
+    if (i < cnt) {
+      lo = min(lo, k[e]);
+      hi = max(hi, k[e]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  // smallest t in [lo, hi] with at least KS keys <= t (hi qualifies: cnt >= KS)
+  while (lo < hi) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    int c = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) c += k[e] <= mid ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (c >= KS)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  int n = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) n += __popc(__ballot_sync(0xffffffffu, k[e] <= hi));
+  if (n > cap) return -1;
+  int base = 0;
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const unsigned b = __ballot_sync(0xffffffffu, k[e] <= hi);
+    if (k[e] <= hi) buf[base + __popc(b & lt)] = v[e];
+    base += __popc(b);
+  }
+  __syncwarp();
+  *tau = order_bits_float(hi);
+  return base;
+}
+
 }  // namespace ssg

@@ -204,6 +204,7 @@ struct TcArgs {
   int stages;
   int self;
   int KS, K;
+  int trig;             // a row buffer holding more than trig keys is compacted (<= C - BN)
   uint64_t* rowbuf;
   int32_t* out_id;
   float* out_d2;
@@ -476,13 +477,17 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           }
           scan64(v0, v1, c);
         }
-        unsigned need = __ballot_sync(0xffffffffu, cnt > C - BN);
+        // a buffer that the next tile could overflow drops to the entries at or below its
+        // KS-th smallest distance (a full sort only if ties would keep too many)
+        unsigned need = __ballot_sync(0xffffffffu, cnt > p.trig);
         while (need) {
           const int l = __ffs(need) - 1;
           need &= need - 1;
           uint64_t* lb = p.rowbuf + ((size_t)blockIdx.x * BM + h * 128 + q * 32 + l) * C;
+          const int cl = __shfl_sync(0xffffffffu, cnt, l);
           float t2;
-          const int c2 = compact_row<C>(lb, __shfl_sync(0xffffffffu, cnt, l), p.KS, &t2);
+          int c2 = select_row<C>(lb, cl, p.KS, (p.KS + p.trig) / 2, &t2);
+          if (c2 < 0) c2 = compact_row<C>(lb, cl, p.KS, &t2);
           if (lane == l) {
             cnt = c2;
             tau = t2;
@@ -496,7 +501,13 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         const int64_t r = rb * BM + rin;
         uint64_t* lb = p.rowbuf + ((size_t)blockIdx.x * BM + rin) * C;
         float t2;
-        const int c2 = compact_row<C>(lb, __shfl_sync(0xffffffffu, cnt, l), p.KS, &t2);
+        int cl = __shfl_sync(0xffffffffu, cnt, l);
+        if (cl > 256 && cl > p.KS) {
+          const int c1 = select_row<C>(lb, cl, p.KS, 256, &t2);
+          if (c1 >= 0) cl = c1;
+        }
+        const int c2 = cl <= 256 ? compact_row<256>(lb, cl, p.KS, &t2)
+                                 : compact_row<C>(lb, cl, p.KS, &t2);
         if (r >= p.na) continue;
         const int64_t ro = p.perm ? (int64_t)p.perm[r] : r;  // the row's original id
         int selfpos = c2;
@@ -695,6 +706,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   a.self = self;
   a.KS = KS;
   a.K = K;
+  a.trig = C - BN;
   a.rowbuf = rowbuf.p;
   a.out_id = out_id;
   a.out_d2 = out_d2;
