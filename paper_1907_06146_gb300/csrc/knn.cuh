@@ -28,13 +28,13 @@ KnnResult knn_exact(const float* A, int64_t na, int lda, const float* a_norm, co
                     StageTimer* gemm_timer);
 
 // Near-first column order: rows clustered and stored cluster by cluster (perm maps a
-// stored position to the original row); for each cluster the ntiles BN-column tiles of the
+// stored position to the original row, inv the other way); for each cluster the ntiles BN-column tiles of the
 // stored order, nearest cluster first (tile_order, ncl x ntiles); rb_cluster gives the
 // cluster of each block of BM stored rows.
 struct KnnOrder {
   int ncl = 0;
   int64_t ntiles = 0;
-  Scratch<int32_t> perm, tile_order, rb_cluster;
+  Scratch<int32_t> perm, inv, tile_order, rb_cluster;
 };
 bool knn_order_fits(int64_t n, int BN);
 void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN, cudaStream_t st,

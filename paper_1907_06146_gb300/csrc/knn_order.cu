@@ -80,10 +80,13 @@ __global__ void k_update(float* __restrict__ C, const float* __restrict__ sums,
 }
 
 __global__ void k_scatter_perm(const int32_t* __restrict__ label, int64_t n, int* __restrict__ cursor,
-                               int32_t* __restrict__ perm) {
+                               int32_t* __restrict__ perm, int32_t* __restrict__ inv) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    perm[atomicAdd(cursor + label[i], 1)] = (int32_t)i;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int pos = atomicAdd(cursor + label[i], 1);
+    perm[pos] = (int32_t)i;
+    inv[i] = pos;
+  }
 }
 
 // Row c of the table: all clusters by (centroid distance from c, id); c itself first.
@@ -194,6 +197,7 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
   Scratch<int32_t> cl_start((size_t)ncl, st), cl_end((size_t)ncl, st), order((size_t)ncl * ncl, st);
   Scratch<int> cursor((size_t)ncl, st), err(1, st);
   o.perm.alloc((size_t)n, st);
+  o.inv.alloc((size_t)n, st);
   o.tile_order.alloc((size_t)ncl * o.ntiles, st);
   const int64_t nrb = ceil_div(n, BM);
   o.rb_cluster.alloc((size_t)nrb, st);
@@ -201,7 +205,7 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
   SSG_CUDA(cudaMemcpyAsync(cl_end.p, end.data(), sizeof(int32_t) * ncl, cudaMemcpyHostToDevice, st));
   SSG_CUDA(cudaMemcpyAsync(cursor.p, start.data(), sizeof(int32_t) * ncl, cudaMemcpyHostToDevice, st));
   SSG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
-  SSG_LAUNCH(k_scatter_perm, grid, 256, 0, st, label.p, n, cursor.p, o.perm.p);
+  SSG_LAUNCH(k_scatter_perm, grid, 256, 0, st, label.p, n, cursor.p, o.perm.p, o.inv.p);
   const int p2 = next_pow2(ncl);
   SSG_LAUNCH(k_cluster_order, ncl, 256, p2 * sizeof(uint64_t), st, C.p, ncl, dc, p2, order.p);
   SSG_LAUNCH(k_tile_order, ncl, 256, (size_t)((o.ntiles + 31) >> 5) * 4, st, order.p, cl_start.p,

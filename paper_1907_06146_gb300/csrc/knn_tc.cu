@@ -210,6 +210,7 @@ struct TcArgs {
   float* out_d2;
   int* err;
   const int32_t* perm;        // stored position -> original id (null: the identity)
+  const int32_t* inv;         // original id -> stored position
   const int32_t* tile_order;  // per cluster, the ntiles tile indices (null: in order)
   const int32_t* rb_cluster;  // cluster of each block of BM stored query rows
 };
@@ -243,14 +244,12 @@ __device__ __forceinline__ void stash32(float* st, int sw, const uint32_t (&v)[3
                     __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
 }
 
-// Appends the parked accumulators above ts to a row's buffer as (|x|^2 - 2 acc, column id)
-// keys; column e of the chunk is stored position jc + e (padding from nb on), mapped
-// through perm when the columns are stored in cluster order.  Out of line: once the
-// threshold has settled it runs for few chunks, and one copy keeps the scan loop small in
-// the instruction cache.
+// Appends the parked accumulators above ts to a row's buffer as (|x|^2 - 2 acc, stored
+// position) keys; column e of the chunk is stored position jc + e (padding from nb on).
+// Out of line: once the threshold has settled it runs for few chunks, and one copy keeps
+// the scan loop small in the instruction cache.
 __device__ __noinline__ int append_stash(const float* st, int sw, float ts, float nx, int32_t jc,
-                                         int64_t nb, const int32_t* __restrict__ perm,
-                                         uint64_t* buf, int cnt) {
+                                         int64_t nb, uint64_t* buf, int cnt) {
   uint32_t m = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -265,9 +264,22 @@ __device__ __noinline__ int append_stash(const float* st, int sw, float ts, floa
     const int32_t j = jc + e;
     if (j >= nb) break;  // padding columns come last within a chunk
     const float acc = st[(((e >> 2) ^ sw) << 2) | (e & 3)];
-    buf[cnt++] = make_key(fmaf(-2.f, acc, nx), perm ? perm[j] : j);
+    buf[cnt++] = make_key(fmaf(-2.f, acc, nx), j);
   }
   return cnt;
+}
+
+// Maps the ids of a row's first cnt keys through map (stored position -> original id, or
+// back), warp-wide; a sort then settles equal distances by original id.  Without a map
+// nothing changes.
+__device__ __forceinline__ void map_key_ids(uint64_t* buf, int cnt, const int32_t* __restrict__ map) {
+  if (!map) return;
+  __syncwarp();
+  for (int i = lane_id(); i < cnt; i += 32) {
+    const uint64_t k = buf[i];
+    buf[i] = (k & 0xFFFFFFFF00000000ull) | (uint32_t)map[(uint32_t)k];
+  }
+  __syncwarp();
 }
 
 template <int C>
@@ -452,11 +464,11 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           if (__any_sync(0xffffffffu, pa || pb)) {
             if (pa) {
               stash32(st, sw, va);
-              cnt = append_stash(st, sw, ts, nx, j0 + c * 32, p.nb, p.perm, buf, cnt);
+              cnt = append_stash(st, sw, ts, nx, j0 + c * 32, p.nb, buf, cnt);
             }
             if (pb) {
               stash32(st, sw, vb);
-              cnt = append_stash(st, sw, ts, nx, j0 + c * 32 + 32, p.nb, p.perm, buf, cnt);
+              cnt = append_stash(st, sw, ts, nx, j0 + c * 32 + 32, p.nb, buf, cnt);
             }
             __syncwarp();
           }
@@ -487,7 +499,13 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           const int cl = __shfl_sync(0xffffffffu, cnt, l);
           float t2;
           int c2 = select_row<C>(lb, cl, p.KS, (p.KS + p.trig) / 2, &t2);
-          if (c2 < 0) c2 = compact_row<C>(lb, cl, p.KS, &t2);
+          if (c2 < 0) {
+            // too many ties at the threshold: a sort settles them by original id, and the
+            // kept keys go back to stored positions like the ones still to come
+            map_key_ids(lb, cl, p.perm);
+            c2 = compact_row<C>(lb, cl, p.KS, &t2);
+            map_key_ids(lb, c2, p.inv);
+          }
           if (lane == l) {
             cnt = c2;
             tau = t2;
@@ -506,6 +524,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           const int c1 = select_row<C>(lb, cl, p.KS, 256, &t2);
           if (c1 >= 0) cl = c1;
         }
+        map_key_ids(lb, cl, p.perm);
         const int c2 = cl <= 256 ? compact_row<256>(lb, cl, p.KS, &t2)
                                  : compact_row<C>(lb, cl, p.KS, &t2);
         if (r >= p.na) continue;
@@ -713,6 +732,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   a.err = err.p;
   if (ordered) {
     a.perm = ord.perm.p;
+    a.inv = ord.inv.p;
     a.tile_order = ord.tile_order.p;
     a.rb_cluster = ord.rb_cluster.p;
   }

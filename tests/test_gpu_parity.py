@@ -129,6 +129,25 @@ def test_knn_bf16_near_first_order(ssg):
     np.testing.assert_array_equal(d2[sel], ((x[:, None, :] - y) ** 2).sum(-1).astype(np.float32))
 
 
+def test_knn_bf16_near_first_order_duplicates(ssg):
+    """Cluster order with 401 copies of one point: ties at distance 0 outnumber the
+    buffer's room, so the compaction falls back to a sort by (distance, original id)."""
+    if not _tc(ssg):
+        pytest.skip("bf16 tensor-core kNN needs sm_103")
+    w = synth.sift_like(n=66_000, nq=10)
+    base = w.base.copy()
+    base[1000:1400] = base[5]
+    K = 200
+    ids, d2 = ssg.knn(_cuda(base), K, prec="bf16")
+    ids, d2 = _np(ids), _np(d2)
+    rows = np.array([5, 1000, 1200, 1399, 7, 65_999])
+    ref_ids, ref_d2 = oracle.knn_queries(base, base[rows], K + 1)
+    for i, r in enumerate(rows):
+        keep = ref_ids[i] != r
+        np.testing.assert_array_equal(ids[r], ref_ids[i][keep][:K])
+        np.testing.assert_array_equal(d2[r], ref_d2[i][keep][:K].astype(np.float32))
+
+
 def test_knn_bf16_signed_integers(ssg):
     """Negative values: the tensor-core path needs 4 d max|x|^2 <= 2^24 (squared distances
     up to 4 d max|x|^2 must stay exact); within it bf16 is taken and exact, beyond it auto
