@@ -337,7 +337,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      int64_t it = 0;
+      int s = 0;         // B stage of the next tile
+      uint32_t ph = 0;   // and the parity of its use
       int rbi = 0;
       bool ok = true;
       for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++rbi) {
@@ -350,11 +351,9 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         tma_load_2d(smem_u32(sA + a_main), &tmAaug, smem_u32(a_full), 0, 0);
         const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * ntiles : nullptr;
         int64_t tn = tl ? tl[0] : 0;  // tile index, read one tile ahead
-        for (int64_t i = 0; i < ntiles; ++i, ++it) {
+        for (int64_t i = 0; i < ntiles; ++i) {
           const int j0 = (int)(tn * BN);
           if (i + 1 < ntiles) tn = tl ? tl[i + 1] : i + 1;
-          const int s = (int)(it % S);
-          const uint32_t ph = (uint32_t)((it / S) & 1);
           ok = mbar_wait(smem_u32(b_empty + s), ph ^ 1, abort_flag);
           if (!ok) break;
           mbar_expect_tx(smem_u32(b_full + s), b_bytes);
@@ -363,6 +362,10 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             tma_load_2d(smem_u32(dst + (size_t)kc * BN * 128), &tmB, smem_u32(b_full + s), kc * 64,
                         j0);
           tma_load_2d(smem_u32(dst + b_main), &tmBaug, smem_u32(b_full + s), 0, j0);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1;
+          }
         }
       }
       if (!ok) {
@@ -375,6 +378,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       int64_t it = 0;
+      int s = 0;
+      uint32_t ph = 0;
       int rbi = 0;
       bool ok = true;
       const uint64_t adesc0 = sdesc_sw128(smem_u32(sA));
@@ -383,8 +388,6 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         ok = mbar_wait(smem_u32(a_full), rbi & 1, abort_flag);
         if (!ok) break;
         for (int64_t ct = 0; ct < ntiles; ++ct, ++it) {
-          const int s = (int)(it % S);
-          const uint32_t ph = (uint32_t)((it / S) & 1);
           const int b = (int)(it & 1);
           const uint32_t tph = (uint32_t)((it >> 1) & 1);
           ok = mbar_wait(smem_u32(t_empty + b), tph ^ 1, abort_flag) &&
@@ -413,6 +416,10 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           }
           umma_commit(smem_u32(b_empty + s));
           umma_commit(smem_u32(t_full + b));
+          if (++s == S) {
+            s = 0;
+            ph ^= 1;
+          }
         }
         if (ok) umma_commit(smem_u32(a_empty));
       }
