@@ -84,6 +84,17 @@ struct Ingested {
   DataInfo info{};
 };
 
+// The prune on the tensor cores where the data are exact in bf16 (and the pool and degree
+// fit its tile), the fp32 warp prune otherwise; both take the same decisions.
+static void prune_dispatch(bool tc_ok, const float* X, int ld, int d, int64_t n,
+                           const int32_t* pool_id, const int32_t* pool_len, int L, int R,
+                           double cos_a, int32_t* adj, int32_t* deg, Counters* ctr, cudaStream_t st) {
+  if (tc_ok && prune_tc_available(d, L, R))
+    prune_run_tc(X, ld, d, n, pool_id, pool_len, L, R, cos_a, adj, deg, ctr, st);
+  else
+    prune_run(X, ld, d, n, pool_id, pool_len, L, R, cos_a, adj, deg, ctr, st);
+}
+
 static void ingest_all(const float* X, int64_t n, int d, cudaStream_t st, Ingested& g,
                        bool want_norms) {
   if (want_norms) g.norms.alloc((size_t)n, st);
@@ -223,8 +234,8 @@ ssg_status ssg_prune(const float* base, int64_t n, int32_t d, const int32_t* poo
     ingest_all(base, n, d, st, g, false);
     Scratch<Counters> ctr(1, st);
     SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
-    prune_run(g.rows.p, g.rows.ld, d, n, pool_id, pool_len, L, R, cos_alpha_of(alpha_deg), adj, deg,
-              ctr.p, st);
+    prune_dispatch(g.info.bf16_exact != 0, g.rows.p, g.rows.ld, d, n, pool_id, pool_len, L, R,
+                   cos_alpha_of(alpha_deg), adj, deg, ctr.p, st);
   });
 }
 
@@ -421,8 +432,8 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     // a3: SSG prune
     Scratch<int32_t> adj0((size_t)n * R, st), deg0((size_t)n, st);
     t_prune.start();
-    prune_run(in.rows.p, in.rows.ld, d, n, pool_id.p, pool_len.p, L, R, cos_a, adj0.p, deg0.p,
-              ctr.p, st);
+    prune_dispatch(opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact, in.rows.p, in.rows.ld, d, n,
+                   pool_id.p, pool_len.p, L, R, cos_a, adj0.p, deg0.p, ctr.p, st);
     t_prune.stop();
     pool_id.release();
     pool_d2.release();

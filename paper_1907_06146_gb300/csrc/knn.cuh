@@ -64,6 +64,13 @@ void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
                const int32_t* pool_len, int L, int R, double cos_a, int32_t* adj,
                int32_t* deg, Counters* dctr, cudaStream_t st);
 
+// The same prune with each pool's Gram matrix on the tensor cores (data exact in bf16,
+// d <= 128, L <= 127, R <= 128; true where that path is available).
+bool prune_tc_available(int d, int L, int R);
+void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
+                  const int32_t* pool_len, int L, int R, double cos_a, int32_t* adj,
+                  int32_t* deg, Counters* dctr, cudaStream_t st);
+
 // Reverse-neighbour merge; returns the largest in-degree.
 int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
                 const int32_t* deg0, int R, double cos_a, int exact, int32_t* adj1,

@@ -252,6 +252,30 @@ def test_prune_angles(ssg, small, small_ref, alpha, R):
     np.testing.assert_array_equal(_np(adj), ref[0])
 
 
+@pytest.mark.parametrize("alpha,R", [(60.0, 50), (30.0, 128), (90.0, 7), (120.0, 20), (150.0, 1)])
+def test_prune_integer_angles(ssg, intdata, int_ref, alpha, R):
+    """Integer data take the tensor-core Gram prune (exact centred Gram from one UMMA)."""
+    ref = oracle.prune(intdata.base, int_ref["pool_id"], int_ref["pool_len"], R, alpha)
+    adj, deg = ssg.prune(_cuda(intdata.base), _cuda(int_ref["pool_id"]),
+                         _cuda(int_ref["pool_len"]), R, alpha)
+    np.testing.assert_array_equal(_np(deg), ref[1])
+    np.testing.assert_array_equal(_np(adj), ref[0])
+
+
+def test_prune_integer_duplicates_full_tile(ssg):
+    """d = 7 (one K-chunk), pools of the tile's limit (L = 127) and duplicate points, so
+    zero-length edges occur; alpha above 90 degrees makes them conflicts."""
+    base = synth.uniform_points(1500, 7, 77, integer=True, hi=6)
+    base[100:140] = base[3]
+    knn, _ = oracle.knn_rows(base, 40)
+    pid, _, pl = oracle.pool(base, knn, 127)
+    for alpha in (60.0, 120.0):
+        ref = oracle.prune(base, pid, pl, 32, alpha)
+        adj, deg = ssg.prune(_cuda(base), _cuda(pid), _cuda(pl), 32, alpha)
+        np.testing.assert_array_equal(_np(deg), ref[1])
+        np.testing.assert_array_equal(_np(adj), ref[0])
+
+
 # ---- a4: reverse merge -------------------------------------------------------------------
 @pytest.mark.parametrize("which", ["small", "int"])
 def test_reverse(ssg, which, small, intdata, small_ref, int_ref):
