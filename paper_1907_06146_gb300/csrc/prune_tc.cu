@@ -6,21 +6,22 @@
 // H = C C^T in TMEM.  Every product and partial sum is an integer below 2^24, so H is
 // exact, and so is every centred dot product the angle rule needs:
 //     G_jk = (c_j - x).(c_k - x) = H_jk - H_j0 - H_k0 + H_00,   G_jj = d2(x, c_j).
-// The selection then follows the rule in candidate order: keep c_j unless
-// cos(j, k) = G_jk / sqrt(G_jj G_kk) > cos(alpha) for a kept c_k (0 for a zero-length
-// edge).  The fp32 cosine decides where it is more than 16 units of roundoff from cos(alpha)
-// (its inputs are exact, so its error is a few units); otherwise, and for zero-length
-// edges, the decision is taken in fp64 from the same exact integers with the operations of
-// the definition, which reproduces the double-precision rule bit for bit.
+// All pairs are tested at once: bit k of row j says whether cos(j, k) = G_jk / sqrt(G_jj
+// G_kk) > cos(alpha) (0 for a zero-length edge).  The fp32 cosine decides where it is more
+// than 16 units of roundoff from cos(alpha) (its inputs are exact, its error a few units);
+// otherwise the bit is taken in fp64 from the same exact integers with the operations of
+// the definition, which reproduces the double-precision rule bit for bit.  The selection
+// in candidate order (keep c_j unless it conflicts with a kept c_k, stop at R) is then a
+// scan over these bit rows.
 //
-// Persistent kernel, one CTA per SM, 9 warps:
-//   warp 0      gathers the node and candidate rows (gather4, 4 rows per TMA) into one of
-//               GSLOTS shared-memory tiles;
-//   warp 1      allocates 512 TMEM columns and issues the Gram UMMAs into one of 4 TMEM
-//               buffers;
-//   warps 2..5  (one per TMEM lane quadrant) turn H into the centred Gram's lower triangle
-//               and diagonal (int32) in one of TSLOTS shared-memory slots;
-//   warps 6..8  select: each takes every third node, lanes over the kept edges.
+// Persistent kernel, one CTA per SM, 13 warps:
+//   warp 0       gathers the node and candidate rows (gather4, 4 rows per TMA) into one
+//                of GSLOTS shared-memory tiles;
+//   warp 1       allocates 512 TMEM columns and issues the Gram UMMAs into one of 4 TMEM
+//                buffers;
+//   warps 2..9   conflict bits: two warps per TMEM lane quadrant (one row per lane), each
+//                taking every other 32-column chunk left of the diagonal;
+//   warps 10..12 select: each takes every third node.
 // Every wait is bounded (about 2 s); a wait that runs out sets an error word, tells the
 // other roles to stop, and the CTA releases its TMEM and exits.
 #include "common.cuh"
@@ -34,12 +35,13 @@ using namespace tc;
 
 constexpr int PT_ROWS = 128;                  // the node and up to 127 candidates
 constexpr int GSLOTS = 3;                     // gather tiles
-constexpr int TSLOTS = 3;                     // triangle slots, one per selection warp
-constexpr int GRAM_WARPS = 4;
-constexpr int THREADS_P = (2 + GRAM_WARPS + TSLOTS) * 32;
+constexpr int SEL_WARPS = 3;
+constexpr int MSLOTS = 6;                     // conflict-bit slots (a multiple of SEL_WARPS)
+constexpr int GRAM_WARPS = 8;
+constexpr int THREADS_P = (2 + GRAM_WARPS + SEL_WARPS) * 32;
 constexpr int TMEM_COLS_P = 512;              // 4 buffers of 128 fp32 columns
-constexpr int TRI = 127 * 126 / 2;            // centred Gram entries (j, k), k < j < 127
-constexpr int TSLOT_BYTES = 32768;            // TRI + 128 diagonal ints, rounded up
+constexpr int MSLOT_BYTES = PT_ROWS * 4 * 4;  // 4 words of conflict bits per row
+constexpr int XCH_FLOATS = 4 * PT_ROWS;       // per node: H_i0, H_ii, d2(x, c_i), 1/sqrt
 
 struct PtArgs {
   const int32_t* pool_id;
@@ -54,25 +56,26 @@ struct PtArgs {
   int* err;
 };
 
-__device__ __forceinline__ int tri_row(int t) { return t * (t - 1) / 2; }
-
 __global__ void __launch_bounds__(THREADS_P, 1)
 k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t g_bytes = (uint32_t)p.kchunks * PT_ROWS * 128;
-  unsigned char* sG = sm;                                       // GSLOTS gather tiles
-  unsigned char* sT = sG + (size_t)GSLOTS * g_bytes;            // TSLOTS triangle slots
-  int32_t* a_s = (int32_t*)(sT + (size_t)TSLOTS * TSLOT_BYTES);  // [2][128]: H_i0 per node
-  uint64_t* bars = (uint64_t*)(a_s + 2 * PT_ROWS);
+  unsigned char* sG = sm;                                            // GSLOTS gather tiles
+  uint32_t* sM = (uint32_t*)(sG + (size_t)GSLOTS * g_bytes);         // MSLOTS x [128][4] bits
+  float* xch = (float*)(sM + (size_t)MSLOTS * PT_ROWS * 4);         // [2][4][128]
+  uint32_t* xz = (uint32_t*)(xch + 2 * XCH_FLOATS);                  // [2][4] zero-edge bits
+  float* stash = (float*)(xz + 8);                                   // 32 floats per thread
+  uint64_t* bars = (uint64_t*)(stash + GRAM_WARPS * 32 * 32);
   uint64_t* g_full = bars;
   uint64_t* g_empty = g_full + GSLOTS;
   uint64_t* t_full = g_empty + GSLOTS;
   uint64_t* t_empty = t_full + 4;
-  uint64_t* r_full = t_empty + 4;
-  uint64_t* r_empty = r_full + TSLOTS;
-  uint64_t* a_ready = r_empty + TSLOTS;
-  uint32_t* tmem_slot = (uint32_t*)(a_ready + 2);
+  uint64_t* m_full = t_empty + 4;
+  uint64_t* m_empty = m_full + MSLOTS;
+  uint64_t* ex1 = m_empty + MSLOTS;
+  uint64_t* ex2 = ex1 + 2;
+  uint32_t* tmem_slot = (uint32_t*)(ex2 + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -85,11 +88,14 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
       mbar_init(smem_u32(t_full + b), 1);
       mbar_init(smem_u32(t_empty + b), GRAM_WARPS);
     }
-    for (int u = 0; u < TSLOTS; ++u) {
-      mbar_init(smem_u32(r_full + u), GRAM_WARPS);
-      mbar_init(smem_u32(r_empty + u), 1);
+    for (int u = 0; u < MSLOTS; ++u) {
+      mbar_init(smem_u32(m_full + u), GRAM_WARPS);
+      mbar_init(smem_u32(m_empty + u), 1);
     }
-    for (int k = 0; k < 2; ++k) mbar_init(smem_u32(a_ready + k), GRAM_WARPS);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(smem_u32(ex1 + k), GRAM_WARPS);
+      mbar_init(smem_u32(ex2 + k), GRAM_WARPS);
+    }
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -177,12 +183,17 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
     }
     __syncwarp();
   } else if (warp < 2 + GRAM_WARPS) {
-    // ---------------- centred Gram: TMEM -> shared-memory triangle ----------------
-    const int q = warp & 3;          // TMEM lane quadrant
-    const int i = q * 32 + lane;     // row: 0 the node, i the candidate i - 1
+    // ---------------- conflict bits: TMEM -> shared-memory bit rows ----------------
+    const int q = warp & 3;                  // TMEM lane quadrant
+    const int hh = (warp - 2) >> 2;          // which of the quadrant's two warps
+    const int i = q * 32 + lane;             // row: 0 the node, i the candidate i - 1
+    float* st = stash + (size_t)((warp - 2) * 32 + lane) * 32;
+    const bool zc = 0.0 > p.cosA64;          // the rule for a zero-length edge
+    const float hi = p.cosA32 + p.margin, lo = p.cosA32 - p.margin;
     int b = 0, u = 0, k = 0;
     uint32_t tph = 0, uph = 0;
     bool ok = true;
+    unsigned long long fp64_tests = 0;
     for (int64_t x = blockIdx.x; x < n; x += gridDim.x, ++k) {
       const int nrows = min(p.pool_len[x], PT_ROWS - 1) + 1;
       ok = mbar_wait(smem_u32(t_full + b), tph, abort_flag);
@@ -192,145 +203,176 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
       }
       tc_fence_after();
       const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 128);
-      int32_t* as = a_s + (k & 1) * PT_ROWS;
+      float* xa = xch + (k & 1) * XCH_FLOATS;  // H_i0
+      float* xh = xa + PT_ROWS;                // H_ii
+      float* xd = xh + PT_ROWS;                // G_ii = d2(x, c_i)
+      float* xr = xd + PT_ROWS;                // 1 / sqrt(G_ii)
+      uint32_t* zq = xz + (k & 1) * 4;         // zero-length edges, one word per quadrant
       uint32_t v[32];
       tmem_ld32(taddr, v);
       tmem_wait_ld(v);
-      const int ai = __float2int_rn(__uint_as_float(v[0]));  // H_i0 = x.c
-      as[i] = ai;
+      const float ai = __uint_as_float(v[0]);
+      if (q != 0) {
+        tmem_ld32(taddr + (uint32_t)(q * 32), v);
+        tmem_wait_ld(v);
+      }
+      float hii = 0.f;
+#pragma unroll
+      for (int e = 0; e < 32; ++e)
+        if (e == lane) hii = __uint_as_float(v[e]);
+      if (hh == 0) {
+        xa[i] = ai;
+        xh[i] = hii;
+      }
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(a_ready + (k & 1)));
-      ok = mbar_wait(smem_u32(a_ready + (k & 1)), (uint32_t)((k >> 1) & 1), abort_flag) &&
-           mbar_wait(smem_u32(r_empty + u), uph ^ 1, abort_flag);
+      if (lane == 0) mbar_arrive(smem_u32(ex1 + (k & 1)));
+      ok = mbar_wait(smem_u32(ex1 + (k & 1)), (uint32_t)((k >> 1) & 1), abort_flag);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
         break;
       }
-      const int h00 = as[0];
-      int32_t* tri = (int32_t*)(sT + (size_t)u * TSLOT_BYTES);
-      int32_t* dg = tri + TRI;
+      const float h00 = xa[0];
+      const float dgi = (hii - 2.f * ai) + h00;  // exact: integers below 2^24
+      const float ri = dgi > 0.f ? __frsqrt_rn(dgi) : 0.f;
+      const uint32_t zb = __ballot_sync(0xffffffffu, dgi == 0.f);
+      if (hh == 0) {
+        xd[i] = dgi;
+        xr[i] = ri;
+        if (lane == 0) zq[q] = zb;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(ex2 + (k & 1)));
+      ok = mbar_wait(smem_u32(ex2 + (k & 1)), (uint32_t)((k >> 1) & 1), abort_flag) &&
+           mbar_wait(smem_u32(m_empty + u), uph ^ 1, abort_flag);
+      if (!__all_sync(0xffffffffu, ok)) {
+        ok = false;
+        break;
+      }
+      const float t2 = h00 - ai;
       const bool row_ok = i >= 1 && i < nrows;
-      const int toff = tri_row(i - 1) - 1;  // entry (i - 1, j - 1) at toff + j
-      int hii = 0;
-      for (int c = 0; c * 32 < nrows; ++c) {
-        if (c > 0) {
-          tmem_ld32(taddr + (uint32_t)(c * 32), v);
-          tmem_wait_ld(v);
-        }
+      const bool zero_i = dgi == 0.f;
+      uint32_t* mrow = sM + ((size_t)u * PT_ROWS + i) * 4;
+      for (int c = hh; c <= q && c * 32 < nrows; c += 2) {
+        tmem_ld32(taddr + (uint32_t)(c * 32), v);
+        tmem_wait_ld(v);
+        // columns j = 32c + e with 1 <= j < i
+        const int lo_e = c == 0 ? 1 : 0;
+        const int hi_e = i - c * 32;  // exclusive
+        uint32_t valid = 0;
+        if (row_ok && hi_e > lo_e)
+          valid = (hi_e >= 32 ? 0xffffffffu : ((1u << hi_e) - 1u)) & ~((1u << lo_e) - 1u);
+        uint32_t cf = 0, bd = 0;
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
           const int j = c * 32 + e;
-          const int h = __float2int_rn(__uint_as_float(v[e]));
-          if (j == i) hii = h;
-          if (row_ok && j >= 1 && j < i) tri[toff + j] = h - ai - as[j] + h00;
+          const float g = (__uint_as_float(v[e]) - xa[j]) + t2;  // exact centred dot product
+          const float cs = g * ri * xr[j];
+          cf |= (cs > hi ? 1u : 0u) << e;
+          bd |= (cs >= lo && cs <= hi ? 1u : 0u) << e;
         }
+        const uint32_t zcol = zq[c];
+        if (zero_i) {
+          cf = zc ? valid : 0u;
+          bd = 0u;
+        } else {
+          cf = ((cf & ~zcol) | (zc ? zcol : 0u)) & valid;
+          bd &= valid & ~zcol;
+        }
+        if (bd) {
+          // near cos(alpha): the double-precision rule on the same exact integers
+#pragma unroll
+          for (int kq = 0; kq < 8; ++kq)
+            *(float4*)(st + 4 * kq) = make_float4(__uint_as_float(v[4 * kq]), __uint_as_float(v[4 * kq + 1]),
+                                                  __uint_as_float(v[4 * kq + 2]), __uint_as_float(v[4 * kq + 3]));
+          while (bd) {
+            const int e = __ffs(bd) - 1;
+            bd &= bd - 1;
+            const int j = c * 32 + e;
+            const float g = (st[e] - xa[j]) + t2;
+            if (cos_from_gram_f64((double)g, (double)dgi, (double)xd[j]) > p.cosA64) cf |= 1u << e;
+            ++fp64_tests;
+          }
+        }
+        mrow[c] = cf;
       }
-      if (row_ok) dg[i - 1] = hii - 2 * ai + h00;
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(smem_u32(t_empty + b));
-        mbar_arrive(smem_u32(r_full + u));
+        mbar_arrive(smem_u32(m_full + u));
       }
       if (++b == 4) {
         b = 0;
         tph ^= 1;
       }
-      if (++u == TSLOTS) {
+      if (++u == MSLOTS) {
         u = 0;
         uph ^= 1;
       }
     }
+    if (fp64_tests) atomicAdd(p.n64, fp64_tests);
     if (!ok && lane == 0) {
       atomicOr(p.err, 4);
       *abort_flag = 1;
     }
   } else {
-    // ---------------- selection: one warp per node, lanes over the kept edges ----------------
-    const int u = warp - 2 - GRAM_WARPS;
-    const int32_t* tri = (const int32_t*)(sT + (size_t)u * TSLOT_BYTES);
-    const int32_t* dg = tri + TRI;
+    // ---------------- selection: candidate order over the bit rows ----------------
+    const int sw = warp - 2 - GRAM_WARPS;
+    int u = sw;
     uint32_t uph = 0;
     bool ok = true;
-    unsigned long long fp64_tests = 0;
     const int R = p.R;
-    for (int64_t x = blockIdx.x + (int64_t)u * gridDim.x; x < n; x += (int64_t)TSLOTS * gridDim.x) {
-      ok = mbar_wait(smem_u32(r_full + u), uph, abort_flag);
+    for (int64_t x = blockIdx.x + (int64_t)sw * gridDim.x; x < n;
+         x += (int64_t)SEL_WARPS * gridDim.x) {
+      ok = mbar_wait(smem_u32(m_full + u), uph, abort_flag);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
         break;
       }
-      const int len = min(p.pool_len[x], PT_ROWS - 1);
-      const int32_t* cand = p.pool_id + x * p.L;
-      int kk[4], dk[4], gv[4];
-      float sk[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        kk[r] = 0;
-        dk[r] = 0;
-        gv[r] = 0;
-        sk[r] = 0.f;
-      }
+      const int nrows = min(p.pool_len[x], PT_ROWS - 1) + 1;
+      const uint32_t* mrows = sM + (size_t)u * PT_ROWS * 4;
+      // bit j of K: candidate j - 1 kept
+      uint32_t K0 = 0, K1 = 0, K2 = 0, K3 = 0;
       int kept = 0;
-      for (int t = 0; t < len && kept < R; ++t) {
-        const int dgt = dg[t];
-        const float st = sqrtf((float)dgt);
-        const int32_t* trow = tri + tri_row(t);
-        bool definite = false;
-        unsigned border = 0;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          if (lane + 32 * r < kept) {
-            const int g = trow[kk[r]];
-            gv[r] = g;
-            if (dgt == 0 || dk[r] == 0) {
-              border |= 1u << r;
-            } else {
-              const float c = (float)g / (st * sk[r]);
-              if (c > p.cosA32 + p.margin)
-                definite = true;
-              else if (c >= p.cosA32 - p.margin)
-                border |= 1u << r;
-            }
+      if (lane == 0) {
+        for (int i = 1; i < nrows && kept < R; ++i) {
+          const uint4 m = *(const uint4*)(mrows + (size_t)i * 4);
+          if (((m.x & K0) | (m.y & K1) | (m.z & K2) | (m.w & K3)) == 0u) {
+            const uint32_t bit = 1u << (i & 31);
+            const int w = i >> 5;
+            K0 |= w == 0 ? bit : 0u;
+            K1 |= w == 1 ? bit : 0u;
+            K2 |= w == 2 ? bit : 0u;
+            K3 |= w == 3 ? bit : 0u;
+            ++kept;
           }
-        }
-        bool conflict = __any_sync(0xffffffffu, definite);
-        if (!conflict && __any_sync(0xffffffffu, border != 0)) {
-          bool c64 = false;
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            if ((border >> r) & 1u) {
-              if (cos_from_gram_f64((double)gv[r], (double)dgt, (double)dk[r]) > p.cosA64)
-                c64 = true;
-              ++fp64_tests;
-            }
-          }
-          conflict = __any_sync(0xffffffffu, c64);
-        }
-        if (!conflict) {
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            if (r == (kept >> 5) && lane == (kept & 31)) {
-              kk[r] = t;
-              dk[r] = dgt;
-              sk[r] = st;
-            }
-          }
-          ++kept;
         }
       }
-      int32_t* out = p.adj + x * R;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int e = lane + 32 * r;
-        if (e < R) out[e] = e < kept ? cand[kk[r]] : -1;
-      }
-      if (lane == 0) p.deg[x] = kept;
+      K0 = __shfl_sync(0xffffffffu, K0, 0);
+      K1 = __shfl_sync(0xffffffffu, K1, 0);
+      K2 = __shfl_sync(0xffffffffu, K2, 0);
+      K3 = __shfl_sync(0xffffffffu, K3, 0);
+      kept = __shfl_sync(0xffffffffu, kept, 0);
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(r_empty + u));
-      uph ^= 1;
+      if (lane == 0) mbar_arrive(smem_u32(m_empty + u));
+      const int32_t* cand = p.pool_id + x * p.L;
+      int32_t* out = p.adj + x * R;
+      const unsigned lt = lanemask_lt();
+      const uint32_t Kw[4] = {K0, K1, K2, K3};
+      int base = 0;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        if ((Kw[w] >> lane) & 1u) out[base + __popc(Kw[w] & lt)] = cand[w * 32 + lane - 1];
+        base += __popc(Kw[w]);
+      }
+      for (int e = kept + lane; e < R; e += 32) out[e] = -1;
+      if (lane == 0) p.deg[x] = kept;
+      u += SEL_WARPS;
+      if (u >= MSLOTS) {
+        u -= MSLOTS;
+        uph ^= 1;
+      }
     }
-    if (fp64_tests) atomicAdd(p.n64, fp64_tests);
     if (!ok && lane == 0) {
       atomicOr(p.err, 8);
       *abort_flag = 1;
@@ -357,9 +399,10 @@ __global__ void k_rows_bf16(const float* __restrict__ X, int64_t n, int d, int l
 }
 
 size_t prune_tc_smem(int kchunks) {
-  return 1024 + (size_t)GSLOTS * kchunks * PT_ROWS * 128 + (size_t)TSLOTS * TSLOT_BYTES +
-         2 * PT_ROWS * sizeof(int32_t) +
-         sizeof(uint64_t) * (2 * GSLOTS + 8 + 2 * TSLOTS + 2) + 16;
+  return 1024 + (size_t)GSLOTS * kchunks * PT_ROWS * 128 + (size_t)MSLOTS * MSLOT_BYTES +
+         2 * XCH_FLOATS * sizeof(float) + 8 * sizeof(uint32_t) +
+         (size_t)GRAM_WARPS * 32 * 32 * sizeof(float) +
+         sizeof(uint64_t) * (2 * GSLOTS + 8 + 2 * MSLOTS + 4) + 16;
 }
 
 }  // namespace
