@@ -253,7 +253,7 @@ ssg_status ssg_reverse(const float* base, int64_t n, int32_t d, const int32_t* a
     Scratch<Counters> ctr(1, st);
     SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
     reverse_run(g.rows.p, g.rows.ld, d, n, adj0, deg0, R, cos_alpha_of(alpha_deg), g.info.exact,
-                adj1, deg1, ctr.p, st);
+                g.info.bf16_exact != 0, adj1, deg1, ctr.p, st);
   });
 }
 
@@ -442,7 +442,9 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     // a4: reverse-neighbour merge
     t_rev.start();
     const int maxin = reverse_run(in.rows.p, in.rows.ld, d, n, adj0.p, deg0.p, R, cos_a,
-                                  in.info.exact, g->adj, g->deg, ctr.p, st);
+                                  in.info.exact,
+                                  opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact != 0,
+                                  g->adj, g->deg, ctr.p, st);
     t_rev.stop();
     adj0.release();
     deg0.release();

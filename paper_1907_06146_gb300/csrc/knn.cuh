@@ -71,9 +71,10 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
                   const int32_t* pool_len, int L, int R, double cos_a, int32_t* adj,
                   int32_t* deg, Counters* dctr, cudaStream_t st);
 
-// Reverse-neighbour merge; returns the largest in-degree.
+// Reverse-neighbour merge; returns the largest in-degree.  tc: the prune of lists of up to
+// 127 candidates on the tensor cores where the data allow it.
 int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
-                const int32_t* deg0, int R, double cos_a, int exact, int32_t* adj1,
+                const int32_t* deg0, int R, double cos_a, int exact, bool tc, int32_t* adj1,
                 int32_t* deg1, Counters* dctr, cudaStream_t st);
 
 // Connectivity from navigating nodes; returns the number of repair edges.

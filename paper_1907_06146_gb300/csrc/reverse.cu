@@ -110,11 +110,13 @@ __global__ void k_reverse_merge(const float* __restrict__ X, int ld, int d, int6
                                 int R, const int64_t* __restrict__ off,
                                 const int32_t* __restrict__ rev,
                                 const int32_t* __restrict__ node_list, int64_t count, int cap,
+                                int limit,
                                 int exact, float rel, float cosA32, double cosA64, float margin,
                                 int32_t* __restrict__ adj1, int32_t* __restrict__ deg1,
                                 int32_t* __restrict__ big_list, int* __restrict__ big_count,
                                 unsigned long long* __restrict__ n_order,
-                                unsigned long long* __restrict__ n_angle, float* __restrict__ Vg) {
+                                unsigned long long* __restrict__ n_angle, float* __restrict__ Vg,
+                                int32_t* __restrict__ lists, int32_t* __restrict__ list_len) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
   const size_t per_warp = (size_t)cap * 20 + merge_prune_bytes(d, R, Vg != nullptr);
@@ -132,8 +134,11 @@ __global__ void k_reverse_merge(const float* __restrict__ X, int ld, int d, int6
     const int64_t j = node_list ? node_list[w] : w;
     const int d0 = deg0[j];
     const int64_t r0 = off[j], r1 = off[j + 1];
-    if (d0 + (r1 - r0) > cap) {
-      if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)j;
+    if (d0 + (r1 - r0) > limit) {
+      if (lane == 0) {
+        big_list[atomicAdd(big_count, 1)] = (int32_t)j;
+        if (list_len) list_len[j] = 0;
+      }
       continue;
     }
     for (int t = lane; t < d0; t += 32) keys[t] = (uint64_t)(uint32_t)adj0[j * R + t];
@@ -161,6 +166,13 @@ __global__ void k_reverse_merge(const float* __restrict__ X, int ld, int d, int6
       int f = warp_fix_runs(keys, m, m, d64, X, ld, d, xj, rel);
       for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
       if (lane == 0 && f) atomicAdd(n_order, (unsigned long long)f);
+    }
+    if (lists) {
+      // merge only: the sorted list goes to the tensor-core prune
+      for (int t = lane; t < m; t += 32) lists[j * limit + t] = key_id(keys[t]);
+      if (lane == 0) list_len[j] = m;
+      __syncwarp();
+      continue;
     }
     for (int t = lane; t < m; t += 32) cand[t] = key_id(keys[t]);
     __syncwarp();
@@ -191,7 +203,7 @@ __global__ void k_max_int(const int* __restrict__ v, int64_t n, int* __restrict_
 }
 
 int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
-                const int32_t* deg0, int R, double cos_a, int exact, int32_t* adj1,
+                const int32_t* deg0, int R, double cos_a, int exact, bool tc, int32_t* adj1,
                 int32_t* deg1, Counters* dctr, cudaStream_t st) {
   const int grid = 8 * num_sms();
   Scratch<int> indeg((size_t)n, st), fill((size_t)n, st), small(2, st);
@@ -209,9 +221,16 @@ int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
   const size_t prune_bytes = merge_prune_bytes(d, R, wide);
   const float rel = dist_rel_fp32(d), margin = angle_margin_fp32(d);
   const int d4 = (d + 3) & ~3;
-  // warp path
-  const int cap = 256;
+  // Tensor-core path (data exact in bf16): the warps only merge and sort, lists of up to
+  // 127 candidates go to the Gram prune, longer ones to the warp prune below.
+  const bool use_tc = tc && exact && prune_tc_available(d, 127, R);
+  // warp path: per-warp buffers of cap keys (a power of two, for the sort); lists longer
+  // than limit go to the second pass
+  const int cap = use_tc ? 128 : 256;
+  const int limit = use_tc ? 127 : cap;
   const size_t per_warp = (size_t)cap * 20 + prune_bytes;
+  SSG_REQUIRE((cap & (cap - 1)) == 0 && (cap * 20) % 16 == 0 && limit <= cap, SSG_EINTERNAL,
+              "reverse merge: bad buffer layout (cap %d, limit %d)", cap, limit);
   const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
   const size_t smem = per_warp * wpb;
   static size_t attr = 0;
@@ -231,9 +250,16 @@ int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
   Scratch<float> Vg;
   if (wide) Vg.alloc((size_t)mgrid * wpb * (R + 1) * d4, st);
   Scratch<int32_t> big((size_t)n, st);
+  Scratch<int32_t> lists, list_len;
+  if (use_tc) {
+    lists.alloc((size_t)n * limit, st);
+    list_len.alloc((size_t)n, st);
+  }
   SSG_LAUNCH(k_reverse_merge, (unsigned)mgrid, wpb * 32, smem, st, X, ld, d, n, adj0, deg0, R, off.p,
-             rev.p, (const int32_t*)nullptr, n, cap, exact, rel, (float)cos_a, cos_a, margin, adj1,
-             deg1, big.p, small.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p);
+             rev.p, (const int32_t*)nullptr, n, cap, limit, exact, rel, (float)cos_a, cos_a, margin, adj1,
+             deg1, big.p, small.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p, lists.p, list_len.p);
+  if (use_tc)
+    prune_run_tc(X, ld, d, n, lists.p, list_len.p, limit, R, cos_a, adj1, deg1, dctr, st);
   int h[2];
   SSG_CUDA(cudaMemcpyAsync(h, small.p, sizeof(h), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
@@ -251,8 +277,9 @@ int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
     Scratch<int> small2(2, st);
     SSG_CUDA(cudaMemsetAsync(small2.p, 0, sizeof(int) * 2, st));
     SSG_LAUNCH(k_reverse_merge, grid_big, 32, smem_big, st, X, ld, d, n, adj0, deg0, R, off.p, rev.p,
-               big.p, (int64_t)h[0], cap_big, exact, rel, (float)cos_a, cos_a, margin, adj1, deg1,
-               none.p, small2.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p);
+               big.p, (int64_t)h[0], cap_big, cap_big, exact, rel, (float)cos_a, cos_a, margin, adj1, deg1,
+               none.p, small2.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p, (int32_t*)nullptr,
+               (int32_t*)nullptr);
   }
   return h[1];
 }

@@ -304,6 +304,28 @@ def test_reverse_hub(ssg):
     np.testing.assert_array_equal(_np(adj1), ref[0])
 
 
+@pytest.mark.parametrize("alpha", [60.0, 120.0])
+def test_reverse_hub_integer(ssg, alpha):
+    """Integer data: lists of up to 127 candidates are pruned on the tensor cores, the hub's
+    (over a thousand) by the warp path; duplicates give zero-length edges."""
+    n, R = 1200, 6
+    base = synth.uniform_points(n, 5, 92, integer=True, hi=40)
+    base[50:60] = base[7]
+    rng = np.random.default_rng(4)
+    adj0 = np.full((n, R), -1, np.int32)
+    deg0 = np.zeros(n, np.int32)
+    for i in range(n):
+        others = rng.choice(n, size=4, replace=False)
+        row = [0] + [int(x) for x in others if x not in (0, i)]
+        row = [x for x in row if x != i][:R]
+        adj0[i, :len(row)] = row
+        deg0[i] = len(row)
+    ref = oracle.reverse(base, adj0, deg0, alpha)
+    adj1, deg1 = ssg.reverse(_cuda(base), _cuda(adj0), _cuda(deg0), alpha)
+    np.testing.assert_array_equal(_np(deg1), ref[1])
+    np.testing.assert_array_equal(_np(adj1), ref[0])
+
+
 # ---- a5: connectivity --------------------------------------------------------------------
 @pytest.mark.parametrize("which", ["small", "int"])
 def test_connect(ssg, which, small, intdata, small_ref, int_ref):
