@@ -127,7 +127,8 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("knn.cu", "knn_tc.cu", "knn_order.cu", "knn_select.cuh", "knn.cuh", "common.cuh"):
+    for f in ("knn.cu", "knn_tc.cu", "knn_order.cu", "knn_select.cuh", "knn.cuh", "common.cuh",
+              "tc_common.cuh"):
         p = os.path.join(ROOT, "paper_1907_06146_gb300", "csrc", f)
         if os.path.exists(p):
             with open(p, "rb") as fh:
