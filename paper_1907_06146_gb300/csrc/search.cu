@@ -258,8 +258,10 @@ void search_run_mixed(const float* X, int ld, int d, const int32_t* adj, const i
   lay.Ls = ls_max;
   lay.RP = std::max(32, next_pow2(R));
   lay.ld = ld;
-  lay.log2h = 12;
-  const int wpb = 4;
+  // 8 warps per block and a 1,024-entry visited cache: 32 warps per SM (the register
+  // limit) keep more row gathers in flight than a larger cache would save
+  lay.log2h = 10;
+  const int wpb = 8;
   const size_t smem = search_smem_setup(lay, wpb);
   int blocks_per_sm = 0;
   SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search, wpb * 32, smem));
@@ -279,8 +281,12 @@ void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
   lay.Ls = Ls;
   lay.RP = std::max(32, next_pow2(R));
   lay.ld = ld;
-  lay.log2h = 12;
-  const int wpb = 4;
+  // 8 warps per block and a 1,024-entry visited cache: 32 warps per SM (the register
+  // limit) keep more row gathers in flight than a larger cache would save.  A call that
+  // counts the work takes a 16,384-entry cache instead, so that its distance count is
+  // Alg. 1's (each node once) and not inflated by recomputations after cache evictions.
+  lay.log2h = work ? 14 : 10;
+  const int wpb = work ? 2 : 8;
   while (lay.per_warp() * wpb > 200 * 1024 && lay.log2h > 8) --lay.log2h;
   const size_t smem = lay.per_warp() * wpb;
   SSG_REQUIRE(smem <= 220 * 1024, SSG_EINVAL, "search: L_search and d too large for shared memory");
