@@ -295,6 +295,42 @@ def run_serving(ssg, g, base, w, seconds: float, rate: float, seed: int = 190706
                    "L_search uniform in [k, 512]"}
 
 
+def run_batched(ssg, count, n_streams):
+    """Independent indices (float Gaussian mixtures, shapes from synth.batched_specs) built
+    by ssg_build_batched and one by one; wall-clock seconds with the device synchronised."""
+    import torch
+    from paper_1907_06146_gb300 import synth
+    specs = synth.batched_specs(count)
+    data = [torch.from_numpy(synth.batched_index(sp).base).cuda() for sp in specs]
+    Ks = [sp["K"] for sp in specs]
+    Ls = [sp["L"] for sp in specs]
+    points = sum(sp["n"] for sp in specs)
+    warm = ssg.build_batched(data[-2:], Ks[-2:], Ls[-2:], 32, 60.0, n_streams=2)
+    del warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gs = ssg.build_batched(data, Ks, Ls, 32, 60.0, n_streams=n_streams)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    degs = [int(g.deg.sum().item()) for g in gs]
+    del gs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    same = True
+    for b, K, L, dg in zip(data, Ks, Ls, degs):
+        g = ssg.build(b, K, L, 32, 60.0)
+        same = same and int(g.deg.sum().item()) == dg
+        del g
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t0
+    return {"indices": count, "points": points, "streams": n_streams,
+            "batched_s": t_batch, "one_by_one_s": t_one, "speedup": t_one / t_batch,
+            "batched_s_per_1M_pts": t_batch * 1e6 / points,
+            "degree_sums_equal": same,
+            "shapes": "n log-uniform 10k-500k, d in {64,96,128,256}, L in {100,200}, K=100, "
+                      "R=32, alpha=60; 16-centre float mixtures"}
+
+
 # ---------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------
@@ -399,6 +435,10 @@ def run_gpu(args):
         serving = run_serving(ssg, g_srv, base, w, args.serve_seconds, args.serve_rate)
         del g_srv
 
+    batched = None
+    if rank == 0 and args.batched > 0:
+        batched = run_batched(ssg, args.batched, args.batched_streams)
+
     # the plain FP32 path on the same input, once (untimed in value): its build time, the
     # recall of its graph at the same L_search, and whether its edge set equals this one's
     fp32_arm = None
@@ -469,6 +509,7 @@ def run_gpu(args):
         "ground_truth_ms": float(np.mean(gt_ms)),
         "serving": serving,
         "fp32_path": fp32_arm,
+        "batched": batched,
         "counters": {k: st0[k] for k in ("n_repair", "n_angle_fp64", "n_order_fp64",
                                          "n_knn_fallback_rows", "max_indegree", "exact_mode")},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -496,6 +537,10 @@ def main():
     ap.add_argument("--target-recall", type=float, default=0.95)
     ap.add_argument("--ref-nodes", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="also build this many independent indices (log-uniform 10k-500k points, "
+                         "d in {64,96,128,256}), batched and one by one")
+    ap.add_argument("--batched-streams", type=int, default=8)
     ap.add_argument("--no-fp32-arm", dest="fp32_arm", action="store_false",
                     help="skip the one plain-FP32 build reported beside the mixed-precision path")
     ap.add_argument("--serve-seconds", type=float, default=3.0,

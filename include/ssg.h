@@ -207,6 +207,22 @@ ssg_status ssg_build_host(const float* base_host, int64_t n, int32_t d, int32_t 
                           ssg_stream stream, ssg_graph** out, int32_t* adj_host,
                           int32_t* deg_host, ssg_build_stats* stats);
 
+/* Many independent indices at once (the multi-tenant case): index i is built from the
+ * device array bases[i] (float32 [n[i]][d[i]]) with K[i], L[i], R[i], alpha_deg[i] and the
+ * shared opts (its navigating nodes drawn from opts->seed; opts->nav_ids_host must be
+ * NULL), into graphs[i].  Builds run concurrently on n_streams (1..64) internal streams,
+ * each driven by its own host thread and taking the largest remaining index (n^2 d) next,
+ * so small indices share the GPU.  Each graph equals what ssg_build returns for the same
+ * input, bit for bit.  stats (NULL or count entries) gets each build's stats.  The call
+ * returns when every build has finished; on failure it returns the first failing status,
+ * ssg_last_error() names the index, and graphs[] keeps the builds that succeeded (the
+ * others are NULL). */
+ssg_status ssg_build_batched(int32_t count, const float* const* bases, const int64_t* n,
+                             const int32_t* d, const int32_t* K, const int32_t* L,
+                             const int32_t* R, const double* alpha_deg,
+                             const ssg_build_opts* opts, int32_t n_streams, ssg_graph** graphs,
+                             ssg_build_stats* stats);
+
 /* Device views of a graph (no copies).  Any output pointer may be NULL. */
 ssg_status ssg_graph_view(const ssg_graph* g, const int32_t** adj, const int32_t** deg,
                           const int32_t** nav, int32_t* n_nav, int32_t* R, int64_t* n,

@@ -5,6 +5,9 @@
 #include <cstdio>
 #include <memory>
 #include <new>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -15,6 +18,7 @@
 namespace ssg {
 
 std::atomic<int64_t> g_launches{0};
+thread_local int64_t t_launches = 0;
 static thread_local char g_err[1024] = "";
 
 void set_error(const char* fmt, ...) {
@@ -373,7 +377,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
       if (s != SSG_OK) throw Fail{s};
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const int64_t launches0 = g_launches.load();
+    const int64_t launches0 = t_launches;
     ssg_build_stats S{};
     StageTimer t_all(st), t_ing(st), t_knn(st), t_gemm(st), t_pool(st), t_prune(st), t_rev(st),
         t_con(st);
@@ -474,9 +478,65 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     S.max_indegree = maxin;
     S.exact_mode = in.info.exact;
     S.gemm_prec_used = tc ? SSG_PREC_BF16 : SSG_PREC_FP32;
-    S.kernel_launches = g_launches.load() - launches0;
+    S.kernel_launches = t_launches - launches0;
     if (stats) *stats = S;
     *out = gp.release();
+  });
+}
+
+ssg_status ssg_build_batched(int32_t count, const float* const* bases, const int64_t* n,
+                             const int32_t* d, const int32_t* K, const int32_t* L,
+                             const int32_t* R, const double* alpha_deg,
+                             const ssg_build_opts* opts, int32_t n_streams, ssg_graph** graphs,
+                             ssg_build_stats* stats) {
+  return guard([&] {
+    SSG_REQUIRE(count >= 0, SSG_EINVAL, "count must be >= 0");
+    if (count == 0) return;
+    SSG_REQUIRE(bases && n && d && K && L && R && alpha_deg && graphs, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(n_streams >= 1 && n_streams <= 64, SSG_EINVAL, "need 1 <= n_streams <= 64");
+    SSG_REQUIRE(!opts || !opts->nav_ids_host, SSG_EINVAL,
+                "batched builds draw navigating nodes from the seed (nav_ids_host must be NULL)");
+    for (int32_t i = 0; i < count; ++i) graphs[i] = nullptr;
+    // largest work first (n^2 d: the kNN graph dominates), so the tail is short
+    std::vector<int32_t> order((size_t)count);
+    for (int32_t i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return (double)n[a] * n[a] * d[a] > (double)n[b] * n[b] * d[b];
+    });
+    int dev = 0;
+    SSG_CUDA(cudaGetDevice(&dev));
+    const int nt = std::min<int32_t>(n_streams, count);
+    std::vector<cudaStream_t> streams((size_t)nt, nullptr);
+    for (int t = 0; t < nt; ++t)
+      SSG_CUDA(cudaStreamCreateWithFlags(&streams[t], cudaStreamNonBlocking));
+    std::atomic<int32_t> next{0};
+    std::mutex mu;
+    ssg_status first = SSG_OK;
+    std::string first_msg;
+    auto worker = [&](int t) {
+      cudaSetDevice(dev);
+      for (;;) {
+        const int32_t k = next.fetch_add(1);
+        if (k >= count) break;
+        const int32_t i = order[k];
+        const ssg_status s = ssg_build(bases[i], n[i], d[i], K[i], L[i], R[i], alpha_deg[i], opts,
+                                       (ssg_stream)streams[t], &graphs[i],
+                                       stats ? &stats[i] : nullptr);
+        if (s != SSG_OK) {
+          std::lock_guard<std::mutex> lk(mu);
+          if (first == SSG_OK) {
+            first = s;
+            first_msg = "index " + std::to_string(i) + ": " + ssg_last_error();
+          }
+        }
+      }
+      cudaStreamSynchronize(streams[t]);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(worker, t);
+    for (auto& th : pool) th.join();
+    for (int t = 0; t < nt; ++t) cudaStreamDestroy(streams[t]);
+    SSG_REQUIRE(first == SSG_OK, first, "%s", first_msg.c_str());
   });
 }
 

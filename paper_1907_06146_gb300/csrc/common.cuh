@@ -8,7 +8,9 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "../../include/ssg.h"
 
@@ -18,7 +20,8 @@ namespace ssg {
 // Errors and launches
 // ---------------------------------------------------------------------------------------
 void set_error(const char* fmt, ...);
-extern std::atomic<int64_t> g_launches;
+extern std::atomic<int64_t> g_launches;   // all threads
+extern thread_local int64_t t_launches;    // this host thread
 
 struct Fail {
   ssg_status st;
@@ -46,6 +49,7 @@ struct Fail {
   do {                                                                         \
     kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                \
     ::ssg::g_launches.fetch_add(1, std::memory_order_relaxed);                 \
+    ++::ssg::t_launches;                                                       \
     cudaError_t e_ = cudaGetLastError();                                       \
     if (e_ != cudaSuccess) {                                                   \
       ::ssg::set_error("%s:%d launch of %s: %s", __FILE__, __LINE__, #kernel,  \
@@ -107,14 +111,26 @@ struct StageTimer {
 };
 
 inline int num_sms() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   return sms;
+}
+
+// Raises a kernel's dynamic shared-memory limit to at least smem (once per kernel and
+// size; the kernel's static shared memory counts on top of it, so even 48 KiB needs the
+// raise).  Thread-safe: concurrent builds on several host threads share it.
+inline void ensure_smem(const void* kernel, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = done[kernel];
+  if (smem <= cur) return;
+  SSG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cur = smem;
 }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -453,12 +453,7 @@ static void launch_select(const float* A, int64_t na, int lda, const float* B, i
                           int direct_K, int32_t* out_id, float* out_d2, uint64_t* out_keys,
                           float* out_thresh, cudaStream_t st) {
   const size_t smem = knn_select_smem_bytes();
-  static bool attr = false;
-  if (!attr) {
-    SSG_CUDA(cudaFuncSetAttribute(k_knn_select_fp32<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    attr = true;
-  }
+  ensure_smem((const void*)k_knn_select_fp32<C>, smem);
   const int64_t nrb = ceil_div(na, BM);
   const int grid = (int)std::min<int64_t>(nrb, 2 * num_sms());
   Scratch<uint64_t> rowbuf((size_t)grid * BM * C, st);
@@ -521,12 +516,7 @@ KnnResult knn_exact(const float* A, int64_t na, int lda, const float* a_norm, co
   if (nfb > 0) {
     const int cap = 4096;
     const size_t smem_fb = (size_t)cap * (sizeof(double) + sizeof(int32_t));
-    static bool attr = false;
-    if (!attr) {
-      SSG_CUDA(cudaFuncSetAttribute(k_knn_fallback, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem_fb));
-      attr = true;
-    }
+    ensure_smem((const void*)k_knn_fallback, smem_fb);
     SSG_LAUNCH(k_knn_fallback, nfb, 256, smem_fb, st, A, lda, B, ldb, d, nb, self, fb_rows.p,
                fb_kth.p, K, cap, out_id, out_d2, fb_count.p + 1);
     int ovf = 0;

@@ -476,26 +476,21 @@ struct TcMaps {
 
 template <int C>
 void launch_tc(const TcMaps& m, TcArgs& a, int grid, size_t smem, cudaStream_t st) {
-  static size_t attr = 0;
-  if (smem > attr) {
-    SSG_CUDA(cudaFuncSetAttribute(k_knn_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  ensure_smem((const void*)k_knn_tc<C>, smem);
   SSG_LAUNCH(k_knn_tc<C>, grid, THREADS, smem, st, m.a, m.b, m.a_aug, m.b_aug, a);
 }
 
 }  // namespace
 
 bool knn_tc_available(int d) {
-  static int avail = -1;
-  if (avail < 0) {
+  static const int avail = [] {
     int dev = 0, major = 0, minor = 0;
-    avail = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
-      avail = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
-  }
+      return (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
+    return 0;
+  }();
   const int kchunks = ((d + 63) & ~63) / 64;
   return avail == 1 && d >= 1 && tc_smem_bytes(kchunks, 2) <= 225 * 1024;
 }

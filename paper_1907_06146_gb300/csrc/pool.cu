@@ -91,11 +91,7 @@ void pool_run(const float* X, int ld, int d, int64_t n, const int32_t* knn, int 
   const size_t per_warp = (size_t)cap * 8 + ((size_t)1 << log2h) * 4;
   int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
   const size_t smem = per_warp * wpb;
-  static size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    SSG_CUDA(cudaFuncSetAttribute(k_pool, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  ensure_smem((const void*)k_pool, smem);
   SSG_LAUNCH(k_pool, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, ld, d, n, knn, K, L, cap,
              log2h, exact, dist_rel_fp32(d), pool_id, pool_d2, pool_len, &dctr->order_fp64);
 }
@@ -144,11 +140,7 @@ void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
       (wide ? prune_wide_smem_floats(d, R) : prune_smem_floats(d, R)) * sizeof(float);
   int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
   const size_t smem = per_warp * wpb;
-  static size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    SSG_CUDA(cudaFuncSetAttribute(k_prune, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  ensure_smem((const void*)k_prune, smem);
   int blocks_per_sm = 0;
   SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_prune, wpb * 32, smem));
   // wide rows: a persistent grid (one device slot per warp); otherwise one warp per node

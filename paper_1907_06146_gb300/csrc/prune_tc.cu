@@ -438,11 +438,7 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
   a.n64 = &dctr->angle_fp64;
   a.err = err.p;
   const size_t smem = prune_tc_smem(kchunks);
-  static size_t attr = 0;
-  if (smem > attr) {
-    SSG_CUDA(cudaFuncSetAttribute(k_prune_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  ensure_smem((const void*)k_prune_tc, smem);
   const int grid = (int)std::min<int64_t>(n, num_sms());
   SSG_LAUNCH(k_prune_tc, grid, THREADS_P, smem, st, mx, a);
   int h = 0;

@@ -233,13 +233,8 @@ int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
               "reverse merge: bad buffer layout (cap %d, limit %d)", cap, limit);
   const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
   const size_t smem = per_warp * wpb;
-  static size_t attr = 0;
   const size_t smem_big_max = 220 * 1024;
-  if (attr < smem_big_max) {
-    SSG_CUDA(cudaFuncSetAttribute(k_reverse_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_big_max));
-    attr = smem_big_max;
-  }
+  ensure_smem((const void*)k_reverse_merge, smem_big_max);
   int blocks_per_sm = 0;
   SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_reverse_merge, wpb * 32,
                                                          smem));

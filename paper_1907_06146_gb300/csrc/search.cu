@@ -241,11 +241,7 @@ static size_t search_smem_setup(SearchLayout& lay, int wpb) {
   while (lay.per_warp() * wpb > 200 * 1024 && lay.log2h > 8) --lay.log2h;
   const size_t smem = lay.per_warp() * wpb;
   SSG_REQUIRE(smem <= 220 * 1024, SSG_EINVAL, "search: L_search and d too large for shared memory");
-  static size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    SSG_CUDA(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  ensure_smem((const void*)k_search, smem);
   return smem;
 }
 
@@ -290,11 +286,7 @@ void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
   while (lay.per_warp() * wpb > 200 * 1024 && lay.log2h > 8) --lay.log2h;
   const size_t smem = lay.per_warp() * wpb;
   SSG_REQUIRE(smem <= 220 * 1024, SSG_EINVAL, "search: L_search and d too large for shared memory");
-  static size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    SSG_CUDA(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  ensure_smem((const void*)k_search, smem);
   int blocks_per_sm = 0;
   SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search, wpb * 32, smem));
   const int64_t want = ceil_div(nq, wpb);

@@ -94,6 +94,10 @@ SYMBOLS = {
     "ssg_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                  ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_build_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "ssg_build_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
@@ -474,6 +478,39 @@ def build(base, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None,
     g = Graph(h, st)
     g._base_ref = b
     return g
+
+
+def build_batched(bases, K, L, R, alpha, n_nav: int = 10, seed=None, prec: str = "auto",
+                  n_streams: int = 8):
+    """Independent indices built concurrently (ssg_build_batched): bases is a list of
+    device float32 [n_i][d_i] tensors; K, L, R, alpha are scalars or per-index lists.
+    Returns the list of Graphs (each equal to ssg_build's for the same input)."""
+    torch = _torch()
+    bs = [_dev(b, torch.float32) for b in bases]
+    m = len(bs)
+
+    def per(v, ctype):
+        vals = list(v) if isinstance(v, (list, tuple)) else [v] * m
+        return (ctype * m)(*vals)
+
+    ptrs = (ctypes.c_void_p * m)(*[_ptr(b) for b in bs])
+    ns = (ctypes.c_int64 * m)(*[b.shape[0] for b in bs])
+    ds = (ctypes.c_int32 * m)(*[b.shape[1] for b in bs])
+    Ks, Ls, Rs = per(K, ctypes.c_int32), per(L, ctypes.c_int32), per(R, ctypes.c_int32)
+    As = per(alpha, ctypes.c_double)
+    o, keep = _opts(n_nav, None, seed, prec)
+    hs = (ctypes.c_void_p * m)()
+    sts = (BuildStats * m)()
+    torch.cuda.synchronize()  # the inputs are read on the library's own streams
+    _check(lib().ssg_build_batched(m, ptrs, ns, ds, Ks, Ls, Rs, As, ctypes.byref(o), n_streams,
+                                   hs, sts))
+    del keep
+    out = []
+    for i in range(m):
+        g = Graph(ctypes.c_void_p(hs[i]), sts[i])
+        g._base_ref = bs[i]
+        out.append(g)
+    return out
 
 
 def build_host(base: np.ndarray, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None,

@@ -63,6 +63,29 @@ def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
 
+def batched_specs(count: int = 64, n_min: int = 10_000, n_max: int = 500_000,
+                  seed: int = SEED_BATCH) -> list:
+    """Shapes of the many-index batch: n log-uniform in [n_min, n_max], d from
+    {64, 96, 128, 256}, L from {100, 200}; K = 100, R = 32, alpha = 60 for all.  Index i's
+    data come from batched_index(spec, seed + 1 + i)."""
+    rng = _rng(seed)
+    specs = []
+    for i in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        d = int(rng.choice([64, 96, 128, 256]))
+        L = int(rng.choice([100, 200]))
+        specs.append({"index": i, "n": n, "d": d, "K": 100, "L": L, "R": 32, "alpha": 60.0,
+                      "seed": seed + 1 + i})
+    return specs
+
+
+def batched_index(spec: dict, nq: int = 0) -> Workload:
+    """One index of the batch: the 16-centre isotropic mixture of `small` at its shape."""
+    w = small(n=spec["n"], d=spec["d"], nq=nq, n_centres=16, seed=spec["seed"])
+    return Workload("batched", w.base, w.queries, K=spec["K"], L=spec["L"], R=spec["R"],
+                    alpha=spec["alpha"], n_nav=10, info=dict(spec))
+
+
 def small(n: int = 10_000, d: int = 32, nq: int = 1_000, n_centres: int = 16,
           seed: int = SEED_SMALL) -> Workload:
     """Isotropic Gaussian mixture: centres ~ N(0, 4I), points = centre + N(0, I)."""

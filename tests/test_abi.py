@@ -78,6 +78,23 @@ def test_invalid_arguments_rejected_without_device(L):
     h = ctypes.c_void_p()
     assert L.ssg_build(P, 20, 4, 5, 10, 8, 60.0, ctypes.byref(opts), s, ctypes.byref(h), None) == 1
     assert h.value is None
+    # batched build: no streams, a host nav list, negative count; count 0 does nothing
+    one = (ctypes.c_int64 * 1)(100)
+    i1 = (ctypes.c_int32 * 1)(8)
+    a1 = (ctypes.c_double * 1)(60.0)
+    bases = (ctypes.c_void_p * 1)(16)
+    graphs = (ctypes.c_void_p * 1)()
+    L.ssg_default_opts(ctypes.byref(opts))
+    assert L.ssg_build_batched(1, bases, one, i1, i1, i1, i1, a1, ctypes.byref(opts), 0, graphs,
+                               None) == 1
+    nav_one = (ctypes.c_int32 * 1)(0)
+    opts.nav_ids_host = ctypes.addressof(nav_one)
+    assert L.ssg_build_batched(1, bases, one, i1, i1, i1, i1, a1, ctypes.byref(opts), 2, graphs,
+                               None) == 1
+    assert L.ssg_build_batched(-1, None, None, None, None, None, None, None, None, 2, None,
+                               None) == 1
+    assert L.ssg_build_batched(0, None, None, None, None, None, None, None, None, 2, None,
+                               None) == 0
 
 
 def test_default_opts(L):
