@@ -435,6 +435,11 @@ def run_gpu(args):
         serving = run_serving(ssg, g_srv, base, w, args.serve_seconds, args.serve_rate)
         del g_srv
 
+    ablations = None
+    if rank == 0 and args.ablations:
+        from paper_1907_06146_gb300 import ablations as abl
+        ablations = abl.run_all(ssg, synth, w)
+
     batched = None
     if rank == 0 and args.batched > 0:
         batched = run_batched(ssg, args.batched, args.batched_streams)
@@ -510,6 +515,7 @@ def run_gpu(args):
         "serving": serving,
         "fp32_path": fp32_arm,
         "batched": batched,
+        "ablations": ablations,
         "counters": {k: st0[k] for k in ("n_repair", "n_angle_fp64", "n_order_fp64",
                                          "n_knn_fallback_rows", "max_indegree", "exact_mode")},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -541,6 +547,8 @@ def main():
                     help="also build this many independent indices (log-uniform 10k-500k points, "
                          "d in {64,96,128,256}), batched and one by one")
     ap.add_argument("--batched-streams", type=int, default=8)
+    ap.add_argument("--ablations", action="store_true",
+                    help="also run the alpha sweep, exact-SSG overlap and edge-time scaling")
     ap.add_argument("--no-fp32-arm", dest="fp32_arm", action="store_false",
                     help="skip the one plain-FP32 build reported beside the mixed-precision path")
     ap.add_argument("--serve-seconds", type=float, default=3.0,

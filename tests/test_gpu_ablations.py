@@ -1,0 +1,37 @@
+"""The ablation runs (bench.py --ablations) on small inputs: the shapes of their results,
+degrees within the cap, and the expected direction of the alpha study (a much wider
+angle keeps far fewer edges)."""
+import pytest
+
+from paper_1907_06146_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ssg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_06146_gb300 import build_ext, ssg as S
+    build_ext.build()
+    S.lib()
+    return S
+
+
+def test_alpha_sweep(ssg):
+    from paper_1907_06146_gb300 import ablations
+    w = synth.small(n=6000, nq=300)
+    r = ablations.alpha_sweep(ssg, w, n=6000, nq=300, alphas=(30.0, 60.0, 80.0))
+    pts = {p["alpha"]: p for p in r["points"]}
+    assert pts[30.0]["avg_out_degree"] > pts[80.0]["avg_out_degree"]
+    assert all(p["max_out_degree"] <= w.R for p in r["points"])
+    assert pts[60.0]["recall"] >= 0.95 and pts[60.0]["qps"] > 0
+
+
+def test_exact_vs_nssg_counts(ssg):
+    from paper_1907_06146_gb300 import ablations
+    r = ablations.exact_vs_nssg(ssg, synth, n=400, d=16)
+    assert 0 < r["shared"] <= min(r["exact_edges"], r["nssg_edges"])
+    assert 0.0 < r["exact_covered"] <= 1.0 and 0.0 < r["nssg_in_exact"] <= 1.0
