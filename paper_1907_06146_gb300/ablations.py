@@ -46,7 +46,13 @@ def alpha_sweep(ssg, w, n=200_000, nq=2_000, alphas=(30.0, 40.0, 50.0, 60.0, 70.
     truth, _ = ssg.knn_query(base, queries, 10)
     out = []
     for a in alphas:
-        g = ssg.build(base, w.K, w.L, w.R, a, n_nav=w.n_nav)
+        try:
+            g = ssg.build(base, w.K, w.L, w.R, a, n_nav=w.n_nav)
+        except ssg.SSGError as e:
+            # a small alpha can fill every reached node's R slots before connectivity is
+            # repaired; the build then stops (the reading taken for that case)
+            out.append({"alpha": a, "error": str(e)})
+            continue
         deg = g.deg.float()
         ls, rec, qps = _qps_at(ssg, g, base, queries, truth)
         out.append({"alpha": a, "avg_out_degree": float(deg.mean().item()),
