@@ -3,9 +3,10 @@
 // One warp per query.  The candidate pool S (at most L_search entries, sorted by
 // (d2, id), with a checked flag each) lives in shared memory; each round expands the
 // first unchecked entry, gathers its adjacency row (coalesced), computes the distances
-// of the neighbours not seen before with teams of 8 lanes (float4 loads), sorts them with
-// a warp bitonic sort and merges them into S with a rank-based parallel merge, cut at
-// L_search.
+// of the neighbours not seen before with teams of 8 lanes, two rows per team at a time
+// (all of both rows' float4 loads issued before the first multiply-add, so a warp keeps
+// 8 row gathers in flight), sorts them with a warp bitonic sort and merges them into S
+// with a rank-based parallel merge, cut at L_search.
 //
 // Visited set: a direct-mapped cache of ids in shared memory.  Alg. 1 never re-adds a
 // visited node; here a node that fell out of the cache may be met again and its distance
@@ -27,23 +28,79 @@ __device__ __forceinline__ float team8_dist_q(const float* __restrict__ qs,
   if (valid) {
     const float4* q4 = (const float4*)qs;
     const float4* x4 = (const float4*)x;
-    for (int f = tl; f < ld4; f += 8) {
-      float4 a = q4[f], b = __ldg(x4 + f);
-      float u;
-      u = a.x - b.x;
-      s = fmaf(u, u, s);
-      u = a.y - b.y;
-      s = fmaf(u, u, s);
-      u = a.z - b.z;
-      s = fmaf(u, u, s);
-      u = a.w - b.w;
-      s = fmaf(u, u, s);
+    // the row's loads (up to four float4 per lane per 128 floats) are all issued before
+    // the first multiply-add
+    for (int f0 = tl; f0 < ld4; f0 += 32) {
+      float4 b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int f = f0 + 8 * i;
+        b[i] = f < ld4 ? __ldg(x4 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int f = f0 + 8 * i;
+        if (f < ld4) {
+          const float4 a = q4[f];
+          float u;
+          u = a.x - b[i].x;
+          s = fmaf(u, u, s);
+          u = a.y - b[i].y;
+          s = fmaf(u, u, s);
+          u = a.z - b[i].z;
+          s = fmaf(u, u, s);
+          u = a.w - b[i].w;
+          s = fmaf(u, u, s);
+        }
+      }
     }
   }
   s += __shfl_xor_sync(0xffffffffu, s, 1);
   s += __shfl_xor_sync(0xffffffffu, s, 2);
   s += __shfl_xor_sync(0xffffffffu, s, 4);
   return s;
+}
+
+// Two rows at once (8 rows in flight per warp).
+__device__ __forceinline__ float2 team8_dist2_q(const float* __restrict__ qs,
+                                                const float* __restrict__ x0,
+                                                const float* __restrict__ x1, int ld4, int tl,
+                                                bool v0, bool v1) {
+  float s0 = 0.f, s1 = 0.f;
+  const float4* q4 = (const float4*)qs;
+  const float4* a4 = (const float4*)x0;
+  const float4* b4 = (const float4*)x1;
+  for (int f0 = tl; f0 < ld4; f0 += 32) {
+    float4 ra[4], rb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int f = f0 + 8 * i;
+      ra[i] = (v0 && f < ld4) ? __ldg(a4 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+      rb[i] = (v1 && f < ld4) ? __ldg(b4 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int f = f0 + 8 * i;
+      if (f < ld4) {
+        const float4 q = q4[f];
+        float u;
+        u = q.x - ra[i].x; s0 = fmaf(u, u, s0);
+        u = q.y - ra[i].y; s0 = fmaf(u, u, s0);
+        u = q.z - ra[i].z; s0 = fmaf(u, u, s0);
+        u = q.w - ra[i].w; s0 = fmaf(u, u, s0);
+        u = q.x - rb[i].x; s1 = fmaf(u, u, s1);
+        u = q.y - rb[i].y; s1 = fmaf(u, u, s1);
+        u = q.z - rb[i].z; s1 = fmaf(u, u, s1);
+        u = q.w - rb[i].w; s1 = fmaf(u, u, s1);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  return make_float2(s0, s1);
 }
 
 // number of entries of a[0, len) that are < x (a sorted ascending)
@@ -166,13 +223,17 @@ __global__ void k_search(const float* __restrict__ X, int ld, int d, const int32
       w_adj += (unsigned long long)dg;
       w_dist += (unsigned long long)cnt;
       __syncwarp();
-      for (int t0 = 0; t0 < cnt; t0 += 4) {
-        const int t = t0 + team;
-        const bool valid = t < cnt;
-        const int32_t id = valid ? key_id(newk[t]) : 0;
-        const float dd = team8_dist_q(qs, X + (int64_t)id * ld, ld4, tl, valid);
+      for (int t0 = 0; t0 < cnt; t0 += 8) {
+        const int t = t0 + team, t2 = t0 + 4 + team;
+        const bool va = t < cnt, vb = t2 < cnt;
+        const int32_t ia = va ? key_id(newk[t]) : 0;
+        const int32_t ib = vb ? key_id(newk[t2]) : 0;
+        const float2 dd = team8_dist2_q(qs, X + (int64_t)ia * ld, X + (int64_t)ib * ld, ld4, tl, va, vb);
         __syncwarp();
-        if (valid && tl == 0) newk[t] = make_key(dd, id);
+        if (tl == 0) {
+          if (va) newk[t] = make_key(dd.x, ia);
+          if (vb) newk[t2] = make_key(dd.y, ib);
+        }
       }
       __syncwarp();
       int cp = 1;
@@ -254,7 +315,7 @@ void search_run_mixed(const float* X, int ld, int d, const int32_t* adj, const i
   lay.Ls = ls_max;
   lay.RP = std::max(32, next_pow2(R));
   lay.ld = ld;
-  // 8 warps per block and a 1,024-entry visited cache: 32 warps per SM (the register
+  // 8 warps per block and a 1,024-entry visited cache: 24 warps per SM (the register
   // limit) keep more row gathers in flight than a larger cache would save
   lay.log2h = 10;
   const int wpb = 8;
@@ -277,7 +338,7 @@ void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
   lay.Ls = Ls;
   lay.RP = std::max(32, next_pow2(R));
   lay.ld = ld;
-  // 8 warps per block and a 1,024-entry visited cache: 32 warps per SM (the register
+  // 8 warps per block and a 1,024-entry visited cache: 24 warps per SM (the register
   // limit) keep more row gathers in flight than a larger cache would save.  A call that
   // counts the work takes a 16,384-entry cache instead, so that its distance count is
   // Alg. 1's (each node once) and not inflated by recomputations after cache evictions.
