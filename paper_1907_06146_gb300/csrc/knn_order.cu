@@ -64,80 +64,99 @@ __global__ void k_centroid_norms(const float* __restrict__ C, int ncl, int dc, f
   cn[c] = s;
 }
 
-// Nearest centroid of every row, tiled: a block takes 32 rows and walks the centroids 64 at
-// a time through shared memory, 32 coordinates per step; thread (row, group) scores 8
-// centroids by |c|^2 - 2 x.c (the row's own |x|^2 does not change the argmin), and the 8
-// threads of a row agree on the smallest (ties to the lower centroid).
-constexpr int AS_ROWS = 32, AS_CENT = 64, AS_DIMS = 32;
+// Nearest centroid of every row, tiled: a block takes 128 rows and walks the centroids 64
+// at a time through shared memory, 32 coordinates per step; thread (row group, centroid
+// group) scores 4 rows x 8 centroids by |c|^2 - 2 x.c (the row's own |x|^2 does not
+// change the argmin), and the 8 threads of a row group agree on each row's smallest (ties
+// to the lower centroid).
+constexpr int AS_ROWS = 128, AS_CENT = 64, AS_DIMS = 32;
 __global__ void __launch_bounds__(256) k_assign_tiled(const float* __restrict__ X, int ld, int d,
                                                       int64_t n, const float* __restrict__ C,
                                                       const float* __restrict__ cn, int ncl, int dc,
                                                       int32_t* __restrict__ label,
                                                       int* __restrict__ counts) {
-  __shared__ float xs[AS_ROWS][AS_DIMS + 1];
+  __shared__ float xs[AS_DIMS][AS_ROWS + 4];
   __shared__ __align__(16) float cs[AS_DIMS][AS_CENT];
   const int t = threadIdx.x;
-  const int r = t >> 3, g = t & 7;
+  const int rg = t >> 3, g = t & 7;  // rows rg * 4 .. + 3, centroids g * 8 .. + 7 of a chunk
   const int64_t row0 = (int64_t)blockIdx.x * AS_ROWS;
-  float best = __int_as_float(0x7f800000);
-  int bc = 0;
-  for (int c0 = 0; c0 < ncl; c0 += AS_CENT) {
-    float acc[8];
+  float best[4];
+  int bc[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+  for (int r = 0; r < 4; ++r) {
+    best[r] = __int_as_float(0x7f800000);
+    bc[r] = 0;
+  }
+  for (int c0 = 0; c0 < ncl; c0 += AS_CENT) {
+    float acc[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[r][j] = 0.f;
     for (int d0 = 0; d0 < d; d0 += AS_DIMS) {
       __syncthreads();
       for (int i = t; i < AS_ROWS * AS_DIMS; i += 256) {
         const int rr = i / AS_DIMS, kk = i % AS_DIMS;
         const int64_t row = row0 + rr;
-        xs[rr][kk] = (row < n && d0 + kk < d) ? X[row * ld + d0 + kk] : 0.f;
+        xs[kk][rr] = (row < n && d0 + kk < d) ? X[row * ld + d0 + kk] : 0.f;
       }
       for (int i = t; i < AS_DIMS * AS_CENT; i += 256) {
         const int kk = i / AS_CENT, cc = i % AS_CENT;
         cs[kk][cc] = (c0 + cc < ncl && d0 + kk < d) ? C[(int64_t)(c0 + cc) * dc + d0 + kk] : 0.f;
       }
       __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
       for (int kk = 0; kk < AS_DIMS; ++kk) {
-        const float xv = xs[r][kk];
+        const float4 xv = *(const float4*)&xs[kk][rg * 4];
         const float4 a = *(const float4*)&cs[kk][g * 8];
         const float4 b = *(const float4*)&cs[kk][g * 8 + 4];
-        acc[0] = fmaf(xv, a.x, acc[0]);
-        acc[1] = fmaf(xv, a.y, acc[1]);
-        acc[2] = fmaf(xv, a.z, acc[2]);
-        acc[3] = fmaf(xv, a.w, acc[3]);
-        acc[4] = fmaf(xv, b.x, acc[4]);
-        acc[5] = fmaf(xv, b.y, acc[5]);
-        acc[6] = fmaf(xv, b.z, acc[6]);
-        acc[7] = fmaf(xv, b.w, acc[7]);
+        const float xr[4] = {xv.x, xv.y, xv.z, xv.w};
+        const float cv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[r][j] = fmaf(xr[r], cv[j], acc[r][j]);
       }
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int c = c0 + g * 8 + j;
       if (c < ncl) {
-        const float sc = fmaf(-2.f, acc[j], cn[c]);
-        if (sc < best) {
-          best = sc;
-          bc = c;
+        const float nc = cn[c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float sc = fmaf(-2.f, acc[r][j], nc);
+          if (sc < best[r]) {
+            best[r] = sc;
+            bc[r] = c;
+          }
         }
       }
     }
   }
-  // the 8 threads of a row are 8 consecutive lanes
+  // the 8 threads of a row group are 8 consecutive lanes
 #pragma unroll
-  for (int o = 1; o < 8; o <<= 1) {
-    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-    if (ob < best || (ob == best && oc < bc)) {
-      best = ob;
-      bc = oc;
+  for (int r = 0; r < 4; ++r) {
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best[r], o);
+      const int oc = __shfl_xor_sync(0xffffffffu, bc[r], o);
+      if (ob < best[r] || (ob == best[r] && oc < bc[r])) {
+        best[r] = ob;
+        bc[r] = oc;
+      }
     }
   }
-  const int64_t row = row0 + r;
-  if (g == 0 && row < n) {
-    label[row] = bc;
-    atomicAdd(counts + bc, 1);
+  if (g < 4) {
+    const int64_t row = row0 + rg * 4 + g;
+    int c = bc[0];
+#pragma unroll
+    for (int r = 1; r < 4; ++r)
+      if (r == g) c = bc[r];
+    if (row < n) {
+      label[row] = c;
+      atomicAdd(counts + c, 1);
+    }
   }
 }
 
