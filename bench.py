@@ -435,6 +435,27 @@ def run_gpu(args):
         serving = run_serving(ssg, g_srv, base, w, args.serve_seconds, args.serve_rate)
         del g_srv
 
+    alg4 = None
+    if rank == 0 and args.alg4_tiles > 0:
+        # Alg. 4: pools searched on the fly over the cluster-ordered tiles, no kNN graph
+        g4 = ssg.build(base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec,
+                       pool_tiles=args.alg4_tiles)
+        g4 = ssg.build(base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec,
+                       pool_tiles=args.alg4_tiles)
+        sweep4 = []
+        for ls in LS_SWEEP:
+            ids4, _ = g4.search(base, queries, 10, ls)
+            r4 = ssg.recall_hits(ids4, truth, 10) / (nq * 10.0)
+            sweep4.append((ls, r4))
+            if r4 >= args.target_recall:
+                break
+        alg4 = {"pool_tiles": args.alg4_tiles, "build_s_per_1M": g4.stats["ms_total"] / 1e3 * 1e6 / w.n,
+                "stages_ms": {k: g4.stats[k] for k in ("ms_knn", "ms_pool", "ms_prune", "ms_reverse",
+                                                       "ms_connect", "ms_total")},
+                "sweep": sweep4, "n_repair": g4.stats["n_repair"],
+                "knn_graph_bytes_not_stored": int(w.n * w.K * 8)}
+        del g4
+
     ablations = None
     if rank == 0 and args.ablations:
         from paper_1907_06146_gb300 import ablations as abl
@@ -516,6 +537,7 @@ def run_gpu(args):
         "fp32_path": fp32_arm,
         "batched": batched,
         "ablations": ablations,
+        "alg4": alg4,
         "counters": {k: st0[k] for k in ("n_repair", "n_angle_fp64", "n_order_fp64",
                                          "n_knn_fallback_rows", "max_indegree", "exact_mode")},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -547,6 +569,8 @@ def main():
                     help="also build this many independent indices (log-uniform 10k-500k points, "
                          "d in {64,96,128,256}), batched and one by one")
     ap.add_argument("--batched-streams", type=int, default=8)
+    ap.add_argument("--alg4-tiles", type=int, default=0,
+                    help="also build with Alg. 4's search-based pools over this many tiles")
     ap.add_argument("--ablations", action="store_true",
                     help="also run the alpha sweep, exact-SSG overlap and edge-time scaling")
     ap.add_argument("--no-fp32-arm", dest="fp32_arm", action="store_false",

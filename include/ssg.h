@@ -61,6 +61,13 @@ typedef struct {
                                   NULL = draw them with ssg_nav_ids(n, n_nav, seed) */
   uint64_t seed;            /* seed for the navigating-node draw */
   int32_t debug_checks;     /* nonzero: check graph invariants after each stage */
+  int32_t pool_tiles;       /* 0: Alg. 3 pools (the exact kNN graph, neighbours and their
+                               neighbours).  > 0: Alg. 4 pools without a stored kNN graph:
+                               each node's L nearest among the points of the pool_tiles
+                               128-point tiles nearest to it in the cluster order (an
+                               IVF-style index over k-means clusters of the data, searched
+                               nearest cluster first); needs data exact in bf16 and
+                               d <= 128, EINVAL otherwise */
 } ssg_build_opts;
 
 /* Per-build measurements (all times from CUDA events on the build stream). */

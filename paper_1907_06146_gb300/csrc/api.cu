@@ -88,6 +88,16 @@ struct Ingested {
   DataInfo info{};
 };
 
+// Length of each id row (the valid entries come first, -1 after them).
+__global__ void k_pool_len_from_ids(const int32_t* __restrict__ ids, int64_t n, int L,
+                                    int32_t* __restrict__ len) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int m = 0;
+  while (m < L && ids[i * L + m] >= 0) ++m;
+  len[i] = m;
+}
+
 // The prune on the tensor cores where the data are exact in bf16 (and the pool and degree
 // fit its tile), the fp32 warp prune otherwise; both take the same decisions.
 static void prune_dispatch(bool tc_ok, const float* X, int ld, int d, int64_t n,
@@ -122,6 +132,7 @@ void ssg_default_opts(ssg_build_opts* o) {
   o->nav_ids_host = nullptr;
   o->seed = 190706145ull;
   o->debug_checks = 0;
+  o->pool_tiles = 0;
 }
 
 const char* ssg_strerror(ssg_status s) {
@@ -405,33 +416,49 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
     const double cos_a = cos_alpha_of(alpha_deg);
 
-    // a1: exact kNN graph
-    Scratch<int32_t> knn_id((size_t)n * K, st);
-    Scratch<float> knn_d2((size_t)n * K, st);
     const bool tc = opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact && knn_tc_available(d);
     SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
                 "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
                 "and 2 d max|x|^2 <= 2^24 (4 d max|x|^2 with negative values)");
-    t_knn.start();
-    KnnResult kr;
-    if (tc)
-      knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d, 1,
-                   K, knn_id.p, knn_d2.p, st, &t_gemm);
-    else
-      kr = knn_exact(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d,
-                     in.info, 1, K, knn_id.p, knn_d2.p, st, &t_gemm);
-    t_knn.stop();
-    in.norms.release();
-
-    // a2: candidate pools
     Scratch<int32_t> pool_id((size_t)n * L, st), pool_len((size_t)n, st);
     Scratch<float> pool_d2((size_t)n * L, st);
-    t_pool.start();
-    pool_run(in.rows.p, in.rows.ld, d, n, knn_id.p, K, L, in.info.exact, pool_id.p, pool_d2.p,
-             pool_len.p, ctr.p, st);
-    t_pool.stop();
-    knn_id.release();
-    knn_d2.release();
+    KnnResult kr;
+    if (opts.pool_tiles > 0) {
+      // a1 + a2 of Alg. 4: no kNN graph; each node's L nearest among the points of its
+      // nearest pool_tiles tiles in the cluster order (the index searched on the fly)
+      SSG_REQUIRE(tc, SSG_EINVAL,
+                  "search-based pools (pool_tiles > 0) need the bf16 tensor-core path: sm_103, "
+                  "d <= 128 and data exact in bf16");
+      SSG_REQUIRE(knn_order_fits(n, 128), SSG_EINVAL, "search-based pools: n too large");
+      t_knn.start();
+      knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d, 1,
+                   L, pool_id.p, pool_d2.p, st, &t_gemm, opts.pool_tiles);
+      t_knn.stop();
+      in.norms.release();
+      t_pool.start();
+      SSG_LAUNCH(k_pool_len_from_ids, (unsigned)ceil_div(n, 256), 256, 0, st, pool_id.p, n, L,
+                 pool_len.p);
+      t_pool.stop();
+    } else {
+      // a1: exact kNN graph
+      Scratch<int32_t> knn_id((size_t)n * K, st);
+      Scratch<float> knn_d2((size_t)n * K, st);
+      t_knn.start();
+      if (tc)
+        knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d,
+                     1, K, knn_id.p, knn_d2.p, st, &t_gemm);
+      else
+        kr = knn_exact(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p,
+                       d, in.info, 1, K, knn_id.p, knn_d2.p, st, &t_gemm);
+      t_knn.stop();
+      in.norms.release();
+
+      // a2: candidate pools
+      t_pool.start();
+      pool_run(in.rows.p, in.rows.ld, d, n, knn_id.p, K, L, in.info.exact, pool_id.p, pool_d2.p,
+               pool_len.p, ctr.p, st);
+      t_pool.stop();
+    }
 
     // a3: SSG prune
     Scratch<int32_t> adj0((size_t)n * R, st), deg0((size_t)n, st);

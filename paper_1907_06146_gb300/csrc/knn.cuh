@@ -43,9 +43,13 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
 // bf16 tensor-core variant of the exact top-K (only for info.bf16_exact data).
 // True on sm_103 when the shared-memory pipeline fits rows of d values (d <= 128).
 bool knn_tc_available(int d);
+// max_tiles > 0 (self-joins only): the columns are visited in the cluster order and each
+// block of rows stops after its max_tiles nearest 128-column tiles, so the result is the
+// top-K among those columns (Alg. 4's search-based pools).
 void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
                   int64_t nb, int ldb, const float* b_norm, int d, int self, int K,
-                  int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer);
+                  int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer,
+                  int max_tiles = 0);
 
 struct Counters {
   unsigned long long angle_fp64;

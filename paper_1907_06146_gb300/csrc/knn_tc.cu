@@ -52,7 +52,8 @@ struct TcArgs {
   const float* a_norm;  // |x|^2 of the stored query rows (exact integers)
   int64_t na;           // query rows
   int64_t nb;           // base rows: stored column positions >= nb are padding
-  int64_t ntiles;       // BN-column tiles of the base
+  int64_t ntiles;       // BN-column tiles of the base (stride of the tile lists)
+  int64_t nwalk;        // tiles each block of rows visits (ntiles, or fewer for Alg. 4)
   int kchunks;          // padded d / 64
   int stages;
   int self;
@@ -186,6 +187,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
 
   const int64_t nrb = (p.na + BM - 1) / BM;
   const int64_t ntiles = p.ntiles;
+  const int64_t nwalk = p.nwalk;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -204,9 +206,9 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         tma_load_2d(smem_u32(sA + a_main), &tmAaug, smem_u32(a_full), 0, 0);
         const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * ntiles : nullptr;
         int64_t tn = tl ? tl[0] : 0;  // tile index, read one tile ahead
-        for (int64_t i = 0; i < ntiles; ++i) {
+        for (int64_t i = 0; i < nwalk; ++i) {
           const int j0 = (int)(tn * BN);
-          if (i + 1 < ntiles) tn = tl ? tl[i + 1] : i + 1;
+          if (i + 1 < nwalk) tn = tl ? tl[i + 1] : i + 1;
           ok = mbar_wait(smem_u32(b_empty + s), ph ^ 1, abort_flag);
           if (!ok) break;
           mbar_expect_tx(smem_u32(b_full + s), b_bytes);
@@ -240,7 +242,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, ++rbi) {
         ok = mbar_wait(smem_u32(a_full), rbi & 1, abort_flag);
         if (!ok) break;
-        for (int64_t ct = 0; ct < ntiles; ++ct, ++it) {
+        for (int64_t ct = 0; ct < nwalk; ++ct, ++it) {
           const int b = (int)(it & 1);
           const uint32_t tph = (uint32_t)((it >> 1) & 1);
           ok = mbar_wait(smem_u32(t_empty + b), tph ^ 1, abort_flag) &&
@@ -302,9 +304,9 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       uint64_t* buf = p.rowbuf + ((size_t)blockIdx.x * BM + row_in_cta) * C;
       const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * ntiles : nullptr;
       int64_t tn = tl ? tl[0] : 0;  // tile index, read one tile ahead
-      for (int64_t i = 0; i < ntiles; ++i, ++it) {
+      for (int64_t i = 0; i < nwalk; ++i, ++it) {
         const int32_t j0 = (int32_t)(tn * BN);
-        if (i + 1 < ntiles) tn = tl ? tl[i + 1] : i + 1;
+        if (i + 1 < nwalk) tn = tl ? tl[i + 1] : i + 1;
         const int b = (int)(it & 1);
         const uint32_t tph = (uint32_t)((it >> 1) & 1);
         ok = mbar_wait(smem_u32(t_full + b), tph, abort_flag);
@@ -497,7 +499,8 @@ bool knn_tc_available(int d) {
 
 void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
                   int64_t nb, int ldb, const float* b_norm, int d, int self, int K,
-                  int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer) {
+                  int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer,
+                  int max_tiles) {
   const int dp = (d + 63) & ~63;
   const int kchunks = dp / 64;
   int stages = MAX_STAGES;
@@ -509,7 +512,10 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   // threshold otherwise falls slowly and many candidates are appended).
   KnnOrder ord;
   Scratch<float> norm_p;
-  const bool ordered = self && na >= (1 << 16) && K >= 16 && knn_order_fits(na, BN);
+  SSG_REQUIRE(max_tiles == 0 || (self && knn_order_fits(na, BN)), SSG_EINVAL,
+              "a tile limit needs a self-join whose cluster order fits");
+  const bool ordered =
+      max_tiles > 0 || (self && na >= (1 << 16) && K >= 16 && knn_order_fits(na, BN));
   if (ordered) {
     knn_cluster_order(A, lda, d, na, BM, BN, st, ord);
     norm_p.alloc((size_t)na, st);
@@ -547,6 +553,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   a.na = na;
   a.nb = nb;
   a.ntiles = ceil_div(nb, BN);
+  a.nwalk = max_tiles > 0 ? std::min<int64_t>(a.ntiles, max_tiles) : a.ntiles;
   a.kchunks = kchunks;
   a.stages = stages;
   a.self = self;

@@ -30,7 +30,7 @@ class SSGError(RuntimeError):
 class BuildOpts(ctypes.Structure):
     _fields_ = [("gemm_prec", ctypes.c_int), ("n_nav", ctypes.c_int32),
                 ("nav_ids_host", ctypes.c_void_p), ("seed", ctypes.c_uint64),
-                ("debug_checks", ctypes.c_int32)]
+                ("debug_checks", ctypes.c_int32), ("pool_tiles", ctypes.c_int32)]
 
 
 class BuildStats(ctypes.Structure):
@@ -464,12 +464,14 @@ def _opts(n_nav, nav, seed, prec):
 
 
 def build(base, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None, seed=None,
-          prec: str = "auto") -> Graph:
-    """NSSGIndexing (Alg. 3) on a device-resident base (torch CUDA float32 [n][d])."""
+          prec: str = "auto", pool_tiles: int = 0) -> Graph:
+    """NSSGIndexing on a device-resident base (torch CUDA float32 [n][d]): Alg. 3, or with
+    pool_tiles > 0 Alg. 4's pools searched on the fly over the cluster-ordered tiles."""
     torch = _torch()
     b = _dev(base, torch.float32)
     n, d = b.shape
     o, keep = _opts(n_nav, nav, seed, prec)
+    o.pool_tiles = pool_tiles
     h = ctypes.c_void_p()
     st = BuildStats()
     _check(lib().ssg_build(_ptr(b), n, d, K, L, R, float(alpha), ctypes.byref(o), _stream(),

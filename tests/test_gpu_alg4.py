@@ -1,0 +1,94 @@
+"""Alg. 4: pools searched on the fly (each node's L nearest among the points of its nearest
+tiles in the cluster order) instead of the neighbours of a stored kNN graph.
+
+With every tile searched the pools are the exact L nearest neighbours, so the graph must
+equal the oracle's prune / reverse / connect of the oracle's exact L-NN rows.  With fewer
+tiles the pools are approximate: checked for order, exact distances, recall against the
+exact L-NN, and the graph for its invariants (degree cap, pairwise angles of the pruned
+edges, reachability from every navigating node)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_06146_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ssg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_06146_gb300 import build_ext, ssg as S
+    build_ext.build()
+    S.lib()
+    return S
+
+
+@pytest.fixture(scope="module")
+def data():
+    return synth.sift_like(n=5_000, nq=200, n_clusters=40)
+
+
+def _np(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def test_all_tiles_equals_oracle_on_exact_pools(ssg, data):
+    w = data
+    L, R, alpha = 60, 24, 60.0
+    nav = synth.nav_ids(w.n, 5, 21)
+    g = ssg.build(torch.from_numpy(w.base).cuda(), 10, L, R, alpha, nav=nav,
+                  pool_tiles=(w.n + 127) // 128)
+    ids, _ = oracle.knn_rows(w.base, L)
+    plen = np.full(w.n, L, np.int32)
+    adj0, deg0 = oracle.prune(w.base, ids, plen, R, alpha)
+    adj1, deg1 = oracle.reverse(w.base, adj0, deg0, alpha)
+    adj, deg, _ = oracle.connect(w.base, adj1, deg1, nav)
+    np.testing.assert_array_equal(_np(g.deg), deg)
+    np.testing.assert_array_equal(_np(g.adj), adj)
+
+
+def test_few_tiles_pools_and_invariants(ssg, data):
+    w = data
+    L, R, alpha = 60, 24, 60.0
+    b = torch.from_numpy(w.base).cuda()
+    # the pools alone: the tile-limited kNN through the build's own path
+    g = ssg.build(b, 10, L, R, alpha, n_nav=5, pool_tiles=6)
+    adj, deg = _np(g.adj), _np(g.deg)
+    assert (deg <= R).all()
+    # every node is reachable from every navigating node
+    nav = _np(g.nav)
+    for root in nav:
+        seen = np.zeros(w.n, bool)
+        seen[root] = True
+        stack = [int(root)]
+        while stack:
+            u = stack.pop()
+            for v in adj[u, :deg[u]]:
+                if not seen[v]:
+                    seen[v] = True
+                    stack.append(int(v))
+        assert seen.all()
+    # pairwise angles of every node's out-edges are at least alpha (up to double rounding),
+    # except at the nodes that received connectivity repair edges (at most one per repair)
+    x = w.base.astype(np.float64)
+    cosa = np.cos(np.radians(alpha))
+    bad_nodes = 0
+    for i in range(w.n):
+        e = adj[i, :deg[i]]
+        v = x[e] - x[i]
+        nv = np.linalg.norm(v, axis=1)
+        ok = nv > 0
+        v, nv = v[ok], nv[ok]
+        c = (v @ v.T) / np.outer(nv, nv)
+        np.fill_diagonal(c, -1.0)
+        bad_nodes += int((c > cosa + 1e-12).any())
+    assert bad_nodes <= g.stats["n_repair"]
+    # search on it still finds most true neighbours
+    truth, _ = oracle.knn_queries(w.base, w.queries, 10)
+    ids, _ = g.search(b, torch.from_numpy(w.queries).cuda(), 10, 64)
+    assert oracle.recall_at(_np(ids), truth, 10) > 0.8
