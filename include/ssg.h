@@ -66,8 +66,11 @@ typedef struct {
                                each node's L nearest among the points of the pool_tiles
                                128-point tiles nearest to it in the cluster order (an
                                IVF-style index over k-means clusters of the data, searched
-                               nearest cluster first); needs data exact in bf16 and
-                               d <= 128, EINVAL otherwise */
+                               nearest cluster first); needs sm_103 and d <= 128 (EINVAL
+                               otherwise).  On data exact in bf16 the selection is exact;
+                               on other data the tensor cores select L + slack candidates
+                               by bf16 distance and each pool is re-ranked exactly (so a
+                               pool may miss a point that only the exact distance ranks in) */
 } ssg_build_opts;
 
 /* Per-build measurements (all times from CUDA events on the build stream). */

@@ -426,13 +426,28 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     if (opts.pool_tiles > 0) {
       // a1 + a2 of Alg. 4: no kNN graph; each node's L nearest among the points of its
       // nearest pool_tiles tiles in the cluster order (the index searched on the fly)
-      SSG_REQUIRE(tc, SSG_EINVAL,
-                  "search-based pools (pool_tiles > 0) need the bf16 tensor-core path: sm_103, "
-                  "d <= 128 and data exact in bf16");
+      const bool tc_any = opts.gemm_prec != SSG_PREC_FP32 && knn_tc_available(d);
+      SSG_REQUIRE(tc_any, SSG_EINVAL,
+                  "search-based pools (pool_tiles > 0) need the bf16 tensor-core path: sm_103 "
+                  "and d <= 128");
       SSG_REQUIRE(knn_order_fits(n, 128), SSG_EINVAL, "search-based pools: n too large");
+      SSG_REQUIRE(L <= 895, SSG_EINVAL, "search-based pools: need L <= 895");
       t_knn.start();
-      knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d, 1,
-                   L, pool_id.p, pool_d2.p, st, &t_gemm, opts.pool_tiles);
+      if (tc) {
+        // data exact in bf16: the selection itself is exact
+        knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p,
+                     d, 1, L, pool_id.p, pool_d2.p, st, &t_gemm, opts.pool_tiles);
+      } else {
+        // other data: a bf16 selection of L + slack candidates (approximate distances), then
+        // each pool re-ranked by exact double-precision distance, the L nearest kept
+        const int Lp = (int)std::min<int64_t>(std::min(L + std::max(8, L / 4), 895), n - 1);
+        Scratch<int32_t> cid((size_t)n * Lp, st);
+        Scratch<float> cd2((size_t)n * Lp, st);
+        knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p,
+                     d, 1, Lp, cid.p, cd2.p, st, &t_gemm, opts.pool_tiles, true);
+        rerank_exact(in.rows.p, in.rows.ld, in.rows.p, in.rows.ld, d, n, cid.p, Lp, L, pool_id.p,
+                     pool_d2.p, st);
+      }
       t_knn.stop();
       in.norms.release();
       t_pool.start();

@@ -45,11 +45,18 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
 bool knn_tc_available(int d);
 // max_tiles > 0 (self-joins only): the columns are visited in the cluster order and each
 // block of rows stops after its max_tiles nearest 128-column tiles, so the result is the
-// top-K among those columns (Alg. 4's search-based pools).
+// top-K among those columns (Alg. 4's search-based pools).  approx: the data need not be
+// exact in bf16 (the distances and the selection are then approximate).
 void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
                   int64_t nb, int ldb, const float* b_norm, int d, int self, int K,
                   int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer,
-                  int max_tiles = 0);
+                  int max_tiles = 0, bool approx = false);
+
+// Re-ranks each row's candidate ids (KS per row, -1 padded) by exact double-precision
+// distance and keeps the K nearest by (d2, id); out may alias ids only when K == KS.
+void rerank_exact(const float* A, int lda, const float* B, int ldb, int d, int64_t na,
+                  const int32_t* cand, int KS, int K, int32_t* out_id, float* out_d2,
+                  cudaStream_t st);
 
 struct Counters {
   unsigned long long angle_fp64;

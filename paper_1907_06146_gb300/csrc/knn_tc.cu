@@ -443,7 +443,7 @@ __global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int d, int ld,
 // what the previous ones leave), then zeros.  err is set if a row's parts do not add up
 // to the value exactly.
 __global__ void k_aug_rows(const float* __restrict__ norm, int64_t n, __nv_bfloat16* __restrict__ aug,
-                           int* __restrict__ err) {
+                           int* __restrict__ err, int approx) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
        r += (int64_t)gridDim.x * blockDim.x) {
     float rest = -0.5f * norm[r];
@@ -453,7 +453,7 @@ __global__ void k_aug_rows(const float* __restrict__ norm, int64_t n, __nv_bfloa
       part[k] = __float2bfloat16_rn(rest);
       rest -= __bfloat162float(part[k]);
     }
-    if (rest != 0.f) atomicOr(err, 1);
+    if (rest != 0.f && !approx) atomicOr(err, 1);
     __nv_bfloat16* o = aug + r * AUG;
 #pragma unroll
     for (int k = 0; k < AUG; ++k) o[k] = k < 4 ? part[k] : __float2bfloat16_rn(0.f);
@@ -500,7 +500,7 @@ bool knn_tc_available(int d) {
 void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
                   int64_t nb, int ldb, const float* b_norm, int d, int self, int K,
                   int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer,
-                  int max_tiles) {
+                  int max_tiles, bool approx) {
   const int dp = (d + 63) & ~63;
   const int kchunks = dp / 64;
   int stages = MAX_STAGES;
@@ -537,7 +537,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   Scratch<int> err(1, st);
   SSG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
   SSG_LAUNCH(k_aug_rows, (unsigned)std::min<int64_t>(ceil_div(nb, 256), cgrid), 256, 0, st, b_norm,
-             nb, aug_b.p, err.p);
+             nb, aug_b.p, err.p, approx ? 1 : 0);
   SSG_LAUNCH(k_aug_ones, 1, 256, 0, st, aug_a.p);
   TcMaps maps;
   maps.a = make_map(ab.p, na, dp, 64, BM, CU_TENSOR_MAP_SWIZZLE_128B);
