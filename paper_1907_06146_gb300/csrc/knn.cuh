@@ -34,11 +34,14 @@ KnnResult knn_exact(const float* A, int64_t na, int lda, const float* a_norm, co
 struct KnnOrder {
   int ncl = 0;
   int64_t ntiles = 0;
+  int64_t tstride = 0;  // length of each cluster's tile list (ntiles, or the walk limit)
   Scratch<int32_t> perm, inv, tile_order, rb_cluster;
 };
 bool knn_order_fits(int64_t n, int BN);
+// walk > 0: every block of rows visits only its first walk tiles (Alg. 4), so each
+// cluster's list stops there and the clusters are kept small.
 void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN, cudaStream_t st,
-                       KnnOrder& o);
+                       KnnOrder& o, int64_t walk = 0);
 
 // bf16 tensor-core variant of the exact top-K (only for info.bf16_exact data).
 // True on sm_103 when the shared-memory pipeline fits rows of d values (d <= 128).

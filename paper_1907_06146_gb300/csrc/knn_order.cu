@@ -24,37 +24,6 @@ __global__ void k_init_centroids(const float* __restrict__ X, int ld, int d, int
   for (int t = threadIdx.x; t < dc; t += blockDim.x) C[(int64_t)c * dc + t] = t < d ? X[src * ld + t] : 0.f;
 }
 
-// Nearest centroid of every row (one warp per row, lanes over coordinates).  Row r of the
-// m rows visited is row r * n / m of X (m = n: every row); counts (nullable) gets the
-// cluster sizes.
-__global__ void k_assign(const float* __restrict__ X, int ld, int d, int64_t n, int64_t m,
-                         const float* __restrict__ C, int ncl, int dc, int32_t* __restrict__ label,
-                         int* __restrict__ counts) {
-  const int lane = lane_id();
-  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= m) return;
-  const float* x = X + (m == n ? r : r * n / m) * ld;
-  float best = __int_as_float(0x7f800000);
-  int bc = 0;
-  for (int c = 0; c < ncl; ++c) {
-    const float* cc = C + (int64_t)c * dc;
-    float s = 0.f;
-    for (int t = lane; t < d; t += 32) {
-      const float u = x[t] - cc[t];
-      s = fmaf(u, u, s);
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (s < best) {
-      best = s;
-      bc = c;
-    }
-  }
-  if (lane == 0) {
-    label[r] = bc;
-    if (counts) atomicAdd(counts + bc, 1);
-  }
-}
-
 // Squared norms of the centroids.
 __global__ void k_centroid_norms(const float* __restrict__ C, int ncl, int dc, float* __restrict__ cn) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -64,14 +33,16 @@ __global__ void k_centroid_norms(const float* __restrict__ C, int ncl, int dc, f
   cn[c] = s;
 }
 
-// Nearest centroid of every row, tiled: a block takes 128 rows and walks the centroids 64
-// at a time through shared memory, 32 coordinates per step; thread (row group, centroid
-// group) scores 4 rows x 8 centroids by |c|^2 - 2 x.c (the row's own |x|^2 does not
-// change the argmin), and the 8 threads of a row group agree on each row's smallest (ties
-// to the lower centroid).
+// Nearest centroid of each of m visited rows (row r of them is row r * n / m of X; m = n:
+// every row), tiled: a block takes 128 rows and walks the centroids 64 at a time through
+// shared memory, 32 coordinates per step; thread (row group, centroid group) scores 4 rows
+// x 8 centroids by |c|^2 - 2 x.c (the row's own |x|^2 does not change the argmin), and the
+// 8 threads of a row group agree on each row's smallest (ties to the lower centroid).
+// counts (nullable) gets the cluster sizes.
 constexpr int AS_ROWS = 128, AS_CENT = 64, AS_DIMS = 32;
 __global__ void __launch_bounds__(256) k_assign_tiled(const float* __restrict__ X, int ld, int d,
-                                                      int64_t n, const float* __restrict__ C,
+                                                      int64_t n, int64_t m,
+                                                      const float* __restrict__ C,
                                                       const float* __restrict__ cn, int ncl, int dc,
                                                       int32_t* __restrict__ label,
                                                       int* __restrict__ counts) {
@@ -98,7 +69,8 @@ __global__ void __launch_bounds__(256) k_assign_tiled(const float* __restrict__ 
       for (int i = t; i < AS_ROWS * AS_DIMS; i += 256) {
         const int rr = i / AS_DIMS, kk = i % AS_DIMS;
         const int64_t row = row0 + rr;
-        xs[kk][rr] = (row < n && d0 + kk < d) ? X[row * ld + d0 + kk] : 0.f;
+        const int64_t src = m == n ? row : row * n / m;
+        xs[kk][rr] = (row < m && d0 + kk < d) ? X[src * ld + d0 + kk] : 0.f;
       }
       for (int i = t; i < AS_DIMS * AS_CENT; i += 256) {
         const int kk = i / AS_CENT, cc = i % AS_CENT;
@@ -153,14 +125,14 @@ __global__ void __launch_bounds__(256) k_assign_tiled(const float* __restrict__ 
 #pragma unroll
     for (int r = 1; r < 4; ++r)
       if (r == g) c = bc[r];
-    if (row < n) {
+    if (row < m) {
       label[row] = c;
-      atomicAdd(counts + c, 1);
+      if (counts) atomicAdd(counts + c, 1);
     }
   }
 }
 
-// Per-cluster coordinate sums and sizes of the m visited rows (as in k_assign).
+// Per-cluster coordinate sums and sizes of the m visited rows (as in k_assign_tiled).
 __global__ void k_accum(const float* __restrict__ X, int ld, int d, int64_t n, int64_t m,
                         const int32_t* __restrict__ label, int dc, float* __restrict__ sums,
                         int* __restrict__ counts) {
@@ -226,34 +198,34 @@ __global__ void k_rb_cluster(const int32_t* __restrict__ label, const int32_t* _
   }
 }
 
-// Row c of the tile table: the BN-column tiles of the stored order, each listed with the
-// first cluster (in cluster c's order) whose stored range it overlaps.  One thread per
-// cluster walks the order with a bitmap of the tiles already listed; err is set if a row
-// does not list every tile exactly once.
+// Row c of the tile table: the first cap BN-column tiles of the stored order, each listed
+// with the first cluster (in cluster c's order) whose stored range it overlaps.  One thread
+// per cluster walks the order with a bitmap of the tiles already listed; err is set if a
+// row does not list cap distinct tiles (cap = ntiles: every tile exactly once).
 __global__ void k_tile_order(const int32_t* __restrict__ order, const int32_t* __restrict__ cl_start,
                              const int32_t* __restrict__ cl_end, int ncl, int BN, int64_t ntiles,
-                             int32_t* __restrict__ tile_order, int* __restrict__ err) {
+                             int64_t cap, int32_t* __restrict__ tile_order, int* __restrict__ err) {
   extern __shared__ uint32_t seen[];
   const int c = blockIdx.x;
   const int64_t words = (ntiles + 31) >> 5;
   for (int64_t w = threadIdx.x; w < words; w += blockDim.x) seen[w] = 0u;
   __syncthreads();
   if (threadIdx.x != 0) return;
-  int32_t* out = tile_order + (int64_t)c * ntiles;
+  int32_t* out = tile_order + (int64_t)c * cap;
   int64_t k = 0;
-  for (int oi = 0; oi < ncl; ++oi) {
+  for (int oi = 0; oi < ncl && k < cap; ++oi) {
     const int cc = order[(int64_t)c * ncl + oi];
     const int64_t s = cl_start[cc], e = cl_end[cc];
     if (e <= s) continue;
-    for (int64_t t = s / BN; t <= (e - 1) / BN; ++t) {
+    for (int64_t t = s / BN; t <= (e - 1) / BN && k < cap; ++t) {
       const uint32_t bit = 1u << (t & 31);
       if (seen[t >> 5] & bit) continue;
       seen[t >> 5] |= bit;
-      if (k < ntiles) out[k] = (int32_t)t;
+      out[k] = (int32_t)t;
       ++k;
     }
   }
-  if (k != ntiles) atomicOr(err, 1);
+  if (k != cap) atomicOr(err, 1);
 }
 
 bool knn_order_fits(int64_t n, int BN) {
@@ -262,12 +234,16 @@ bool knn_order_fits(int64_t n, int BN) {
 }
 
 void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN, cudaStream_t st,
-                       KnnOrder& o) {
+                       KnnOrder& o, int64_t walk) {
   SSG_REQUIRE(knn_order_fits(n, BN), SSG_EINTERNAL, "cluster order: too many column tiles");
-  const int ncl = (int)std::max<int64_t>(16, std::min<int64_t>(512, n / 2048));
+  // About 2,048 rows per cluster.  A full walk only needs the near tiles first, so a few
+  // hundred clusters do; a limited walk (Alg. 4) takes its pools from the first tiles
+  // alone, so the clusters stay that small up to 8,192 of them.
+  const int ncl = (int)std::max<int64_t>(16, std::min<int64_t>(walk > 0 ? 8192 : 512, n / 2048));
   const int dc = (d + 3) & ~3;
   o.ncl = ncl;
   o.ntiles = (n + BN - 1) / BN;
+  o.tstride = walk > 0 ? std::min<int64_t>(walk, o.ntiles) : o.ntiles;
   // Lloyd steps on an evenly spaced sample of about 64 rows per cluster, then one
   // assignment of every row.
   const int64_t m = std::min<int64_t>(n, (int64_t)ncl * 64);
@@ -276,19 +252,20 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
   Scratch<int32_t> label((size_t)n, st);
   SSG_LAUNCH(k_init_centroids, ncl, 128, 0, st, X, ld, d, n, ncl, dc, C.p);
   const int grid = 8 * num_sms();
+  Scratch<float> cn((size_t)ncl, st);
   for (int iter = 0; iter < 4; ++iter) {
-    SSG_LAUNCH(k_assign, (unsigned)ceil_div(m, 8), 256, 0, st, X, ld, d, n, m, C.p, ncl, dc, label.p,
-               (int*)nullptr);
+    SSG_LAUNCH(k_centroid_norms, (unsigned)ceil_div(ncl, 128), 128, 0, st, C.p, ncl, dc, cn.p);
+    SSG_LAUNCH(k_assign_tiled, (unsigned)ceil_div(m, AS_ROWS), 256, 0, st, X, ld, d, n, m, C.p,
+               cn.p, ncl, dc, label.p, (int*)nullptr);
     SSG_CUDA(cudaMemsetAsync(sums.p, 0, sizeof(float) * ncl * dc, st));
     SSG_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * ncl, st));
     SSG_LAUNCH(k_accum, grid, 256, 0, st, X, ld, d, n, m, label.p, dc, sums.p, counts.p);
     SSG_LAUNCH(k_update, ncl, 128, 0, st, C.p, sums.p, counts.p, ncl, dc);
   }
   SSG_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * ncl, st));
-  Scratch<float> cn((size_t)ncl, st);
   SSG_LAUNCH(k_centroid_norms, (unsigned)ceil_div(ncl, 128), 128, 0, st, C.p, ncl, dc, cn.p);
-  SSG_LAUNCH(k_assign_tiled, (unsigned)ceil_div(n, AS_ROWS), 256, 0, st, X, ld, d, n, C.p, cn.p,
-             ncl, dc, label.p, counts.p);
+  SSG_LAUNCH(k_assign_tiled, (unsigned)ceil_div(n, AS_ROWS), 256, 0, st, X, ld, d, n, n, C.p,
+             cn.p, ncl, dc, label.p, counts.p);
   std::vector<int> h((size_t)ncl);
   SSG_CUDA(cudaMemcpyAsync(h.data(), counts.p, sizeof(int) * ncl, cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
@@ -305,7 +282,7 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
   Scratch<int> cursor((size_t)ncl, st), err(1, st);
   o.perm.alloc((size_t)n, st);
   o.inv.alloc((size_t)n, st);
-  o.tile_order.alloc((size_t)ncl * o.ntiles, st);
+  o.tile_order.alloc((size_t)ncl * o.tstride, st);
   const int64_t nrb = ceil_div(n, BM);
   o.rb_cluster.alloc((size_t)nrb, st);
   SSG_CUDA(cudaMemcpyAsync(cl_start.p, start.data(), sizeof(int32_t) * ncl, cudaMemcpyHostToDevice, st));
@@ -314,9 +291,10 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
   SSG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
   SSG_LAUNCH(k_scatter_perm, grid, 256, 0, st, label.p, n, cursor.p, o.perm.p, o.inv.p);
   const int p2 = next_pow2(ncl);
+  ensure_smem((const void*)k_cluster_order, p2 * sizeof(uint64_t));
   SSG_LAUNCH(k_cluster_order, ncl, 256, p2 * sizeof(uint64_t), st, C.p, ncl, dc, p2, order.p);
   SSG_LAUNCH(k_tile_order, ncl, 256, (size_t)((o.ntiles + 31) >> 5) * 4, st, order.p, cl_start.p,
-             cl_end.p, ncl, BN, o.ntiles, o.tile_order.p, err.p);
+             cl_end.p, ncl, BN, o.ntiles, o.tstride, o.tile_order.p, err.p);
   SSG_LAUNCH(k_rb_cluster, (unsigned)ceil_div(nrb, 256), 256, 0, st, label.p, o.perm.p, n, BM, nrb,
              o.rb_cluster.p);
   int herr = 0;

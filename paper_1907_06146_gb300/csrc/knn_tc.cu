@@ -52,7 +52,8 @@ struct TcArgs {
   const float* a_norm;  // |x|^2 of the stored query rows (exact integers)
   int64_t na;           // query rows
   int64_t nb;           // base rows: stored column positions >= nb are padding
-  int64_t ntiles;       // BN-column tiles of the base (stride of the tile lists)
+  int64_t ntiles;       // BN-column tiles of the base
+  int64_t tstride;      // length of each cluster's tile list
   int64_t nwalk;        // tiles each block of rows visits (ntiles, or fewer for Alg. 4)
   int kchunks;          // padded d / 64
   int stages;
@@ -204,7 +205,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           tma_load_2d(smem_u32(sA + (size_t)kc * BM * 128), &tmA, smem_u32(a_full), kc * 64,
                       (int)(rb * BM));
         tma_load_2d(smem_u32(sA + a_main), &tmAaug, smem_u32(a_full), 0, 0);
-        const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * ntiles : nullptr;
+        const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * p.tstride : nullptr;
         int64_t tn = tl ? tl[0] : 0;  // tile index, read one tile ahead
         for (int64_t i = 0; i < nwalk; ++i) {
           const int j0 = (int)(tn * BN);
@@ -302,7 +303,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       float tau = INF;
       int cnt = 0;
       uint64_t* buf = p.rowbuf + ((size_t)blockIdx.x * BM + row_in_cta) * C;
-      const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * ntiles : nullptr;
+      const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * p.tstride : nullptr;
       int64_t tn = tl ? tl[0] : 0;  // tile index, read one tile ahead
       for (int64_t i = 0; i < nwalk; ++i, ++it) {
         const int32_t j0 = (int32_t)(tn * BN);
@@ -517,7 +518,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   const bool ordered =
       max_tiles > 0 || (self && na >= (1 << 16) && K >= 16 && knn_order_fits(na, BN));
   if (ordered) {
-    knn_cluster_order(A, lda, d, na, BM, BN, st, ord);
+    knn_cluster_order(A, lda, d, na, BM, BN, st, ord, max_tiles);
     norm_p.alloc((size_t)na, st);
   }
   Scratch<__nv_bfloat16> ab((size_t)na * dp, st);
@@ -554,6 +555,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   a.nb = nb;
   a.ntiles = ceil_div(nb, BN);
   a.nwalk = max_tiles > 0 ? std::min<int64_t>(a.ntiles, max_tiles) : a.ntiles;
+  a.tstride = ordered ? ord.tstride : a.ntiles;
   a.kchunks = kchunks;
   a.stages = stages;
   a.self = self;

@@ -48,6 +48,7 @@ __global__ void k_pool(const float* __restrict__ X, int ld, int d, int64_t n,
   int m = 0;
   for (int t = 0; t < K; ++t) {
     const int32_t nb = knn[i * K + t];
+    if (nb < 0) break;  // a row of an approximate graph with fewer than K neighbours
     for (int c = 0; c <= K; c += 32) {  // the batch {nb} + knn(nb): K + 1 distinct ids
       const int idx = c + lane;
       int32_t id = -1;
