@@ -437,23 +437,27 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
         // data exact in bf16: the selection itself is exact
         knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p,
                      d, 1, L, pool_id.p, pool_d2.p, st, &t_gemm, opts.pool_tiles);
+        t_knn.stop();
+        in.norms.release();
+        t_pool.start();
+        SSG_LAUNCH(k_pool_len_from_ids, (unsigned)ceil_div(n, 256), 256, 0, st, pool_id.p, n, L,
+                   pool_len.p);
+        t_pool.stop();
       } else {
         // other data: a bf16 selection of L + slack candidates (approximate distances), then
-        // each pool re-ranked by exact double-precision distance, the L nearest kept
+        // each pool ordered from the original vectors as Alg. 3's pools are and cut to L
         const int Lp = (int)std::min<int64_t>(std::min(L + std::max(8, L / 4), 895), n - 1);
         Scratch<int32_t> cid((size_t)n * Lp, st);
         Scratch<float> cd2((size_t)n * Lp, st);
         knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p,
                      d, 1, Lp, cid.p, cd2.p, st, &t_gemm, opts.pool_tiles, true);
-        rerank_exact(in.rows.p, in.rows.ld, in.rows.p, in.rows.ld, d, n, cid.p, Lp, L, pool_id.p,
-                     pool_d2.p, st);
+        t_knn.stop();
+        in.norms.release();
+        t_pool.start();
+        pool_from_candidates(in.rows.p, in.rows.ld, d, n, cid.p, Lp, L, in.info.exact, pool_id.p,
+                             pool_d2.p, pool_len.p, ctr.p, st);
+        t_pool.stop();
       }
-      t_knn.stop();
-      in.norms.release();
-      t_pool.start();
-      SSG_LAUNCH(k_pool_len_from_ids, (unsigned)ceil_div(n, 256), 256, 0, st, pool_id.p, n, L,
-                 pool_len.p);
-      t_pool.stop();
     } else {
       // a1: exact kNN graph
       Scratch<int32_t> knn_id((size_t)n * K, st);

@@ -336,44 +336,6 @@ __global__ void k_knn_rerank(const float* __restrict__ A, int lda, const float* 
   }
 }
 
-// Exact re-rank of candidate ids: one warp per row, double-precision distances, sorted by
-// (d2, id); the K nearest are written (ids of -1 sort last and come out as -1 / inf).
-__global__ void k_rerank_ids(const float* __restrict__ A, int lda, const float* __restrict__ B,
-                             int ldb, int d, int64_t na, const int32_t* __restrict__ cand, int KS,
-                             int K, int KSP, int32_t* __restrict__ out_id,
-                             float* __restrict__ out_d2) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
-  double* dv = (double*)sm_raw + (size_t)warp * KSP;
-  int32_t* iv = (int32_t*)((double*)sm_raw + (size_t)wpb * KSP) + (size_t)warp * KSP;
-  const int64_t row = (int64_t)blockIdx.x * wpb + warp;
-  if (row >= na) return;
-  const float* a = A + row * lda;
-  for (int e = lane; e < KSP; e += 32) {
-    const int32_t j = e < KS ? cand[row * KS + e] : -1;
-    dv[e] = j >= 0 ? dist2_f64(a, B + (int64_t)j * ldb, d)
-                   : __longlong_as_double(0x7ff0000000000000ll);
-    iv[e] = j;
-  }
-  __syncwarp();
-  warp_sort_pairs(dv, iv, KSP);
-  for (int e = lane; e < K; e += 32) {
-    out_id[row * K + e] = iv[e];
-    out_d2[row * K + e] = iv[e] >= 0 ? (float)dv[e] : __int_as_float(0x7f800000);
-  }
-}
-
-void rerank_exact(const float* A, int lda, const float* B, int ldb, int d, int64_t na,
-                  const int32_t* cand, int KS, int K, int32_t* out_id, float* out_d2,
-                  cudaStream_t st) {
-  const int KSP = next_pow2(KS);
-  const int wpb = 4;
-  const size_t smem = (size_t)wpb * KSP * (sizeof(double) + sizeof(int32_t));
-  ensure_smem((const void*)k_rerank_ids, smem);
-  SSG_LAUNCH(k_rerank_ids, (unsigned)ceil_div(na, wpb), wpb * 32, smem, st, A, lda, B, ldb, d, na,
-             cand, KS, K, KSP, out_id, out_d2);
-}
-
 // Exhaustive double-precision recomputation of flagged rows: every column whose
 // single-precision direct distance could be <= the K-th re-ranked value is recomputed in
 // double and collected; the collected set is sorted by (d2, id).

@@ -55,12 +55,6 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
                   int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer,
                   int max_tiles = 0, bool approx = false);
 
-// Re-ranks each row's candidate ids (KS per row, -1 padded) by exact double-precision
-// distance and keeps the K nearest by (d2, id); out may alias ids only when K == KS.
-void rerank_exact(const float* A, int lda, const float* B, int ldb, int d, int64_t na,
-                  const int32_t* cand, int KS, int K, int32_t* out_id, float* out_d2,
-                  cudaStream_t st);
-
 struct Counters {
   unsigned long long angle_fp64;
   unsigned long long order_fp64;
@@ -72,6 +66,12 @@ struct Counters {
 void pool_run(const float* X, int ld, int d, int64_t n, const int32_t* knn, int K, int L,
               int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len, Counters* dctr,
               cudaStream_t st);
+
+// Pools from arbitrary candidate lists (cand [n][KS], -1 padded): the L nearest by
+// (d2, id), ordered exactly as pool_run orders its pools.
+void pool_from_candidates(const float* X, int ld, int d, int64_t n, const int32_t* cand, int KS,
+                          int L, int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
+                          Counters* dctr, cudaStream_t st);
 
 // SSG prune of each node's pool.
 void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,

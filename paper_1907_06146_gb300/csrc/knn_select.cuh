@@ -83,11 +83,13 @@ __device__ __noinline__ int compact_row(uint64_t* __restrict__ buf, int cnt, int
 // Threshold step of a row's buffer without sorting: finds the KS-th smallest distance t
 // by bisection over the 32-bit order keys (each step counts the entries at or below the
 // midpoint), then keeps, unsorted and in their old relative order, every entry with a
-// distance at most t (all ties at t stay).  Returns the new count with *tau = t, or -1 with
-// the buffer untouched when more than cap entries would stay.  Needs cnt >= KS.
+// distance at most t (all ties at t stay).  The bisection stops early at a t with between
+// KS and `good` entries at or below it (a looser t, still above every one of the KS
+// smallest).  Returns the new count with *tau = t, or -1 with the buffer untouched when more
+// than cap entries would stay.  Needs cnt >= KS.
 template <int C>
-__device__ __noinline__ int select_row(uint64_t* __restrict__ buf, int cnt, int KS, int cap,
-                                       float* tau) {
+__device__ __noinline__ int select_row(uint64_t* __restrict__ buf, int cnt, int KS, int good,
+                                       int cap, float* tau) {
   constexpr int E = C / 32;
   const int lane = lane_id();
   uint32_t k[E];
@@ -116,10 +118,12 @@ __device__ __noinline__ int select_row(uint64_t* __restrict__ buf, int cnt, int 
     for (int e = 0; e < E; ++e) c += k[e] <= mid ? 1 : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (c >= KS)
+    if (c >= KS) {
       hi = mid;
-    else
+      if (c <= good) break;
+    } else {
       lo = mid + 1;
+    }
   }
   int n = 0;
 #pragma unroll

@@ -361,7 +361,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           uint64_t* lb = p.rowbuf + ((size_t)blockIdx.x * BM + h * 128 + q * 32 + l) * C;
           const int cl = __shfl_sync(0xffffffffu, cnt, l);
           float t2;
-          int c2 = select_row<C>(lb, cl, p.KS, (p.KS + p.trig) / 2, &t2);
+          int c2 = select_row<C>(lb, cl, p.KS, (p.KS + p.trig) / 2, p.trig, &t2);
           if (c2 < 0) {
             // too many ties at the threshold: a sort settles them by original id, and the
             // kept keys go back to stored positions like the ones still to come
@@ -384,7 +384,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         float t2;
         int cl = __shfl_sync(0xffffffffu, cnt, l);
         if (cl > 256 && cl > p.KS) {
-          const int c1 = select_row<C>(lb, cl, p.KS, 256, &t2);
+          const int c1 = select_row<C>(lb, cl, p.KS, 256, 256, &t2);
           if (c1 >= 0) cl = c1;
         }
         map_key_ids(lb, cl, p.perm);
@@ -547,7 +547,11 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   maps.b_aug = make_map(aug_b.p, nb, AUG, AUG, BN, CU_TENSOR_MAP_SWIZZLE_32B);
   const int64_t nrb = ceil_div(na, BM);
   const int grid = (int)std::min<int64_t>(nrb, num_sms());
-  const int C = KS + BN <= 256 ? 256 : (KS + BN <= 512 ? 512 : 1024);
+  // A row buffer holds C keys and is compacted once a tile could overflow it.  A limited
+  // walk spends most of its tiles while the threshold is still falling, so it gets room
+  // for about KS more keys between compactions.
+  const int need = max_tiles > 0 ? 2 * KS + BN : KS + BN;
+  const int C = need <= 256 ? 256 : (need <= 512 ? 512 : 1024);
   Scratch<uint64_t> rowbuf((size_t)grid * BM * C, st);
   TcArgs a{};
   a.a_norm = a_norm;

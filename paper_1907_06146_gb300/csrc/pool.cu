@@ -29,6 +29,37 @@ __device__ __forceinline__ bool hash_insert(int32_t* h, int log2cap, int32_t id)
   }
 }
 
+// keys[0, m): node i's candidate ids.  Orders them by (d2, id) -- fp32 distances, runs of
+// near-equal values re-sorted in fp64 unless the data are exact -- and writes the first
+// L as node i's pool.  keys has room for the next power of two >= m; d64 for m doubles.
+__device__ __forceinline__ void pool_finish(uint64_t* keys, int m, int L, int exact, double* d64,
+                                            const float* __restrict__ X, int ld, int d,
+                                            int64_t i, float rel, int32_t* __restrict__ pool_id,
+                                            float* __restrict__ pool_d2,
+                                            int32_t* __restrict__ pool_len,
+                                            unsigned long long* __restrict__ n_order) {
+  const int lane = lane_id();
+  const float* xi = X + i * ld;
+  warp_fill_dist_keys(keys, m, X, ld, xi);
+  int mp = 1;
+  while (mp < m) mp <<= 1;
+  for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
+  __syncwarp();
+  warp_sort_keys(keys, mp);
+  const int keep = m < L ? m : L;
+  if (!exact && m > 1) {
+    int f = warp_fix_runs(keys, m, keep, d64, X, ld, d, xi, rel);
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0 && f) atomicAdd(n_order, (unsigned long long)f);
+  }
+  for (int t = lane; t < L; t += 32) {
+    const bool v = t < keep;
+    pool_id[i * L + t] = v ? key_id(keys[t]) : -1;
+    pool_d2[i * L + t] = v ? key_dist(keys[t]) : __int_as_float(0x7f800000);
+  }
+  if (lane == 0) pool_len[i] = keep;
+}
+
 __global__ void k_pool(const float* __restrict__ X, int ld, int d, int64_t n,
                        const int32_t* __restrict__ knn, int K, int L, int cap, int log2h,
                        int exact, float rel, int32_t* __restrict__ pool_id,
@@ -61,26 +92,33 @@ __global__ void k_pool(const float* __restrict__ X, int ld, int d, int64_t n,
     if (m >= L) break;
   }
   __syncwarp();
+  pool_finish(keys, m, L, exact, (double*)hset, X, ld, d, i, rel, pool_id, pool_d2, pool_len,
+              n_order);
+}
 
-  const float* xi = X + i * ld;
-  warp_fill_dist_keys(keys, m, X, ld, xi);
-  int mp = 1;
-  while (mp < m) mp <<= 1;
-  for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
+// Pools from given candidates: row i's pool is the L nearest of its KS candidate ids
+// (cand [n][KS], -1 padded; i itself skipped), ordered as k_pool orders them.
+__global__ void k_pool_cand(const float* __restrict__ X, int ld, int d, int64_t n,
+                            const int32_t* __restrict__ cand, int KS, int L, int cap, int exact,
+                            float rel, int32_t* __restrict__ pool_id, float* __restrict__ pool_d2,
+                            int32_t* __restrict__ pool_len, unsigned long long* __restrict__ n_order) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
+  uint64_t* keys = (uint64_t*)(sm_raw + (size_t)warp * cap * 16);
+  double* d64 = (double*)(keys + cap);
+  const int64_t i = (int64_t)blockIdx.x * wpb + warp;
+  if (i >= n) return;
+  int m = 0;
+  for (int c = 0; c < KS; c += 32) {
+    const int t = c + lane;
+    const int32_t id = t < KS ? cand[i * KS + t] : -1;
+    const bool v = id >= 0 && id != (int32_t)i;
+    const unsigned bal = __ballot_sync(0xffffffffu, v);
+    if (v) keys[m + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
+    m += __popc(bal);
+  }
   __syncwarp();
-  warp_sort_keys(keys, mp);
-  const int keep = m < L ? m : L;
-  if (!exact && m > 1) {
-    int f = warp_fix_runs(keys, m, keep, (double*)hset, X, ld, d, xi, rel);
-    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-    if (lane == 0 && f) atomicAdd(n_order, (unsigned long long)f);
-  }
-  for (int t = lane; t < L; t += 32) {
-    const bool v = t < keep;
-    pool_id[i * L + t] = v ? key_id(keys[t]) : -1;
-    pool_d2[i * L + t] = v ? key_dist(keys[t]) : __int_as_float(0x7f800000);
-  }
-  if (lane == 0) pool_len[i] = keep;
+  pool_finish(keys, m, L, exact, d64, X, ld, d, i, rel, pool_id, pool_d2, pool_len, n_order);
 }
 
 void pool_run(const float* X, int ld, int d, int64_t n, const int32_t* knn, int K, int L,
@@ -95,6 +133,17 @@ void pool_run(const float* X, int ld, int d, int64_t n, const int32_t* knn, int 
   ensure_smem((const void*)k_pool, smem);
   SSG_LAUNCH(k_pool, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, ld, d, n, knn, K, L, cap,
              log2h, exact, dist_rel_fp32(d), pool_id, pool_d2, pool_len, &dctr->order_fp64);
+}
+
+void pool_from_candidates(const float* X, int ld, int d, int64_t n, const int32_t* cand, int KS,
+                          int L, int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
+                          Counters* dctr, cudaStream_t st) {
+  const int cap = next_pow2(KS);
+  const int wpb = 8;
+  const size_t smem = (size_t)cap * 16 * wpb;
+  ensure_smem((const void*)k_pool_cand, smem);
+  SSG_LAUNCH(k_pool_cand, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, ld, d, n, cand, KS,
+             L, cap, exact, dist_rel_fp32(d), pool_id, pool_d2, pool_len, &dctr->order_fp64);
 }
 
 // ---------------------------------------------------------------------------------------
