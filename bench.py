@@ -295,6 +295,55 @@ def run_serving(ssg, g, base, w, seconds: float, rate: float, seed: int = 190706
                    "L_search uniform in [k, 512]"}
 
 
+def run_serve_deep(ssg, n, tiles, seconds, rate, target):
+    """The 96-d L2-normalised workload at n points: built with Alg. 4's search-based pools
+    over `tiles` tiles (no O(n^2) kNN graph), its recall@10 sweep, and the serving run on
+    it.  Returns build time, stage times, the sweep and the serving figures."""
+    import torch
+    from paper_1907_06146_gb300 import synth
+    t0 = time.perf_counter()
+    w = synth.deep_like(n=n, nq=10_000)
+    gen_s = time.perf_counter() - t0
+    base = torch.from_numpy(w.base).cuda()
+    queries = torch.from_numpy(w.queries).cuda()
+    nq = w.queries.shape[0]
+    truth, _ = ssg.knn_query(base, queries, 10)
+    g = ssg.build(base, w.K, w.L, w.R, w.alpha, n_nav=w.n_nav, pool_tiles=tiles)
+    del g
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = ssg.build(base, w.K, w.L, w.R, w.alpha, n_nav=w.n_nav, pool_tiles=tiles)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    sweep, at = [], None
+    for ls in LS_SWEEP:
+        ids, _ = g.search(base, queries, 10, ls)
+        r = ssg.recall_hits(ids, truth, 10) / (nq * 10.0)
+        sweep.append((ls, r))
+        if r >= target:
+            ts = []
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.search(base, queries, 10, ls)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            at = {"L_search": ls, "recall@10": r, "qps": nq / (min(ts) / 1e3)}
+            break
+    serving = run_serving(ssg, g, base, w, seconds, rate) if seconds > 0 else None
+    out = {"workload": f"deep_like n={n} d=96 (2,000-Gaussian mixture, L2-normalised)",
+           "K": w.K, "L": w.L, "R": w.R, "alpha": w.alpha, "pool_tiles": tiles,
+           "host_generation_s": gen_s, "build_s": build_s,
+           "stages_ms": {k: g.stats[k] for k in ("ms_knn", "ms_knn_gemm", "ms_pool", "ms_prune",
+                                                  "ms_reverse", "ms_connect", "ms_total")},
+           "n_repair": g.stats["n_repair"], "avg_out_degree": float(g.deg.float().mean().item()),
+           "sweep": sweep, "at_target": at, "serving": serving}
+    del g
+    return out
+
+
 def run_batched(ssg, count, n_streams):
     """Independent indices (float Gaussian mixtures, shapes from synth.batched_specs) built
     by ssg_build_batched and one by one; wall-clock seconds with the device synchronised."""
@@ -461,6 +510,11 @@ def run_gpu(args):
         from paper_1907_06146_gb300 import ablations as abl
         ablations = abl.run_all(ssg, synth, w)
 
+    serving_deep = None
+    if rank == 0 and args.serve_deep > 0:
+        serving_deep = run_serve_deep(ssg, args.serve_deep, args.serve_deep_tiles,
+                                      args.serve_seconds, args.serve_rate, args.target_recall)
+
     batched = None
     if rank == 0 and args.batched > 0:
         batched = run_batched(ssg, args.batched, args.batched_streams)
@@ -534,6 +588,7 @@ def run_gpu(args):
                        "ms_connect", "ms_total")},
         "ground_truth_ms": float(np.mean(gt_ms)),
         "serving": serving,
+        "serving_deep": serving_deep,
         "fp32_path": fp32_arm,
         "batched": batched,
         "ablations": ablations,
@@ -578,6 +633,11 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="length of the serving run (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="requests per second offered")
+    ap.add_argument("--serve-deep", type=int, default=0,
+                    help="also build the 96-d L2-normalised workload at this many points with "
+                         "search-based pools and serve it (10000000: the 10M serving case)")
+    ap.add_argument("--serve-deep-tiles", type=int, default=256,
+                    help="tiles each node's pool is searched over for --serve-deep")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
