@@ -429,8 +429,9 @@ def run_gpu(args):
             break
     # the search's work at that L_search (untimed): algorithmic bytes per query
     _, _, work = ssg.search_work(base, g.adj, g.deg, g.nav, queries, 10, ls_used)
+    row_b = g.stats["search_row_bytes"]  # 1: the graph searches a byte copy of the rows
     search_bytes = (work["adjacency_entries"] * 4 + work["expansions"] * 4
-                    + work["distances"] * w.d * 4 + nq * w.d * 4)
+                    + work["distances"] * w.d * row_b + nq * w.d * 4)
     del g
 
     for _ in range(args.warmup):
@@ -581,8 +582,8 @@ def run_gpu(args):
                                 "frac": search_bytes / (np.mean(search_ms) / 1e3) / 1e9 / peaks["hbm_gbs"],
                                 "traffic": None, "kernel": "k_search",
                                 "algorithmic": "per query: 4 B per adjacency entry read and per "
-                                               "expansion (degree), d x 4 B per distance, d x 4 B "
-                                               "query"}},
+                                               f"expansion (degree), d x {row_b} B per distance "
+                                               "(the rows the search reads), d x 4 B query"}},
         "stages_ms": {k: float(np.mean([s[k] for s in stats])) for k in
                       ("ms_ingest", "ms_knn", "ms_knn_gemm", "ms_pool", "ms_prune", "ms_reverse",
                        "ms_connect", "ms_total")},

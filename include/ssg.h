@@ -85,6 +85,10 @@ typedef struct {
   int64_t kernel_launches;      /* kernels this call launched */
   int32_t gemm_prec_used;       /* ssg_precision actually used for the kNN GEMM */
   double ms_knn_gemm;           /* time of the distance-GEMM + selection kernel alone */
+  int32_t search_row_bytes;     /* bytes per value of the rows this graph's searches read:
+                                   1 for data that are integers 0..255 (the graph keeps a byte
+                                   copy of the rows, used when ssg_search is given the base it
+                                   was built from), 4 otherwise */
 } ssg_build_stats;
 
 typedef struct ssg_graph ssg_graph; /* opaque, owned by the library; ssg_free releases it */

@@ -306,8 +306,8 @@ ssg_status ssg_search_adj(const float* base, int64_t n, int32_t d, const int32_t
     PaddedRows b, q;
     pad_rows(base, n, d, st, b);
     pad_rows(queries, nq, d, st, q);
-    search_run(b.p, b.ld, d, n, adj, deg, R, nav, n_nav, q.p, q.ld, nq, k, L_search, out_ids,
-               out_d2, st);
+    search_run(b.p, nullptr, b.ld, d, n, adj, deg, R, nav, n_nav, q.p, q.ld, nq, k, L_search,
+               out_ids, out_d2, st);
   });
 }
 
@@ -330,8 +330,8 @@ ssg_status ssg_search_work(const float* base, int64_t n, int32_t d, const int32_
       PaddedRows b, q;
       pad_rows(base, n, d, st, b);
       pad_rows(queries, nq, d, st, q);
-      search_run(b.p, b.ld, d, n, adj, deg, R, nav, n_nav, q.p, q.ld, nq, k, L_search, out_ids,
-                 out_d2, st, w.p);
+      search_run(b.p, nullptr, b.ld, d, n, adj, deg, R, nav, n_nav, q.p, q.ld, nq, k, L_search,
+                 out_ids, out_d2, st, w.p);
     }
     unsigned long long h[3];
     SSG_CUDA(cudaMemcpyAsync(h, w.p, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -504,6 +504,14 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     const int64_t rep = connect_run(in.rows.p, in.rows.ld, d, n, g->adj, g->deg, R, g->nav_dev,
                                     nav.data(), opts.n_nav, st);
     t_con.stop();
+    // integers 0..255: the search reads a byte copy of the rows (a quarter of the bytes,
+    // the same distances)
+    if (in.info.exact && in.info.nonneg && in.info.max_abs <= 255.f) {
+      SSG_CUDA(cudaMalloc(&g->rows_u8, (size_t)n * in.rows.ld));
+      g->rows_ld = in.rows.ld;
+      g->rows_src = base;
+      rows_to_u8(in.rows.p, in.rows.ld, d, n, g->rows_u8, st);
+    }
     t_all.stop();
 
     Counters hc;
@@ -525,6 +533,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     S.exact_mode = in.info.exact;
     S.gemm_prec_used = tc ? SSG_PREC_BF16 : SSG_PREC_FP32;
     S.kernel_launches = t_launches - launches0;
+    S.search_row_bytes = g->rows_u8 ? 1 : 4;
     if (stats) *stats = S;
     *out = gp.release();
   });
@@ -646,8 +655,24 @@ ssg_status ssg_search(const ssg_graph* g, const float* base, const float* querie
     set_error("no base vectors: pass the device array the graph was built from");
     return SSG_EINVAL;
   }
-  return ssg_search_adj(b, g->n, g->d, g->adj, g->deg, g->R, g->nav_dev, g->n_nav, queries, nq, k,
-                        L_search, out_ids, out_d2, stream);
+  if (!(g->rows_u8 && b == g->rows_src))
+    return ssg_search_adj(b, g->n, g->d, g->adj, g->deg, g->R, g->nav_dev, g->n_nav, queries, nq,
+                          k, L_search, out_ids, out_d2, stream);
+  // the base the graph was built from, held as bytes: search the byte rows
+  return guard([&] {
+    SSG_REQUIRE(queries && out_ids, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(k >= 1 && k <= L_search && L_search <= 1024, SSG_EINVAL,
+                "need 1 <= k <= L_search <= 1024");
+    SSG_REQUIRE(nq >= 0, SSG_EINVAL, "bad sizes");
+    if (nq == 0) return;
+    cudaStream_t st = (cudaStream_t)stream;
+    PaddedRows q;
+    pad_rows(queries, nq, g->d, st, q);
+    SSG_REQUIRE(q.ld == g->rows_ld, SSG_EINTERNAL, "byte rows: stride %d, queries %d", g->rows_ld,
+                q.ld);
+    search_run(b, g->rows_u8, g->rows_ld, g->d, g->n, g->adj, g->deg, g->R, g->nav_dev, g->n_nav,
+               q.p, q.ld, nq, k, L_search, out_ids, out_d2, st);
+  });
 }
 
 ssg_status ssg_search_host(const ssg_graph* g, const float* queries_host, int64_t nq, int32_t k,

@@ -14,7 +14,13 @@ struct ssg_graph {
   int32_t* nav_dev = nullptr;  // device [n_nav]
   std::vector<int32_t> nav_host;
   float* base_owned = nullptr;  // device copy of the base when built from host vectors
+  // Byte copy of the base rows [n][rows_ld] when the data are integers 0..255, read by
+  // searches given the base it was made from (rows_src) instead of the float rows.
+  uint8_t* rows_u8 = nullptr;
+  int32_t rows_ld = 0;
+  const float* rows_src = nullptr;
   ~ssg_graph() {
+    if (rows_u8) cudaFree(rows_u8);
     if (adj) cudaFree(adj);
     if (deg) cudaFree(deg);
     if (nav_dev) cudaFree(nav_dev);

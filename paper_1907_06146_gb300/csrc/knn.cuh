@@ -96,18 +96,23 @@ int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int3
                     int R, const int32_t* nav_dev, const int32_t* nav_host, int n_nav,
                     cudaStream_t st);
 
-// Search-on-Graph.
+// Search-on-Graph.  X: float rows at stride ld; X8 (nullable): the same values as bytes
+// (integers 0..255) at the same stride, read instead of X when given (same results).
 // work (nullable, device): totals of expansions, distance evaluations, adjacency entries.
-void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
+void search_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const int32_t* adj,
                 const int32_t* deg, int R, const int32_t* nav, int n_nav, const float* Q,
                 int ldq, int64_t nq, int k, int Ls, int32_t* out_ids, float* out_d2,
                 cudaStream_t st, unsigned long long* work = nullptr);
 
 // Search with a per-query k (qk) and pool size (qls <= ls_max); results at stride ldo.
-void search_run_mixed(const float* X, int ld, int d, const int32_t* adj, const int32_t* deg, int R,
-                      const int32_t* nav, int n_nav, const float* Q, int ldq, int64_t nq,
-                      const int32_t* qk, const int32_t* qls, int ls_max, int ldo,
-                      int32_t* out_ids, float* out_d2, cudaStream_t st);
+void search_run_mixed(const float* X, const uint8_t* X8, int ld, int d, const int32_t* adj,
+                      const int32_t* deg, int R, const int32_t* nav, int n_nav, const float* Q,
+                      int ldq, int64_t nq, const int32_t* qk, const int32_t* qls, int ls_max,
+                      int ldo, int32_t* out_ids, float* out_d2, cudaStream_t st);
+
+// Byte copy [n][ld] of rows that hold integers 0..255 (ld: the float rows' stride, a
+// multiple of 4; padding bytes 0).
+void rows_to_u8(const float* X, int ld, int d, int64_t n, uint8_t* out, cudaStream_t st);
 
 // Padded view of X only (no statistics, no synchronisation).
 void pad_rows(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out);

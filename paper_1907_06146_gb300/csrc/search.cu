@@ -8,6 +8,11 @@
 // 8 row gathers in flight), sorts them with a warp bitonic sort and merges them into S
 // with a rank-based parallel merge, cut at L_search.
 //
+// Rows: float32, or -- for data that are integers 0..255 -- a byte copy of the same
+// values.  A byte row of 128 dimensions is one 128-byte line instead of four; every lane
+// converts its bytes to the same float values and sums them in the same order as the
+// float path, so the distances and results are bit for bit those of the float rows.
+//
 // Visited set: a direct-mapped cache of ids in shared memory.  Alg. 1 never re-adds a
 // visited node; here a node that fell out of the cache may be met again and its distance
 // recomputed, but the result is the same: a node that is still in S has the same key and
@@ -21,35 +26,67 @@
 
 namespace ssg {
 
+// Four consecutive values of a row as floats: one float4 load, or one 32-bit load of four
+// bytes (each byte b becomes the float 2^23 + b by placing it under the exponent bits of
+// 2^23, then b exactly by subtracting 2^23).
+__device__ __forceinline__ float4 row_raw(const float* x, int f) {
+  return __ldg((const float4*)x + f);
+}
+__device__ __forceinline__ uint32_t row_raw(const uint8_t* x, int f) {
+  return __ldg((const unsigned int*)x + f);
+}
+__device__ __forceinline__ float4 raw_f4(float4 v) { return v; }
+__device__ __forceinline__ float byte_f(uint32_t w, uint32_t sel) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - 8388608.f;
+}
+__device__ __forceinline__ float4 raw_f4(uint32_t w) {
+  return make_float4(byte_f(w, 0x7440), byte_f(w, 0x7441), byte_f(w, 0x7442), byte_f(w, 0x7443));
+}
+template <typename T>
+struct RawOf;
+template <>
+struct RawOf<float> {
+  using type = float4;
+  static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <>
+struct RawOf<uint8_t> {
+  using type = uint32_t;
+  static __device__ __forceinline__ uint32_t zero() { return 0u; }
+};
+
+// x: a row of ld values (ld4 = ld / 4 groups of four)
+template <typename T>
 __device__ __forceinline__ float team8_dist_q(const float* __restrict__ qs,
-                                              const float* __restrict__ x, int ld4, int tl,
+                                              const T* __restrict__ x, int ld4, int tl,
                                               bool valid) {
+  using Raw = typename RawOf<T>::type;
   float s = 0.f;
   if (valid) {
     const float4* q4 = (const float4*)qs;
-    const float4* x4 = (const float4*)x;
-    // the row's loads (up to four float4 per lane per 128 floats) are all issued before
-    // the first multiply-add
+    // the row's loads (up to four per lane per 128 values) are all issued before the first
+    // multiply-add
     for (int f0 = tl; f0 < ld4; f0 += 32) {
-      float4 b[4];
+      Raw b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int f = f0 + 8 * i;
-        b[i] = f < ld4 ? __ldg(x4 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        b[i] = f < ld4 ? row_raw(x, f) : RawOf<T>::zero();
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int f = f0 + 8 * i;
         if (f < ld4) {
           const float4 a = q4[f];
+          const float4 v = raw_f4(b[i]);
           float u;
-          u = a.x - b[i].x;
+          u = a.x - v.x;
           s = fmaf(u, u, s);
-          u = a.y - b[i].y;
+          u = a.y - v.y;
           s = fmaf(u, u, s);
-          u = a.z - b[i].z;
+          u = a.z - v.z;
           s = fmaf(u, u, s);
-          u = a.w - b[i].w;
+          u = a.w - v.w;
           s = fmaf(u, u, s);
         }
       }
@@ -61,46 +98,51 @@ __device__ __forceinline__ float team8_dist_q(const float* __restrict__ qs,
   return s;
 }
 
-// Two rows at once (8 rows in flight per warp).
-__device__ __forceinline__ float2 team8_dist2_q(const float* __restrict__ qs,
-                                                const float* __restrict__ x0,
-                                                const float* __restrict__ x1, int ld4, int tl,
-                                                bool v0, bool v1) {
-  float s0 = 0.f, s1 = 0.f;
+// NR rows per team at once (4 NR rows in flight per warp): the loads of all NR rows are
+// issued before the first multiply-add.  Each row's sum runs in the same order as in
+// team8_dist_q.  Rows are X + ids[r] * ld; rows with valid[r] false give 0.
+template <typename T, int NR>
+__device__ __forceinline__ void team8_distN_q(const float* __restrict__ qs,
+                                              const T* __restrict__ X, int ld,
+                                              const int32_t (&ids)[NR], const bool (&valid)[NR],
+                                              int ld4, int tl, float (&out)[NR]) {
+  using Raw = typename RawOf<T>::type;
   const float4* q4 = (const float4*)qs;
-  const float4* a4 = (const float4*)x0;
-  const float4* b4 = (const float4*)x1;
-  for (int f0 = tl; f0 < ld4; f0 += 32) {
-    float4 ra[4], rb[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int f = f0 + 8 * i;
-      ra[i] = (v0 && f < ld4) ? __ldg(a4 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
-      rb[i] = (v1 && f < ld4) ? __ldg(b4 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int r = 0; r < NR; ++r) out[r] = 0.f;
+  for (int f0 = tl; f0 < ld4; f0 += 32) {
+    Raw raw[NR][4];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const T* x = X + (int64_t)ids[r] * ld;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int f = f0 + 8 * i;
+        raw[r][i] = (valid[r] && f < ld4) ? row_raw(x, f) : RawOf<T>::zero();
+      }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int f = f0 + 8 * i;
       if (f < ld4) {
         const float4 q = q4[f];
-        float u;
-        u = q.x - ra[i].x; s0 = fmaf(u, u, s0);
-        u = q.y - ra[i].y; s0 = fmaf(u, u, s0);
-        u = q.z - ra[i].z; s0 = fmaf(u, u, s0);
-        u = q.w - ra[i].w; s0 = fmaf(u, u, s0);
-        u = q.x - rb[i].x; s1 = fmaf(u, u, s1);
-        u = q.y - rb[i].y; s1 = fmaf(u, u, s1);
-        u = q.z - rb[i].z; s1 = fmaf(u, u, s1);
-        u = q.w - rb[i].w; s1 = fmaf(u, u, s1);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const float4 v = raw_f4(raw[r][i]);
+          float u;
+          u = q.x - v.x; out[r] = fmaf(u, u, out[r]);
+          u = q.y - v.y; out[r] = fmaf(u, u, out[r]);
+          u = q.z - v.z; out[r] = fmaf(u, u, out[r]);
+          u = q.w - v.w; out[r] = fmaf(u, u, out[r]);
+        }
       }
     }
   }
 #pragma unroll
   for (int o = 1; o < 8; o <<= 1) {
-    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) out[r] += __shfl_xor_sync(0xffffffffu, out[r], o);
   }
-  return make_float2(s0, s1);
 }
 
 // number of entries of a[0, len) that are < x (a sorted ascending)
@@ -126,7 +168,22 @@ struct SearchLayout {
   }
 };
 
-__global__ void k_search(const float* __restrict__ X, int ld, int d, const int32_t* __restrict__ adj,
+// Rows per team in the distance loop: a float row takes 16 registers per lane at d = 128,
+// a byte row 4, so byte rows keep twice as many rows in flight at the same 24 warps per SM
+// (measured on 1M x 128, L_search 40: 1.30 ms with 4 rows per team at 24 warps, 1.35 ms
+// with 2 at 32 warps, 1.76 ms with 8 at 16 warps; float rows 1.45 ms).
+template <typename T>
+struct RowsPerTeam {
+  static constexpr int value = 2;
+};
+template <>
+struct RowsPerTeam<uint8_t> {
+  static constexpr int value = 4;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256, 3)
+    k_search(const T* __restrict__ X, int ld, int d, const int32_t* __restrict__ adj,
                          const int32_t* __restrict__ deg, int R, const int32_t* __restrict__ nav,
                          int n_nav, const float* __restrict__ Q, int ldq, int64_t nq, int k,
                          const int32_t* __restrict__ qk, const int32_t* __restrict__ qls, int ldo,
@@ -223,16 +280,23 @@ __global__ void k_search(const float* __restrict__ X, int ld, int d, const int32
       w_adj += (unsigned long long)dg;
       w_dist += (unsigned long long)cnt;
       __syncwarp();
-      for (int t0 = 0; t0 < cnt; t0 += 8) {
-        const int t = t0 + team, t2 = t0 + 4 + team;
-        const bool va = t < cnt, vb = t2 < cnt;
-        const int32_t ia = va ? key_id(newk[t]) : 0;
-        const int32_t ib = vb ? key_id(newk[t2]) : 0;
-        const float2 dd = team8_dist2_q(qs, X + (int64_t)ia * ld, X + (int64_t)ib * ld, ld4, tl, va, vb);
+      constexpr int NR = RowsPerTeam<T>::value;
+      for (int t0 = 0; t0 < cnt; t0 += 4 * NR) {
+        int32_t ir[NR];
+        bool vr[NR];
+        float dd[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const int t = t0 + 4 * r + team;
+          vr[r] = t < cnt;
+          ir[r] = vr[r] ? key_id(newk[t]) : 0;
+        }
+        team8_distN_q<T, NR>(qs, X, ld, ir, vr, ld4, tl, dd);
         __syncwarp();
         if (tl == 0) {
-          if (va) newk[t] = make_key(dd.x, ia);
-          if (vb) newk[t2] = make_key(dd.y, ib);
+#pragma unroll
+          for (int r = 0; r < NR; ++r)
+            if (vr[r]) newk[t0 + 4 * r + team] = make_key(dd[r], ir[r]);
         }
       }
       __syncwarp();
@@ -298,18 +362,42 @@ __global__ void k_search(const float* __restrict__ X, int ld, int d, const int32
   }
 }
 
-static size_t search_smem_setup(SearchLayout& lay, int wpb) {
+__global__ void k_rows_u8(const float* __restrict__ X, int ld, int d, int64_t n,
+                          uint8_t* __restrict__ out) {
+  const int64_t total = n * (int64_t)ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e % ld);
+    out[e] = t < d ? (uint8_t)__float2uint_rn(X[e]) : (uint8_t)0;
+  }
+}
+
+void rows_to_u8(const float* X, int ld, int d, int64_t n, uint8_t* out, cudaStream_t st) {
+  SSG_LAUNCH(k_rows_u8, 8 * num_sms(), 256, 0, st, X, ld, d, n, out);
+}
+
+template <typename T>
+static void launch_search(const T* X, int ld, int d, const int32_t* adj, const int32_t* deg, int R,
+                          const int32_t* nav, int n_nav, const float* Q, int ldq, int64_t nq, int k,
+                          const int32_t* qk, const int32_t* qls, int ldo, SearchLayout lay, int wpb,
+                          int32_t* out_ids, float* out_d2, unsigned long long* work,
+                          cudaStream_t st) {
   while (lay.per_warp() * wpb > 200 * 1024 && lay.log2h > 8) --lay.log2h;
   const size_t smem = lay.per_warp() * wpb;
   SSG_REQUIRE(smem <= 220 * 1024, SSG_EINVAL, "search: L_search and d too large for shared memory");
-  ensure_smem((const void*)k_search, smem);
-  return smem;
+  ensure_smem((const void*)k_search<T>, smem);
+  int blocks_per_sm = 0;
+  SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search<T>, wpb * 32, smem));
+  const int64_t want = ceil_div(nq, wpb);
+  const int grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, blocks_per_sm) * num_sms());
+  SSG_LAUNCH(k_search<T>, grid, wpb * 32, smem, st, X, ld, d, adj, deg, R, nav, n_nav, Q, ldq, nq,
+             k, qk, qls, ldo, lay, out_ids, out_d2, work);
 }
 
-void search_run_mixed(const float* X, int ld, int d, const int32_t* adj, const int32_t* deg, int R,
-                      const int32_t* nav, int n_nav, const float* Q, int ldq, int64_t nq,
-                      const int32_t* qk, const int32_t* qls, int ls_max, int ldo,
-                      int32_t* out_ids, float* out_d2, cudaStream_t st) {
+void search_run_mixed(const float* X, const uint8_t* X8, int ld, int d, const int32_t* adj,
+                      const int32_t* deg, int R, const int32_t* nav, int n_nav, const float* Q,
+                      int ldq, int64_t nq, const int32_t* qk, const int32_t* qls, int ls_max,
+                      int ldo, int32_t* out_ids, float* out_d2, cudaStream_t st) {
   if (nq == 0) return;
   SearchLayout lay;
   lay.Ls = ls_max;
@@ -318,17 +406,15 @@ void search_run_mixed(const float* X, int ld, int d, const int32_t* adj, const i
   // 8 warps per block and a 1,024-entry visited cache: 24 warps per SM (the register
   // limit) keep more row gathers in flight than a larger cache would save
   lay.log2h = 10;
-  const int wpb = 8;
-  const size_t smem = search_smem_setup(lay, wpb);
-  int blocks_per_sm = 0;
-  SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search, wpb * 32, smem));
-  const int64_t want = ceil_div(nq, wpb);
-  const int grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, blocks_per_sm) * num_sms());
-  SSG_LAUNCH(k_search, grid, wpb * 32, smem, st, X, ld, d, adj, deg, R, nav, n_nav, Q, ldq, nq, 0,
-             qk, qls, ldo, lay, out_ids, out_d2, (unsigned long long*)nullptr);
+  if (X8)
+    launch_search(X8, ld, d, adj, deg, R, nav, n_nav, Q, ldq, nq, 0, qk, qls, ldo, lay, 8,
+                  out_ids, out_d2, (unsigned long long*)nullptr, st);
+  else
+    launch_search(X, ld, d, adj, deg, R, nav, n_nav, Q, ldq, nq, 0, qk, qls, ldo, lay, 8, out_ids,
+                  out_d2, (unsigned long long*)nullptr, st);
 }
 
-void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
+void search_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const int32_t* adj,
                 const int32_t* deg, int R, const int32_t* nav, int n_nav, const float* Q,
                 int ldq, int64_t nq, int k, int Ls, int32_t* out_ids, float* out_d2,
                 cudaStream_t st, unsigned long long* work) {
@@ -344,16 +430,12 @@ void search_run(const float* X, int ld, int d, int64_t n, const int32_t* adj,
   // Alg. 1's (each node once) and not inflated by recomputations after cache evictions.
   lay.log2h = work ? 14 : 10;
   const int wpb = work ? 2 : 8;
-  while (lay.per_warp() * wpb > 200 * 1024 && lay.log2h > 8) --lay.log2h;
-  const size_t smem = lay.per_warp() * wpb;
-  SSG_REQUIRE(smem <= 220 * 1024, SSG_EINVAL, "search: L_search and d too large for shared memory");
-  ensure_smem((const void*)k_search, smem);
-  int blocks_per_sm = 0;
-  SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search, wpb * 32, smem));
-  const int64_t want = ceil_div(nq, wpb);
-  const int grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, blocks_per_sm) * num_sms());
-  SSG_LAUNCH(k_search, grid, wpb * 32, smem, st, X, ld, d, adj, deg, R, nav, n_nav, Q, ldq, nq, k,
-             (const int32_t*)nullptr, (const int32_t*)nullptr, k, lay, out_ids, out_d2, work);
+  if (X8)
+    launch_search(X8, ld, d, adj, deg, R, nav, n_nav, Q, ldq, nq, k, (const int32_t*)nullptr,
+                  (const int32_t*)nullptr, k, lay, wpb, out_ids, out_d2, work, st);
+  else
+    launch_search(X, ld, d, adj, deg, R, nav, n_nav, Q, ldq, nq, k, (const int32_t*)nullptr,
+                  (const int32_t*)nullptr, k, lay, wpb, out_ids, out_d2, work, st);
 }
 
 }  // namespace ssg

@@ -76,6 +76,7 @@ struct ssg_server {
   int dev = 0;
   int d = 0, ld = 0;
   const float* base = nullptr;
+  const uint8_t* rows_u8 = nullptr;  // the graph's byte rows when they are of this base
   ssg::Scratch<float> base_pad;
   ssg_server_opts opts{};
   std::vector<std::unique_ptr<Slot>> slots;
@@ -180,7 +181,7 @@ bool launch_batch(ssg_server* s, Slot& sl) {
     SSG_CUDA(cudaMemcpyAsync(sl.d_par, sl.h_par, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, sl.st));
     SSG_CUDA(cudaMemcpyAsync(sl.d_par + s->opts.max_batch, sl.h_par + s->opts.max_batch,
                              sizeof(int32_t) * nq, cudaMemcpyHostToDevice, sl.st));
-    ssg::search_run_mixed(s->base, s->ld, s->d, g->adj, g->deg, g->R, g->nav_dev, g->n_nav, sl.d_q,
+    ssg::search_run_mixed(s->base, s->rows_u8, s->ld, s->d, g->adj, g->deg, g->R, g->nav_dev, g->n_nav, sl.d_q,
                           s->ld, nq, sl.d_par, sl.d_par + s->opts.max_batch, lsmax, kmax, sl.d_ids,
                           sl.d_d2, sl.st);
     SSG_CUDA(cudaMemcpyAsync(sl.h_ids, sl.d_ids, sizeof(int32_t) * nq * kmax, cudaMemcpyDeviceToHost,
@@ -262,6 +263,7 @@ ssg_status ssg_server_create(const ssg_graph* g, const float* base, const ssg_se
       pr.own.p = nullptr;
     }
     s->base = s->base_pad.p ? s->base_pad.p : b;
+    if (g->rows_u8 && b == g->rows_src && g->rows_ld == s->ld) s->rows_u8 = g->rows_u8;
     SSG_CUDA(cudaStreamSynchronize(s->slots[0]->st));
     const size_t mb = (size_t)o.max_batch;
     for (auto& sl : s->slots) {

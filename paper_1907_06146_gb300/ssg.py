@@ -41,7 +41,8 @@ class BuildStats(ctypes.Structure):
                 ("n_angle_fp64", ctypes.c_int64), ("n_order_fp64", ctypes.c_int64),
                 ("n_knn_fallback_rows", ctypes.c_int64), ("max_indegree", ctypes.c_int32),
                 ("exact_mode", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
-                ("gemm_prec_used", ctypes.c_int32), ("ms_knn_gemm", ctypes.c_double)]
+                ("gemm_prec_used", ctypes.c_int32), ("ms_knn_gemm", ctypes.c_double),
+                ("search_row_bytes", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
