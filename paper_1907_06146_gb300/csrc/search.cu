@@ -20,6 +20,8 @@
 // entered it) did so because S was full and its key was above the L_search-th key, which
 // never increases once S is full, so it is cut again.  Before S first fills nothing has
 // left it.  The cache only saves distance computations.
+#include <type_traits>
+
 #include "common.cuh"
 #include "graph_dev.cuh"
 #include "knn.cuh"
@@ -145,6 +147,70 @@ __device__ __forceinline__ void team8_distN_q(const float* __restrict__ qs,
   }
 }
 
+// Integer queries (every value an integer 0..255) against byte rows: with the query's bytes
+// packed four to a word (qw) and q2 = |q|^2, d2 = q2 + |x|^2 - 2 q.x from byte dot products
+// (dp4a), all in exact integer arithmetic.  Every value and partial sum of the float path
+// is an integer below 2^24 in that case, so the float path's sums are exact too and the two
+// give the same distances.
+template <int NR>
+__device__ __forceinline__ void team8_distN_qi(const uint32_t* __restrict__ qw,
+                                               const uint8_t* __restrict__ X, int ld,
+                                               const int32_t (&ids)[NR],
+                                               const bool (&valid)[NR], int ld4, int tl, int q2,
+                                               float (&out)[NR]) {
+  unsigned dot[NR], xx[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) dot[r] = xx[r] = 0u;
+  for (int f0 = tl; f0 < ld4; f0 += 32) {
+    uint32_t raw[NR][4];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const uint8_t* x = X + (int64_t)ids[r] * ld;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int f = f0 + 8 * i;
+        raw[r][i] = (valid[r] && f < ld4) ? row_raw(x, f) : 0u;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int f = f0 + 8 * i;
+      if (f < ld4) {
+        const uint32_t q = qw[f];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          dot[r] = __dp4a(q, raw[r][i], dot[r]);
+          xx[r] = __dp4a(raw[r][i], raw[r][i], xx[r]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      dot[r] += __shfl_xor_sync(0xffffffffu, dot[r], o);
+      xx[r] += __shfl_xor_sync(0xffffffffu, xx[r], o);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) out[r] = (float)((int)q2 + (int)xx[r] - 2 * (int)dot[r]);
+}
+
+// Ascending bitonic sort of one key per lane across the warp (in registers).
+__device__ __forceinline__ uint64_t warp_bitonic32(uint64_t b, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint64_t o = __shfl_xor_sync(0xffffffffu, b, j);
+      const bool take_min = ((lane & j) == 0) == ((lane & k) == 0);
+      b = take_min ? (o < b ? o : b) : (o > b ? o : b);
+    }
+  }
+  return b;
+}
+
 // number of entries of a[0, len) that are < x (a sorted ascending)
 __device__ __forceinline__ int count_less(const uint64_t* a, int len, uint64_t x) {
   int lo = 0, hi = len;
@@ -163,7 +229,7 @@ struct SearchLayout {
   __host__ __device__ size_t pool_bytes() const { return (size_t)Ls * 8; }
   __host__ __device__ size_t per_warp() const {
     size_t b = 2 * pool_bytes() + (((size_t)2 * Ls + 15) & ~(size_t)15) + (size_t)RP * 8 +
-               (size_t)ld * 4 + ((size_t)4 << log2h);
+               (size_t)ld * 4 + ((size_t)4 << log2h) + (((size_t)ld + 15) & ~(size_t)15);
     return (b + 15) & ~(size_t)15;
   }
 };
@@ -202,6 +268,7 @@ __global__ void __launch_bounds__(256, 3)
   float* qs = (float*)(newk + lay.RP);
   int32_t* cache = (int32_t*)(qs + ld);
   const int hcap = 1 << lay.log2h;
+  uint32_t* qw = (uint32_t*)(cache + hcap);  // the query's bytes, when it is integer 0..255
   const int ld4 = ld >> 2;
   (void)d;
 
@@ -218,6 +285,28 @@ __global__ void __launch_bounds__(256, 3)
     for (int t = lane; t < ld; t += 32) qs[t] = t < d ? qg[t] : 0.f;
     for (int t = lane; t < hcap; t += 32) cache[t] = -1;
     __syncwarp();
+    bool qint = false;
+    int q2 = 0;
+    if constexpr (std::is_same<T, uint8_t>::value) {
+      bool ok = true;
+      int sq = 0;
+      for (int t = lane; t < ld; t += 32) {
+        const float v = qs[t];
+        ok = ok && v >= 0.f && v <= 255.f && v == rintf(v);
+        const int iv = ok ? (int)v : 0;
+        sq += iv * iv;
+      }
+      qint = __all_sync(0xffffffffu, ok);
+      if (qint) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        q2 = sq;
+        for (int w = lane; w < ld4; w += 32)
+          qw[w] = (uint32_t)qs[4 * w] | ((uint32_t)qs[4 * w + 1] << 8) |
+                  ((uint32_t)qs[4 * w + 2] << 16) | ((uint32_t)qs[4 * w + 3] << 24);
+        __syncwarp();
+      }
+    }
 
     // entry: the nearest navigating node by (d2, id)
     uint64_t best = KEY_NONE;
@@ -291,7 +380,14 @@ __global__ void __launch_bounds__(256, 3)
           vr[r] = t < cnt;
           ir[r] = vr[r] ? key_id(newk[t]) : 0;
         }
-        team8_distN_q<T, NR>(qs, X, ld, ir, vr, ld4, tl, dd);
+        if constexpr (std::is_same<T, uint8_t>::value) {
+          if (qint)
+            team8_distN_qi<NR>(qw, X, ld, ir, vr, ld4, tl, q2, dd);
+          else
+            team8_distN_q<T, NR>(qs, X, ld, ir, vr, ld4, tl, dd);
+        } else {
+          team8_distN_q<T, NR>(qs, X, ld, ir, vr, ld4, tl, dd);
+        }
         __syncwarp();
         if (tl == 0) {
 #pragma unroll
@@ -300,11 +396,50 @@ __global__ void __launch_bounds__(256, 3)
         }
       }
       __syncwarp();
+      if (cnt <= 32) {
+        // one new key per lane: sorted in registers; one binary search in S gives both
+        // the duplicate test and the key's place in the merge
+        uint64_t b = lane < cnt ? newk[lane] : KEY_NONE;
+        b = warp_bitonic32(b, lane);
+        int r = 0;
+        bool keep = false;
+        if (lane < cnt) {
+          r = count_less(pA, s, b);
+          keep = !(r < s && pA[r] == b);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int j = __popc(bal & lanemask_lt());
+        const int kept = __popc(bal);
+        __syncwarp();
+        if (keep) newk[j] = b;
+        __syncwarp();
+        for (int i = lane; i < s; i += 32) {
+          const uint64_t a = pA[i];
+          const int pos = i + count_less(newk, kept, a);
+          if (pos < Ls) {
+            pB[pos] = a;
+            fB[pos] = fA[i];
+          }
+        }
+        if (keep && j + r < Ls) {
+          pB[j + r] = b;
+          fB[j + r] = 0;
+        }
+        s = s + kept < Ls ? s + kept : Ls;
+        __syncwarp();
+        uint64_t* tp = pA;
+        pA = pB;
+        pB = tp;
+        unsigned char* tf = fA;
+        fA = fB;
+        fB = tf;
+        continue;
+      }
       int cp = 1;
       while (cp < cnt) cp <<= 1;
       for (int t = cnt + lane; t < cp; t += 32) newk[t] = KEY_NONE;
       __syncwarp();
-      if (cnt > 1) warp_sort_keys(newk, cp);
+      warp_sort_keys(newk, cp);
       // drop keys already in S (same id => same key), compacting in place
       int kept = 0;
       for (int c = 0; c < cnt; c += 32) {

@@ -154,3 +154,22 @@ def test_float_few_tiles_invariants(ssg, fdata):
     oids = oracle.search(w.base, oa, od, nav, w.queries, 10, 64)[0]
     assert oracle.recall_at(_np(ids), truth, 10) >= oracle.recall_at(oids, truth, 10) - 0.15
 
+
+
+@pytest.mark.parametrize("n,d,L", [(70, 30, 60), (300, 30, 250)])
+def test_float_every_point_a_candidate_equals_oracle(ssg, n, d, L):
+    # L + slack >= n - 1: every other point is a candidate of the bf16 selection, so each
+    # pool is the exact L nearest after the exact ordering, and the float build must equal
+    # the oracle's prune / reverse / connect of the exact L-NN rows bit for bit (ragged
+    # tiles, rows padded to a multiple of 4)
+    w = synth.small(n=n, d=d, nq=0, seed=4100 + n)
+    R, alpha = 16, 60.0
+    nav = synth.nav_ids(n, 3, 41)
+    g = ssg.build(torch.from_numpy(w.base).cuda(), 10, L, R, alpha, nav=nav,
+                  pool_tiles=(n + 127) // 128)
+    ids, _ = oracle.knn_rows(w.base, L)
+    adj0, deg0 = oracle.prune(w.base, ids, np.full(n, L, np.int32), R, alpha)
+    adj1, deg1 = oracle.reverse(w.base, adj0, deg0, alpha)
+    adj, deg, _ = oracle.connect(w.base, adj1, deg1, nav)
+    np.testing.assert_array_equal(_np(g.deg), deg)
+    np.testing.assert_array_equal(_np(g.adj), adj)
