@@ -211,6 +211,38 @@ __device__ __forceinline__ uint64_t warp_bitonic32(uint64_t b, int lane) {
   return b;
 }
 
+// Same for two keys per lane (element e * 32 + lane in v[e]), 64 in all.
+__device__ __forceinline__ void warp_bitonic64(uint64_t (&v)[2], int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const uint64_t o = __shfl_xor_sync(0xffffffffu, v[e], j);
+        const bool up = (((e << 5) | lane) & k) == 0;
+        const bool take_min = ((lane & j) == 0) == up;
+        v[e] = take_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+      }
+    }
+  }
+  // k = 64: the pair within a lane, then the halves
+  if (v[1] < v[0]) {
+    const uint64_t t = v[0];
+    v[0] = v[1];
+    v[1] = t;
+  }
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const uint64_t o = __shfl_xor_sync(0xffffffffu, v[e], j);
+      const bool take_min = (lane & j) == 0;
+      v[e] = take_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+    }
+  }
+}
+
 // number of entries of a[0, len) that are < x (a sorted ascending)
 __device__ __forceinline__ int count_less(const uint64_t* a, int len, uint64_t x) {
   int lo = 0, hi = len;
@@ -396,22 +428,33 @@ __global__ void __launch_bounds__(256, 3)
         }
       }
       __syncwarp();
-      if (cnt <= 32) {
-        // one new key per lane: sorted in registers; one binary search in S gives both
-        // the duplicate test and the key's place in the merge
-        uint64_t b = lane < cnt ? newk[lane] : KEY_NONE;
-        b = warp_bitonic32(b, lane);
-        int r = 0;
-        bool keep = false;
-        if (lane < cnt) {
-          r = count_less(pA, s, b);
-          keep = !(r < s && pA[r] == b);
+      if (cnt <= 64) {
+        // one or two new keys per lane (element e * 32 + lane), sorted in registers; one
+        // binary search in S gives both the duplicate test and the key's place in the merge
+        uint64_t b[2];
+        b[0] = lane < cnt ? newk[lane] : KEY_NONE;
+        b[1] = lane + 32 < cnt ? newk[lane + 32] : KEY_NONE;
+        if (cnt <= 32)
+          b[0] = warp_bitonic32(b[0], lane);
+        else
+          warp_bitonic64(b, lane);
+        int r[2] = {0, 0}, j[2];
+        bool keep[2] = {false, false};
+        int kept = 0;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (e * 32 + lane < cnt) {
+            r[e] = count_less(pA, s, b[e]);
+            keep[e] = !(r[e] < s && pA[r[e]] == b[e]);
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, keep[e]);
+          j[e] = kept + __popc(bal & lanemask_lt());
+          kept += __popc(bal);
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        const int j = __popc(bal & lanemask_lt());
-        const int kept = __popc(bal);
         __syncwarp();
-        if (keep) newk[j] = b;
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+          if (keep[e]) newk[j[e]] = b[e];
         __syncwarp();
         for (int i = lane; i < s; i += 32) {
           const uint64_t a = pA[i];
@@ -421,9 +464,12 @@ __global__ void __launch_bounds__(256, 3)
             fB[pos] = fA[i];
           }
         }
-        if (keep && j + r < Ls) {
-          pB[j + r] = b;
-          fB[j + r] = 0;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (keep[e] && j[e] + r[e] < Ls) {
+            pB[j[e] + r[e]] = b[e];
+            fB[j[e] + r[e]] = 0;
+          }
         }
         s = s + kept < Ls ? s + kept : Ls;
         __syncwarp();
