@@ -125,10 +125,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash():
+KNN_SOURCES = ("knn.cu", "knn_tc.cu", "knn_order.cu", "knn_select.cuh", "knn.cuh", "common.cuh",
+               "tc_common.cuh")
+SEARCH_SOURCES = ("search.cu", "graph_dev.cuh", "knn.cuh", "common.cuh")
+
+
+def kernel_source_hash(files=KNN_SOURCES):
     h = hashlib.sha256()
-    for f in ("knn.cu", "knn_tc.cu", "knn_order.cu", "knn_select.cuh", "knn.cuh", "common.cuh",
-              "tc_common.cuh"):
+    for f in files:
         p = os.path.join(ROOT, "paper_1907_06146_gb300", "csrc", f)
         if os.path.exists(p):
             with open(p, "rb") as fh:
@@ -136,7 +140,7 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel: str, workload: str):
+def committed_traffic(kernel: str, workload: str, files=KNN_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -144,7 +148,7 @@ def committed_traffic(kernel: str, workload: str):
     with open(p) as f:
         d = json.load(f)
     e = d.get(f"{kernel}:{workload}")
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(files):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -580,7 +584,8 @@ def run_gpu(args):
                    "roofline": {"bound": "hbm", "achieved": search_bytes / (np.mean(search_ms) / 1e3) / 1e9,
                                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                 "frac": search_bytes / (np.mean(search_ms) / 1e3) / 1e9 / peaks["hbm_gbs"],
-                                "traffic": None, "kernel": "k_search",
+                                "traffic": committed_traffic("k_search", w.name, SEARCH_SOURCES),
+                                "kernel": "k_search",
                                 "algorithmic": "per query: 4 B per adjacency entry read and per "
                                                f"expansion (degree), d x {row_b} B per distance "
                                                "(the rows the search reads), d x 4 B query"}},
