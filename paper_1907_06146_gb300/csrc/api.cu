@@ -231,7 +231,8 @@ ssg_status ssg_pool(const float* base, int64_t n, int32_t d, const int32_t* knn_
     ingest_all(base, n, d, st, g, false);
     Scratch<Counters> ctr(1, st);
     SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
-    pool_run(g.rows.p, g.rows.ld, d, n, knn_id, K, L, g.info.exact, pool_id, pool_d2, pool_len,
+    pool_run(g.rows.p, nullptr, g.rows.ld, d, n, knn_id, K, L, g.info.exact, pool_id, pool_d2,
+             pool_len,
              ctr.p, st);
   });
 }
@@ -267,7 +268,8 @@ ssg_status ssg_reverse(const float* base, int64_t n, int32_t d, const int32_t* a
     ingest_all(base, n, d, st, g, false);
     Scratch<Counters> ctr(1, st);
     SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
-    reverse_run(g.rows.p, g.rows.ld, d, n, adj0, deg0, R, cos_alpha_of(alpha_deg), g.info.exact,
+    reverse_run(g.rows.p, nullptr, g.rows.ld, d, n, adj0, deg0, R, cos_alpha_of(alpha_deg),
+                g.info.exact,
                 g.info.bf16_exact != 0, adj1, deg1, ctr.p, st);
   });
 }
@@ -411,11 +413,20 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     t_ing.start();
     Ingested in;
     ingest_all(base, n, d, st, in, true);
+    // integers 0..255: a byte copy of the rows (a quarter of the bytes, the same distances)
+    // for the pool, reverse-merge and search distances
+    if (in.info.exact && in.info.nonneg && in.info.max_abs <= 255.f) {
+      SSG_CUDA(cudaMalloc(&g->rows_u8, (size_t)n * in.rows.ld));
+      g->rows_ld = in.rows.ld;
+      g->rows_src = base;
+      rows_to_u8(in.rows.p, in.rows.ld, d, n, g->rows_u8, st);
+    }
     t_ing.stop();
     Scratch<Counters> ctr(1, st);
     SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
     const double cos_a = cos_alpha_of(alpha_deg);
 
+    const uint8_t* X8 = g->rows_u8;
     const bool tc = opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact && knn_tc_available(d);
     SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
                 "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
@@ -454,7 +465,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
         t_knn.stop();
         in.norms.release();
         t_pool.start();
-        pool_from_candidates(in.rows.p, in.rows.ld, d, n, cid.p, Lp, L, in.info.exact, pool_id.p,
+        pool_from_candidates(in.rows.p, X8, in.rows.ld, d, n, cid.p, Lp, L, in.info.exact, pool_id.p,
                              pool_d2.p, pool_len.p, ctr.p, st);
         t_pool.stop();
       }
@@ -474,7 +485,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
 
       // a2: candidate pools
       t_pool.start();
-      pool_run(in.rows.p, in.rows.ld, d, n, knn_id.p, K, L, in.info.exact, pool_id.p, pool_d2.p,
+      pool_run(in.rows.p, X8, in.rows.ld, d, n, knn_id.p, K, L, in.info.exact, pool_id.p, pool_d2.p,
                pool_len.p, ctr.p, st);
       t_pool.stop();
     }
@@ -491,7 +502,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
 
     // a4: reverse-neighbour merge
     t_rev.start();
-    const int maxin = reverse_run(in.rows.p, in.rows.ld, d, n, adj0.p, deg0.p, R, cos_a,
+    const int maxin = reverse_run(in.rows.p, X8, in.rows.ld, d, n, adj0.p, deg0.p, R, cos_a,
                                   in.info.exact,
                                   opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact != 0,
                                   g->adj, g->deg, ctr.p, st);
@@ -504,14 +515,6 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     const int64_t rep = connect_run(in.rows.p, in.rows.ld, d, n, g->adj, g->deg, R, g->nav_dev,
                                     nav.data(), opts.n_nav, st);
     t_con.stop();
-    // integers 0..255: the search reads a byte copy of the rows (a quarter of the bytes,
-    // the same distances)
-    if (in.info.exact && in.info.nonneg && in.info.max_abs <= 255.f) {
-      SSG_CUDA(cudaMalloc(&g->rows_u8, (size_t)n * in.rows.ld));
-      g->rows_ld = in.rows.ld;
-      g->rows_src = base;
-      rows_to_u8(in.rows.p, in.rows.ld, d, n, g->rows_u8, st);
-    }
     t_all.stop();
 
     Counters hc;

@@ -57,6 +57,48 @@ __device__ __forceinline__ void warp_fill_dist_keys(uint64_t* keys, int m,
   __syncwarp();
 }
 
+// Byte rows (integers 0..255, ld bytes per row, a multiple of 4): the squared distance of
+// two rows by a team of 8 lanes in exact integer arithmetic, |a|^2 + |b|^2 - 2 a.b from
+// byte dot products.  For such data every fp32 partial sum of team8_dist is an exact
+// integer too, so the two functions return the same value.
+__device__ __forceinline__ float team8_dist_u8(const uint8_t* __restrict__ a,
+                                               const uint8_t* __restrict__ b, int ldw, int tl,
+                                               bool valid) {
+  unsigned aa = 0u, bb = 0u, ab = 0u;
+  if (valid) {
+    const unsigned int* a4 = (const unsigned int*)a;
+    const unsigned int* b4 = (const unsigned int*)b;
+    for (int f = tl; f < ldw; f += 8) {
+      const unsigned x = __ldg(a4 + f), y = __ldg(b4 + f);
+      aa = __dp4a(x, x, aa);
+      bb = __dp4a(y, y, bb);
+      ab = __dp4a(x, y, ab);
+    }
+  }
+  int s = (int)aa + (int)bb - 2 * (int)ab;
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  return (float)s;
+}
+
+// warp_fill_dist_keys from byte rows (X8 [n][ld] bytes, xi8 node i's row).
+__device__ __forceinline__ void warp_fill_dist_keys_u8(uint64_t* keys, int m,
+                                                       const uint8_t* __restrict__ X8, int ld,
+                                                       const uint8_t* __restrict__ xi8) {
+  const int lane = lane_id(), team = lane >> 3, tl = lane & 7;
+  const int ldw = ld >> 2;
+  for (int t0 = 0; t0 < m; t0 += 4) {
+    const int t = t0 + team;
+    const bool valid = t < m;
+    const int32_t id = valid ? key_id(keys[t]) : 0;
+    const float dd = team8_dist_u8(xi8, X8 + (int64_t)id * ld, ldw, tl, valid);
+    __syncwarp();
+    if (valid && tl == 0) keys[t] = make_key(dd, id);
+  }
+  __syncwarp();
+}
+
 // keys[0, m) are sorted by their fp32 distances.  The fp32 value of a direct sum of d
 // squared differences lies within a relative `rel` of the exact value, so two entries
 // can be out of their true (d2, id) order only inside a run of neighbours whose fp32

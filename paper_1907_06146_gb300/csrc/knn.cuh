@@ -40,8 +40,10 @@ struct KnnOrder {
 bool knn_order_fits(int64_t n, int BN);
 // walk > 0: every block of rows visits only its first walk tiles (Alg. 4), so each
 // cluster's list stops there and the clusters are kept small.
+// x_norm (nullable): squared row norms; with them, large assignments run on the tensor
+// cores.
 void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN, cudaStream_t st,
-                       KnnOrder& o, int64_t walk = 0);
+                       KnnOrder& o, int64_t walk = 0, const float* x_norm = nullptr);
 
 // bf16 tensor-core variant of the exact top-K (only for info.bf16_exact data).
 // True on sm_103 when the shared-memory pipeline fits rows of d values (d <= 128).
@@ -62,16 +64,17 @@ struct Counters {
   int status;
 };
 
-// Pools (Alg. 3 neighbour / neighbour's-neighbour loop).
-void pool_run(const float* X, int ld, int d, int64_t n, const int32_t* knn, int K, int L,
-              int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len, Counters* dctr,
-              cudaStream_t st);
+// Pools (Alg. 3 neighbour / neighbour's-neighbour loop).  X8 (nullable): the rows as
+// bytes (data integers 0..255, same stride), read instead of X for the distances.
+void pool_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const int32_t* knn,
+              int K, int L, int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
+              Counters* dctr, cudaStream_t st);
 
 // Pools from arbitrary candidate lists (cand [n][KS], -1 padded): the L nearest by
-// (d2, id), ordered exactly as pool_run orders its pools.
-void pool_from_candidates(const float* X, int ld, int d, int64_t n, const int32_t* cand, int KS,
-                          int L, int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
-                          Counters* dctr, cudaStream_t st);
+// (d2, id), ordered exactly as pool_run orders its pools.  X8 as for pool_run.
+void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
+                          const int32_t* cand, int KS, int L, int exact, int32_t* pool_id,
+                          float* pool_d2, int32_t* pool_len, Counters* dctr, cudaStream_t st);
 
 // SSG prune of each node's pool.
 void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
@@ -86,10 +89,10 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
                   int32_t* deg, Counters* dctr, cudaStream_t st);
 
 // Reverse-neighbour merge; returns the largest in-degree.  tc: the prune of lists of up to
-// 127 candidates on the tensor cores where the data allow it.
-int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
-                const int32_t* deg0, int R, double cos_a, int exact, bool tc, int32_t* adj1,
-                int32_t* deg1, Counters* dctr, cudaStream_t st);
+// 127 candidates on the tensor cores where the data allow it.  X8 as for pool_run.
+int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
+                const int32_t* adj0, const int32_t* deg0, int R, double cos_a, int exact, bool tc,
+                int32_t* adj1, int32_t* deg1, Counters* dctr, cudaStream_t st);
 
 // Connectivity from navigating nodes; returns the number of repair edges.
 int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int32_t* deg,

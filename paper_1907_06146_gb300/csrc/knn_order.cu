@@ -156,6 +156,20 @@ __global__ void k_update(float* __restrict__ C, const float* __restrict__ sums,
     C[(int64_t)c * dc + t] = sums[(int64_t)c * dc + t] / (float)k;
 }
 
+// Cluster sizes; a label outside [0, ncl) (a row whose distances were all NaN) becomes 0.
+__global__ void k_count_labels(int32_t* __restrict__ label, int64_t n, int ncl,
+                               int* __restrict__ counts) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t l = label[i];
+    if ((uint32_t)l >= (uint32_t)ncl) {
+      l = 0;
+      label[i] = 0;
+    }
+    atomicAdd(counts + l, 1);
+  }
+}
+
 __global__ void k_scatter_perm(const int32_t* __restrict__ label, int64_t n, int* __restrict__ cursor,
                                int32_t* __restrict__ perm, int32_t* __restrict__ inv) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -234,7 +248,7 @@ bool knn_order_fits(int64_t n, int BN) {
 }
 
 void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN, cudaStream_t st,
-                       KnnOrder& o, int64_t walk) {
+                       KnnOrder& o, int64_t walk, const float* x_norm) {
   SSG_REQUIRE(knn_order_fits(n, BN), SSG_EINTERNAL, "cluster order: too many column tiles");
   // About 2,048 rows per cluster.  A full walk only needs the near tiles first, so a few
   // hundred clusters do; a limited walk (Alg. 4) takes its pools from the first tiles
@@ -264,8 +278,17 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
   }
   SSG_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * ncl, st));
   SSG_LAUNCH(k_centroid_norms, (unsigned)ceil_div(ncl, 128), 128, 0, st, C.p, ncl, dc, cn.p);
-  SSG_LAUNCH(k_assign_tiled, (unsigned)ceil_div(n, AS_ROWS), 256, 0, st, X, ld, d, n, n, C.p,
-             cn.p, ncl, dc, label.p, counts.p);
+  if (x_norm && knn_tc_available(d) && n >= 65536) {
+    // the full assignment on the tensor cores: each row's nearest centroid by bf16
+    // distance (the order is a heuristic; any assignment keeps the kNN graph exact)
+    Scratch<float> d2((size_t)n, st);
+    knn_exact_tc(X, n, ld, x_norm, C.p, ncl, dc, cn.p, d, 0, 1, label.p, d2.p, st, nullptr, 0,
+                 true);
+    SSG_LAUNCH(k_count_labels, grid, 256, 0, st, label.p, n, ncl, counts.p);
+  } else {
+    SSG_LAUNCH(k_assign_tiled, (unsigned)ceil_div(n, AS_ROWS), 256, 0, st, X, ld, d, n, n, C.p,
+               cn.p, ncl, dc, label.p, counts.p);
+  }
   std::vector<int> h((size_t)ncl);
   SSG_CUDA(cudaMemcpyAsync(h.data(), counts.p, sizeof(int) * ncl, cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));

@@ -518,7 +518,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   const bool ordered =
       max_tiles > 0 || (self && na >= (1 << 16) && K >= 16 && knn_order_fits(na, BN));
   if (ordered) {
-    knn_cluster_order(A, lda, d, na, BM, BN, st, ord, max_tiles);
+    knn_cluster_order(A, lda, d, na, BM, BN, st, ord, max_tiles, a_norm);
     norm_p.alloc((size_t)na, st);
   }
   Scratch<__nv_bfloat16> ab((size_t)na * dp, st);

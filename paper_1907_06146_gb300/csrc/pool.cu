@@ -33,14 +33,18 @@ __device__ __forceinline__ bool hash_insert(int32_t* h, int log2cap, int32_t id)
 // near-equal values re-sorted in fp64 unless the data are exact -- and writes the first
 // L as node i's pool.  keys has room for the next power of two >= m; d64 for m doubles.
 __device__ __forceinline__ void pool_finish(uint64_t* keys, int m, int L, int exact, double* d64,
-                                            const float* __restrict__ X, int ld, int d,
+                                            const float* __restrict__ X,
+                                            const uint8_t* __restrict__ X8, int ld, int d,
                                             int64_t i, float rel, int32_t* __restrict__ pool_id,
                                             float* __restrict__ pool_d2,
                                             int32_t* __restrict__ pool_len,
                                             unsigned long long* __restrict__ n_order) {
   const int lane = lane_id();
   const float* xi = X + i * ld;
-  warp_fill_dist_keys(keys, m, X, ld, xi);
+  if (X8)
+    warp_fill_dist_keys_u8(keys, m, X8, ld, X8 + i * ld);
+  else
+    warp_fill_dist_keys(keys, m, X, ld, xi);
   int mp = 1;
   while (mp < m) mp <<= 1;
   for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
@@ -60,7 +64,8 @@ __device__ __forceinline__ void pool_finish(uint64_t* keys, int m, int L, int ex
   if (lane == 0) pool_len[i] = keep;
 }
 
-__global__ void k_pool(const float* __restrict__ X, int ld, int d, int64_t n,
+__global__ void k_pool(const float* __restrict__ X, const uint8_t* __restrict__ X8, int ld, int d,
+                       int64_t n,
                        const int32_t* __restrict__ knn, int K, int L, int cap, int log2h,
                        int exact, float rel, int32_t* __restrict__ pool_id,
                        float* __restrict__ pool_d2, int32_t* __restrict__ pool_len,
@@ -92,13 +97,14 @@ __global__ void k_pool(const float* __restrict__ X, int ld, int d, int64_t n,
     if (m >= L) break;
   }
   __syncwarp();
-  pool_finish(keys, m, L, exact, (double*)hset, X, ld, d, i, rel, pool_id, pool_d2, pool_len,
+  pool_finish(keys, m, L, exact, (double*)hset, X, X8, ld, d, i, rel, pool_id, pool_d2, pool_len,
               n_order);
 }
 
 // Pools from given candidates: row i's pool is the L nearest of its KS candidate ids
 // (cand [n][KS], -1 padded; i itself skipped), ordered as k_pool orders them.
-__global__ void k_pool_cand(const float* __restrict__ X, int ld, int d, int64_t n,
+__global__ void k_pool_cand(const float* __restrict__ X, const uint8_t* __restrict__ X8, int ld,
+                            int d, int64_t n,
                             const int32_t* __restrict__ cand, int KS, int L, int cap, int exact,
                             float rel, int32_t* __restrict__ pool_id, float* __restrict__ pool_d2,
                             int32_t* __restrict__ pool_len, unsigned long long* __restrict__ n_order) {
@@ -118,12 +124,12 @@ __global__ void k_pool_cand(const float* __restrict__ X, int ld, int d, int64_t 
     m += __popc(bal);
   }
   __syncwarp();
-  pool_finish(keys, m, L, exact, d64, X, ld, d, i, rel, pool_id, pool_d2, pool_len, n_order);
+  pool_finish(keys, m, L, exact, d64, X, X8, ld, d, i, rel, pool_id, pool_d2, pool_len, n_order);
 }
 
-void pool_run(const float* X, int ld, int d, int64_t n, const int32_t* knn, int K, int L,
-              int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len, Counters* dctr,
-              cudaStream_t st) {
+void pool_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const int32_t* knn,
+              int K, int L, int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
+              Counters* dctr, cudaStream_t st) {
   const int cap = next_pow2(L + K + 1);
   int log2h = 0;
   while ((1 << log2h) < 2 * cap) ++log2h;
@@ -131,18 +137,18 @@ void pool_run(const float* X, int ld, int d, int64_t n, const int32_t* knn, int 
   int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
   const size_t smem = per_warp * wpb;
   ensure_smem((const void*)k_pool, smem);
-  SSG_LAUNCH(k_pool, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, ld, d, n, knn, K, L, cap,
+  SSG_LAUNCH(k_pool, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, X8, ld, d, n, knn, K, L, cap,
              log2h, exact, dist_rel_fp32(d), pool_id, pool_d2, pool_len, &dctr->order_fp64);
 }
 
-void pool_from_candidates(const float* X, int ld, int d, int64_t n, const int32_t* cand, int KS,
-                          int L, int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
-                          Counters* dctr, cudaStream_t st) {
+void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
+                          const int32_t* cand, int KS, int L, int exact, int32_t* pool_id,
+                          float* pool_d2, int32_t* pool_len, Counters* dctr, cudaStream_t st) {
   const int cap = next_pow2(KS);
   const int wpb = 8;
   const size_t smem = (size_t)cap * 16 * wpb;
   ensure_smem((const void*)k_pool_cand, smem);
-  SSG_LAUNCH(k_pool_cand, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, ld, d, n, cand, KS,
+  SSG_LAUNCH(k_pool_cand, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, X8, ld, d, n, cand, KS,
              L, cap, exact, dist_rel_fp32(d), pool_id, pool_d2, pool_len, &dctr->order_fp64);
 }
 

@@ -105,7 +105,8 @@ __host__ __device__ inline size_t merge_prune_bytes(int d, int R, bool wide) {
   return (f * sizeof(float) + 15) & ~(size_t)15;
 }
 
-__global__ void k_reverse_merge(const float* __restrict__ X, int ld, int d, int64_t n,
+__global__ void k_reverse_merge(const float* __restrict__ X, const uint8_t* __restrict__ X8,
+                                int ld, int d, int64_t n,
                                 const int32_t* __restrict__ adj0, const int32_t* __restrict__ deg0,
                                 int R, const int64_t* __restrict__ off,
                                 const int32_t* __restrict__ rev,
@@ -156,7 +157,10 @@ __global__ void k_reverse_merge(const float* __restrict__ X, int ld, int d, int6
     }
     __syncwarp();
     const float* xj = X + j * ld;
-    warp_fill_dist_keys(keys, m, X, ld, xj);
+    if (X8)
+      warp_fill_dist_keys_u8(keys, m, X8, ld, X8 + j * ld);
+    else
+      warp_fill_dist_keys(keys, m, X, ld, xj);
     int mp = 1;
     while (mp < m) mp <<= 1;
     for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
@@ -202,9 +206,9 @@ __global__ void k_max_int(const int* __restrict__ v, int64_t n, int* __restrict_
   if (lane_id() == 0) atomicMax(out, m);
 }
 
-int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
-                const int32_t* deg0, int R, double cos_a, int exact, bool tc, int32_t* adj1,
-                int32_t* deg1, Counters* dctr, cudaStream_t st) {
+int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
+                const int32_t* adj0, const int32_t* deg0, int R, double cos_a, int exact, bool tc,
+                int32_t* adj1, int32_t* deg1, Counters* dctr, cudaStream_t st) {
   const int grid = 8 * num_sms();
   Scratch<int> indeg((size_t)n, st), fill((size_t)n, st), small(2, st);
   SSG_CUDA(cudaMemsetAsync(indeg.p, 0, sizeof(int) * n, st));
@@ -250,7 +254,7 @@ int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
     lists.alloc((size_t)n * limit, st);
     list_len.alloc((size_t)n, st);
   }
-  SSG_LAUNCH(k_reverse_merge, (unsigned)mgrid, wpb * 32, smem, st, X, ld, d, n, adj0, deg0, R, off.p,
+  SSG_LAUNCH(k_reverse_merge, (unsigned)mgrid, wpb * 32, smem, st, X, X8, ld, d, n, adj0, deg0, R, off.p,
              rev.p, (const int32_t*)nullptr, n, cap, limit, exact, rel, (float)cos_a, cos_a, margin, adj1,
              deg1, big.p, small.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p, lists.p, list_len.p);
   if (use_tc)
@@ -271,7 +275,7 @@ int reverse_run(const float* X, int ld, int d, int64_t n, const int32_t* adj0,
     Scratch<int32_t> none(1, st);
     Scratch<int> small2(2, st);
     SSG_CUDA(cudaMemsetAsync(small2.p, 0, sizeof(int) * 2, st));
-    SSG_LAUNCH(k_reverse_merge, grid_big, 32, smem_big, st, X, ld, d, n, adj0, deg0, R, off.p, rev.p,
+    SSG_LAUNCH(k_reverse_merge, grid_big, 32, smem_big, st, X, X8, ld, d, n, adj0, deg0, R, off.p, rev.p,
                big.p, (int64_t)h[0], cap_big, cap_big, exact, rel, (float)cos_a, cos_a, margin, adj1, deg1,
                none.p, small2.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p, (int32_t*)nullptr,
                (int32_t*)nullptr);
