@@ -278,9 +278,11 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
   }
   SSG_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * ncl, st));
   SSG_LAUNCH(k_centroid_norms, (unsigned)ceil_div(ncl, 128), 128, 0, st, C.p, ncl, dc, cn.p);
-  if (x_norm && knn_tc_available(d) && n >= 65536) {
-    // the full assignment on the tensor cores: each row's nearest centroid by bf16
-    // distance (the order is a heuristic; any assignment keeps the kNN graph exact)
+  if (x_norm && knn_tc_available(d) && ncl >= 1024) {
+    // many centroids: the full assignment on the tensor cores, each row's nearest centroid
+    // by bf16 distance (the order is a heuristic; any assignment keeps the kNN graph
+    // exact).  With a few hundred centroids the per-row output of the top-K kernel costs
+    // more than the tiled assignment saves.
     Scratch<float> d2((size_t)n, st);
     knn_exact_tc(X, n, ld, x_norm, C.p, ncl, dc, cn.p, d, 0, 1, label.p, d2.p, st, nullptr, 0,
                  true);

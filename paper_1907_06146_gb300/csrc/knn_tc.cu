@@ -66,7 +66,7 @@ struct TcArgs {
   int* err;
   const int32_t* perm;        // stored position -> original id (null: the identity)
   const int32_t* inv;         // original id -> stored position
-  const int32_t* tile_order;  // per cluster, the ntiles tile indices (null: in order)
+  const int32_t* tile_order;  // per cluster, its first tstride tile indices (null: in order)
   const int32_t* rb_cluster;  // cluster of each block of BM stored query rows
 };
 
@@ -187,7 +187,6 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   const uint32_t tmem_base = *tmem_slot;
 
   const int64_t nrb = (p.na + BM - 1) / BM;
-  const int64_t ntiles = p.ntiles;
   const int64_t nwalk = p.nwalk;
 
   if (warp == 0) {
