@@ -472,11 +472,14 @@ def run_gpu(args):
     # inside the timed region
     pinned = torch.from_numpy(w.base).pin_memory()
     host_base = pinned.numpy()
+    adj_pin = torch.empty((w.n, w.R), dtype=torch.int32).pin_memory().numpy()
+    deg_pin = torch.empty((w.n,), dtype=torch.int32).pin_memory().numpy()
     e2e_ms = []
     for s in range(1 + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g, adj_h, deg_h = ssg.build_host(host_base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec)
+        g, adj_h, deg_h = ssg.build_host(host_base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec,
+                                         adj_out=adj_pin, deg_out=deg_pin)
         t1 = time.perf_counter()
         del g
         if s > 0:

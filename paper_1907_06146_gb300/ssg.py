@@ -517,13 +517,18 @@ def build_batched(bases, K, L, R, alpha, n_nav: int = 10, seed=None, prec: str =
 
 
 def build_host(base: np.ndarray, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None,
-               seed=None, prec: str = "auto"):
-    """NSSGIndexing from host vectors; returns (graph, adj numpy [n][R], deg numpy [n])."""
+               seed=None, prec: str = "auto", adj_out=None, deg_out=None):
+    """NSSGIndexing from host vectors; returns (graph, adj numpy [n][R], deg numpy [n]).
+    adj_out / deg_out: optional int32 C-contiguous host arrays of those shapes to receive the
+    graph (pinned memory makes the copy back faster)."""
     x = np.ascontiguousarray(base, dtype=np.float32)
     n, d = x.shape
     o, keep = _opts(n_nav, nav, seed, prec)
-    adj = np.empty((n, R), np.int32)
-    deg = np.empty(n, np.int32)
+    adj = adj_out if adj_out is not None else np.empty((n, R), np.int32)
+    deg = deg_out if deg_out is not None else np.empty(n, np.int32)
+    if (adj.shape != (n, R) or deg.shape != (n,) or adj.dtype != np.int32
+            or deg.dtype != np.int32 or not adj.flags.c_contiguous or not deg.flags.c_contiguous):
+        raise ValueError("adj_out must be int32 [n][R] and deg_out int32 [n], C-contiguous")
     h = ctypes.c_void_p()
     st = BuildStats()
     _check(lib().ssg_build_host(x.ctypes.data_as(ctypes.c_void_p), n, d, K, L, R, float(alpha),
