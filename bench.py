@@ -366,7 +366,17 @@ def run_batched(ssg, count, n_streams):
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     degs = [int(g.deg.sum().item()) for g in gs]
-    del gs
+    # the mixed-precision batch: bf16 tensor-core candidate selection with exact re-rank
+    # for d <= 128 (fp32 elsewhere); how many adjacency rows equal the exact batch's
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gm = ssg.build_batched(data, Ks, Ls, 32, 60.0, n_streams=n_streams, prec="bf16_rerank")
+    torch.cuda.synchronize()
+    t_mixed = time.perf_counter() - t0
+    rows_same = 0
+    for ge, gx in zip(gs, gm):
+        rows_same += int(((ge.adj == gx.adj).all(dim=1) & (ge.deg == gx.deg)).sum().item())
+    del gs, gm
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     same = True
@@ -380,6 +390,9 @@ def run_batched(ssg, count, n_streams):
             "batched_s": t_batch, "one_by_one_s": t_one, "speedup": t_one / t_batch,
             "batched_s_per_1M_pts": t_batch * 1e6 / points,
             "degree_sums_equal": same,
+            "mixed_bf16_rerank_batched_s": t_mixed,
+            "mixed_over_exact_batched_speedup": t_batch / t_mixed,
+            "mixed_rows_equal_exact_frac": rows_same / points,
             "shapes": "n log-uniform 10k-500k, d in {64,96,128,256}, L in {100,200}, K=100, "
                       "R=32, alpha=60; 16-centre float mixtures"}
 

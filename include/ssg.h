@@ -48,7 +48,14 @@ typedef enum {
 typedef enum {
   SSG_PREC_FP32 = 0,  /* single-precision SIMT distance GEMM */
   SSG_PREC_BF16 = 1,  /* bf16 tensor-core distance GEMM (exact on small integers) */
-  SSG_PREC_AUTO = 2   /* bf16 where the data make it exact, fp32 otherwise */
+  SSG_PREC_AUTO = 2,  /* bf16 where the data make it exact, fp32 otherwise */
+  SSG_PREC_BF16_RERANK = 3 /* mixed precision for any data: where the bf16 tensor-core path
+                              runs (sm_103, d <= 128) it selects K + max(8, K/4) candidates
+                              per row by bf16 distance and orders them by exact distance,
+                              keeping K (exact on data exact in bf16; on other data a true
+                              neighbour that bf16 rounding ranks below the slack is missed);
+                              elsewhere the exact fp32 path runs.  ssg_knn_query treats it
+                              as SSG_PREC_AUTO (ground truth stays exact). */
 } ssg_precision;
 
 typedef void* ssg_stream; /* cudaStream_t */

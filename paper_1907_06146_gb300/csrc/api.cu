@@ -165,6 +165,20 @@ ssg_status ssg_nav_ids(int64_t n, int32_t s, uint64_t seed, int32_t* out) {
   });
 }
 
+// Mixed-precision kNN rows for data not exact in bf16: the tensor cores select K + slack
+// candidates per row by bf16 distance, and each row's candidates are ordered by exact
+// distance (fp32 values, near ties re-sorted in fp64) and cut to K.
+static void knn_bf16_rerank(const Ingested& g, int64_t n, int d, int K, int32_t* knn_id,
+                            float* knn_d2, Counters* ctr, cudaStream_t st, StageTimer* t_gemm) {
+  const int Kp = (int)std::min<int64_t>(std::min(K + std::max(8, K / 4), 895), n - 1);
+  Scratch<int32_t> cid((size_t)n * Kp, st), len((size_t)n, st);
+  Scratch<float> cd2((size_t)n * Kp, st);
+  knn_exact_tc(g.rows.p, n, g.rows.ld, g.norms.p, g.rows.p, n, g.rows.ld, g.norms.p, d, 1, Kp,
+               cid.p, cd2.p, st, t_gemm, 0, true);
+  pool_from_candidates(g.rows.p, nullptr, g.rows.ld, d, n, cid.p, Kp, K, g.info.exact, knn_id,
+                       knn_d2, len.p, ctr, st);
+}
+
 ssg_status ssg_knn(const float* base, int64_t n, int32_t d, int32_t K, ssg_precision prec,
                    int32_t* knn_id, float* knn_d2, ssg_stream stream) {
   return guard([&] {
@@ -178,12 +192,17 @@ ssg_status ssg_knn(const float* base, int64_t n, int32_t d, int32_t K, ssg_preci
     SSG_REQUIRE(prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
                 "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
                 "and 2 d max|x|^2 <= 2^24 (4 d max|x|^2 with negative values)");
-    if (tc)
+    if (tc) {
       knn_exact_tc(g.rows.p, n, g.rows.ld, g.norms.p, g.rows.p, n, g.rows.ld, g.norms.p, d, 1, K,
                    knn_id, knn_d2, st, nullptr);
-    else
+    } else if (prec == SSG_PREC_BF16_RERANK && knn_tc_available(d)) {
+      Scratch<Counters> ctr(1, st);
+      SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
+      knn_bf16_rerank(g, n, d, K, knn_id, knn_d2, ctr.p, st, nullptr);
+    } else {
       knn_exact(g.rows.p, n, g.rows.ld, g.norms.p, g.rows.p, n, g.rows.ld, g.norms.p, d, g.info,
                 1, K, knn_id, knn_d2, st, nullptr);
+    }
   });
 }
 
@@ -428,6 +447,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
 
     const uint8_t* X8 = g->rows_u8;
     const bool tc = opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact && knn_tc_available(d);
+    const bool tc_rr = !tc && opts.gemm_prec == SSG_PREC_BF16_RERANK && knn_tc_available(d);
     SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
                 "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
                 "and 2 d max|x|^2 <= 2^24 (4 d max|x|^2 with negative values)");
@@ -477,6 +497,8 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
       if (tc)
         knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d,
                      1, K, knn_id.p, knn_d2.p, st, &t_gemm);
+      else if (tc_rr)
+        knn_bf16_rerank(in, n, d, K, knn_id.p, knn_d2.p, ctr.p, st, &t_gemm);
       else
         kr = knn_exact(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p,
                        d, in.info, 1, K, knn_id.p, knn_d2.p, st, &t_gemm);
@@ -534,7 +556,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     S.n_knn_fallback_rows = kr.fallback_rows;
     S.max_indegree = maxin;
     S.exact_mode = in.info.exact;
-    S.gemm_prec_used = tc ? SSG_PREC_BF16 : SSG_PREC_FP32;
+    S.gemm_prec_used = tc ? SSG_PREC_BF16 : (tc_rr ? SSG_PREC_BF16_RERANK : SSG_PREC_FP32);
     S.kernel_launches = t_launches - launches0;
     S.search_row_bytes = g->rows_u8 ? 1 : 4;
     if (stats) *stats = S;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libssg.so")
 _lock = threading.Lock()
 _lib = None
 
-PREC = {"fp32": 0, "bf16": 1, "auto": 2}
+PREC = {"fp32": 0, "bf16": 1, "auto": 2, "bf16_rerank": 3}
 
 
 class SSGError(RuntimeError):
