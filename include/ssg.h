@@ -215,7 +215,10 @@ ssg_status ssg_recall_hits(const int32_t* found, int32_t ld_found, const int32_t
 
 /* NSSGIndexing (Alg. 3) end to end on device-resident base vectors.  `base` must stay
  * alive and unchanged while the graph is searched.  *out receives a graph owned by the
- * library.  stats may be NULL. */
+ * library.  stats may be NULL.  When every value is an integer 0..255 the graph also
+ * holds a byte copy of the rows (n x round_up(d, 4) bytes), which the build's pool and
+ * reverse-merge distances and later searches given this same `base` read instead of the
+ * float rows (same results). */
 ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
                      double alpha_deg, const ssg_build_opts* opts, ssg_stream stream,
                      ssg_graph** out, ssg_build_stats* stats);
