@@ -53,6 +53,7 @@ def _load():
         lib.or_knn_rows.argtypes = [P, i64, i32, P, i64, i32, P, P]
         lib.or_knn_queries.argtypes = [P, i64, i32, P, i64, i32, P, P]
         lib.or_pool.argtypes = [P, i64, i32, P, i32, i32, P, i64, P, P, P]
+        lib.or_pool2.argtypes = [P, i64, i32, P, i32, i32, P, i64, i32, P, P, P]
         lib.or_prune.argtypes = [P, i64, i32, P, i64, P, P, i32, i32, dbl, P, P]
         lib.or_reverse.argtypes = [P, i64, i32, P, P, i32, dbl, P, P]
         lib.or_connect.argtypes = [P, i64, i32, P, P, i32, P, i32, P]
@@ -126,8 +127,10 @@ def knn_queries(base, queries, k):
     return ids, d2
 
 
-def pool(base, knn, L, rows=None):
+def pool(base, knn, L, rows=None, own_row_first=False):
     """Candidate pools (Alg. 3) for the given rows.  knn: int32 [n][K] for all nodes.
+    own_row_first: the node's whole kNN row first, then its neighbours' rows (the
+    alternative reading of the pool loop).
     Returns (ids int32 [m][L] -1 padded, d2 float64 [m][L], len int32 [m])."""
     base, knn = _f32(base), _i32(knn)
     n, d = base.shape
@@ -136,7 +139,8 @@ def pool(base, knn, L, rows=None):
     ids = np.empty((rows.size, L), np.int32)
     d2 = np.empty((rows.size, L), np.float64)
     ln = np.empty(rows.size, np.int32)
-    _load().or_pool(_p(base), n, d, _p(knn), K, L, _p(rows), rows.size, _p(ids), _p(d2), _p(ln))
+    _load().or_pool2(_p(base), n, d, _p(knn), K, L, _p(rows), rows.size, int(own_row_first),
+                     _p(ids), _p(d2), _p(ln))
     return ids, d2, ln
 
 

@@ -148,25 +148,45 @@ static int in_list(const int32_t* a, int m, int32_t x) {
  * knn: [n][K] for all nodes.  Outputs for each selected node r: pool_ids/pool_d2
  * [nrows][L] (padded with -1 / INFINITY), pool_len[nrows].
  */
-int or_pool(const float* base, int64_t n, int d, const int32_t* knn, int K, int L,
-            const int64_t* rows, int64_t nrows, int32_t* pool_ids, double* pool_d2,
-            int32_t* pool_len) {
+/*
+ * own_first = 1: the "own row first" reading of the same loop (the alternative to R2):
+ * the node's whole kNN row enters the pool first, then the rows of its neighbours, whole
+ * and in kNN order, until the pool holds >= L ids; sorted and cut to L as above.  With
+ * K >= L the pool is the node's L nearest neighbours.
+ */
+int or_pool2(const float* base, int64_t n, int d, const int32_t* knn, int K, int L,
+             const int64_t* rows, int64_t nrows, int own_first, int32_t* pool_ids,
+             double* pool_d2, int32_t* pool_len) {
   (void)n;
   int64_t r;
 #pragma omp parallel for schedule(dynamic, 16)
   for (r = 0; r < nrows; ++r) {
     int64_t i = rows[r];
-    int cap = L + K + 1;
+    int cap = L + 2 * K + 1;
     int32_t* P = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
     int m = 0;
-    for (int t = 0; t < K; ++t) {
-      int32_t nb = knn[i * K + t];
-      if (nb != i && !in_list(P, m, nb)) P[m++] = nb;
-      for (int t2 = 0; t2 < K; ++t2) {
-        int32_t nb2 = knn[(int64_t)nb * K + t2];
-        if (nb2 != i && !in_list(P, m, nb2)) P[m++] = nb2;
+    if (own_first) {
+      for (int t = 0; t < K; ++t) {
+        int32_t nb = knn[i * K + t];
+        if (nb != i && !in_list(P, m, nb)) P[m++] = nb;
       }
-      if (m >= L) break;
+      for (int t = 0; t < K && m < L; ++t) {
+        int32_t nb = knn[i * K + t];
+        for (int t2 = 0; t2 < K; ++t2) {
+          int32_t nb2 = knn[(int64_t)nb * K + t2];
+          if (nb2 != i && !in_list(P, m, nb2)) P[m++] = nb2;
+        }
+      }
+    } else {
+      for (int t = 0; t < K; ++t) {
+        int32_t nb = knn[i * K + t];
+        if (nb != i && !in_list(P, m, nb)) P[m++] = nb;
+        for (int t2 = 0; t2 < K; ++t2) {
+          int32_t nb2 = knn[(int64_t)nb * K + t2];
+          if (nb2 != i && !in_list(P, m, nb2)) P[m++] = nb2;
+        }
+        if (m >= L) break;
+      }
     }
     or_pair* pr = (or_pair*)malloc(sizeof(or_pair) * (size_t)(m > 0 ? m : 1));
     for (int t = 0; t < m; ++t) {
@@ -184,6 +204,12 @@ int or_pool(const float* base, int64_t n, int d, const int32_t* knn, int K, int 
     free(P);
   }
   return 0;
+}
+
+int or_pool(const float* base, int64_t n, int d, const int32_t* knn, int K, int L,
+            const int64_t* rows, int64_t nrows, int32_t* pool_ids, double* pool_d2,
+            int32_t* pool_len) {
+  return or_pool2(base, n, d, knn, K, L, rows, nrows, 0, pool_ids, pool_d2, pool_len);
 }
 
 /*

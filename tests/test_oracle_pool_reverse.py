@@ -123,3 +123,50 @@ def test_reverse_invariants():
                 if np.dot(u, v) / np.sqrt(np.dot(u, u) * np.dot(v, v)) > ca:
                     confl = True
             assert confl, (j, c)
+
+
+# ---- the "own row first" reading of the pool loop ------------------------------------
+# Points 0, 1, 3, 6, 10, 15 with K = 2 (LINE_KNN).  Node 3 (x = 6), L = 3: its own row
+# {2, 4} enters first; the pool then holds 2 < 3 ids, so the row of node 2 (x = 3) adds
+# {1, 0}; by squared distance from 6 that is 2 (9), 4 (16), 1 (25), 0 (36), cut to 3.
+# The literal loop instead takes {2} u knn(2) = {2, 1, 0} and stops (3 >= L).
+# Node 4 (x = 10), L = 2: own row {3 (16), 5 (25)} already fills the pool; the literal loop
+# gives {3} u knn(3) minus 4 = {3, 2}, i.e. 3 (16), 2 (49).
+@pytest.mark.parametrize("node,L,own,want", [
+    (3, 3, True, [2, 4, 1]), (3, 3, False, [2, 1, 0]),
+    (4, 2, True, [3, 5]), (4, 2, False, [3, 2]),
+])
+def test_pool_own_row_first_line(node, L, own, want):
+    ids, d2, ln = oracle.pool(LINE, LINE_KNN, L, rows=[node], own_row_first=own)
+    assert ids[0, :ln[0]].tolist() == want
+
+
+def test_pool_own_row_first_is_the_exact_l_nn_when_k_at_least_l():
+    from scipy.spatial.distance import cdist
+    w = synth.small(n=400, d=6, nq=0, seed=77)
+    K, L = 24, 16
+    knn, _ = oracle.knn_rows(w.base, K)
+    ids, d2, ln = oracle.pool(w.base, knn, L, own_row_first=True)
+    x = w.base.astype(np.float64)
+    D = cdist(x, x, "sqeuclidean")
+    np.fill_diagonal(D, np.inf)
+    for i in range(w.n):
+        order = np.lexsort((np.arange(w.n), D[i]))[:L]
+        assert ids[i].tolist() == order.tolist()
+        assert ln[i] == L
+
+
+def test_pool_own_row_first_invariants_when_k_below_l():
+    w = synth.small(n=500, d=5, nq=0, seed=78)
+    K, L = 6, 20
+    knn, _ = oracle.knn_rows(w.base, K)
+    ids, d2, ln = oracle.pool(w.base, knn, L, own_row_first=True)
+    for i in range(w.n):
+        p = ids[i, :ln[i]].tolist()
+        two_hop = set(knn[i].tolist()) | {int(v) for nb in knn[i] for v in knn[nb]}
+        two_hop.discard(i)
+        assert len(p) == len(set(p)) and i not in p
+        assert set(p) <= two_hop
+        assert set(knn[i].tolist()) <= set(p)  # the own row is the nearest K, always kept
+        assert ln[i] == min(L, len(two_hop)) or ln[i] == L
+        assert np.all(np.diff(d2[i, :ln[i]]) >= 0)
