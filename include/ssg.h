@@ -78,6 +78,10 @@ typedef struct {
                                on other data the tensor cores select L + slack candidates
                                by bf16 distance and each pool is re-ranked exactly (so a
                                pool may miss a point that only the exact distance ranks in) */
+  int32_t pool_own_row_first; /* 0: Alg. 3's pool loop as printed (for each neighbour n in
+                               kNN order: n, then knn(n); stop once >= L ids).  1: the node's
+                               own kNN row first, whole, then its neighbours' rows until >= L
+                               ids (with K >= L the pool is the L nearest neighbours) */
 } ssg_build_opts;
 
 /* Per-build measurements (all times from CUDA events on the build stream). */

@@ -5,6 +5,8 @@
 * exact_vs_nssg: the exact SSG (Alg. 2 on the complete graph) against the NSSG built by
   Alg. 3 on the same points: how many edges they share (the paper's comparison of the two
   graphs, Sec. 4.1 / appendix).
+* pool_variant: the pool loop as printed against the own-row-first reading (the node's
+  whole kNN row first), built and searched on the same points.
 * edge_scaling: time of the edge stages (pools, prune, reverse merge, connectivity) and of
   the kNN graph against n (the paper's scaling of index construction, Sec. 5.5).
 
@@ -84,6 +86,26 @@ def exact_vs_nssg(ssg, synth, n=700, d=32, alpha=60.0, seed=7001):
             "exact_nodes_at_cap_128": int((de >= 128).sum())}
 
 
+def pool_variant(ssg, w, n=200_000, nq=2_000):
+    """Alg. 3's pool loop as printed against the own-row-first reading (the node's whole kNN
+    row, then its neighbours' rows): build time, out-degree and search at recall 0.95."""
+    import torch
+    base = torch.from_numpy(np.ascontiguousarray(w.base[:n])).cuda()
+    queries = torch.from_numpy(np.ascontiguousarray(w.queries[:nq])).cuda()
+    truth, _ = ssg.knn_query(base, queries, 10)
+    out = {}
+    for name, own in (("as_printed", False), ("own_row_first", True)):
+        g = ssg.build(base, w.K, w.L, w.R, w.alpha, n_nav=w.n_nav, pool_own_row_first=own)
+        del g
+        g = ssg.build(base, w.K, w.L, w.R, w.alpha, n_nav=w.n_nav, pool_own_row_first=own)
+        ls, rec, qps = _qps_at(ssg, g, base, queries, truth)
+        out[name] = {"build_ms": g.stats["ms_total"], "pool_ms": g.stats["ms_pool"],
+                     "avg_out_degree": float(g.deg.float().mean().item()),
+                     "L_search_at_0.95": ls, "recall": rec, "qps": qps}
+        del g
+    return {"n": n, "queries": nq, "K": w.K, "L": w.L, "R": w.R, "variants": out}
+
+
 def edge_scaling(ssg, w, ns=(62_500, 125_000, 250_000, 500_000, 1_000_000)):
     """kNN-graph and edge-stage times of builds on the first n points."""
     import torch
@@ -112,6 +134,7 @@ def run_all(ssg, synth, w):
     t0 = time.perf_counter()
     res = {"alpha_sweep": alpha_sweep(ssg, w),
            "exact_vs_nssg": exact_vs_nssg(ssg, synth),
+           "pool_variant": pool_variant(ssg, w),
            "edge_scaling": edge_scaling(ssg, w)}
     res["seconds"] = time.perf_counter() - t0
     return res

@@ -133,6 +133,7 @@ void ssg_default_opts(ssg_build_opts* o) {
   o->seed = 190706145ull;
   o->debug_checks = 0;
   o->pool_tiles = 0;
+  o->pool_own_row_first = 0;
 }
 
 const char* ssg_strerror(ssg_status s) {
@@ -508,7 +509,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
       // a2: candidate pools
       t_pool.start();
       pool_run(in.rows.p, X8, in.rows.ld, d, n, knn_id.p, K, L, in.info.exact, pool_id.p, pool_d2.p,
-               pool_len.p, ctr.p, st);
+               pool_len.p, ctr.p, st, opts.pool_own_row_first);
       t_pool.stop();
     }
 

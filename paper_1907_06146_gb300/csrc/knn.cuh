@@ -66,9 +66,11 @@ struct Counters {
 
 // Pools (Alg. 3 neighbour / neighbour's-neighbour loop).  X8 (nullable): the rows as
 // bytes (data integers 0..255, same stride), read instead of X for the distances.
+// own_first: the node's own kNN row first, then its neighbours' rows (the alternative
+// reading of the loop).
 void pool_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const int32_t* knn,
               int K, int L, int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
-              Counters* dctr, cudaStream_t st);
+              Counters* dctr, cudaStream_t st, int own_first = 0);
 
 // Pools from arbitrary candidate lists (cand [n][KS], -1 padded): the L nearest by
 // (d2, id), ordered exactly as pool_run orders its pools.  X8 as for pool_run.

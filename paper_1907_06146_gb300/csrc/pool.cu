@@ -67,7 +67,7 @@ __device__ __forceinline__ void pool_finish(uint64_t* keys, int m, int L, int ex
 __global__ void k_pool(const float* __restrict__ X, const uint8_t* __restrict__ X8, int ld, int d,
                        int64_t n,
                        const int32_t* __restrict__ knn, int K, int L, int cap, int log2h,
-                       int exact, float rel, int32_t* __restrict__ pool_id,
+                       int own_first, int exact, float rel, int32_t* __restrict__ pool_id,
                        float* __restrict__ pool_d2, int32_t* __restrict__ pool_len,
                        unsigned long long* __restrict__ n_order) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -82,19 +82,36 @@ __global__ void k_pool(const float* __restrict__ X, const uint8_t* __restrict__ 
   for (int t = lane; t < hcap; t += 32) hset[t] = -1;
   __syncwarp();
   int m = 0;
-  for (int t = 0; t < K; ++t) {
-    const int32_t nb = knn[i * K + t];
-    if (nb < 0) break;  // a row of an approximate graph with fewer than K neighbours
-    for (int c = 0; c <= K; c += 32) {  // the batch {nb} + knn(nb): K + 1 distinct ids
-      const int idx = c + lane;
-      int32_t id = -1;
-      if (idx <= K) id = idx == 0 ? nb : knn[(int64_t)nb * K + idx - 1];
-      bool fresh = id >= 0 && id != (int32_t)i && hash_insert(hset, log2h, id);
-      const unsigned bal = __ballot_sync(0xffffffffu, fresh);
-      if (fresh) keys[m + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
-      m += __popc(bal);
+  if (own_first) {
+    // the node's own row whole, then its neighbours' rows while the pool holds < L ids
+    for (int t = -1; t < K; ++t) {
+      if (t >= 0 && m >= L) break;
+      const int32_t src = t < 0 ? (int32_t)i : knn[i * K + t];
+      if (src < 0) break;  // a row of an approximate graph with fewer than K neighbours
+      for (int c = 0; c < K; c += 32) {
+        const int idx = c + lane;
+        const int32_t id = idx < K ? knn[(int64_t)src * K + idx] : -1;
+        bool fresh = id >= 0 && id != (int32_t)i && hash_insert(hset, log2h, id);
+        const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+        if (fresh) keys[m + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
+        m += __popc(bal);
+      }
     }
-    if (m >= L) break;
+  } else {
+    for (int t = 0; t < K; ++t) {
+      const int32_t nb = knn[i * K + t];
+      if (nb < 0) break;  // a row of an approximate graph with fewer than K neighbours
+      for (int c = 0; c <= K; c += 32) {  // the batch {nb} + knn(nb): K + 1 distinct ids
+        const int idx = c + lane;
+        int32_t id = -1;
+        if (idx <= K) id = idx == 0 ? nb : knn[(int64_t)nb * K + idx - 1];
+        bool fresh = id >= 0 && id != (int32_t)i && hash_insert(hset, log2h, id);
+        const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+        if (fresh) keys[m + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
+        m += __popc(bal);
+      }
+      if (m >= L) break;
+    }
   }
   __syncwarp();
   pool_finish(keys, m, L, exact, (double*)hset, X, X8, ld, d, i, rel, pool_id, pool_d2, pool_len,
@@ -129,7 +146,7 @@ __global__ void k_pool_cand(const float* __restrict__ X, const uint8_t* __restri
 
 void pool_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const int32_t* knn,
               int K, int L, int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
-              Counters* dctr, cudaStream_t st) {
+              Counters* dctr, cudaStream_t st, int own_first) {
   const int cap = next_pow2(L + K + 1);
   int log2h = 0;
   while ((1 << log2h) < 2 * cap) ++log2h;
@@ -138,7 +155,7 @@ void pool_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const
   const size_t smem = per_warp * wpb;
   ensure_smem((const void*)k_pool, smem);
   SSG_LAUNCH(k_pool, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, X8, ld, d, n, knn, K, L, cap,
-             log2h, exact, dist_rel_fp32(d), pool_id, pool_d2, pool_len, &dctr->order_fp64);
+             log2h, own_first, exact, dist_rel_fp32(d), pool_id, pool_d2, pool_len, &dctr->order_fp64);
 }
 
 void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int64_t n,

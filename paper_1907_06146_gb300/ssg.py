@@ -30,7 +30,8 @@ class SSGError(RuntimeError):
 class BuildOpts(ctypes.Structure):
     _fields_ = [("gemm_prec", ctypes.c_int), ("n_nav", ctypes.c_int32),
                 ("nav_ids_host", ctypes.c_void_p), ("seed", ctypes.c_uint64),
-                ("debug_checks", ctypes.c_int32), ("pool_tiles", ctypes.c_int32)]
+                ("debug_checks", ctypes.c_int32), ("pool_tiles", ctypes.c_int32),
+                ("pool_own_row_first", ctypes.c_int32)]
 
 
 class BuildStats(ctypes.Structure):
@@ -465,7 +466,7 @@ def _opts(n_nav, nav, seed, prec):
 
 
 def build(base, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None, seed=None,
-          prec: str = "auto", pool_tiles: int = 0) -> Graph:
+          prec: str = "auto", pool_tiles: int = 0, pool_own_row_first: bool = False) -> Graph:
     """NSSGIndexing on a device-resident base (torch CUDA float32 [n][d]): Alg. 3, or with
     pool_tiles > 0 Alg. 4's pools searched on the fly over the cluster-ordered tiles."""
     torch = _torch()
@@ -473,6 +474,7 @@ def build(base, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None,
     n, d = b.shape
     o, keep = _opts(n_nav, nav, seed, prec)
     o.pool_tiles = pool_tiles
+    o.pool_own_row_first = int(pool_own_row_first)
     h = ctypes.c_void_p()
     st = BuildStats()
     _check(lib().ssg_build(_ptr(b), n, d, K, L, R, float(alpha), ctypes.byref(o), _stream(),

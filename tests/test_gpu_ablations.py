@@ -41,3 +41,13 @@ def test_exact_vs_nssg_counts(ssg):
     r = ablations.exact_vs_nssg(ssg, synth, n=400, d=16)
     assert 0 < r["shared"] <= min(r["exact_edges"], r["nssg_edges"])
     assert 0.0 < r["exact_covered"] <= 1.0 and 0.0 < r["nssg_in_exact"] <= 1.0
+
+
+def test_pool_variant_shapes(ssg):
+    from paper_1907_06146_gb300 import ablations
+    w = synth.sift_like(n=6000, nq=300, n_clusters=40)
+    r = ablations.pool_variant(ssg, w, n=6000, nq=300)
+    v = r["variants"]
+    assert set(v) == {"as_printed", "own_row_first"}
+    for p in v.values():
+        assert 0 < p["avg_out_degree"] <= w.R and 0.0 <= p["recall"] <= 1.0

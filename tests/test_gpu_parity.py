@@ -453,3 +453,20 @@ def test_recall_hits(ssg, small):
     found[1::3, 0] = 10**6
     hits = ssg.recall_hits(_cuda(found), _cuda(truth), 10)
     assert hits / truth.size == pytest.approx(oracle.recall_at(found, truth))
+
+
+# ---- the own-row-first pool reading through the whole build ---------------------------
+@pytest.mark.parametrize("which", ["small", "intdata"])
+def test_build_own_row_first_equals_oracle(ssg, request, which):
+    # small: K = 20 < L = 100, so neighbours' rows follow the own row; intdata: K = 200 >= L,
+    # so the pool is the node's own 100 nearest
+    w = request.getfixturevalue(which)
+    nav = synth.nav_ids(w.n, w.n_nav, 61)
+    g = ssg.build(_cuda(w.base), w.K, w.L, w.R, w.alpha, nav=nav, pool_own_row_first=True)
+    knn, _ = oracle.knn_rows(w.base, w.K)
+    pid, _, plen = oracle.pool(w.base, knn, w.L, own_row_first=True)
+    adj0, deg0 = oracle.prune(w.base, pid, plen, w.R, w.alpha)
+    adj1, deg1 = oracle.reverse(w.base, adj0, deg0, w.alpha)
+    adj, deg, _ = oracle.connect(w.base, adj1, deg1, nav)
+    np.testing.assert_array_equal(_np(g.deg), deg)
+    np.testing.assert_array_equal(_np(g.adj), adj)
