@@ -20,6 +20,7 @@ import hashlib
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -84,7 +85,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the raw samples (the JSON line carries their summary); SSG_BENCH_OUT picks the folder
+        out = os.environ.get("SSG_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_gpu{gpu_index}.csv")
 
     def start(self):
         try:
