@@ -110,6 +110,14 @@ const char* ssg_strerror(ssg_status s);
 const char* ssg_last_error(void);        /* message of the last failure on this thread */
 int64_t ssg_kernel_launch_count(void);   /* kernels launched by this process so far */
 
+/* Failure-detection self-test of the bounded waits inside the tensor-core kernels: one
+ * kernel waits, with the library's own bounded mbarrier wait, on a barrier that nothing
+ * completes (mode 0: it gives up after its 2 s limit; mode 1: another warp raises the
+ * abort flag after 20 ms; mode 2: the barrier completes first).  *ok_host = 1 if the wait
+ * succeeded, *elapsed_ms_host = the wait's duration.  No mode faults or hangs the GPU; the
+ * kernel always returns and the context stays usable.  EINVAL for another mode. */
+ssg_status ssg_selftest_wait(int32_t mode, int32_t* ok_host, int32_t* elapsed_ms_host);
+
 /* Navigating nodes (Alg. 3: "random select s points"): s distinct ids in [0, n), the
  * successive SplitMix64 outputs (Steele, Lea, Flood 2014) modulo n with repeats skipped.
  * Host only; out_host has room for s ids.  EINVAL if s < 1 or s > n. */

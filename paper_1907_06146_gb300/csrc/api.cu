@@ -145,6 +145,17 @@ const char* ssg_last_error(void) { return g_err; }
 
 int64_t ssg_kernel_launch_count(void) { return g_launches.load(); }
 
+ssg_status ssg_selftest_wait(int32_t mode, int32_t* ok_host, int32_t* elapsed_ms_host) {
+  return guard([&] {
+    SSG_REQUIRE(ok_host && elapsed_ms_host, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(mode >= 0 && mode <= 2, SSG_EINVAL, "mode must be 0, 1 or 2");
+    int ok = 0, ms = 0;
+    wait_selftest(mode, &ok, &ms, (cudaStream_t)0);
+    *ok_host = ok;
+    *elapsed_ms_host = ms;
+  });
+}
+
 ssg_status ssg_nav_ids(int64_t n, int32_t s, uint64_t seed, int32_t* out) {
   return guard([&] {
     SSG_REQUIRE(out && s >= 1 && s <= n, SSG_EINVAL, "need 1 <= s <= n (s=%d, n=%lld)", s,

@@ -119,6 +119,9 @@ void search_run_mixed(const float* X, const uint8_t* X8, int ld, int d, const in
 // multiple of 4; padding bytes 0).
 void rows_to_u8(const float* X, int ld, int d, int64_t n, uint8_t* out, cudaStream_t st);
 
+// Bounded-wait self-test (csrc/selftest.cu): mode 0 times out, 1 aborts, 2 succeeds.
+void wait_selftest(int mode, int* ok_host, int* elapsed_ms_host, cudaStream_t st);
+
 // Padded view of X only (no statistics, no synchronisation).
 void pad_rows(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out);
 

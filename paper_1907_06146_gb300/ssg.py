@@ -51,6 +51,7 @@ class BuildStats(ctypes.Structure):
 
 SYMBOLS = {
     # name: (restype, argtypes)
+    "ssg_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "ssg_default_opts": (None, [ctypes.c_void_p]),
     "ssg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ssg_last_error": (ctypes.c_char_p, []),
@@ -181,6 +182,14 @@ def _dev(t, dtype):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def selftest_wait(mode: int):
+    """The bounded-wait self-test (ssg_selftest_wait): returns (wait succeeded, elapsed ms)."""
+    ok = ctypes.c_int32()
+    ms = ctypes.c_int32()
+    _check(lib().ssg_selftest_wait(mode, ctypes.byref(ok), ctypes.byref(ms)))
+    return bool(ok.value), int(ms.value)
 
 
 def knn(base, K: int, prec: str = "auto"):

@@ -95,6 +95,11 @@ def test_invalid_arguments_rejected_without_device(L):
                                None) == 1
     assert L.ssg_build_batched(0, None, None, None, None, None, None, None, None, 2, None,
                                None) == 0
+    # the bounded-wait self-test: only modes 0..2, outputs required
+    ok, ms = ctypes.c_int32(), ctypes.c_int32()
+    assert L.ssg_selftest_wait(3, ctypes.byref(ok), ctypes.byref(ms)) == 1
+    assert L.ssg_selftest_wait(-1, ctypes.byref(ok), ctypes.byref(ms)) == 1
+    assert L.ssg_selftest_wait(0, None, ctypes.byref(ms)) == 1
 
 
 def test_default_opts(L):
