@@ -67,7 +67,11 @@ typedef struct {
   const int32_t* nav_ids_host; /* optional: n_nav distinct ids in [0, n) (host memory);
                                   NULL = draw them with ssg_nav_ids(n, n_nav, seed) */
   uint64_t seed;            /* seed for the navigating-node draw */
-  int32_t debug_checks;     /* nonzero: check graph invariants after each stage */
+  int32_t debug_checks;     /* nonzero: after the pools, the prune, the reverse merge and
+                               connectivity, check their arrays' invariants on the device
+                               (ids in range, no self loops or repeats, degrees within the
+                               cap, -1 padding, pools in order); a failure stops the build
+                               with SSG_EINTERNAL naming the stage, the row and the rule */
   int32_t pool_tiles;       /* 0: Alg. 3 pools (the exact kNN graph, neighbours and their
                                neighbours).  > 0: Alg. 4 pools without a stored kNN graph:
                                each node's L nearest among the points of the pool_tiles
@@ -109,6 +113,15 @@ void ssg_default_opts(ssg_build_opts* opts);
 const char* ssg_strerror(ssg_status s);
 const char* ssg_last_error(void);        /* message of the last failure on this thread */
 int64_t ssg_kernel_launch_count(void);   /* kernels launched by this process so far */
+
+/* Invariant check of an adjacency (device int32 adj [n][R] -1 padded, deg [n]; R <= 128):
+ * 0 <= deg <= R, listed ids in [0, n), no self loop, no id twice, -1 past the degree.  The
+ * check reads the arrays within those shapes and never follows an id.  *bad_row_host = -1
+ * when every row passes, else the smallest failing row, with *bad_code_host = 1 degree,
+ * 2 id range, 3 self loop, 4 repeated id, 5 padding.  EINVAL for null pointers or R
+ * outside [1, 128]. */
+ssg_status ssg_check_graph(const int32_t* adj, const int32_t* deg, int64_t n, int32_t R,
+                           int64_t* bad_row_host, int32_t* bad_code_host, ssg_stream stream);
 
 /* Failure-detection self-test of the bounded waits inside the tensor-core kernels: one
  * kernel waits, with the library's own bounded mbarrier wait, on a barrier that nothing

@@ -145,6 +145,17 @@ const char* ssg_last_error(void) { return g_err; }
 
 int64_t ssg_kernel_launch_count(void) { return g_launches.load(); }
 
+ssg_status ssg_check_graph(const int32_t* adj, const int32_t* deg, int64_t n, int32_t R,
+                           int64_t* bad_row_host, int32_t* bad_code_host, ssg_stream stream) {
+  return guard([&] {
+    SSG_REQUIRE(adj && deg && bad_row_host && bad_code_host, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(n >= 0 && R >= 1 && R <= 128, SSG_EINVAL, "need n >= 0 and 1 <= R <= 128");
+    const CheckResult r = check_adj(adj, deg, n, R, (cudaStream_t)stream);
+    *bad_row_host = r.row;
+    *bad_code_host = r.code;
+  });
+}
+
 ssg_status ssg_selftest_wait(int32_t mode, int32_t* ok_host, int32_t* elapsed_ms_host) {
   return guard([&] {
     SSG_REQUIRE(ok_host && elapsed_ms_host, SSG_EINVAL, "null pointer");
@@ -524,12 +535,21 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
       t_pool.stop();
     }
 
+    auto debug_check = [&](const CheckResult& r, const char* stage) {
+      SSG_REQUIRE(r.row < 0, SSG_EINTERNAL, "debug check after %s: row %lld: %s", stage,
+                  (long long)r.row, check_name(r.code));
+    };
+    if (opts.debug_checks)
+      debug_check(check_pool(pool_id.p, pool_d2.p, pool_len.p, n, L, in.info.exact, d, st),
+                  "the pools");
+
     // a3: SSG prune
     Scratch<int32_t> adj0((size_t)n * R, st), deg0((size_t)n, st);
     t_prune.start();
     prune_dispatch(opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact, in.rows.p, in.rows.ld, d, n,
                    pool_id.p, pool_len.p, L, R, cos_a, adj0.p, deg0.p, ctr.p, st);
     t_prune.stop();
+    if (opts.debug_checks) debug_check(check_adj(adj0.p, deg0.p, n, R, st), "the prune");
     pool_id.release();
     pool_d2.release();
     pool_len.release();
@@ -541,6 +561,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
                                   opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact != 0,
                                   g->adj, g->deg, ctr.p, st);
     t_rev.stop();
+    if (opts.debug_checks) debug_check(check_adj(g->adj, g->deg, n, R, st), "the reverse merge");
     adj0.release();
     deg0.release();
 
@@ -549,6 +570,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     const int64_t rep = connect_run(in.rows.p, in.rows.ld, d, n, g->adj, g->deg, R, g->nav_dev,
                                     nav.data(), opts.n_nav, st);
     t_con.stop();
+    if (opts.debug_checks) debug_check(check_adj(g->adj, g->deg, n, R, st), "connectivity");
     t_all.stop();
 
     Counters hc;

@@ -119,6 +119,19 @@ void search_run_mixed(const float* X, const uint8_t* X8, int ld, int d, const in
 // multiple of 4; padding bytes 0).
 void rows_to_u8(const float* X, int ld, int d, int64_t n, uint8_t* out, cudaStream_t st);
 
+// Invariant checks (csrc/check.cu).  row = -1: every row passed; else the smallest failing
+// row and its code.
+enum CheckCode { CHECK_DEGREE = 1, CHECK_RANGE, CHECK_SELF, CHECK_DUPLICATE, CHECK_PADDING,
+                 CHECK_ORDER };
+struct CheckResult {
+  int64_t row = -1;
+  int code = 0;
+};
+CheckResult check_adj(const int32_t* adj, const int32_t* deg, int64_t n, int R, cudaStream_t st);
+CheckResult check_pool(const int32_t* pid, const float* pd2, const int32_t* plen, int64_t n, int L,
+                       int exact, int d, cudaStream_t st);
+const char* check_name(int code);
+
 // Bounded-wait self-test (csrc/selftest.cu): mode 0 times out, 1 aborts, 2 succeeds.
 void wait_selftest(int mode, int* ok_host, int* elapsed_ms_host, cudaStream_t st);
 

@@ -52,6 +52,9 @@ class BuildStats(ctypes.Structure):
 SYMBOLS = {
     # name: (restype, argtypes)
     "ssg_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_check_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
     "ssg_default_opts": (None, [ctypes.c_void_p]),
     "ssg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ssg_last_error": (ctypes.c_char_p, []),
@@ -182,6 +185,18 @@ def _dev(t, dtype):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def check_graph(adj, deg):
+    """Invariant check of a device adjacency (ssg_check_graph): (bad row or -1, code)."""
+    torch = _torch()
+    a = _dev(adj, torch.int32)
+    dg = _dev(deg, torch.int32)
+    row = ctypes.c_int64()
+    code = ctypes.c_int32()
+    _check(lib().ssg_check_graph(_ptr(a), _ptr(dg), a.shape[0], a.shape[1], ctypes.byref(row),
+                                 ctypes.byref(code), _stream()))
+    return int(row.value), int(code.value)
 
 
 def selftest_wait(mode: int):
@@ -475,7 +490,8 @@ def _opts(n_nav, nav, seed, prec):
 
 
 def build(base, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None, seed=None,
-          prec: str = "auto", pool_tiles: int = 0, pool_own_row_first: bool = False) -> Graph:
+          prec: str = "auto", pool_tiles: int = 0, pool_own_row_first: bool = False,
+          debug_checks: bool = False) -> Graph:
     """NSSGIndexing on a device-resident base (torch CUDA float32 [n][d]): Alg. 3, or with
     pool_tiles > 0 Alg. 4's pools searched on the fly over the cluster-ordered tiles."""
     torch = _torch()
@@ -484,6 +500,7 @@ def build(base, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None,
     o, keep = _opts(n_nav, nav, seed, prec)
     o.pool_tiles = pool_tiles
     o.pool_own_row_first = int(pool_own_row_first)
+    o.debug_checks = int(debug_checks)
     h = ctypes.c_void_p()
     st = BuildStats()
     _check(lib().ssg_build(_ptr(b), n, d, K, L, R, float(alpha), ctypes.byref(o), _stream(),

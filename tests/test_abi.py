@@ -95,6 +95,11 @@ def test_invalid_arguments_rejected_without_device(L):
                                None) == 1
     assert L.ssg_build_batched(0, None, None, None, None, None, None, None, None, 2, None,
                                None) == 0
+    # the invariant check: outputs required, R within [1, 128]
+    row, code = ctypes.c_int64(), ctypes.c_int32()
+    assert L.ssg_check_graph(P, P, 10, 8, None, ctypes.byref(code), s) == 1
+    assert L.ssg_check_graph(P, P, 10, 0, ctypes.byref(row), ctypes.byref(code), s) == 1
+    assert L.ssg_check_graph(P, P, 10, 129, ctypes.byref(row), ctypes.byref(code), s) == 1
     # the bounded-wait self-test: only modes 0..2, outputs required
     ok, ms = ctypes.c_int32(), ctypes.c_int32()
     assert L.ssg_selftest_wait(3, ctypes.byref(ok), ctypes.byref(ms)) == 1

@@ -46,3 +46,48 @@ def test_wait_times_out_and_the_context_survives(ssg):
 def test_invalid_mode_rejected(ssg):
     with pytest.raises(ssg.SSGError):
         ssg.selftest_wait(3)
+
+
+# ---- invariant checks (ssg_build_opts.debug_checks, ssg_check_graph) -------------------
+@pytest.fixture(scope="module")
+def ref():
+    w = synth.small(n=800, d=16, nq=0, seed=93)
+    nav = synth.nav_ids(w.n, 3, 95)
+    return w, nav, oracle.build_graph(w.base, 10, 40, 12, 60.0, nav)
+
+
+def test_debug_checks_pass_on_correct_builds(ssg, ref):
+    w, nav, o = ref
+    b = torch.from_numpy(w.base).cuda()
+    g = ssg.build(b, 10, 40, 12, 60.0, nav=nav, debug_checks=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(g.deg.cpu().numpy(), o["deg"])
+    np.testing.assert_array_equal(g.adj.cpu().numpy(), o["adj"])
+    iw = synth.sift_like(n=3000, nq=0, n_clusters=30)
+    g = ssg.build(torch.from_numpy(iw.base).cuda(), 20, 60, 24, 60.0, n_nav=4, debug_checks=True)
+    assert ssg.check_graph(g.adj, g.deg) == (-1, 0)
+
+
+def test_check_graph_reports_each_planted_error(ssg, ref):
+    w, nav, o = ref
+    adj, deg = o["adj"].copy(), o["deg"].copy()
+    assert ssg.check_graph(adj, deg) == (-1, 0)
+    R = adj.shape[1]
+    rows = [i for i in range(w.n) if 2 <= deg[i] < R]
+    a, b, c, e, f = rows[:5]
+
+    def planted(fn):
+        x, y = adj.copy(), deg.copy()
+        fn(x, y)
+        return ssg.check_graph(x, y)
+
+    assert planted(lambda x, y: y.__setitem__(a, R + 1)) == (a, 1)
+    assert planted(lambda x, y: x.__setitem__((b, 0), w.n)) == (b, 2)
+    assert planted(lambda x, y: x.__setitem__((c, 0), c)) == (c, 3)
+    assert planted(lambda x, y: x.__setitem__((e, 1), x[e, 0])) == (e, 4)
+    assert planted(lambda x, y: x.__setitem__((f, y[f]), 0)) == (f, 5)
+
+    def several(x, y):
+        x[f, 0] = w.n
+        x[c, 0] = c
+    assert planted(several) == (min(c, f), 3 if c < f else 2)
