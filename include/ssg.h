@@ -114,6 +114,12 @@ const char* ssg_strerror(ssg_status s);
 const char* ssg_last_error(void);        /* message of the last failure on this thread */
 int64_t ssg_kernel_launch_count(void);   /* kernels launched by this process so far */
 
+/* Fault injection for tests, on the host: the nth stream-ordered scratch allocation from
+ * now on (counted over all calls and threads) fails as an out-of-memory would, so that call
+ * returns SSG_ENOMEM after releasing what it holds; nth <= 0 switches it off.  No device
+ * fault is involved. */
+void ssg_debug_fail_alloc(int64_t nth);
+
 /* Invariant check of an adjacency (device int32 adj [n][R] -1 padded, deg [n]; R <= 128):
  * 0 <= deg <= R, listed ids in [0, n), no self loop, no id twice, -1 past the degree.  The
  * check reads the arrays within those shapes and never follows an id.  *bad_row_host = -1

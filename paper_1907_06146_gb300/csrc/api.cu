@@ -18,6 +18,7 @@
 namespace ssg {
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_fail_alloc{0};
 thread_local int64_t t_launches = 0;
 static thread_local char g_err[1024] = "";
 
@@ -144,6 +145,8 @@ const char* ssg_strerror(ssg_status s) {
 const char* ssg_last_error(void) { return g_err; }
 
 int64_t ssg_kernel_launch_count(void) { return g_launches.load(); }
+
+void ssg_debug_fail_alloc(int64_t nth) { g_fail_alloc.store(nth > 0 ? nth : 0); }
 
 ssg_status ssg_check_graph(const int32_t* adj, const int32_t* deg, int64_t n, int32_t R,
                            int64_t* bad_row_host, int32_t* bad_code_host, ssg_stream stream) {

@@ -21,6 +21,13 @@ namespace ssg {
 // ---------------------------------------------------------------------------------------
 void set_error(const char* fmt, ...);
 extern std::atomic<int64_t> g_launches;   // all threads
+// Host-side fault injection (ssg_debug_fail_alloc): while positive, counts scratch
+// allocations down; the one that brings it to zero fails as an out-of-memory would.
+extern std::atomic<int64_t> g_fail_alloc;
+inline bool alloc_fault_injected() {
+  if (g_fail_alloc.load(std::memory_order_relaxed) <= 0) return false;
+  return g_fail_alloc.fetch_sub(1) == 1;
+}
 extern thread_local int64_t t_launches;    // this host thread
 
 struct Fail {
@@ -71,6 +78,10 @@ struct Scratch {
     s = st;
     count = n;
     if (n == 0) return;
+    if (alloc_fault_injected()) {
+      set_error("scratch allocation of %zu bytes failed: injected", n * sizeof(T));
+      throw Fail{SSG_ENOMEM};
+    }
     cudaError_t e = cudaMallocAsync((void**)&p, n * sizeof(T), st);
     if (e != cudaSuccess) {
       p = nullptr;

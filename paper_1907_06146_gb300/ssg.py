@@ -52,6 +52,7 @@ class BuildStats(ctypes.Structure):
 SYMBOLS = {
     # name: (restype, argtypes)
     "ssg_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_debug_fail_alloc": (None, [ctypes.c_int64]),
     "ssg_check_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p]),
@@ -197,6 +198,12 @@ def check_graph(adj, deg):
     _check(lib().ssg_check_graph(_ptr(a), _ptr(dg), a.shape[0], a.shape[1], ctypes.byref(row),
                                  ctypes.byref(code), _stream()))
     return int(row.value), int(code.value)
+
+
+def debug_fail_alloc(nth: int):
+    """Fault injection on the host: the nth scratch allocation from now on fails (ENOMEM);
+    0 switches it off (ssg_debug_fail_alloc)."""
+    lib().ssg_debug_fail_alloc(int(nth))
 
 
 def selftest_wait(mode: int):

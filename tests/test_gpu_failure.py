@@ -91,3 +91,23 @@ def test_check_graph_reports_each_planted_error(ssg, ref):
         x[f, 0] = w.n
         x[c, 0] = c
     assert planted(several) == (min(c, f), 3 if c < f else 2)
+
+
+# ---- injected allocation failures (ssg_debug_fail_alloc, on the host) ------------------
+def test_injected_allocation_failure_returns_enomem(ssg, ref):
+    w, nav, o = ref
+    b = torch.from_numpy(w.base).cuda()
+    for nth in (1, 2, 3, 8):
+        ssg.debug_fail_alloc(nth)
+        try:
+            with pytest.raises(ssg.SSGError) as e:
+                ssg.build(b, 10, 40, 12, 60.0, nav=nav)
+            assert e.value.status == 2 and "injected" in str(e.value)
+        finally:
+            ssg.debug_fail_alloc(0)
+        # what the failed call held was released; the next build is whole and right
+        g = ssg.build(b, 10, 40, 12, 60.0, nav=nav)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(g.deg.cpu().numpy(), o["deg"])
+        np.testing.assert_array_equal(g.adj.cpu().numpy(), o["adj"])
+        del g
