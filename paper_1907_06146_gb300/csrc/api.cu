@@ -437,8 +437,9 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t launches0 = t_launches;
     ssg_build_stats S{};
-    StageTimer t_all(st), t_ing(st), t_knn(st), t_gemm(st), t_pool(st), t_prune(st), t_rev(st),
-        t_con(st);
+    StageTimer t_all(st, "ssg_build"), t_ing(st, "ingest"), t_knn(st, "knn graph"),
+        t_gemm(st, "knn kernel"), t_pool(st, "pools"), t_prune(st, "prune"),
+        t_rev(st, "reverse merge"), t_con(st, "connectivity");
     t_all.start();
 
     ssg_graph* g = new ssg_graph();

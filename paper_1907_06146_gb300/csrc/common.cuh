@@ -12,6 +12,8 @@
 #include <string>
 #include <unordered_map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ssg.h"
 
 namespace ssg {
@@ -100,15 +102,31 @@ struct Scratch {
 };
 
 // Event pair for stage timing on a stream.
+// A named timer also marks its stage as an NVTX range on the calling thread, so that a
+// timeline tool shows the build's stages (the events time the device work).
 struct StageTimer {
   cudaEvent_t a = nullptr, b = nullptr;
   cudaStream_t s;
-  explicit StageTimer(cudaStream_t st) : s(st) {
+  const char* name;
+  bool open = false;
+  explicit StageTimer(cudaStream_t st, const char* nm = nullptr) : s(st), name(nm) {
     SSG_CUDA(cudaEventCreate(&a));
     SSG_CUDA(cudaEventCreate(&b));
   }
-  void start() { SSG_CUDA(cudaEventRecord(a, s)); }
-  void stop() { SSG_CUDA(cudaEventRecord(b, s)); }
+  void start() {
+    if (name && !open) {
+      nvtxRangePushA(name);
+      open = true;
+    }
+    SSG_CUDA(cudaEventRecord(a, s));
+  }
+  void stop() {
+    SSG_CUDA(cudaEventRecord(b, s));
+    if (open) {
+      nvtxRangePop();
+      open = false;
+    }
+  }
   double ms() {
     float t = 0.f;
     SSG_CUDA(cudaEventSynchronize(b));
@@ -116,6 +134,7 @@ struct StageTimer {
     return (double)t;
   }
   ~StageTimer() {
+    if (open) nvtxRangePop();  // a stage left by an error
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
   }
