@@ -104,3 +104,31 @@ def test_sift_like_integers_with_zero_fraction():
     assert x.dtype == np.float32 and x.shape == (20_000, 128)
     assert (x == np.rint(x)).all() and x.min() >= 0 and x.max() <= 255
     assert abs(float(np.mean(x == 0)) - 0.30) < 0.02
+
+
+def test_splitmix64_published_outputs():
+    # the first outputs of SplitMix64 from state 0 (Steele, Lea, Flood 2014; the values
+    # every published implementation reproduces)
+    g = synth.splitmix64_stream(0)
+    assert [next(g) for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                           0x06C45D188009454F]
+
+
+def test_nav_ids_distinct_in_range_and_complete():
+    for n, s, seed in ((10, 10, 1), (1000, 37, 2), (5, 3, 3)):
+        v = synth.nav_ids(n, s, seed)
+        assert v.dtype == np.int32 and len(v) == s and len(set(v.tolist())) == s
+        assert (v >= 0).all() and (v < n).all()
+    assert sorted(synth.nav_ids(10, 10, 4).tolist()) == list(range(10))
+    with pytest.raises(ValueError):
+        synth.nav_ids(3, 4, 0)
+
+
+def test_batched_specs_shapes():
+    specs = synth.batched_specs(64)
+    assert len(specs) == 64
+    assert all(10_000 <= s["n"] <= 500_000 for s in specs)
+    assert {s["d"] for s in specs} <= {64, 96, 128, 256}
+    assert {s["L"] for s in specs} <= {100, 200}
+    assert all(s["K"] == 100 and s["R"] == 32 and s["alpha"] == 60.0 for s in specs)
+    assert specs == synth.batched_specs(64)  # seeded
