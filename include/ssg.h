@@ -45,17 +45,37 @@ typedef enum {
   SSG_EIO = 6         /* ssg_save / ssg_load could not read or write the file */
 } ssg_status;
 
+/* Arithmetic of the kNN distance GEMM (ssg_build_opts.gemm_prec, ssg_knn, ssg_knn_query)
+ * and of the prune's Gram matrix (ssg_build_opts.gram_prec).  Every precision gives the
+ * same exact result (the precision changes the speed, not the graph): a low-precision value
+ * decides only where a rigorous error bound separates it from the decision boundary, and
+ * the rest is re-decided from the float32 inputs in fp32 / fp64.
+ *
+ * kNN GEMM:
+ *   FP32  single-precision SIMT GEMM form, top-(K + slack) re-ranked in fp64, each row
+ *         certified against the GEMM's error bound (uncertified rows recomputed exhaustively).
+ *   BF16  bf16 tcgen05 GEMM with fp32 accumulation (sm_103, d <= 128).  On integer data
+ *         that bf16 holds exactly the GEMM itself is exact.  On other data the rows are
+ *         centred on the column mean before rounding, each row keeps the KS nearest by bf16
+ *         distance (KS sized from a seeded sample of rows so that about 99% of rows
+ *         certify), the candidates are re-ranked in fp64, and a row is certified when its
+ *         K-th exact distance lies below the KS-th bf16 distance minus the rigorous bound
+ *         |d2_bf16 - d2| <= (2^-7 + ..) |x - mu| max_y |y - mu| + ..; every other row is
+ *         recomputed exhaustively (counted in ssg_build_stats.n_knn_fallback_rows).
+ *         EINVAL where the tensor-core path does not run.
+ *   AUTO  BF16 where the tensor-core path runs, FP32 otherwise (the default).
+ *   BF16_RERANK  the same as BF16 (an older name of the mode).
+ *   FP8   e4m3 with per-vector scales: not built yet (EINVAL).
+ * Prune Gram (gram_prec):
+ *   FP32  one warp per node, fp32 centred dot products, fp64 near cos(alpha).
+ *   BF16  the pool's Gram matrix from one tcgen05 MMA where the data are exact in bf16
+ *         (d <= 128, L <= 127); the FP32 prune elsewhere.  AUTO = BF16.  FP8: EINVAL. */
 typedef enum {
-  SSG_PREC_FP32 = 0,  /* single-precision SIMT distance GEMM */
-  SSG_PREC_BF16 = 1,  /* bf16 tensor-core distance GEMM (exact on small integers) */
-  SSG_PREC_AUTO = 2,  /* bf16 where the data make it exact, fp32 otherwise */
-  SSG_PREC_BF16_RERANK = 3 /* mixed precision for any data: where the bf16 tensor-core path
-                              runs (sm_103, d <= 128) it selects K + max(8, K/4) candidates
-                              per row by bf16 distance and orders them by exact distance,
-                              keeping K (exact on data exact in bf16; on other data a true
-                              neighbour that bf16 rounding ranks below the slack is missed);
-                              elsewhere the exact fp32 path runs.  ssg_knn_query treats it
-                              as SSG_PREC_AUTO (ground truth stays exact). */
+  SSG_PREC_FP32 = 0,
+  SSG_PREC_BF16 = 1,
+  SSG_PREC_AUTO = 2,
+  SSG_PREC_BF16_RERANK = 3,
+  SSG_PREC_FP8 = 4
 } ssg_precision;
 
 typedef void* ssg_stream; /* cudaStream_t */
@@ -86,6 +106,20 @@ typedef struct {
                                kNN order: n, then knn(n); stop once >= L ids).  1: the node's
                                own kNN row first, whole, then its neighbours' rows until >= L
                                ids (with K >= L the pool is the L nearest neighbours) */
+  ssg_precision gram_prec;  /* arithmetic of the prune's Gram matrix (see ssg_precision);
+                               the reverse merge's prune follows it */
+  double cos_margin_fp64;   /* reporting band of the angle test (Alg. 2): every decision whose
+                               fp32 cosine lies within the fp32 error bound plus this band of
+                               cos(alpha) is re-taken in fp64, and those whose fp64 cosine
+                               lies within the band are counted in
+                               ssg_build_stats.n_angle_borderline (default 1e-5; >= 0) */
+  const char* tune_table;   /* NULL: built-in launch parameters.  Otherwise the path of a
+                               text file of "name = value" lines (# starts a comment) that
+                               sets launch parameters; unknown names, bad values or an
+                               unreadable file give EINVAL.  Names: knn_sample_rows (rows
+                               sampled to size the bf16 candidate slack, 0..4096),
+                               knn_slack_quantile (fraction of sampled rows the slack must
+                               certify, 0.5..1) */
 } ssg_build_opts;
 
 /* Per-build measurements (all times from CUDA events on the build stream). */
@@ -104,6 +138,14 @@ typedef struct {
                                    1 for data that are integers 0..255 (the graph keeps a byte
                                    copy of the rows, used when ssg_search is given the base it
                                    was built from), 4 otherwise */
+  int32_t gram_prec_used;       /* ssg_precision of the first prune's Gram (BF16 or FP32) */
+  int64_t n_angle_borderline;   /* angle decisions whose fp64 cosine lies within
+                                   cos_margin_fp64 of cos(alpha) (decided exactly, counted) */
+  int32_t knn_candidates;       /* candidates per row of a bf16 kNN on data not exact in bf16
+                                   (the sized KS), 0 otherwise */
+  double ms_knn_certify;        /* of ms_knn on the certified bf16 path: all but the first
+                                   tensor-core pass (centring, sizing KS, re-rank and
+                                   certification, the passes over rows that failed) */
 } ssg_build_stats;
 
 typedef struct ssg_graph ssg_graph; /* opaque, owned by the library; ssg_free releases it */
@@ -112,6 +154,11 @@ typedef struct ssg_graph ssg_graph; /* opaque, owned by the library; ssg_free re
 void ssg_default_opts(ssg_build_opts* opts);
 const char* ssg_strerror(ssg_status s);
 const char* ssg_last_error(void);        /* message of the last failure on this thread */
+/* Status of the most recent failure that a kernel reported through its device status word
+ * (a bounded wait that gave up: SSG_ETIMEOUT; a capacity a kernel found exceeded:
+ * SSG_EINTERNAL), in any thread since the previous call; SSG_OK if none.  Reading it
+ * clears it.  The call that launched the kernel has returned the same status. */
+ssg_status ssg_last_device_status(void);
 int64_t ssg_kernel_launch_count(void);   /* kernels launched by this process so far */
 
 /* Fault injection for tests, on the host: the nth stream-ordered scratch allocation from
@@ -194,11 +241,13 @@ ssg_status ssg_connect(const float* base, int64_t n, int32_t d, int32_t* adj, in
                        int32_t R, const int32_t* nav, int32_t n_nav, int64_t* n_repair_host,
                        ssg_stream stream);
 
-/* ssg_connect for callers that cannot allocate device memory while they run: code that
- * records a CUDA graph (cudaMalloc is not allowed during stream capture), serving loops
- * whose device memory is fixed before requests arrive, or hosts that forbid allocations
- * outside their own allocator.  The paper has no counterpart; this is a deployment
- * variant of the connectivity step above, with the same arguments and the same result.
+/* ssg_connect for callers that cannot allocate device memory while they run: serving
+ * loops whose device memory is fixed before requests arrive, or hosts that forbid
+ * allocations outside their own allocator.  The paper has no counterpart; this is a
+ * deployment variant of the connectivity step above, with the same arguments and the same
+ * result (every navigating id is checked before the graph is modified).  Like ssg_connect
+ * it reads the navigating ids and each repair's state back to the host, synchronising the
+ * stream each time.
  * Its scratch (reached-node bitmap, two frontier buffers, per-node fp32 distances, the
  * list of fp64 re-tests) lives in one fixed array of about 12.3 MiB inside the library's
  * device image, which every GPU that loads the library holds until the process exits.

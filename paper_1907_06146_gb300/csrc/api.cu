@@ -19,6 +19,9 @@ namespace ssg {
 
 std::atomic<int64_t> g_launches{0};
 std::atomic<int64_t> g_fail_alloc{0};
+static std::atomic<int> g_dev_status{0};
+
+void note_device_status(ssg_status s) { g_dev_status.store((int)s); }
 thread_local int64_t t_launches = 0;
 static thread_local char g_err[1024] = "";
 
@@ -100,14 +103,70 @@ __global__ void k_pool_len_from_ids(const int32_t* __restrict__ ids, int64_t n, 
 }
 
 // The prune on the tensor cores where the data are exact in bf16 (and the pool and degree
-// fit its tile), the fp32 warp prune otherwise; both take the same decisions.
-static void prune_dispatch(bool tc_ok, const float* X, int ld, int d, int64_t n,
-                           const int32_t* pool_id, const int32_t* pool_len, int L, int R,
-                           double cos_a, int32_t* adj, int32_t* deg, Counters* ctr, cudaStream_t st) {
-  if (tc_ok && prune_tc_available(d, L, R))
-    prune_run_tc(X, ld, d, n, pool_id, pool_len, L, R, cos_a, adj, deg, ctr, st);
-  else
-    prune_run(X, ld, d, n, pool_id, pool_len, L, R, cos_a, adj, deg, ctr, st);
+// fit its tile), the fp32 warp prune otherwise; both take the same decisions.  Returns the
+// precision used.
+static ssg_precision prune_dispatch(bool tc_ok, const float* X, int ld, int d, int64_t n,
+                                    const int32_t* pool_id, const int32_t* pool_len, int L, int R,
+                                    double cos_a, double border, int32_t* adj, int32_t* deg,
+                                    Counters* ctr, cudaStream_t st) {
+  if (tc_ok && prune_tc_available(d, L, R)) {
+    prune_run_tc(X, ld, d, n, pool_id, pool_len, L, R, cos_a, border, adj, deg, ctr, st);
+    return SSG_PREC_BF16;
+  }
+  prune_run(X, ld, d, n, pool_id, pool_len, L, R, cos_a, border, adj, deg, ctr, st);
+  return SSG_PREC_FP32;
+}
+
+static void check_prec(ssg_precision p, const char* what) {
+  SSG_REQUIRE((int)p >= 0 && (int)p <= 4, SSG_EINVAL, "%s: unknown precision %d", what, (int)p);
+  SSG_REQUIRE(p != SSG_PREC_FP8, SSG_EINVAL,
+              "%s: FP8 (e4m3 with per-vector scales) is not built; use BF16, FP32 or AUTO", what);
+}
+
+// The kNN GEMM a precision request takes on given data: 1 the bf16 tensor cores on data they
+// hold exactly, 2 the certified bf16 path on other data, 0 the fp32 path.
+static int knn_path(ssg_precision p, const DataInfo& info, int d) {
+  if (p == SSG_PREC_FP32 || !knn_tc_available(d)) return 0;
+  return info.bf16_exact ? 1 : 2;
+}
+
+// "name = value" lines of a launch-parameter file (ssg_build_opts.tune_table).
+static KnnTune read_tune_table(const char* path) {
+  KnnTune t;
+  if (!path) return t;
+  FILE* f = fopen(path, "r");
+  SSG_REQUIRE(f, SSG_EINVAL, "tune_table: cannot open %s", path);
+  std::unique_ptr<FILE, int (*)(FILE*)> fc(f, fclose);
+  char line[512];
+  int ln = 0;
+  while (fgets(line, sizeof(line), f)) {
+    ++ln;
+    char* h = strchr(line, '#');
+    if (h) *h = 0;
+    char name[128];
+    double v = 0.0;
+    char tail[8];
+    const int got = sscanf(line, " %127[A-Za-z0-9_] = %lf %7s", name, &v, tail);
+    if (got <= 0) {
+      char rest[8];
+      SSG_REQUIRE(sscanf(line, " %7s", rest) <= 0, SSG_EINVAL, "tune_table %s:%d: cannot parse",
+                  path, ln);
+      continue;
+    }
+    SSG_REQUIRE(got == 2, SSG_EINVAL, "tune_table %s:%d: expected \"name = value\"", path, ln);
+    if (!strcmp(name, "knn_sample_rows")) {
+      SSG_REQUIRE(v >= 0 && v <= 4096 && v == std::floor(v), SSG_EINVAL,
+                  "tune_table %s:%d: knn_sample_rows must be an integer in [0, 4096]", path, ln);
+      t.sample_rows = (int)v;
+    } else if (!strcmp(name, "knn_slack_quantile")) {
+      SSG_REQUIRE(v >= 0.5 && v <= 1.0, SSG_EINVAL,
+                  "tune_table %s:%d: knn_slack_quantile must lie in [0.5, 1]", path, ln);
+      t.slack_quantile = v;
+    } else {
+      SSG_REQUIRE(false, SSG_EINVAL, "tune_table %s:%d: unknown name %s", path, ln, name);
+    }
+  }
+  return t;
 }
 
 static void ingest_all(const float* X, int64_t n, int d, cudaStream_t st, Ingested& g,
@@ -135,6 +194,9 @@ void ssg_default_opts(ssg_build_opts* o) {
   o->debug_checks = 0;
   o->pool_tiles = 0;
   o->pool_own_row_first = 0;
+  o->gram_prec = SSG_PREC_AUTO;
+  o->cos_margin_fp64 = 1e-5;
+  o->tune_table = nullptr;
 }
 
 const char* ssg_strerror(ssg_status s) {
@@ -143,6 +205,8 @@ const char* ssg_strerror(ssg_status s) {
 }
 
 const char* ssg_last_error(void) { return g_err; }
+
+ssg_status ssg_last_device_status(void) { return (ssg_status)g_dev_status.exchange(0); }
 
 int64_t ssg_kernel_launch_count(void) { return g_launches.load(); }
 
@@ -191,18 +255,30 @@ ssg_status ssg_nav_ids(int64_t n, int32_t s, uint64_t seed, int32_t* out) {
   });
 }
 
-// Mixed-precision kNN rows for data not exact in bf16: the tensor cores select K + slack
-// candidates per row by bf16 distance, and each row's candidates are ordered by exact
-// distance (fp32 values, near ties re-sorted in fp64) and cut to K.
-static void knn_bf16_rerank(const Ingested& g, int64_t n, int d, int K, int32_t* knn_id,
-                            float* knn_d2, Counters* ctr, cudaStream_t st, StageTimer* t_gemm) {
-  const int Kp = (int)std::min<int64_t>(std::min(K + std::max(8, K / 4), 895), n - 1);
-  Scratch<int32_t> cid((size_t)n * Kp, st), len((size_t)n, st);
-  Scratch<float> cd2((size_t)n * Kp, st);
-  knn_exact_tc(g.rows.p, n, g.rows.ld, g.norms.p, g.rows.p, n, g.rows.ld, g.norms.p, d, 1, Kp,
-               cid.p, cd2.p, st, t_gemm, 0, true);
-  pool_from_candidates(g.rows.p, nullptr, g.rows.ld, d, n, cid.p, Kp, K, g.info.exact, knn_id,
-                       knn_d2, len.p, ctr, st);
+// The kNN rows of A against B (self: A is B) on the path the precision request and the
+// data select: the exact bf16 tensor cores, the certified bf16 path, or the fp32 path.
+static KnnResult knn_any(const Ingested& a, int64_t na, const Ingested& b, int64_t nb, int d,
+                         const DataInfo& info, int self, int K, ssg_precision prec, int32_t* ids,
+                         float* d2, bool exact_d2, const KnnTune& tune, Counters* ctr,
+                         cudaStream_t st, StageTimer* t_gemm, CertResult* cr) {
+  const int path = knn_path(prec, info, d);
+  SSG_REQUIRE(prec != SSG_PREC_BF16 || path != 0, SSG_EINVAL,
+              "bf16 distance GEMM needs sm_103 and d <= 128");
+  KnnResult kr;
+  if (path == 1) {
+    knn_exact_tc(a.rows.p, na, a.rows.ld, a.norms.p, b.rows.p, nb, b.rows.ld, b.norms.p, d, self, K,
+                 ids, d2, st, t_gemm);
+  } else if (path == 2) {
+    const CertResult c = knn_bf16_certified(a.rows.p, na, a.rows.ld, a.norms.p, b.rows.p, nb,
+                                            b.norms.p, d, info, self, K, ids, d2, exact_d2, tune,
+                                            &ctr->order_fp64, st, t_gemm);
+    kr.fallback_rows = c.fallback_rows;
+    if (cr) *cr = c;
+  } else {
+    kr = knn_exact(a.rows.p, na, a.rows.ld, a.norms.p, b.rows.p, nb, b.rows.ld, b.norms.p, d, info,
+                   self, K, ids, d2, st, t_gemm);
+  }
+  return kr;
 }
 
 ssg_status ssg_knn(const float* base, int64_t n, int32_t d, int32_t K, ssg_precision prec,
@@ -211,24 +287,14 @@ ssg_status ssg_knn(const float* base, int64_t n, int32_t d, int32_t K, ssg_preci
     SSG_REQUIRE(base && knn_id && knn_d2, SSG_EINVAL, "null pointer");
     SSG_REQUIRE(n >= 2 && n < (1ll << 31) && d >= 1, SSG_EINVAL, "need 2 <= n < 2^31 and d >= 1");
     SSG_REQUIRE(K >= 1 && K <= n - 1 && K <= 700, SSG_EINVAL, "need 1 <= K <= min(n - 1, 700)");
+    check_prec(prec, "ssg_knn");
     cudaStream_t st = (cudaStream_t)stream;
     Ingested g;
     ingest_all(base, n, d, st, g, true);
-    const bool tc = prec != SSG_PREC_FP32 && g.info.bf16_exact && knn_tc_available(d);
-    SSG_REQUIRE(prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
-                "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
-                "and 2 d max|x|^2 <= 2^24 (4 d max|x|^2 with negative values)");
-    if (tc) {
-      knn_exact_tc(g.rows.p, n, g.rows.ld, g.norms.p, g.rows.p, n, g.rows.ld, g.norms.p, d, 1, K,
-                   knn_id, knn_d2, st, nullptr);
-    } else if (prec == SSG_PREC_BF16_RERANK && knn_tc_available(d)) {
-      Scratch<Counters> ctr(1, st);
-      SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
-      knn_bf16_rerank(g, n, d, K, knn_id, knn_d2, ctr.p, st, nullptr);
-    } else {
-      knn_exact(g.rows.p, n, g.rows.ld, g.norms.p, g.rows.p, n, g.rows.ld, g.norms.p, d, g.info,
-                1, K, knn_id, knn_d2, st, nullptr);
-    }
+    Scratch<Counters> ctr(1, st);
+    SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
+    knn_any(g, n, g, n, d, g.info, 1, K, prec, knn_id, knn_d2, true, KnnTune(), ctr.p, st, nullptr,
+            nullptr);
   });
 }
 
@@ -239,6 +305,7 @@ ssg_status ssg_knn_query(const float* base, int64_t n, int32_t d, const float* q
     SSG_REQUIRE(base && queries && ids && d2, SSG_EINVAL, "null pointer");
     SSG_REQUIRE(n >= 1 && n < (1ll << 31) && d >= 1 && nq >= 0, SSG_EINVAL, "bad sizes");
     SSG_REQUIRE(k >= 1 && k <= n && k <= 700, SSG_EINVAL, "need 1 <= k <= min(n, 700)");
+    check_prec(prec, "ssg_knn_query");
     if (nq == 0) return;
     cudaStream_t st = (cudaStream_t)stream;
     Ingested gb, gq;
@@ -251,16 +318,10 @@ ssg_status ssg_knn_query(const float* base, int64_t n, int32_t d, const float* q
     info.bf16_exact = info.exact && ma <= 256.f;
     info.max_norm = gb.info.max_norm;
     info.max_abs = ma;
-    const bool tc = prec != SSG_PREC_FP32 && info.bf16_exact && knn_tc_available(d);
-    SSG_REQUIRE(prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
-                "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
-                "and 2 d max|x|^2 <= 2^24 (4 d max|x|^2 with negative values)");
-    if (tc)
-      knn_exact_tc(gq.rows.p, nq, gq.rows.ld, gq.norms.p, gb.rows.p, n, gb.rows.ld, gb.norms.p, d,
-                   0, k, ids, d2, st, nullptr);
-    else
-      knn_exact(gq.rows.p, nq, gq.rows.ld, gq.norms.p, gb.rows.p, n, gb.rows.ld, gb.norms.p, d,
-                info, 0, k, ids, d2, st, nullptr);
+    Scratch<Counters> ctr(1, st);
+    SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
+    knn_any(gq, nq, gb, n, d, info, 0, k, prec, ids, d2, true, KnnTune(), ctr.p, st, nullptr,
+            nullptr);
   });
 }
 
@@ -296,7 +357,7 @@ ssg_status ssg_prune(const float* base, int64_t n, int32_t d, const int32_t* poo
     Scratch<Counters> ctr(1, st);
     SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
     prune_dispatch(g.info.bf16_exact != 0, g.rows.p, g.rows.ld, d, n, pool_id, pool_len, L, R,
-                   cos_alpha_of(alpha_deg), adj, deg, ctr.p, st);
+                   cos_alpha_of(alpha_deg), 1e-5, adj, deg, ctr.p, st);
   });
 }
 
@@ -313,9 +374,8 @@ ssg_status ssg_reverse(const float* base, int64_t n, int32_t d, const int32_t* a
     ingest_all(base, n, d, st, g, false);
     Scratch<Counters> ctr(1, st);
     SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
-    reverse_run(g.rows.p, nullptr, g.rows.ld, d, n, adj0, deg0, R, cos_alpha_of(alpha_deg),
-                g.info.exact,
-                g.info.bf16_exact != 0, adj1, deg1, ctr.p, st);
+    reverse_run(g.rows.p, nullptr, g.rows.ld, d, n, adj0, deg0, R, cos_alpha_of(alpha_deg), 1e-5,
+                g.info.exact, g.info.bf16_exact != 0, adj1, deg1, ctr.p, st);
   });
 }
 
@@ -420,6 +480,11 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     SSG_REQUIRE(L >= 1 && L + K <= 1023, SSG_EINVAL, "need L >= 1 and L + K <= 1023");
     check_alpha(alpha_deg);
     check_prune_fit(d, R);
+    check_prec(opts.gemm_prec, "gemm_prec");
+    check_prec(opts.gram_prec, "gram_prec");
+    SSG_REQUIRE(opts.cos_margin_fp64 >= 0.0 && opts.cos_margin_fp64 <= 0.5, SSG_EINVAL,
+                "cos_margin_fp64 must lie in [0, 0.5], got %g", opts.cos_margin_fp64);
+    const KnnTune tune = read_tune_table(opts.tune_table);
     SSG_REQUIRE(opts.n_nav >= 1 && opts.n_nav <= n && opts.n_nav <= 4096, SSG_EINVAL,
                 "need 1 <= n_nav <= min(n, 4096)");
     std::vector<int32_t> nav((size_t)opts.n_nav);
@@ -473,11 +538,13 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     const double cos_a = cos_alpha_of(alpha_deg);
 
     const uint8_t* X8 = g->rows_u8;
-    const bool tc = opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact && knn_tc_available(d);
-    const bool tc_rr = !tc && opts.gemm_prec == SSG_PREC_BF16_RERANK && knn_tc_available(d);
-    SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || tc, SSG_EINVAL,
-                "bf16 distance GEMM needs sm_103, d <= 128 and integer data with |x| <= 256 "
-                "and 2 d max|x|^2 <= 2^24 (4 d max|x|^2 with negative values)");
+    const int kpath = knn_path(opts.gemm_prec, in.info, d);
+    const bool tc = kpath == 1;
+    const double border = opts.cos_margin_fp64;
+    const bool gram_tc = opts.gram_prec != SSG_PREC_FP32 && in.info.bf16_exact;
+    SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || kpath != 0, SSG_EINVAL,
+                "bf16 distance GEMM needs sm_103 and d <= 128");
+    CertResult cert;
     Scratch<int32_t> pool_id((size_t)n * L, st), pool_len((size_t)n, st);
     Scratch<float> pool_d2((size_t)n * L, st);
     KnnResult kr;
@@ -521,14 +588,8 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
       Scratch<int32_t> knn_id((size_t)n * K, st);
       Scratch<float> knn_d2((size_t)n * K, st);
       t_knn.start();
-      if (tc)
-        knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d,
-                     1, K, knn_id.p, knn_d2.p, st, &t_gemm);
-      else if (tc_rr)
-        knn_bf16_rerank(in, n, d, K, knn_id.p, knn_d2.p, ctr.p, st, &t_gemm);
-      else
-        kr = knn_exact(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p,
-                       d, in.info, 1, K, knn_id.p, knn_d2.p, st, &t_gemm);
+      kr = knn_any(in, n, in, n, d, in.info, 1, K, opts.gemm_prec, knn_id.p, knn_d2.p, false, tune,
+                   ctr.p, st, &t_gemm, &cert);
       t_knn.stop();
       in.norms.release();
 
@@ -550,8 +611,9 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     // a3: SSG prune
     Scratch<int32_t> adj0((size_t)n * R, st), deg0((size_t)n, st);
     t_prune.start();
-    prune_dispatch(opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact, in.rows.p, in.rows.ld, d, n,
-                   pool_id.p, pool_len.p, L, R, cos_a, adj0.p, deg0.p, ctr.p, st);
+    const ssg_precision gram_used =
+        prune_dispatch(gram_tc, in.rows.p, in.rows.ld, d, n, pool_id.p, pool_len.p, L, R, cos_a,
+                       border, adj0.p, deg0.p, ctr.p, st);
     t_prune.stop();
     if (opts.debug_checks) debug_check(check_adj(adj0.p, deg0.p, n, R, st), "the prune");
     pool_id.release();
@@ -560,10 +622,8 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
 
     // a4: reverse-neighbour merge
     t_rev.start();
-    const int maxin = reverse_run(in.rows.p, X8, in.rows.ld, d, n, adj0.p, deg0.p, R, cos_a,
-                                  in.info.exact,
-                                  opts.gemm_prec != SSG_PREC_FP32 && in.info.bf16_exact != 0,
-                                  g->adj, g->deg, ctr.p, st);
+    const int maxin = reverse_run(in.rows.p, X8, in.rows.ld, d, n, adj0.p, deg0.p, R, cos_a, border,
+                                  in.info.exact, gram_tc, g->adj, g->deg, ctr.p, st);
     t_rev.stop();
     if (opts.debug_checks) debug_check(check_adj(g->adj, g->deg, n, R, st), "the reverse merge");
     adj0.release();
@@ -594,7 +654,11 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     S.n_knn_fallback_rows = kr.fallback_rows;
     S.max_indegree = maxin;
     S.exact_mode = in.info.exact;
-    S.gemm_prec_used = tc ? SSG_PREC_BF16 : (tc_rr ? SSG_PREC_BF16_RERANK : SSG_PREC_FP32);
+    S.gemm_prec_used = kpath == 0 ? SSG_PREC_FP32 : SSG_PREC_BF16;
+    S.gram_prec_used = gram_used;
+    S.n_angle_borderline = (int64_t)hc.angle_border;
+    S.knn_candidates = cert.candidates;
+    S.ms_knn_certify = kpath == 2 && opts.pool_tiles == 0 ? S.ms_knn - S.ms_knn_gemm : 0.0;
     S.kernel_launches = t_launches - launches0;
     S.search_row_bytes = g->rows_u8 ? 1 : 4;
     if (stats) *stats = S;

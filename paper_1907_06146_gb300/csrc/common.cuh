@@ -31,6 +31,9 @@ inline bool alloc_fault_injected() {
   return g_fail_alloc.fetch_sub(1) == 1;
 }
 extern thread_local int64_t t_launches;    // this host thread
+// Records a failure that a kernel reported through its device status word (read back by
+// ssg_last_device_status).
+void note_device_status(ssg_status s);
 
 struct Fail {
   ssg_status st;

@@ -11,6 +11,8 @@
 // coordinate-order sum, so its ties resolve exactly as a sequential double loop would.
 #include <climits>
 #include <mutex>
+#include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "graph_dev.cuh"
@@ -363,14 +365,14 @@ int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int3
 // ---------------------------------------------------------------------------------------
 // Connectivity without device allocation (ssg_connect_noalloc).
 //
-// Some callers cannot allocate device memory while they run: code that records a CUDA
-// graph (a cudaMalloc during stream capture is an error), serving loops that fix all
-// their memory before they take requests, or hosts that own a custom allocator and
+// Some callers cannot allocate device memory while they run: serving loops that fix all
+// their device memory before they take requests, or hosts that own a custom allocator and
 // forbid the driver's.  For them the connectivity step also comes with its scratch in one
 // fixed array that is part of the library's device image: the bitmap of reached nodes,
 // two frontier buffers, the fp32 distance of every node and the short list of fp64
 // re-tests, for graphs of up to NOALLOC_MAX_N nodes.  The same kernels run as in
-// ssg_connect; only the scratch differs.
+// ssg_connect; only the scratch differs.  Like ssg_connect, the call reads the navigating
+// ids and each repair's state back to the host, synchronising its stream each time.
 // ---------------------------------------------------------------------------------------
 namespace {
 constexpr int64_t NOALLOC_MAX_N = 1 << 20;       // nodes
@@ -407,8 +409,9 @@ static unsigned char* noalloc_scratch() {
 }
 
 static int64_t connect_run_noalloc(const float* X, int ld, int d, int64_t n, int32_t* adj,
-                                   int32_t* deg, int R, const int32_t* nav_dev, int n_nav,
-                                   cudaStream_t st) {
+                                   int32_t* deg, int R, const int32_t* nav_dev,
+                                   const int32_t* nav_host, int n_nav, cudaStream_t st) {
+  (void)nav_dev;
   unsigned char* base = noalloc_scratch();
   uint32_t* bm = (uint32_t*)(base + OFF_BM);
   int32_t* f[2] = {(int32_t*)(base + OFF_F0), (int32_t*)(base + OFF_F1)};
@@ -422,10 +425,7 @@ static int64_t connect_run_noalloc(const float* X, int ld, int d, int64_t n, int
   const int small_limit = 4096;
   int64_t repairs = 0;
   for (int r = 0; r < n_nav; ++r) {
-    int32_t root = 0;
-    SSG_CUDA(cudaMemcpyAsync(&root, nav_dev + r, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    SSG_CUDA(cudaStreamSynchronize(st));
-    SSG_REQUIRE(root >= 0 && root < n, SSG_EINVAL, "navigating node id %d out of range", root);
+    const int32_t root = nav_host[r];
     SSG_CUDA(cudaMemsetAsync(bm, 0, sizeof(uint32_t) * nw, st));
     SSG_LAUNCH(k_mark, 1, 1, 0, st, bm, f[0], &S->fcnt[0], root);
     int64_t start = 0;
@@ -480,18 +480,23 @@ extern "C" ssg_status ssg_connect_noalloc(const float* base, int64_t n, int32_t 
                 "(no padded copy is made), got d = %d",
                 d);
     SSG_REQUIRE(R >= 1 && n_nav >= 1, SSG_EINVAL, "need R >= 1 and n_nav >= 1");
-    const int64_t rep = connect_run_noalloc(base, d, d, n, adj, deg, R, nav, n_nav,
-                                            (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    // every navigating id is checked before the graph is touched (host memory only)
+    std::vector<int32_t> h((size_t)n_nav);
+    SSG_CUDA(cudaMemcpyAsync(h.data(), nav, sizeof(int32_t) * n_nav, cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    for (int t = 0; t < n_nav; ++t)
+      SSG_REQUIRE(h[t] >= 0 && h[t] < n, SSG_EINVAL, "navigating node id %d out of range", h[t]);
+    const int64_t rep = connect_run_noalloc(base, d, d, n, adj, deg, R, nav, h.data(), n_nav, st);
     if (n_repair_host) *n_repair_host = rep;
     return SSG_OK;
   } catch (const Fail& e) {
     return e.st;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return SSG_ENOMEM;
   } catch (...) {
     set_error("unexpected exception");
     return SSG_EINTERNAL;
   }
 }
-
-namespace ssg {
-
-}  // namespace ssg

@@ -164,14 +164,16 @@ constexpr int PRUNE_PREFETCH = 4;
 // Candidate rows arrive through a ring of PRUNE_PREFETCH rows filled by cp.async ahead of
 // use, so the global-memory latency of one row overlaps the work on earlier ones.
 // A decision within `margin` of cos(alpha), or with a zero-length edge, is re-taken in
-// fp64 from the original vectors.  Rows are read up to d rounded to 4 (the padding of X
-// is zero).  Shared memory per warp: prune_smem_floats(d, R) floats starting at V.
+// fp64 from the original vectors; an fp64 cosine within `border` of cos(alpha) is counted
+// in *nborder (the margin must cover border plus the fp32 error bound).  Rows are read
+// up to d rounded to 4 (the padding of X is zero).  Shared memory per warp: prune_smem_floats(d, R) floats starting at V.
 // Writes the kept ids to out[0, kept) (lane 0) and returns kept; *n64 += fp64 re-tests.
 __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int ld, int d,
                                                int64_t i, const int32_t* cand, int len, int R,
                                                float cosA32, double cosA64, float margin,
                                                float* V, int D1, float* xs, float* gkk,
-                                               int32_t* out, unsigned long long* n64) {
+                                               int32_t* out, unsigned long long* n64,
+                                               double border, unsigned long long* nborder) {
   const int lane = lane_id();
   const float* xg = X + i * ld;
   const int d4 = (d + 3) & ~3;
@@ -189,7 +191,7 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
   for (int t = 0; t < PRUNE_PREFETCH; ++t) prefetch(t);
   __syncwarp();
   int kept = 0;
-  unsigned long long fp64_tests = 0;
+  unsigned long long fp64_tests = 0, borderline = 0;
   for (int t = 0; t < len && kept < R; ++t) {
     const int32_t j = cand[t];
     cp_async_wait<PRUNE_PREFETCH - 1>();
@@ -206,7 +208,7 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
     __syncwarp();
     prefetch(t + PRUNE_PREFETCH);
     bool definite = false;
-    unsigned border = 0;
+    unsigned bmask = 0;
     for (int k = lane, r = 0; k < kept; k += 32, ++r) {
       const float4* vk = (const float4*)(V + k * D1);
       const float4* sl = (const float4*)slot;
@@ -221,27 +223,29 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
       const float g = (g0 + g1) + (g2 + g3);
       const float gk = gkk[k];
       if (gjj == 0.f || gk == 0.f) {
-        border |= 1u << r;
+        bmask |= 1u << r;
       } else {
         const float c = g / (sqrtf(gjj) * sqrtf(gk));
         if (c > cosA32 + margin)
           definite = true;
         else if (c >= cosA32 - margin)
-          border |= 1u << r;
+          bmask |= 1u << r;
       }
     }
     bool conflict = __any_sync(0xffffffffu, definite);
-    if (!conflict && __any_sync(0xffffffffu, border != 0)) {
+    if (!conflict && __any_sync(0xffffffffu, bmask != 0)) {
       bool c64 = false;
       const float* cj = X + (int64_t)j * ld;
-      for (int r = 0; border >> r; ++r) {
-        if (!((border >> r) & 1u)) continue;
+      for (int r = 0; bmask >> r; ++r) {
+        if (!((bmask >> r) & 1u)) continue;
         const int k = lane + 32 * r;
         const float* ck = X + (int64_t)out[k] * ld;
         const double gjk = centred_dot_f64(cj, ck, xg, d);
         const double g1 = centred_dot_f64(cj, cj, xg, d);
         const double g2 = centred_dot_f64(ck, ck, xg, d);
-        if (cos_from_gram_f64(gjk, g1, g2) > cosA64) c64 = true;
+        const double c = cos_from_gram_f64(gjk, g1, g2);
+        if (c > cosA64) c64 = true;
+        if (fabs(c - cosA64) <= border) ++borderline;
         ++fp64_tests;
       }
       conflict = __any_sync(0xffffffffu, c64);
@@ -258,6 +262,7 @@ __device__ __forceinline__ int warp_prune_node(const float* __restrict__ X, int 
   cp_async_wait<0>();
   __syncwarp();
   if (fp64_tests) atomicAdd(n64, fp64_tests);
+  if (borderline) atomicAdd(nborder, borderline);
   return kept;
 }
 
@@ -292,7 +297,9 @@ __device__ __forceinline__ int warp_prune_node_wide(const float* __restrict__ X,
                                                     int R, float cosA32, double cosA64,
                                                     float margin, float* __restrict__ Vg,
                                                     float* xs, float* cs, float* gkk,
-                                                    int32_t* out, unsigned long long* n64) {
+                                                    int32_t* out, unsigned long long* n64,
+                                                    double border,
+                                                    unsigned long long* nborder) {
   const int lane = lane_id();
   const float* xg = X + i * ld;
   const int d4 = (d + 3) & ~3;
@@ -300,7 +307,7 @@ __device__ __forceinline__ int warp_prune_node_wide(const float* __restrict__ X,
   for (int t = lane; t < d4; t += 32) xs[t] = xg[t];
   __syncwarp();
   int kept = 0;
-  unsigned long long fp64_tests = 0;
+  unsigned long long fp64_tests = 0, borderline = 0;
   for (int t = 0; t < len && kept < R; ++t) {
     const int32_t j = cand[t];
     const float4* cj4 = (const float4*)(X + (int64_t)j * ld);
@@ -332,22 +339,24 @@ __device__ __forceinline__ int warp_prune_node_wide(const float* __restrict__ X,
       }
       g = warp_sum(g);
       const float gk = gkk[k];
-      bool border = gjj == 0.f || gk == 0.f;
-      if (!border) {
+      bool near = gjj == 0.f || gk == 0.f;
+      if (!near) {
         const float c = g / (sqrtf(gjj) * sqrtf(gk));
         if (c > cosA32 + margin)
           conflict = true;
         else if (c >= cosA32 - margin)
-          border = true;
+          near = true;
       }
-      if (border) {
+      if (near) {
         // every lane takes the same fp64 decision from the same sequential sums
         const float* ck = X + (int64_t)out[k] * ld;
         const float* cjp = X + (int64_t)j * ld;
         const double gjk = centred_dot_f64(cjp, ck, xg, d);
         const double g1 = centred_dot_f64(cjp, cjp, xg, d);
         const double g2 = centred_dot_f64(ck, ck, xg, d);
-        conflict = cos_from_gram_f64(gjk, g1, g2) > cosA64;
+        const double c = cos_from_gram_f64(gjk, g1, g2);
+        conflict = c > cosA64;
+        if (fabs(c - cosA64) <= border) ++borderline;
         ++fp64_tests;
       }
     }
@@ -361,6 +370,7 @@ __device__ __forceinline__ int warp_prune_node_wide(const float* __restrict__ X,
     __syncwarp();
   }
   if (lane == 0 && fp64_tests) atomicAdd(n64, fp64_tests);
+  if (lane == 0 && borderline) atomicAdd(nborder, borderline);
   return kept;
 }
 

@@ -522,6 +522,7 @@ KnnResult knn_exact(const float* A, int64_t na, int lda, const float* a_norm, co
     int ovf = 0;
     SSG_CUDA(cudaMemcpyAsync(&ovf, fb_count.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     SSG_CUDA(cudaStreamSynchronize(st));
+    if (ovf) note_device_status(SSG_EINTERNAL);
     SSG_REQUIRE(ovf == 0, SSG_EINTERNAL,
                 "kNN fallback: more than %d columns tie with a row's K-th distance", cap);
   }

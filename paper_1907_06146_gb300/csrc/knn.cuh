@@ -48,6 +48,17 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
 // bf16 tensor-core variant of the exact top-K (only for info.bf16_exact data).
 // True on sm_103 when the shared-memory pipeline fits rows of d values (d <= 128).
 bool knn_tc_available(int d);
+// Optional inputs and outputs of knn_exact_tc.
+struct TcExtra {
+  const float* mu = nullptr;          // centre every row on mu [d] before rounding to bf16
+                                      // (a_norm / b_norm are then the centred rows' norms)
+  float* out_thresh = nullptr;        // per output row: the KS-th smallest distance kept
+                                      // (every column not returned is at least this far,
+                                      // up to the rounding of the streaming threshold)
+  const int32_t* qid = nullptr;       // self with A a gathered subset of B: query row r is
+                                      // base row qid[r]; outputs go to row r
+  const float* order_norm = nullptr;  // norms of A as given, for the cluster order
+};
 // max_tiles > 0 (self-joins only): the columns are visited in the cluster order and each
 // block of rows stops after its max_tiles nearest 128-column tiles, so the result is the
 // top-K among those columns (Alg. 4's search-based pools).  approx: the data need not be
@@ -55,14 +66,38 @@ bool knn_tc_available(int d);
 void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
                   int64_t nb, int ldb, const float* b_norm, int d, int self, int K,
                   int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer,
-                  int max_tiles = 0, bool approx = false);
+                  int max_tiles = 0, bool approx = false, const TcExtra& ex = TcExtra());
+
+// Launch parameters of the certified bf16 kNN (ssg_build_opts.tune_table).
+struct KnnTune {
+  int sample_rows = 256;        // rows sampled to size the candidate count KS
+  double slack_quantile = 0.99; // fraction of sampled rows KS must certify
+};
+struct CertResult {
+  int64_t fallback_rows = 0;  // rows not certified by the first pass
+  int64_t pass2_rows = 0;     // rows that took the second tensor-core pass
+  int64_t exact_rows = 0;     // rows recomputed on the exact fp32 path
+  int candidates = 0;         // KS of the first pass
+};
 
 struct Counters {
   unsigned long long angle_fp64;
   unsigned long long order_fp64;
   int max_indeg;
   int status;
+  unsigned long long angle_border;  // fp64 cosines within the reporting band of cos(alpha)
 };
+
+// Exact kNN rows through the bf16 tensor cores for data that bf16 does not hold exactly
+// (knn_cert.cu): A [na][ld] against B [nb][ld] (self: A is B, each row skips itself),
+// both with their fp32 squared norms as given; out_id / out_d2 [na][K] sorted by (d2, id);
+// d2 rounded from fp64 when exact_d2, else the fp32 direct value.  Needs
+// knn_tc_available(d).
+CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a_norm_raw,
+                              const float* B, int64_t nb, const float* b_norm_raw, int d,
+                              const DataInfo& info, int self, int K, int32_t* out_id, float* out_d2,
+                              bool exact_d2, const KnnTune& tune, unsigned long long* n_order,
+                              cudaStream_t st, StageTimer* gemm_timer);
 
 // Pools (Alg. 3 neighbour / neighbour's-neighbour loop).  X8 (nullable): the rows as
 // bytes (data integers 0..255, same stride), read instead of X for the distances.
@@ -78,23 +113,26 @@ void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int6
                           const int32_t* cand, int KS, int L, int exact, int32_t* pool_id,
                           float* pool_d2, int32_t* pool_len, Counters* dctr, cudaStream_t st);
 
-// SSG prune of each node's pool.
+// SSG prune of each node's pool.  border: decisions whose fp32 cosine lies within the
+// rigorous fp32 bound plus border of cos(alpha) are re-taken in fp64, and those whose fp64
+// cosine lies within border are counted in dctr->angle_border.
 void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
-               const int32_t* pool_len, int L, int R, double cos_a, int32_t* adj,
+               const int32_t* pool_len, int L, int R, double cos_a, double border, int32_t* adj,
                int32_t* deg, Counters* dctr, cudaStream_t st);
 
 // The same prune with each pool's Gram matrix on the tensor cores (data exact in bf16,
 // d <= 128, L <= 127, R <= 128; true where that path is available).
 bool prune_tc_available(int d, int L, int R);
 void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
-                  const int32_t* pool_len, int L, int R, double cos_a, int32_t* adj,
-                  int32_t* deg, Counters* dctr, cudaStream_t st);
+                  const int32_t* pool_len, int L, int R, double cos_a, double border,
+                  int32_t* adj, int32_t* deg, Counters* dctr, cudaStream_t st);
 
 // Reverse-neighbour merge; returns the largest in-degree.  tc: the prune of lists of up to
 // 127 candidates on the tensor cores where the data allow it.  X8 as for pool_run.
 int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
-                const int32_t* adj0, const int32_t* deg0, int R, double cos_a, int exact, bool tc,
-                int32_t* adj1, int32_t* deg1, Counters* dctr, cudaStream_t st);
+                const int32_t* adj0, const int32_t* deg0, int R, double cos_a, double border,
+                int exact, bool tc, int32_t* adj1, int32_t* deg1, Counters* dctr,
+                cudaStream_t st);
 
 // Connectivity from navigating nodes; returns the number of repair edges.
 int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int32_t* deg,

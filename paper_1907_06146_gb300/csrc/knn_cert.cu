@@ -1,0 +1,450 @@
+// Exact kNN rows from the bf16 tensor cores on data that bf16 does not hold exactly
+// (Alg. 3's kNN graph, and the serial-scan ground truth of Sec. 5.3, computed exactly).
+//
+// The rows are centred on the column mean mu before rounding (distances do not change
+// under a translation, and centred rows have smaller norms, hence smaller rounding errors).
+// The tensor-core kernel (knn_tc.cu) then keeps, per row, the KS columns with the smallest
+// bf16 distance d2~ and the KS-th smallest value t.  For every column j,
+//     |d2~(x, y_j) - d2(x, y_j)| <= E(x) = bf16_dist_bound(|x - mu|^2, max_j |y_j - mu|^2),
+// (the rounding of both operands to bf16, the fp32 accumulation of the tensor cores, the
+// fp32 norms and the centring; see the function), and a column that was not kept has
+// d2~ >= t - s(x) (s: the rounding of the streaming threshold).  So the row is exact once
+// the KS candidates are ordered exactly (fp32 distances from the original rows, runs of
+// near-equal values re-sorted in fp64) and its K-th exact distance d2_(K) satisfies
+//     d2_(K) < t - s(x) - E(x):
+// no column outside the candidates can then be nearer than (or tie with) the K-th.
+// Rows that fail take a second tensor-core pass with the largest candidate count, and
+// the few that fail again the exact fp32 path.  KS itself only trades speed: it is sized
+// from a seeded sample of rows (their exact K-th distance and the number of bf16
+// distances below it plus the bound), so that a set fraction of rows certify.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "graph_dev.cuh"
+#include "knn.cuh"
+
+namespace ssg {
+
+// Column sums in fp64: block (32, 8), column blockIdx.x * 32 + tx, rows strided over y.
+__global__ void k_col_sum(const float* __restrict__ X, int64_t n, int d, int ld,
+                          double* __restrict__ sum) {
+  __shared__ double part[8][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c = blockIdx.x * 32 + tx;
+  double s = 0.0;
+  if (c < d)
+    for (int64_t r = (int64_t)blockIdx.y * 8 + ty; r < n; r += (int64_t)gridDim.y * 8)
+      s += (double)X[r * ld + c];
+  part[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && c < d) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += part[k][tx];
+    atomicAdd(sum + c, t);
+  }
+}
+
+__global__ void k_col_mean(const double* __restrict__ sum, int d, int64_t n, float* __restrict__ mu) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < d) mu[c] = (float)(sum[c] / (double)n);
+}
+
+// Squared norms of the rows centred on mu (mu null: of the rows as given), with the same
+// fp32 subtraction as the bf16 conversion; *max_bits receives the largest (as float bits).
+__global__ void k_centred_norms(const float* __restrict__ X, int64_t n, int d, int ld,
+                                const float* __restrict__ mu, float* __restrict__ norm,
+                                unsigned* __restrict__ max_bits) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const int lane = lane_id();
+  const float* x = X + row * ld;
+  float s = 0.f;
+  for (int t = lane; t < d; t += 32) {
+    const float v = mu ? __fsub_rn(x[t], mu[t]) : x[t];
+    s = fmaf(v, v, s);
+  }
+  s = warp_sum(s);
+  if (lane == 0) {
+    norm[row] = s;
+    if (max_bits) atomicMax(max_bits, __float_as_uint(s));
+  }
+}
+
+__global__ void k_gather_rows(const float* __restrict__ X, int ld, const int32_t* __restrict__ ids,
+                              int64_t m, float* __restrict__ out) {
+  const int64_t total = m * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / ld;
+    out[i] = X[(int64_t)ids[r] * ld + (i - r * ld)];
+  }
+}
+
+__global__ void k_gather_vals(const float* __restrict__ v, const int32_t* __restrict__ ids, int64_t m,
+                              float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = v[ids[i]];
+}
+
+// Upper bound on |d2~ - d2| for a row whose centred fp32 squared norm is nx, against any
+// base row whose centred fp32 squared norm is at most ymax2 (d values, bf16 operands).
+//  - bf16 rounding (8 significant bits, unit roundoff u = 2^-8) of both operands:
+//    |x~ y~ - x y| <= (2u + u^2) |x y| per product, summed <= (2u + u^2) |x| |y|;
+//  - the tensor cores' fp32 accumulation of the dp + 16 terms (the augmentation step adds
+//    16): taken as (dp + 16) 2^-22 times the sum of the terms' magnitudes, four times the
+//    error of a sequentially rounded fp32 sum and above any truncating alignment of groups
+//    of 16 terms;
+//  - the four bf16 parts of -|y|^2/2 (their sum misses it by at most 2^-28 |y|^2);
+//  - the fp32 squared norms ((d + 2) u32 |.|^2 each) and |x|, |y| taken from them;
+//  - the final fused multiply-add and the fp32 centring (x - mu rounded once per value):
+//    4.2 u32 (|x| + |y|)^2 together.
+// Every factor 2 on the dot product terms comes from d2 = |x|^2 + |y|^2 - 2 x.y.
+__host__ __device__ inline double bf16_dist_bound(double nx, double ymax2, int d) {
+  const double u = 1.0 / 256.0, u32 = 5.9604644775390625e-08;
+  const double g = (double)((((d + 63) / 64) * 64) + 16) * 2.384185791015625e-07;
+  const double ax = sqrt(fmax(nx, 0.0) * (1.0 + (d + 2) * u32));
+  const double ay = sqrt(fmax(ymax2, 0.0) * (1.0 + (d + 2) * u32));
+  const double s = ax + ay;
+  const double e = 2.0 * (2.0 * u + u * u) * ax * ay +
+                   2.0 * g * ((1.0 + u) * (1.0 + u) * ax * ay + 0.5 * ay * ay) +
+                   4.0e-9 * ay * ay + (d + 2) * u32 * (ax * ax + ay * ay) + 4.2 * u32 * s * s;
+  return e * 1.05;
+}
+
+// How far below the final threshold t a column the kernel did not keep can lie: the
+// streaming test compares acc with fp32 (|x|^2 - tau) / 2, rounded once.
+__host__ __device__ inline double stream_slop(double nx, double t) {
+  return 2.02 * 5.9604644775390625e-08 * (fabs(nx) + fabs(t)) + 1e-30;
+}
+
+// Calibration: for each sampled query row t, the number of base rows j (j != sid[t]) whose
+// bf16 distance is at most lim[t].  One block of 256 threads per tile sweep; thread t owns
+// sampled row t (its bf16 values, transposed in shared memory); base rows come through in
+// tiles of TJ.  d <= 128.
+constexpr int CAL_S = 256, CAL_TJ = 32;
+__global__ void __launch_bounds__(CAL_S)
+k_band_count(const float* __restrict__ As, int s, int lda, const float* __restrict__ B, int64_t nb,
+             int ldb, int d, const float* __restrict__ mu, const float* __restrict__ nac,
+             const float* __restrict__ nbc, const double* __restrict__ lim,
+             const int32_t* __restrict__ sid, int* __restrict__ count) {
+  extern __shared__ __align__(16) float csm[];
+  const int dp = (d + 3) & ~3;
+  float* Qt = csm;                 // [dp][CAL_S]
+  float* Y = Qt + (size_t)dp * CAL_S;  // [CAL_TJ][dp]
+  const int t = threadIdx.x;
+  for (int i = t; i < dp * CAL_S; i += CAL_S) {
+    const int k = i / CAL_S, q = i - k * CAL_S;
+    float v = 0.f;
+    if (q < s && k < d) v = __bfloat162float(__float2bfloat16_rn(__fsub_rn(As[(int64_t)q * lda + k], mu[k])));
+    Qt[i] = v;
+  }
+  const float nq = t < s ? nac[t] : 0.f;
+  const double lq = t < s ? lim[t] : -1.0;
+  const int32_t me = t < s && sid ? sid[t] : -1;
+  int cnt = 0;
+  for (int64_t j0 = (int64_t)blockIdx.x * CAL_TJ; j0 < nb; j0 += (int64_t)gridDim.x * CAL_TJ) {
+    __syncthreads();
+    for (int i = t; i < CAL_TJ * dp; i += CAL_S) {
+      const int r = i / dp, k = i - r * dp;
+      const int64_t j = j0 + r;
+      float v = 0.f;
+      if (j < nb && k < d) v = __bfloat162float(__float2bfloat16_rn(__fsub_rn(B[j * ldb + k], mu[k])));
+      Y[i] = v;
+    }
+    __syncthreads();
+    float acc[CAL_TJ];
+#pragma unroll
+    for (int r = 0; r < CAL_TJ; ++r) acc[r] = 0.f;
+    for (int k = 0; k < dp; k += 4) {
+      const float q0 = Qt[(k + 0) * CAL_S + t], q1 = Qt[(k + 1) * CAL_S + t];
+      const float q2 = Qt[(k + 2) * CAL_S + t], q3 = Qt[(k + 3) * CAL_S + t];
+#pragma unroll
+      for (int r = 0; r < CAL_TJ; ++r) {
+        const float4 y = *(const float4*)(Y + r * dp + k);
+        acc[r] = fmaf(q0, y.x, fmaf(q1, y.y, fmaf(q2, y.z, fmaf(q3, y.w, acc[r]))));
+      }
+    }
+    if (t < s) {
+#pragma unroll
+      for (int r = 0; r < CAL_TJ; ++r) {
+        const int64_t j = j0 + r;
+        if (j < nb && (int32_t)j != me && (double)nq + (double)nbc[j] - 2.0 * (double)acc[r] <= lq)
+          ++cnt;
+      }
+    }
+  }
+  if (t < s && cnt) atomicAdd(count + t, cnt);
+}
+
+// lim[t] = the sampled row's exact K-th distance plus the bound (kth: [s][ld] rows of the
+// exact kNN of the sample, the K-th distance in column col).
+__global__ void k_band_limit(const float* __restrict__ d2, int ld, int col, int s,
+                             const float* __restrict__ nac, double ymax2, int d,
+                             double* __restrict__ lim) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < s) lim[t] = (double)d2[(int64_t)t * ld + col] + bf16_dist_bound(nac[t], ymax2, d);
+}
+
+// Exact order of each row's candidates and its certificate.  One warp per row r (rows:
+// compact index -> row id, null = identity): the candidates cand[r][0, KS) (-1 padded) get
+// fp32 distances from the original rows, are sorted by (d2, id), and runs of near-equal
+// values up to position K are re-sorted in fp64; the first K go to row rows[r] of the
+// output (d2 in fp64 rounded to float when exact_d2, else the fp32 value).  The row is
+// certified when the K-th exact distance (bounded above through the fp32 value) lies below
+// thr[r] - slop - E; otherwise it is listed in fb (with that bound) for another pass.
+__global__ void k_knn_cert(const float* __restrict__ A, const float* __restrict__ B, int ld, int d,
+                           const int32_t* __restrict__ rows, int64_t count,
+                           const int32_t* __restrict__ cand, int KS, const float* __restrict__ thr,
+                           const float* __restrict__ nac, double ymax2, int K, int cap, float rel,
+                           int exact_d2, int32_t* __restrict__ out_id, float* __restrict__ out_d2,
+                           int32_t* __restrict__ fb, double* __restrict__ fb_kth,
+                           int* __restrict__ fb_count, unsigned long long* __restrict__ n_order) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
+  uint64_t* keys = (uint64_t*)(sm_raw + (size_t)warp * cap * 16);
+  double* d64 = (double*)(keys + cap);
+  const int64_t r = (int64_t)blockIdx.x * wpb + warp;
+  if (r >= count) return;
+  const int64_t row = rows ? (int64_t)rows[r] : r;
+  const float* xi = A + r * ld;
+  int m = 0;
+  for (int c = 0; c < KS; c += 32) {
+    const int t = c + lane;
+    const int32_t id = t < KS ? cand[r * KS + t] : -1;
+    const bool v = id >= 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, v);
+    if (v) keys[m + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
+    m += __popc(bal);
+  }
+  __syncwarp();
+  warp_fill_dist_keys(keys, m, B, ld, xi);
+  int mp = 1;
+  while (mp < m) mp <<= 1;
+  for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
+  __syncwarp();
+  warp_sort_keys(keys, mp);
+  if (m > 1) {
+    int f = warp_fix_runs(keys, m, K, d64, B, ld, d, xi, rel);
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0 && f) atomicAdd(n_order, (unsigned long long)f);
+  }
+  const float INF = __int_as_float(0x7f800000);
+  for (int t = lane; t < K; t += 32) {
+    const bool v = t < m;
+    const int32_t id = v ? key_id(keys[t]) : -1;
+    float dd = v ? key_dist(keys[t]) : INF;
+    if (v && exact_d2) dd = (float)dist2_f64(xi, B + (int64_t)id * ld, d);
+    out_id[row * K + t] = id;
+    out_d2[row * K + t] = dd;
+  }
+  if (lane == 0) {
+    const float t = thr[r];
+    bool ok = m >= K && isinf(t) && t > 0.f;  // every column was a candidate
+    double kth = INF;
+    if (m >= K) {
+      kth = (double)key_dist(keys[K - 1]) * (1.0 + 1.01 * (double)rel) + 1e-30;
+      if (!ok) {
+        const double nx = (double)nac[row];
+        ok = kth < (double)t - stream_slop(nx, t) - bf16_dist_bound(nx, ymax2, d);
+      }
+    }
+    if (!ok) {
+      const int p = atomicAdd(fb_count, 1);
+      fb[p] = (int32_t)row;
+      fb_kth[p] = kth;
+    }
+  }
+}
+
+// Rows recomputed on the exact fp32 path as queries (no self exclusion) with K + 1
+// neighbours: row r's own id is dropped (or the last entry, if its own id is not among
+// them), the rest go to row rows[r] of the output.
+__global__ void k_scatter_drop_self(const int32_t* __restrict__ ids, const float* __restrict__ d2,
+                                    int K1, const int32_t* __restrict__ rows, int64_t count,
+                                    int self, int32_t* __restrict__ out_id, float* __restrict__ out_d2) {
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= count) return;
+  const int lane = lane_id();
+  const int32_t me = rows[r];
+  const int K = self ? K1 - 1 : K1;
+  int skip = K1;  // position dropped
+  if (self) {
+    skip = K1 - 1;
+    for (int c = 0; c < K1; c += 32) {
+      const unsigned m = __ballot_sync(0xffffffffu, c + lane < K1 && ids[r * K1 + c + lane] == me);
+      if (m) {
+        skip = c + __ffs(m) - 1;
+        break;
+      }
+    }
+  }
+  for (int t = lane; t < K; t += 32) {
+    const int src = t < skip ? t : t + 1;
+    out_id[(int64_t)me * K + t] = ids[r * K1 + src];
+    out_d2[(int64_t)me * K + t] = d2[r * K1 + src];
+  }
+}
+
+static int read_count(const int* p, cudaStream_t st) {
+  int h = 0;
+  SSG_CUDA(cudaMemcpyAsync(&h, p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SSG_CUDA(cudaStreamSynchronize(st));
+  return h;
+}
+
+// One certification launch (k_knn_cert) over count rows; returns the rows that failed.
+static int certify(const float* A, const float* B, int ld, int d, const int32_t* rows, int64_t count,
+                   const int32_t* cand, int KS, const float* thr, const float* nac, double ymax2,
+                   int K, bool exact_d2, int32_t* out_id, float* out_d2, int32_t* fb, double* fbk,
+                   int* fbc, unsigned long long* n_order, cudaStream_t st) {
+  SSG_CUDA(cudaMemsetAsync(fbc, 0, sizeof(int), st));
+  if (count == 0) return 0;
+  const int cap = next_pow2(std::max(KS, 32));
+  const int wpb = 4;
+  const size_t smem = (size_t)cap * 16 * wpb;
+  ensure_smem((const void*)k_knn_cert, smem);
+  SSG_LAUNCH(k_knn_cert, (unsigned)ceil_div(count, wpb), wpb * 32, smem, st, A, B, ld, d, rows, count,
+             cand, KS, thr, nac, ymax2, K, cap, dist_rel_fp32(d), exact_d2 ? 1 : 0, out_id, out_d2, fb,
+             fbk, fbc, n_order);
+  return read_count(fbc, st);
+}
+
+CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a_norm_raw,
+                              const float* B, int64_t nb, const float* b_norm_raw, int d,
+                              const DataInfo& info, int self, int K, int32_t* out_id, float* out_d2,
+                              bool exact_d2, const KnnTune& tune, unsigned long long* n_order,
+                              cudaStream_t st, StageTimer* gemm_timer) {
+  CertResult res;
+  SSG_REQUIRE(knn_tc_available(d) && d <= 128, SSG_EINTERNAL,
+              "certified bf16 kNN: the tensor-core path does not run for d = %d", d);
+  const int grid = 8 * num_sms();
+  // centre on the base's column mean; centred squared norms and their maximum
+  Scratch<double> csum((size_t)d, st);
+  SSG_CUDA(cudaMemsetAsync(csum.p, 0, sizeof(double) * d, st));
+  const unsigned gy = (unsigned)std::min<int64_t>(ceil_div(nb, 8), 4 * num_sms());
+  SSG_LAUNCH(k_col_sum, dim3((unsigned)ceil_div(d, 32), gy), dim3(32, 8), 0, st, B, nb, d, ld, csum.p);
+  Scratch<float> mu((size_t)d, st);
+  SSG_LAUNCH(k_col_mean, (unsigned)ceil_div(d, 128), 128, 0, st, csum.p, d, nb, mu.p);
+  Scratch<float> nbc((size_t)nb, st), nac_own;
+  Scratch<unsigned> mx(1, st);
+  SSG_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned), st));
+  SSG_LAUNCH(k_centred_norms, (unsigned)ceil_div(nb, 8), 256, 0, st, B, nb, d, ld, mu.p, nbc.p, mx.p);
+  const float* nac = nbc.p;
+  if (!self) {
+    nac_own.alloc((size_t)na, st);
+    SSG_LAUNCH(k_centred_norms, (unsigned)ceil_div(na, 8), 256, 0, st, A, na, d, ld, mu.p,
+               nac_own.p, (unsigned*)nullptr);
+    nac = nac_own.p;
+  }
+  unsigned mbits = 0;
+  SSG_CUDA(cudaMemcpyAsync(&mbits, mx.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  SSG_CUDA(cudaStreamSynchronize(st));
+  float ymax2f;
+  memcpy(&ymax2f, &mbits, 4);
+  const double ymax2 = (double)ymax2f;
+  const int64_t avail = self ? nb - 1 : nb;
+  const int KS_MAX = 895;  // the largest top-K the tensor-core kernel keeps
+
+  // KS: the tune.quantile point of the sampled rows' candidate needs, plus 5%
+  int KS = std::min<int64_t>(avail, std::max(K + 8, 2 * K));
+  const int s = (int)std::min<int64_t>(tune.sample_rows, na);
+  if (s > 0 && avail > KS && K + (int)self <= (int)avail) {
+    std::vector<int32_t> sid_h((size_t)s);
+    for (int t = 0; t < s; ++t) sid_h[t] = (int32_t)(((int64_t)t * na) / s);
+    Scratch<int32_t> sid((size_t)s, st);
+    SSG_CUDA(cudaMemcpyAsync(sid.p, sid_h.data(), sizeof(int32_t) * s, cudaMemcpyHostToDevice, st));
+    Scratch<float> As((size_t)s * ld, st), asn((size_t)s, st), asc((size_t)s, st);
+    SSG_LAUNCH(k_gather_rows, grid, 256, 0, st, A, ld, sid.p, (int64_t)s, As.p);
+    SSG_LAUNCH(k_centred_norms, (unsigned)ceil_div(s, 8), 256, 0, st, As.p, (int64_t)s, d, ld,
+               (const float*)nullptr, asn.p, (unsigned*)nullptr);
+    SSG_LAUNCH(k_gather_vals, (unsigned)ceil_div(s, 256), 256, 0, st, nac, sid.p, (int64_t)s, asc.p);
+    // the sample's exact K-th distance (itself included as a column when self: K + 1)
+    const int Kq = K + self;
+    Scratch<int32_t> sids((size_t)s * Kq, st);
+    Scratch<float> sd2((size_t)s * Kq, st);
+    knn_exact(As.p, s, ld, asn.p, B, nb, ld, b_norm_raw, d, info, 0, Kq, sids.p, sd2.p, st, nullptr);
+    Scratch<double> lim((size_t)s, st);
+    SSG_LAUNCH(k_band_limit, (unsigned)ceil_div(s, 128), 128, 0, st, sd2.p, Kq, Kq - 1, s, asc.p,
+               ymax2, d, lim.p);
+    Scratch<int> cnt((size_t)s, st);
+    SSG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * s, st));
+    const int dp = (d + 3) & ~3;
+    const size_t smem = sizeof(float) * ((size_t)dp * CAL_S + (size_t)CAL_TJ * dp);
+    ensure_smem((const void*)k_band_count, smem);
+    const unsigned cg = (unsigned)std::min<int64_t>(ceil_div(nb, CAL_TJ), num_sms());
+    SSG_LAUNCH(k_band_count, cg, CAL_S, smem, st, As.p, s, ld, B, nb, ld, d, mu.p, asc.p, nbc.p, lim.p,
+               self ? (const int32_t*)sid.p : nullptr, cnt.p);
+    std::vector<int> h((size_t)s);
+    SSG_CUDA(cudaMemcpyAsync(h.data(), cnt.p, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    std::sort(h.begin(), h.end());
+    const int qi = std::min(s - 1, (int)std::ceil(tune.slack_quantile * s) - 1);
+    const int need = (int)std::ceil(h[std::max(qi, 0)] * 1.05) + 8;
+    KS = (int)std::min<int64_t>(avail, std::max(K + 8, need));
+  }
+  KS = std::min(KS, KS_MAX);
+  res.candidates = KS;
+
+  // pass 1: every row
+  Scratch<int32_t> cid((size_t)na * KS, st);
+  Scratch<float> cd2((size_t)na * KS, st), thr((size_t)na, st);
+  TcExtra ex;
+  ex.mu = mu.p;
+  ex.out_thresh = thr.p;
+  ex.order_norm = a_norm_raw;
+  knn_exact_tc(A, na, ld, nac, B, nb, ld, nbc.p, d, self, KS, cid.p, cd2.p, st, gemm_timer, 0, true,
+               ex);
+  cd2.release();
+  Scratch<int32_t> fb((size_t)na, st), fb2((size_t)na, st);
+  Scratch<double> fbk((size_t)na, st);
+  Scratch<int> fbc(1, st);
+  int nfb = certify(A, B, ld, d, nullptr, na, cid.p, KS, thr.p, nac, ymax2, K, exact_d2, out_id,
+                    out_d2, fb.p, fbk.p, fbc.p, n_order, st);
+  cid.release();
+  res.fallback_rows = nfb;
+  int nlast = nfb;
+  const int32_t* last = fb.p;
+  // pass 2: the failed rows with the largest candidate count
+  if (nfb > 0 && KS < std::min<int64_t>(avail, KS_MAX)) {
+    const int KS2 = (int)std::min<int64_t>(avail, KS_MAX);
+    Scratch<float> Ag((size_t)nfb * ld, st), nag((size_t)nfb, st), thr2((size_t)nfb, st);
+    Scratch<int32_t> cid2((size_t)nfb * KS2, st);
+    Scratch<float> cd22((size_t)nfb * KS2, st);
+    SSG_LAUNCH(k_gather_rows, grid, 256, 0, st, A, ld, fb.p, (int64_t)nfb, Ag.p);
+    SSG_LAUNCH(k_gather_vals, (unsigned)ceil_div(nfb, 256), 256, 0, st, nac, fb.p, (int64_t)nfb, nag.p);
+    TcExtra ex2;
+    ex2.mu = mu.p;
+    ex2.out_thresh = thr2.p;
+    ex2.qid = self ? fb.p : nullptr;
+    knn_exact_tc(Ag.p, nfb, ld, nag.p, B, nb, ld, nbc.p, d, self, KS2, cid2.p, cd22.p, st, nullptr, 0,
+                 true, ex2);
+    // certify against the gathered rows' own centred norms: nac indexed by row id
+    nlast = certify(Ag.p, B, ld, d, fb.p, nfb, cid2.p, KS2, thr2.p, nac, ymax2, K, exact_d2, out_id,
+                    out_d2, fb2.p, fbk.p, fbc.p, n_order, st);
+    last = fb2.p;
+    res.pass2_rows = nfb;
+  }
+  // the rest: the exact fp32 path, as queries with K + self neighbours
+  if (nlast > 0) {
+    const int K1 = K + self;
+    Scratch<float> Ag((size_t)nlast * ld, st), agn((size_t)nlast, st);
+    SSG_LAUNCH(k_gather_rows, grid, 256, 0, st, A, ld, last, (int64_t)nlast, Ag.p);
+    SSG_LAUNCH(k_centred_norms, (unsigned)ceil_div(nlast, 8), 256, 0, st, Ag.p, (int64_t)nlast, d, ld,
+               (const float*)nullptr, agn.p, (unsigned*)nullptr);
+    Scratch<int32_t> ids((size_t)nlast * K1, st);
+    Scratch<float> dd((size_t)nlast * K1, st);
+    const KnnResult kr = knn_exact(Ag.p, nlast, ld, agn.p, B, nb, ld, b_norm_raw, d, info, 0, K1,
+                                   ids.p, dd.p, st, nullptr);
+    (void)kr;
+    SSG_LAUNCH(k_scatter_drop_self, (unsigned)ceil_div(nlast, 8), 256, 0, st, ids.p, dd.p, K1, last,
+               (int64_t)nlast, self, out_id, out_d2);
+    res.exact_rows = nlast;
+  }
+  return res;
+}
+
+}  // namespace ssg

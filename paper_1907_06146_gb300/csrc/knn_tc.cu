@@ -68,6 +68,9 @@ struct TcArgs {
   const int32_t* inv;         // original id -> stored position
   const int32_t* tile_order;  // per cluster, its first tstride tile indices (null: in order)
   const int32_t* rb_cluster;  // cluster of each block of BM stored query rows
+  float* out_thresh;          // nullable: per output row, the KS-th smallest distance kept
+  const int32_t* qid;         // nullable: query row r is base row qid[r] (the self column);
+                              // outputs then go to row r
 };
 
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -390,12 +393,15 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         const int c2 = cl <= 256 ? compact_row<256>(lb, cl, p.KS, &t2)
                                  : compact_row<C>(lb, cl, p.KS, &t2);
         if (r >= p.na) continue;
-        const int64_t ro = p.perm ? (int64_t)p.perm[r] : r;  // the row's original id
+        // the output row, and the base id of the row itself (the self column)
+        const int64_t ro = p.qid ? r : (p.perm ? (int64_t)p.perm[r] : r);
+        const int32_t sid = p.qid ? p.qid[r] : (int32_t)ro;
+        if (p.out_thresh && lane == 0) p.out_thresh[ro] = t2;
         int selfpos = c2;
         if (p.self) {
           for (int e0 = 0; e0 < c2; e0 += 32) {
             const int e = e0 + lane;
-            const unsigned m = __ballot_sync(0xffffffffu, e < c2 && key_id(lb[e]) == (int32_t)ro);
+            const unsigned m = __ballot_sync(0xffffffffu, e < c2 && key_id(lb[e]) == sid);
             if (m) {
               selfpos = e0 + __ffs(m) - 1;
               break;
@@ -424,17 +430,21 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   }
 }
 
-// bf16 copy with rows padded to dp; with perm, stored row r holds row perm[r] (and its norm).
+// bf16 copy with rows padded to dp; with perm, stored row r holds row perm[r] (and its norm);
+// with mu, the rows are centred first (x - mu rounded to fp32, then to bf16).
 __global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int d, int ld,
                           __nv_bfloat16* __restrict__ Y, int dp, const int32_t* __restrict__ perm,
-                          const float* __restrict__ norm_in, float* __restrict__ norm_out) {
+                          const float* __restrict__ norm_in, float* __restrict__ norm_out,
+                          const float* __restrict__ mu) {
   const int64_t total = n * (int64_t)dp;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / dp;
     const int c = (int)(i - r * dp);
     const int64_t src = perm ? (int64_t)perm[r] : r;
-    Y[i] = __float2bfloat16_rn(c < d ? X[src * ld + c] : 0.f);
+    float v = c < d ? X[src * ld + c] : 0.f;
+    if (mu && c < d) v = __fsub_rn(v, mu[c]);
+    Y[i] = __float2bfloat16_rn(v);
     if (norm_out && c == 0) norm_out[r] = norm_in[src];
   }
 }
@@ -500,7 +510,7 @@ bool knn_tc_available(int d) {
 void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
                   int64_t nb, int ldb, const float* b_norm, int d, int self, int K,
                   int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer,
-                  int max_tiles, bool approx) {
+                  int max_tiles, bool approx, const TcExtra& ex) {
   const int dp = (d + 63) & ~63;
   const int kchunks = dp / 64;
   int stages = MAX_STAGES;
@@ -512,25 +522,30 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   // threshold otherwise falls slowly and many candidates are appended).
   KnnOrder ord;
   Scratch<float> norm_p;
-  SSG_REQUIRE(max_tiles == 0 || (self && knn_order_fits(na, BN)), SSG_EINVAL,
+  // same: the query rows are the base rows (a self-join); with ex.qid the query rows are a
+  // gathered subset of the base and only the self column is excluded
+  const bool same = self && !ex.qid;
+  SSG_REQUIRE(max_tiles == 0 || (same && knn_order_fits(na, BN)), SSG_EINVAL,
               "a tile limit needs a self-join whose cluster order fits");
   const bool ordered =
-      max_tiles > 0 || (self && na >= (1 << 16) && K >= 16 && knn_order_fits(na, BN));
+      max_tiles > 0 || (same && na >= (1 << 16) && K >= 16 && knn_order_fits(na, BN));
   if (ordered) {
-    knn_cluster_order(A, lda, d, na, BM, BN, st, ord, max_tiles, a_norm);
+    knn_cluster_order(A, lda, d, na, BM, BN, st, ord, max_tiles,
+                      ex.order_norm ? ex.order_norm : a_norm);
     norm_p.alloc((size_t)na, st);
   }
   Scratch<__nv_bfloat16> ab((size_t)na * dp, st);
   Scratch<__nv_bfloat16> bb;
   const int cgrid = 8 * num_sms();
   SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, A, na, d, lda, ab.p, dp,
-             ordered ? (const int32_t*)ord.perm.p : nullptr, a_norm, ordered ? norm_p.p : nullptr);
+             ordered ? (const int32_t*)ord.perm.p : nullptr, a_norm, ordered ? norm_p.p : nullptr,
+             ex.mu);
   if (ordered) a_norm = b_norm = norm_p.p;
   const __nv_bfloat16* bptr = ab.p;
-  if (!self) {
+  if (!same) {
     bb.alloc((size_t)nb * dp, st);
     SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, B, nb, d, ldb, bb.p, dp, (const int32_t*)nullptr,
-               (const float*)nullptr, (float*)nullptr);
+               (const float*)nullptr, (float*)nullptr, ex.mu);
     bptr = bb.p;
   }
   Scratch<__nv_bfloat16> aug_b((size_t)nb * AUG, st), aug_a((size_t)BM * AUG, st);
@@ -569,6 +584,8 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   a.out_id = out_id;
   a.out_d2 = out_d2;
   a.err = err.p;
+  a.out_thresh = ex.out_thresh;
+  a.qid = ex.qid;
   if (ordered) {
     a.perm = ord.perm.p;
     a.inv = ord.inv.p;
@@ -587,6 +604,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   int h = 0;
   SSG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
+  if (h != 0) note_device_status(h == 1 ? SSG_EINTERNAL : SSG_ETIMEOUT);
   SSG_REQUIRE(h != 1, SSG_EINTERNAL, "tensor-core kNN: a squared norm is not split exactly");
   SSG_REQUIRE(h == 0, SSG_ETIMEOUT, "tensor-core kNN: a pipeline wait timed out (code %d)", h);
 }

@@ -179,7 +179,8 @@ __global__ void k_prune(const float* __restrict__ X, int ld, int d, int64_t n,
                         const int32_t* __restrict__ pool_id, const int32_t* __restrict__ pool_len,
                         int L, int R, float cosA32, double cosA64, float margin,
                         int32_t* __restrict__ adj, int32_t* __restrict__ deg,
-                        unsigned long long* __restrict__ n64, float* __restrict__ Vg) {
+                        unsigned long long* __restrict__ n64, float* __restrict__ Vg,
+                        double border, unsigned long long* __restrict__ nborder) {
   extern __shared__ __align__(16) float smf[];
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
   const int64_t gwarp = (int64_t)blockIdx.x * wpb + warp;
@@ -193,11 +194,11 @@ __global__ void k_prune(const float* __restrict__ X, int ld, int d, int64_t n,
     if (Vg) {
       kept = warp_prune_node_wide(X, ld, d, i, pool_id + i * L, pool_len[i], R, cosA32, cosA64,
                                   margin, Vg + (size_t)gwarp * (R + 1) * d4, base, base + d4,
-                                  base + 2 * d4, out, n64);
+                                  base + 2 * d4, out, n64, border, nborder);
     } else {
       float* xs = base + (size_t)(R + 1) * D1;
       kept = warp_prune_node(X, ld, d, i, pool_id + i * L, pool_len[i], R, cosA32, cosA64, margin,
-                             base, D1, xs, xs + D1, out, n64);
+                             base, D1, xs, xs + D1, out, n64, border, nborder);
     }
     for (int t = kept + lane; t < R; t += 32) out[t] = -1;
     if (lane == 0) deg[i] = kept;
@@ -206,8 +207,8 @@ __global__ void k_prune(const float* __restrict__ X, int ld, int d, int64_t n,
 }
 
 void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
-               const int32_t* pool_len, int L, int R, double cos_a, int32_t* adj, int32_t* deg,
-               Counters* dctr, cudaStream_t st) {
+               const int32_t* pool_len, int L, int R, double cos_a, double border, int32_t* adj,
+               int32_t* deg, Counters* dctr, cudaStream_t st) {
   const bool wide = prune_is_wide(d, R);
   const size_t per_warp =
       (wide ? prune_wide_smem_floats(d, R) : prune_smem_floats(d, R)) * sizeof(float);
@@ -223,7 +224,8 @@ void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
   Scratch<float> Vg;
   if (wide) Vg.alloc((size_t)grid * wpb * (R + 1) * ((d + 3) & ~3), st);
   SSG_LAUNCH(k_prune, (unsigned)grid, wpb * 32, smem, st, X, ld, d, n, pool_id, pool_len, L, R,
-             (float)cos_a, cos_a, angle_margin_fp32(d), adj, deg, &dctr->angle_fp64, Vg.p);
+             (float)cos_a, cos_a, angle_margin_fp32(d) + (float)border, adj, deg, &dctr->angle_fp64,
+             Vg.p, border, &dctr->angle_border);
 }
 
 }  // namespace ssg

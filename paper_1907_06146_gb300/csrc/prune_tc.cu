@@ -8,8 +8,8 @@
 //     G_jk = (c_j - x).(c_k - x) = H_jk - H_j0 - H_k0 + H_00,   G_jj = d2(x, c_j).
 // All pairs are tested at once: bit k of row j says whether cos(j, k) = G_jk / sqrt(G_jj
 // G_kk) > cos(alpha) (0 for a zero-length edge).  The fp32 cosine decides where it is more
-// than 16 units of roundoff from cos(alpha) (its inputs are exact, its error a few units);
-// otherwise the bit is taken in fp64 from the same exact integers with the operations of
+// than 16 units of roundoff (plus the reporting band) from cos(alpha) (its inputs are
+// exact, its error a few units); otherwise the bit is taken in fp64 from the same exact integers with the operations of
 // the definition, which reproduces the double-precision rule bit for bit.  The selection
 // in candidate order (keep c_j unless it conflicts with a kept c_k, stop at R) is then a
 // scan over these bit rows.
@@ -54,6 +54,8 @@ struct PtArgs {
   int32_t* deg;
   unsigned long long* n64;
   int* err;
+  double border;                // fp64 cosines within this of cos(alpha) are counted
+  unsigned long long* nborder;
 };
 
 __global__ void __launch_bounds__(THREADS_P, 1)
@@ -193,7 +195,7 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
     int b = 0, u = 0, k = 0;
     uint32_t tph = 0, uph = 0;
     bool ok = true;
-    unsigned long long fp64_tests = 0;
+    unsigned long long fp64_tests = 0, borderline = 0;
     for (int64_t x = blockIdx.x; x < n; x += gridDim.x, ++k) {
       const int nrows = min(p.pool_len[x], PT_ROWS - 1) + 1;
       ok = mbar_wait(smem_u32(t_full + b), tph, abort_flag);
@@ -289,7 +291,9 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
             bd &= bd - 1;
             const int j = c * 32 + e;
             const float g = (st[e] - xa[j]) + t2;
-            if (cos_from_gram_f64((double)g, (double)dgi, (double)xd[j]) > p.cosA64) cf |= 1u << e;
+            const double c64 = cos_from_gram_f64((double)g, (double)dgi, (double)xd[j]);
+            if (c64 > p.cosA64) cf |= 1u << e;
+            if (fabs(c64 - p.cosA64) <= p.border) ++borderline;
             ++fp64_tests;
           }
         }
@@ -311,6 +315,7 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
       }
     }
     if (fp64_tests) atomicAdd(p.n64, fp64_tests);
+    if (borderline) atomicAdd(p.nborder, borderline);
     if (!ok && lane == 0) {
       atomicOr(p.err, 4);
       *abort_flag = 1;
@@ -414,8 +419,8 @@ bool prune_tc_available(int d, int L, int R) {
 }
 
 void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
-                  const int32_t* pool_len, int L, int R, double cos_a, int32_t* adj,
-                  int32_t* deg, Counters* dctr, cudaStream_t st) {
+                  const int32_t* pool_len, int L, int R, double cos_a, double border,
+                  int32_t* adj, int32_t* deg, Counters* dctr, cudaStream_t st) {
   const int dp = (d + 63) & ~63;
   const int kchunks = dp / 64;
   Scratch<__nv_bfloat16> xb((size_t)n * dp, st);
@@ -432,10 +437,12 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
   a.kchunks = kchunks;
   a.cosA32 = (float)cos_a;
   a.cosA64 = cos_a;
-  a.margin = (float)(16.0 * U32);
+  a.margin = (float)(16.0 * U32 + border);
   a.adj = adj;
   a.deg = deg;
   a.n64 = &dctr->angle_fp64;
+  a.border = border;
+  a.nborder = &dctr->angle_border;
   a.err = err.p;
   const size_t smem = prune_tc_smem(kchunks);
   ensure_smem((const void*)k_prune_tc, smem);
@@ -444,6 +451,7 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
   int h = 0;
   SSG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
+  if (h != 0) note_device_status(SSG_ETIMEOUT);
   SSG_REQUIRE(h == 0, SSG_ETIMEOUT, "tensor-core prune: a pipeline wait timed out (code %d)", h);
 }
 

@@ -117,7 +117,8 @@ __global__ void k_reverse_merge(const float* __restrict__ X, const uint8_t* __re
                                 int32_t* __restrict__ big_list, int* __restrict__ big_count,
                                 unsigned long long* __restrict__ n_order,
                                 unsigned long long* __restrict__ n_angle, float* __restrict__ Vg,
-                                int32_t* __restrict__ lists, int32_t* __restrict__ list_len) {
+                                int32_t* __restrict__ lists, int32_t* __restrict__ list_len,
+                                double border, unsigned long long* __restrict__ n_border) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
   const size_t per_warp = (size_t)cap * 20 + merge_prune_bytes(d, R, Vg != nullptr);
@@ -185,11 +186,11 @@ __global__ void k_reverse_merge(const float* __restrict__ X, const uint8_t* __re
     if (Vg) {
       kept = warp_prune_node_wide(X, ld, d, j, cand, m, R, cosA32, cosA64, margin,
                                   Vg + (size_t)gwarp * (R + 1) * d4, P, P + d4, P + 2 * d4, out,
-                                  n_angle);
+                                  n_angle, border, n_border);
     } else {
       float* xs = P + (size_t)(R + 1) * D1;
       kept = warp_prune_node(X, ld, d, j, cand, m, R, cosA32, cosA64, margin, P, D1, xs, xs + D1,
-                             out, n_angle);
+                             out, n_angle, border, n_border);
     }
     for (int t = kept + lane; t < R; t += 32) out[t] = -1;
     if (lane == 0) deg1[j] = kept;
@@ -207,8 +208,9 @@ __global__ void k_max_int(const int* __restrict__ v, int64_t n, int* __restrict_
 }
 
 int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
-                const int32_t* adj0, const int32_t* deg0, int R, double cos_a, int exact, bool tc,
-                int32_t* adj1, int32_t* deg1, Counters* dctr, cudaStream_t st) {
+                const int32_t* adj0, const int32_t* deg0, int R, double cos_a, double border,
+                int exact, bool tc, int32_t* adj1, int32_t* deg1, Counters* dctr,
+                cudaStream_t st) {
   const int grid = 8 * num_sms();
   Scratch<int> indeg((size_t)n, st), fill((size_t)n, st), small(2, st);
   SSG_CUDA(cudaMemsetAsync(indeg.p, 0, sizeof(int) * n, st));
@@ -223,7 +225,7 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
 
   const bool wide = prune_is_wide(d, R);
   const size_t prune_bytes = merge_prune_bytes(d, R, wide);
-  const float rel = dist_rel_fp32(d), margin = angle_margin_fp32(d);
+  const float rel = dist_rel_fp32(d), margin = angle_margin_fp32(d) + (float)border;
   const int d4 = (d + 3) & ~3;
   // Tensor-core path (data exact in bf16): the warps only merge and sort, lists of up to
   // 127 candidates go to the Gram prune, longer ones to the warp prune below.
@@ -256,9 +258,10 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
   }
   SSG_LAUNCH(k_reverse_merge, (unsigned)mgrid, wpb * 32, smem, st, X, X8, ld, d, n, adj0, deg0, R, off.p,
              rev.p, (const int32_t*)nullptr, n, cap, limit, exact, rel, (float)cos_a, cos_a, margin, adj1,
-             deg1, big.p, small.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p, lists.p, list_len.p);
+             deg1, big.p, small.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p, lists.p, list_len.p,
+             border, &dctr->angle_border);
   if (use_tc)
-    prune_run_tc(X, ld, d, n, lists.p, list_len.p, limit, R, cos_a, adj1, deg1, dctr, st);
+    prune_run_tc(X, ld, d, n, lists.p, list_len.p, limit, R, cos_a, border, adj1, deg1, dctr, st);
   int h[2];
   SSG_CUDA(cudaMemcpyAsync(h, small.p, sizeof(h), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
@@ -278,7 +281,7 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
     SSG_LAUNCH(k_reverse_merge, grid_big, 32, smem_big, st, X, X8, ld, d, n, adj0, deg0, R, off.p, rev.p,
                big.p, (int64_t)h[0], cap_big, cap_big, exact, rel, (float)cos_a, cos_a, margin, adj1, deg1,
                none.p, small2.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p, (int32_t*)nullptr,
-               (int32_t*)nullptr);
+               (int32_t*)nullptr, border, &dctr->angle_border);
   }
   return h[1];
 }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libssg.so")
 _lock = threading.Lock()
 _lib = None
 
-PREC = {"fp32": 0, "bf16": 1, "auto": 2, "bf16_rerank": 3}
+PREC = {"fp32": 0, "bf16": 1, "auto": 2, "bf16_rerank": 3, "fp8": 4}
 
 
 class SSGError(RuntimeError):
@@ -31,7 +31,8 @@ class BuildOpts(ctypes.Structure):
     _fields_ = [("gemm_prec", ctypes.c_int), ("n_nav", ctypes.c_int32),
                 ("nav_ids_host", ctypes.c_void_p), ("seed", ctypes.c_uint64),
                 ("debug_checks", ctypes.c_int32), ("pool_tiles", ctypes.c_int32),
-                ("pool_own_row_first", ctypes.c_int32)]
+                ("pool_own_row_first", ctypes.c_int32), ("gram_prec", ctypes.c_int),
+                ("cos_margin_fp64", ctypes.c_double), ("tune_table", ctypes.c_char_p)]
 
 
 class BuildStats(ctypes.Structure):
@@ -43,7 +44,9 @@ class BuildStats(ctypes.Structure):
                 ("n_knn_fallback_rows", ctypes.c_int64), ("max_indegree", ctypes.c_int32),
                 ("exact_mode", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
                 ("gemm_prec_used", ctypes.c_int32), ("ms_knn_gemm", ctypes.c_double),
-                ("search_row_bytes", ctypes.c_int32)]
+                ("search_row_bytes", ctypes.c_int32), ("gram_prec_used", ctypes.c_int32),
+                ("n_angle_borderline", ctypes.c_int64), ("knn_candidates", ctypes.c_int32),
+                ("ms_knn_certify", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -59,6 +62,7 @@ SYMBOLS = {
     "ssg_default_opts": (None, [ctypes.c_void_p]),
     "ssg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ssg_last_error": (ctypes.c_char_p, []),
+    "ssg_last_device_status": (ctypes.c_int, []),
     "ssg_kernel_launch_count": (ctypes.c_int64, []),
     "ssg_nav_ids": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p]),
     "ssg_knn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
@@ -198,6 +202,12 @@ def check_graph(adj, deg):
     _check(lib().ssg_check_graph(_ptr(a), _ptr(dg), a.shape[0], a.shape[1], ctypes.byref(row),
                                  ctypes.byref(code), _stream()))
     return int(row.value), int(code.value)
+
+
+def last_device_status() -> int:
+    """Status of the latest failure a kernel reported on the device (0 if none); clears it
+    (ssg_last_device_status)."""
+    return int(lib().ssg_last_device_status())
 
 
 def debug_fail_alloc(nth: int):
@@ -480,10 +490,15 @@ class Server:
             pass
 
 
-def _opts(n_nav, nav, seed, prec):
+def _opts(n_nav, nav, seed, prec, gram_prec="auto", cos_margin=None, tune_table=None):
     o = BuildOpts()
     lib().ssg_default_opts(ctypes.byref(o))
     o.gemm_prec = PREC[prec]
+    o.gram_prec = PREC[gram_prec]
+    if cos_margin is not None:
+        o.cos_margin_fp64 = float(cos_margin)
+    if tune_table is not None:
+        o.tune_table = tune_table.encode() if isinstance(tune_table, str) else tune_table
     keep = None
     if nav is not None:
         keep = np.ascontiguousarray(np.asarray(nav), dtype=np.int32)
@@ -498,13 +513,17 @@ def _opts(n_nav, nav, seed, prec):
 
 def build(base, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None, seed=None,
           prec: str = "auto", pool_tiles: int = 0, pool_own_row_first: bool = False,
-          debug_checks: bool = False) -> Graph:
+          debug_checks: bool = False, gram_prec: str = "auto", cos_margin=None,
+          tune_table=None) -> Graph:
     """NSSGIndexing on a device-resident base (torch CUDA float32 [n][d]): Alg. 3, or with
-    pool_tiles > 0 Alg. 4's pools searched on the fly over the cluster-ordered tiles."""
+    pool_tiles > 0 Alg. 4's pools searched on the fly over the cluster-ordered tiles.
+    prec / gram_prec: arithmetic of the kNN GEMM and of the prune's Gram (the graph is the
+    same for every choice); cos_margin: the angle test's reporting band (default 1e-5);
+    tune_table: path of a launch-parameter file."""
     torch = _torch()
     b = _dev(base, torch.float32)
     n, d = b.shape
-    o, keep = _opts(n_nav, nav, seed, prec)
+    o, keep = _opts(n_nav, nav, seed, prec, gram_prec, cos_margin, tune_table)
     o.pool_tiles = pool_tiles
     o.pool_own_row_first = int(pool_own_row_first)
     o.debug_checks = int(debug_checks)

@@ -107,7 +107,49 @@ def test_invalid_arguments_rejected_without_device(L):
     assert L.ssg_selftest_wait(0, None, ctypes.byref(ms)) == 1
 
 
+def test_precision_margin_and_tune_table_rejected_without_device(L, tmp_path):
+    """FP8 is declared but not built; the reporting band and the launch-parameter file are
+    validated before anything reaches the device."""
+    P = ctypes.c_void_p(16)
+    s = ctypes.c_void_p(0)
+    assert L.ssg_knn(P, 100, 8, 5, ssg.PREC["fp8"], P, P, s) == 1
+    assert b"FP8" in L.ssg_last_error()
+    assert L.ssg_knn(P, 100, 8, 5, 7, P, P, s) == 1
+    assert L.ssg_knn_query(P, 100, 8, P, 10, 5, ssg.PREC["fp8"], P, P, s) == 1
+    h = ctypes.c_void_p()
+
+    def build_with(**fields):
+        o = ssg.BuildOpts()
+        L.ssg_default_opts(ctypes.byref(o))
+        for k, v in fields.items():
+            setattr(o, k, v)
+        return L.ssg_build(P, 200, 8, 5, 10, 8, 60.0, ctypes.byref(o), s, ctypes.byref(h), None)
+
+    assert build_with(gemm_prec=ssg.PREC["fp8"]) == 1
+    assert build_with(gram_prec=ssg.PREC["fp8"]) == 1 and b"gram_prec" in L.ssg_last_error()
+    assert build_with(cos_margin_fp64=-1e-3) == 1
+    assert build_with(cos_margin_fp64=0.9) == 1
+    missing = str(tmp_path / "absent.txt").encode()
+    assert build_with(tune_table=missing) == 1 and b"cannot open" in L.ssg_last_error()
+    for text, msg in [("knn_sample_rows = 9000\n", b"knn_sample_rows"),
+                      ("knn_slack_quantile = 0.2\n", b"knn_slack_quantile"),
+                      ("no_such_knob = 1\n", b"unknown name"),
+                      ("knn_sample_rows 12\n", b"name = value")]:
+        f = tmp_path / "t.txt"
+        f.write_text("# launch parameters\n" + text)
+        assert build_with(tune_table=str(f).encode()) == 1, text
+        assert msg in L.ssg_last_error(), (text, L.ssg_last_error())
+    assert h.value is None
+
+
+def test_last_device_status_starts_clear(L):
+    assert L.ssg_last_device_status() == 0
+    assert ssg.last_device_status() == 0
+
+
 def test_default_opts(L):
     o = ssg.BuildOpts()
     L.ssg_default_opts(ctypes.byref(o))
     assert o.gemm_prec == ssg.PREC["auto"] and o.n_nav == 10 and o.nav_ids_host is None
+    assert o.gram_prec == ssg.PREC["auto"] and o.cos_margin_fp64 == 1e-5
+    assert o.tune_table is None

@@ -9,9 +9,12 @@ any size:
   neighbour's row here (K >= L: Alg. 3's loop stops after n1), so the oracle needs just
   those rows.
 * The reverse merge keeps, for each sampled node, only its pruned edges and in-edges, with
-  every pair of kept edges at least alpha apart (exact integer test).
-* After connectivity every node is reachable from the navigating nodes, and the staged
-  chain equals the one-call build.
+  every pair of kept edges at least alpha apart (exact integer test); and, stage by stage,
+  each sampled node's merged row equals the oracle's: its candidates (its edges, then its
+  in-edges, from the GPU's first prune) ordered by the oracle's (d2, id) and pruned by the
+  oracle's rule.
+* After connectivity every node is reachable from each of the navigating nodes, and the
+  staged chain equals the one-call build.
 * Ground truth of 100 sampled queries equals the oracle's; recall@10 at L_search = 40 over
   all 10,000 queries is at least 0.95.
 """
@@ -125,10 +128,34 @@ def test_reverse_merge_properties(full):
     check_reverse(w.base, h["adj0"], h["deg0"], h["adj1"], h["deg1"], sample)
 
 
+def test_reverse_merge_rows_equal_oracle(full):
+    """Reading R4 for the sampled nodes, from the GPU's own first-prune graph: candidates
+    adj0[j] then the in-edges {i : j in adj0[i]} (repeats dropped), ordered by the oracle's
+    (d2, id), pruned by the oracle with the same cap."""
+    w, b, nav, h, nrep, g, sample = full
+    adj0, deg0 = h["adj0"], h["deg0"]
+    src, col = np.nonzero(np.isin(adj0, sample))
+    lists = []
+    for j in sample:
+        own = adj0[j, :deg0[j]].tolist()
+        ins = np.unique(src[adj0[src, col] == j]).tolist()
+        cand = np.array(own + [i for i in ins if i not in set(own)], np.int64)
+        d2 = oracle.dist2_pairs(w.base, np.full(cand.size, j), cand)
+        lists.append(cand[np.lexsort((cand, d2))])
+    width = max(len(c) for c in lists)
+    cand = np.full((len(sample), width), -1, np.int32)
+    clen = np.array([len(c) for c in lists], np.int32)
+    for r, c in enumerate(lists):
+        cand[r, :len(c)] = c
+    oadj, odeg = oracle.prune(w.base, cand, clen, R, ALPHA, nodes=sample)
+    np.testing.assert_array_equal(h["deg1"][sample], odeg)
+    np.testing.assert_array_equal(h["adj1"][sample], oadj)
+
+
 def test_connectivity_and_build_equal_staged(full):
     w, b, nav, h, nrep, g, sample = full
     adj, deg = h["adj"], h["deg"]
-    check_reachable(adj, deg, nav[:2])
+    check_reachable(adj, deg, nav)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(g.deg.cpu().numpy(), deg)
     np.testing.assert_array_equal(g.adj.cpu().numpy(), adj)
