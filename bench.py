@@ -211,6 +211,51 @@ def oracle_sample_seconds_per_million(w, n_nodes: int, seed: int):
                                         "sec": (t1 - t0) + (t3 - t2) + (t5 - t4)}
 
 
+def oracle_edge_seconds_per_million(w, n_sub: int = 10_000, seed: int = 77):
+    """The oracle's reverse merge and connectivity per point: the oracle builds the graph of
+    the first n_sub points (exact kNN, pools, prune, untimed), then its reverse merge and
+    connectivity from w.n_nav navigating nodes are timed and scaled to 1M points (both
+    stages are linear in the number of points)."""
+    import oracle
+    from paper_1907_06146_gb300 import synth
+    sub = np.ascontiguousarray(w.base[:n_sub])
+    ids, _ = oracle.knn_rows(sub, w.K)
+    pid, _, pl = oracle.pool(sub, ids, w.L)
+    adj0, deg0 = oracle.prune(sub, pid, pl, w.R, w.alpha)
+    nav = synth.nav_ids(n_sub, w.n_nav, seed)
+    t0 = time.perf_counter()
+    adj1, deg1 = oracle.reverse(sub, adj0, deg0, w.alpha)
+    t1 = time.perf_counter()
+    oracle.connect(sub, adj1, deg1, nav)
+    t2 = time.perf_counter()
+    return (t2 - t0) / n_sub * 1e6, {"reverse_s": t1 - t0, "connect_s": t2 - t1, "points": n_sub}
+
+
+def cpu_baseline_line(w, nodes: int, nodes_1core: int, seed: int):
+    """The oracle on the host cores: kNN rows, pools and prunes of a seeded node sample plus
+    the reverse merge and connectivity of a 10,000-point build, on all cores and on one."""
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    v, info = oracle_sample_seconds_per_million(w, nodes, seed)
+    e, einfo = oracle_edge_seconds_per_million(w)
+    oracle.set_threads(1)
+    try:
+        v1, info1 = oracle_sample_seconds_per_million(w, nodes_1core, seed + 1)
+        e1, _ = oracle_edge_seconds_per_million(w)
+    finally:
+        oracle.set_threads(cores)
+    return {"value": v + e, "unit": "s/1M pts", "cores": cores, "kind": "oracle",
+            "value_1core": v1 + e1,
+            "parts_s_per_1M": {"knn_pool_prune": v, "reverse_connect": e,
+                               "knn_pool_prune_1core": v1, "reverse_connect_1core": e1},
+            "sample": f"{nodes} seeded random nodes ({nodes_1core} on one core): their exact kNN "
+                      f"rows and those of the neighbours their pools read ({info['knn_rows']} "
+                      f"rows of {w.n}x{w.d}), pools and prunes, per node; plus the reverse merge "
+                      f"and connectivity of the oracle's own graph of the first "
+                      f"{einfo['points']} points, per point; both scaled to 1M points"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -219,21 +264,24 @@ def run_reference(args):
     oracle.build()
     w = make_workload(args.workload, args.n, 0)
     cores = oracle.max_threads()
+    # the reverse merge and connectivity per point, from the oracle's own 10,000-point build
+    edge, einfo = oracle_edge_seconds_per_million(w)
     per_step = []
     for s in range(args.warmup + args.steps):
         v, info = oracle_sample_seconds_per_million(w, args.ref_nodes, 1000 + s)
         if s >= args.warmup:
-            per_step.append(v)
+            per_step.append(v + edge)
     value = float(np.mean(per_step))
-    sample = (f"oracle kNN rows + pools + prunes of {args.ref_nodes} seeded random nodes of the "
-              f"{w.n}x{w.d} workload per step, extrapolated to 1M points; reverse merge and "
-              f"connectivity not sampled")
+    sample = (f"per step: oracle kNN rows + pools + prunes of {args.ref_nodes} seeded random "
+              f"nodes of the {w.n}x{w.d} workload, per node; plus (measured once) the reverse "
+              f"merge and connectivity of the oracle's own graph of the first {einfo['points']} "
+              f"points, per point; scaled to 1M points")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/1M pts",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{w.name} n={w.n} d={w.d} K={w.K} L={w.L} R={w.R} "
-                                   f"alpha={w.alpha} nav={w.n_nav}"},
+                                   f"alpha={w.alpha} nav={w.n_nav} queries={w.queries.shape[0]}"},
             "cpu_baseline": {"value": value, "unit": "s/1M pts", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "s/1M pts", "h2d_bytes_per_step": 0,
@@ -241,10 +289,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(ssg, g, base, w, seconds: float, rate: float, seed: int = 190706145):
+def run_serving(ssg, g, base, w, seconds: float, rate: float, seed: int = 190706145,
+                recall: bool = True):
     """Open-loop Poisson stream of requests against a continuous-batching server: batch
-    sizes log-uniform in [1, 4096], k in {1, 10, 100}, L_search uniform in [k, 512].
-    Returns latency percentiles, throughput and recall@10 of the requests with k >= 10."""
+    sizes log-uniform in [1, 4096], k in {1, 10, 100}, L_search uniform in [k, 512]; each
+    request's queries are a contiguous block of the query set (a view, so submitting costs
+    no gather).  Returns latency percentiles, throughput and recall@10 of the requests with
+    k >= 10."""
     import threading
     import time as _t
 
@@ -255,11 +306,11 @@ def run_serving(ssg, g, base, w, seconds: float, rate: float, seed: int = 190706
     t = 0.0
     while t < seconds:
         t += rng.exponential(1.0 / rate)
-        nq = int(np.exp(rng.uniform(0.0, np.log(4096.0))))
+        nq = min(int(np.exp(rng.uniform(0.0, np.log(4096.0)))), nq_all)
         k = int(rng.choice([1, 10, 100]))
         ls = int(rng.integers(k, 513))
-        rows = rng.integers(0, nq_all, size=nq)
-        reqs.append((t, rows, k, ls))
+        s0 = int(rng.integers(0, nq_all - nq + 1))
+        reqs.append((t, np.arange(s0, s0 + nq), k, ls))
     tickets = [None] * len(reqs)
     results = [None] * len(reqs)
     done = threading.Event()
@@ -278,7 +329,8 @@ def run_serving(ssg, g, base, w, seconds: float, rate: float, seed: int = 190706
         now = _t.perf_counter() - t0
         if ta > now:
             _t.sleep(ta - now)
-        tickets[i] = srv.submit(w.queries[rows], k, ls)
+        tickets[i] = srv.submit(w.queries[rows[0]:rows[-1] + 1], k, ls)
+    submit_s = _t.perf_counter() - t0
     done.wait()
     wall = _t.perf_counter() - t0
     th.join()
@@ -286,21 +338,78 @@ def run_serving(ssg, g, base, w, seconds: float, rate: float, seed: int = 190706
     srv.close()
     lat = np.array([r[2] for r in results])
     total_q = int(sum(len(r[1]) for r in reqs))
-    # recall@10 of the k >= 10 requests, first 10 ids against brute force
-    import torch
-    sel = [i for i, r in enumerate(reqs) if r[2] >= 10]
-    rows = np.concatenate([reqs[i][1] for i in sel])
-    found = np.concatenate([results[i][0][:, :10] for i in sel])
-    truth, _ = ssg.knn_query(base, torch.from_numpy(w.queries[rows]).cuda(), 10)
-    hits = ssg.recall_hits(torch.from_numpy(np.ascontiguousarray(found)).cuda(), truth, 10)
+    rec = None
+    if recall:
+        # recall@10 of the k >= 10 requests, first 10 ids against brute force
+        import torch
+        sel = [i for i, r in enumerate(reqs) if r[2] >= 10]
+        rows = np.concatenate([reqs[i][1] for i in sel])
+        found = np.concatenate([results[i][0][:, :10] for i in sel])
+        truth, _ = ssg.knn_query(base, torch.from_numpy(w.queries[rows]).cuda(), 10)
+        hits = ssg.recall_hits(torch.from_numpy(np.ascontiguousarray(found)).cuda(), truth, 10)
+        rec = hits / (10.0 * len(rows))
     return {"requests": len(reqs), "queries": total_q, "offered_rate_req_s": rate,
+            "achieved_submit_rate_req_s": len(reqs) / submit_s,
             "seconds": wall, "qps": total_q / wall, "latency_ms_p50": float(np.percentile(lat, 50)),
             "latency_ms_p99": float(np.percentile(lat, 99)),
-            "recall@10_k>=10": hits / (10.0 * len(rows)), "batches": st["batches"],
+            "recall@10_k>=10": rec, "batches": st["batches"],
             "max_batches_in_flight": st["max_batches_in_flight"],
             "max_queries_in_flight": st["max_queries_in_flight"],
             "mix": "Poisson arrivals; batch 1..4096 log-uniform; k in {1,10,100}; "
                    "L_search uniform in [k, 512]"}
+
+
+def run_serving_curve(ssg, g, base, w, seconds: float, rates):
+    """The serving run at each offered rate (requests per second): achieved QPS, p50 and p99
+    latency; the saturation point is the largest achieved QPS.  Recall is scored at the
+    first rate (a query's result does not depend on the load)."""
+    pts = []
+    for i, r in enumerate(rates):
+        p = run_serving(ssg, g, base, w, seconds, r, seed=190706145 + i, recall=(i == 0))
+        pts.append({k: p[k] for k in ("offered_rate_req_s", "achieved_submit_rate_req_s", "qps",
+                                      "latency_ms_p50", "latency_ms_p99", "requests", "queries",
+                                      "max_batches_in_flight", "recall@10_k>=10")})
+    best = max(pts, key=lambda p: p["qps"])
+    return {"points": pts, "saturation_qps": best["qps"],
+            "saturation_at_offered_req_s": best["offered_rate_req_s"],
+            "seconds_per_point": seconds,
+            "mix": "Poisson arrivals; batch 1..4096 log-uniform; k in {1,10,100}; "
+                   "L_search uniform in [k, 512]; 4 batch slots"}
+
+
+def run_float_arm(ssg, n, d, K, L, R, ls=64, seed=190706144):
+    """One float index shaped like the many-index batch (a 16-centre Gaussian mixture, the
+    recipe of synth.batched_index): built through the certified bf16 path and through the
+    plain fp32 path (fp32 kNN GEMM, fp32 warp prune); build times, whether the edge sets
+    are identical, and recall@10 at one L_search on 1,000 queries."""
+    import torch
+    from paper_1907_06146_gb300 import synth
+    w = synth.small(n=n, d=d, nq=1000, seed=seed)
+    base = torch.from_numpy(w.base).cuda()
+    q = torch.from_numpy(w.queries).cuda()
+    nav = synth.nav_ids(n, 10, seed)
+    truth, _ = ssg.knn_query(base, q, 10)
+    out = {"workload": f"16-centre Gaussian mixture n={n} d={d} (float32) K={K} L={L} R={R} "
+                       f"alpha=60 nav=10"}
+    graphs = {}
+    for arm, kw in (("bf16", {"prec": "auto"}), ("fp32", {"prec": "fp32", "gram_prec": "fp32"})):
+        g = ssg.build(base, K, L, R, 60.0, nav=nav, **kw)  # warm-up
+        del g
+        g = ssg.build(base, K, L, R, 60.0, nav=nav, **kw)
+        ids, _ = g.search(base, q, 10, ls)
+        st = g.stats
+        out[arm] = {"build_s_per_1M": st["ms_total"] / 1e3 * 1e6 / n, "ms_total": st["ms_total"],
+                    "ms_knn": st["ms_knn"], "ms_knn_gemm": st["ms_knn_gemm"],
+                    "ms_knn_certify": st["ms_knn_certify"],
+                    "gemm_prec_used": st["gemm_prec_used"],
+                    "knn_candidates": st["knn_candidates"],
+                    "knn_rows_not_certified_by_first_pass": st["n_knn_fallback_rows"],
+                    "recall@10": ssg.recall_hits(ids, truth, 10) / 10000.0, "L_search": ls}
+        graphs[arm] = g
+    out["edge_sets_identical"] = bool(torch.equal(graphs["bf16"].adj, graphs["fp32"].adj)
+                                      and torch.equal(graphs["bf16"].deg, graphs["fp32"].deg))
+    out["bf16_over_fp32_speedup"] = out["fp32"]["ms_total"] / out["bf16"]["ms_total"]
+    return out
 
 
 def run_serve_deep(ssg, n, tiles, seconds, rate, target):
@@ -370,13 +479,13 @@ def run_batched(ssg, count, n_streams):
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     degs = [int(g.deg.sum().item()) for g in gs]
-    # the mixed-precision batch: bf16 tensor-core candidate selection with exact re-rank
-    # for d <= 128 (fp32 elsewhere); how many adjacency rows equal the exact batch's
+    # the plain fp32 batch (fp32 kNN GEMM and prune); how many adjacency rows equal the
+    # mixed-precision batch's (certified: all of them)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    gm = ssg.build_batched(data, Ks, Ls, 32, 60.0, n_streams=n_streams, prec="bf16_rerank")
+    gm = ssg.build_batched(data, Ks, Ls, 32, 60.0, n_streams=n_streams, prec="fp32")
     torch.cuda.synchronize()
-    t_mixed = time.perf_counter() - t0
+    t_fp32 = time.perf_counter() - t0
     rows_same = 0
     for ge, gx in zip(gs, gm):
         rows_same += int(((ge.adj == gx.adj).all(dim=1) & (ge.deg == gx.deg)).sum().item())
@@ -394,9 +503,9 @@ def run_batched(ssg, count, n_streams):
             "batched_s": t_batch, "one_by_one_s": t_one, "speedup": t_one / t_batch,
             "batched_s_per_1M_pts": t_batch * 1e6 / points,
             "degree_sums_equal": same,
-            "mixed_bf16_rerank_batched_s": t_mixed,
-            "mixed_over_exact_batched_speedup": t_batch / t_mixed,
-            "mixed_rows_equal_exact_frac": rows_same / points,
+            "fp32_batched_s": t_fp32,
+            "mixed_over_fp32_batched_speedup": t_fp32 / t_batch,
+            "rows_equal_fp32_frac": rows_same / points,
             "shapes": "n log-uniform 10k-500k, d in {64,96,128,256}, L in {100,200}, K=100, "
                       "R=32, alpha=60; 16-centre float mixtures"}
 
@@ -425,7 +534,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     def step(ls):
-        g = ssg.build(base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec)
+        g = ssg.build(base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec,
+                      tune_table=args.tune_table)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         ids, _ = g.search(base, queries, 10, ls)
@@ -506,8 +616,13 @@ def run_gpu(args):
     serving = None
     if rank == 0 and args.serve_seconds > 0:
         g_srv = ssg.build(base, w.K, w.L, w.R, w.alpha, nav=nav, prec=args.prec)
-        serving = run_serving(ssg, g_srv, base, w, args.serve_seconds, args.serve_rate)
+        rates = [float(r) for r in args.serve_rates.split(",")]
+        serving = run_serving_curve(ssg, g_srv, base, w, args.serve_seconds, rates)
         del g_srv
+
+    float_arm = None
+    if rank == 0 and args.float_n > 0:
+        float_arm = run_float_arm(ssg, args.float_n, args.float_d, 100, 200, 32)
 
     alg4 = None
     if rank == 0 and args.alg4_tiles > 0:
@@ -577,14 +692,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        v, info = oracle_sample_seconds_per_million(w, args.ref_nodes, 4242)
-        cpu = {"value": v, "unit": "s/1M pts", "cores": oracle.max_threads(), "kind": "oracle",
-               "sample": f"{args.ref_nodes} seeded random nodes: their exact kNN rows and those "
-                         f"of the neighbours their pools read ({info['knn_rows']} rows of "
-                         f"{w.n}x{w.d}), pools and prunes; extrapolated to 1M points; reverse "
-                         f"merge and connectivity not sampled"}
+        cpu = cpu_baseline_line(w, args.cpu_nodes, args.cpu_nodes_1core, 4242)
 
     if rank != 0:
         return
@@ -597,6 +705,7 @@ def run_gpu(args):
         "config": {"workload": f"{w.name} n={w.n} d={w.d} K={w.K} L={w.L} R={w.R} "
                                f"alpha={w.alpha} nav={w.n_nav} queries={nq}",
                    "l2": "inputs larger than L2 (base 512 MB)", "gemm_prec": args.prec,
+                   "tune_table": args.tune_table,
                    "parallelism": f"replicas x{ws}"},
         "search": {"qps": qps, "recall@10": float(np.mean(recalls)), "L_search": ls_used,
                    "k": 10, "ms": float(np.mean(search_ms)), "sweep": sweep,
@@ -616,6 +725,7 @@ def run_gpu(args):
         "serving": serving,
         "serving_deep": serving_deep,
         "fp32_path": fp32_arm,
+        "float_mixed": float_arm,
         "batched": batched,
         "ablations": ablations,
         "alg4": alg4,
@@ -644,7 +754,15 @@ def main():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--target-recall", type=float, default=0.95)
-    ap.add_argument("--ref-nodes", type=int, default=128)
+    ap.add_argument("--tune-table", default=None,
+                    help="launch-parameter file passed to every timed build (ssg_build_opts."
+                         "tune_table)")
+    ap.add_argument("--ref-nodes", type=int, default=128,
+                    help="nodes the reference arm (the oracle) samples per step")
+    ap.add_argument("--cpu-nodes", type=int, default=2000,
+                    help="nodes the cpu_baseline samples on all host cores")
+    ap.add_argument("--cpu-nodes-1core", type=int, default=48,
+                    help="nodes the cpu_baseline samples on one host core")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=0,
                     help="also build this many independent indices (log-uniform 10k-500k points, "
@@ -656,9 +774,15 @@ def main():
                     help="also run the alpha sweep, exact-SSG overlap and edge-time scaling")
     ap.add_argument("--no-fp32-arm", dest="fp32_arm", action="store_false",
                     help="skip the one plain-FP32 build reported beside the mixed-precision path")
-    ap.add_argument("--serve-seconds", type=float, default=3.0,
-                    help="length of the serving run (0 = skip)")
-    ap.add_argument("--serve-rate", type=float, default=200.0, help="requests per second offered")
+    ap.add_argument("--serve-seconds", type=float, default=1.5,
+                    help="length of each serving run of the curve (0 = skip)")
+    ap.add_argument("--serve-rates", default="200,1000,2000,4000,8000",
+                    help="offered request rates of the serving curve (requests per second)")
+    ap.add_argument("--serve-rate", type=float, default=200.0,
+                    help="requests per second offered to the 10M serving case (--serve-deep)")
+    ap.add_argument("--float-n", type=int, default=200_000,
+                    help="points of the float index built through both precisions (0 = skip)")
+    ap.add_argument("--float-d", type=int, default=128)
     ap.add_argument("--serve-deep", type=int, default=0,
                     help="also build the 96-d L2-normalised workload at this many points with "
                          "search-based pools and serve it (10000000: the 10M serving case)")

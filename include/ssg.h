@@ -119,7 +119,8 @@ typedef struct {
                                unreadable file give EINVAL.  Names: knn_sample_rows (rows
                                sampled to size the bf16 candidate slack, 0..4096),
                                knn_slack_quantile (fraction of sampled rows the slack must
-                               certify, 0.5..1) */
+                               certify, 0.5..1), knn_prepass_tiles (tiles of the first,
+                               threshold-only walk of the tensor-core kNN, 0..4096, 0 = none) */
 } ssg_build_opts;
 
 /* Per-build measurements (all times from CUDA events on the build stream). */

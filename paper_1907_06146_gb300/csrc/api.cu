@@ -158,6 +158,10 @@ static KnnTune read_tune_table(const char* path) {
       SSG_REQUIRE(v >= 0 && v <= 4096 && v == std::floor(v), SSG_EINVAL,
                   "tune_table %s:%d: knn_sample_rows must be an integer in [0, 4096]", path, ln);
       t.sample_rows = (int)v;
+    } else if (!strcmp(name, "knn_prepass_tiles")) {
+      SSG_REQUIRE(v >= 0 && v <= 4096 && v == std::floor(v), SSG_EINVAL,
+                  "tune_table %s:%d: knn_prepass_tiles must be an integer in [0, 4096]", path, ln);
+      t.prepass_tiles = (int)v;
     } else if (!strcmp(name, "knn_slack_quantile")) {
       SSG_REQUIRE(v >= 0.5 && v <= 1.0, SSG_EINVAL,
                   "tune_table %s:%d: knn_slack_quantile must lie in [0.5, 1]", path, ln);
@@ -266,8 +270,10 @@ static KnnResult knn_any(const Ingested& a, int64_t na, const Ingested& b, int64
               "bf16 distance GEMM needs sm_103 and d <= 128");
   KnnResult kr;
   if (path == 1) {
+    TcExtra ex;
+    ex.prepass_tiles = tune.prepass_tiles;
     knn_exact_tc(a.rows.p, na, a.rows.ld, a.norms.p, b.rows.p, nb, b.rows.ld, b.norms.p, d, self, K,
-                 ids, d2, st, t_gemm);
+                 ids, d2, st, t_gemm, 0, false, ex);
   } else if (path == 2) {
     const CertResult c = knn_bf16_certified(a.rows.p, na, a.rows.ld, a.norms.p, b.rows.p, nb,
                                             b.norms.p, d, info, self, K, ids, d2, exact_d2, tune,

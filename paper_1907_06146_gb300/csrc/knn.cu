@@ -410,6 +410,25 @@ __global__ void k_knn_fallback(const float* __restrict__ A, int lda, const float
   }
 }
 
+void knn_fallback_rows(const float* A, int lda, const float* B, int ldb, int d, int64_t nb,
+                       int self, const int32_t* rows, const double* kth, int count, int K,
+                       int32_t* out_id, float* out_d2, cudaStream_t st) {
+  if (count <= 0) return;
+  const int cap = 4096;
+  const size_t smem_fb = (size_t)cap * (sizeof(double) + sizeof(int32_t));
+  ensure_smem((const void*)k_knn_fallback, smem_fb);
+  Scratch<int> ovf(1, st);
+  SSG_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
+  SSG_LAUNCH(k_knn_fallback, count, 256, smem_fb, st, A, lda, B, ldb, d, nb, self, rows, kth, K, cap,
+             out_id, out_d2, ovf.p);
+  int h = 0;
+  SSG_CUDA(cudaMemcpyAsync(&h, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SSG_CUDA(cudaStreamSynchronize(st));
+  if (h) note_device_status(SSG_EINTERNAL);
+  SSG_REQUIRE(h == 0, SSG_EINTERNAL,
+              "kNN fallback: more than %d columns tie with a row's K-th distance", cap);
+}
+
 // ---------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------

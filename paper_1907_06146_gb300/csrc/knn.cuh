@@ -52,12 +52,19 @@ bool knn_tc_available(int d);
 struct TcExtra {
   const float* mu = nullptr;          // centre every row on mu [d] before rounding to bf16
                                       // (a_norm / b_norm are then the centred rows' norms)
-  float* out_thresh = nullptr;        // per output row: the KS-th smallest distance kept
-                                      // (every column not returned is at least this far,
-                                      // up to the rounding of the streaming threshold)
+  float* out_thresh = nullptr;        // per output row: the KS-th smallest distance kept, or
+                                      // the final admission bound if fewer were kept (every
+                                      // column not returned is at least this far, up to the
+                                      // rounding of the streaming threshold)
+  const float* tau_in = nullptr;      // per query row: the admission bound to start from
+                                      // (columns above it are never kept)
   const int32_t* qid = nullptr;       // self with A a gathered subset of B: query row r is
                                       // base row qid[r]; outputs go to row r
   const float* order_norm = nullptr;  // norms of A as given, for the cluster order
+  int prepass_tiles = 0;              // near-first self-joins: a first walk over this many
+                                      // tiles gives each row an upper bound of its KS-th
+                                      // distance, from which the full walk starts (0: off;
+                                      // measured slower at 4-16 tiles on the SIFT-shaped set)
 };
 // max_tiles > 0 (self-joins only): the columns are visited in the cluster order and each
 // block of rows stops after its max_tiles nearest 128-column tiles, so the result is the
@@ -72,6 +79,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
 struct KnnTune {
   int sample_rows = 256;        // rows sampled to size the candidate count KS
   double slack_quantile = 0.99; // fraction of sampled rows KS must certify
+  int prepass_tiles = 0;        // TcExtra::prepass_tiles of the kNN graph
 };
 struct CertResult {
   int64_t fallback_rows = 0;  // rows not certified by the first pass
@@ -87,6 +95,13 @@ struct Counters {
   int status;
   unsigned long long angle_border;  // fp64 cosines within the reporting band of cos(alpha)
 };
+
+// Exhaustive exact rows (k_knn_fallback): row rows[t] of A gets the K nearest of B by
+// (fp64 d2, id) among the columns whose fp64 d2 is at most kth[t] (an upper bound of the
+// row's K-th distance); EINTERNAL if more than 4,096 columns lie within it.
+void knn_fallback_rows(const float* A, int lda, const float* B, int ldb, int d, int64_t nb,
+                       int self, const int32_t* rows, const double* kth, int count, int K,
+                       int32_t* out_id, float* out_d2, cudaStream_t st);
 
 // Exact kNN rows through the bf16 tensor cores for data that bf16 does not hold exactly
 // (knn_cert.cu): A [na][ld] against B [nb][ld] (self: A is B, each row skips itself),

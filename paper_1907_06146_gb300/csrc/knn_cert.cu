@@ -289,6 +289,22 @@ __global__ void k_scatter_drop_self(const int32_t* __restrict__ ids, const float
   }
 }
 
+// The second pass's admission bound of each failed row: its K-th exact distance so far
+// (an upper bound of the true one) plus the bf16 bound, widened by three times the
+// threshold rounding and four times the fp32 distance error (the K-th fp32 value of the new
+// candidates may exceed the old one by up to twice that), so that every column that can be
+// a true neighbour is admitted and a band that fits certifies against it.
+__global__ void k_band_start(const double* __restrict__ kth, const float* __restrict__ nag, int m,
+                             double ymax2, int d, float* __restrict__ tau) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const double nx = (double)nag[t];
+  const double b = kth[t] + bf16_dist_bound(nx, ymax2, d);
+  const double rel = (d + 4.0) * 5.9604644775390625e-08 * 1.01;
+  const double v = b + 3.0 * stream_slop(nx, b) + 4.0 * rel * fabs(b) + 1e-30;
+  tau[t] = isfinite(v) ? (float)v * (1.f + 1e-6f) : __int_as_float(0x7f800000);
+}
+
 static int read_count(const int* p, cudaStream_t st) {
   int h = 0;
   SSG_CUDA(cudaMemcpyAsync(&h, p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -396,6 +412,7 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
   ex.mu = mu.p;
   ex.out_thresh = thr.p;
   ex.order_norm = a_norm_raw;
+  ex.prepass_tiles = tune.prepass_tiles;
   knn_exact_tc(A, na, ld, nac, B, nb, ld, nbc.p, d, self, KS, cid.p, cd2.p, st, gemm_timer, 0, true,
                ex);
   cd2.release();
@@ -408,40 +425,53 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
   res.fallback_rows = nfb;
   int nlast = nfb;
   const int32_t* last = fb.p;
-  // pass 2: the failed rows with the largest candidate count
-  if (nfb > 0 && KS < std::min<int64_t>(avail, KS_MAX)) {
-    const int KS2 = (int)std::min<int64_t>(avail, KS_MAX);
-    Scratch<float> Ag((size_t)nfb * ld, st), nag((size_t)nfb, st), thr2((size_t)nfb, st);
+  // pass 2: the failed rows again, admitting every column whose bf16 distance is at most
+  // their K-th exact distance so far plus the bound (the band that can hold a true
+  // neighbour), up to KS2 columns; a band that fits certifies the row
+  if (nfb > 0 && KS < avail) {
+    const int KS2 = (int)std::min<int64_t>(avail, std::max(KS, 640));
+    Scratch<float> Ag((size_t)nfb * ld, st), nag((size_t)nfb, st), thr2((size_t)nfb, st),
+        tau2((size_t)nfb, st);
     Scratch<int32_t> cid2((size_t)nfb * KS2, st);
     Scratch<float> cd22((size_t)nfb * KS2, st);
     SSG_LAUNCH(k_gather_rows, grid, 256, 0, st, A, ld, fb.p, (int64_t)nfb, Ag.p);
     SSG_LAUNCH(k_gather_vals, (unsigned)ceil_div(nfb, 256), 256, 0, st, nac, fb.p, (int64_t)nfb, nag.p);
+    SSG_LAUNCH(k_band_start, (unsigned)ceil_div(nfb, 128), 128, 0, st, fbk.p, nag.p, nfb, ymax2, d,
+               tau2.p);
     TcExtra ex2;
     ex2.mu = mu.p;
     ex2.out_thresh = thr2.p;
     ex2.qid = self ? fb.p : nullptr;
+    ex2.tau_in = tau2.p;
     knn_exact_tc(Ag.p, nfb, ld, nag.p, B, nb, ld, nbc.p, d, self, KS2, cid2.p, cd22.p, st, nullptr, 0,
                  true, ex2);
-    // certify against the gathered rows' own centred norms: nac indexed by row id
     nlast = certify(Ag.p, B, ld, d, fb.p, nfb, cid2.p, KS2, thr2.p, nac, ymax2, K, exact_d2, out_id,
                     out_d2, fb2.p, fbk.p, fbc.p, n_order, st);
     last = fb2.p;
     res.pass2_rows = nfb;
   }
-  // the rest: the exact fp32 path, as queries with K + self neighbours
+  // the rest: exhaustively (few rows), else the exact fp32 path as queries
   if (nlast > 0) {
-    const int K1 = K + self;
-    Scratch<float> Ag((size_t)nlast * ld, st), agn((size_t)nlast, st);
-    SSG_LAUNCH(k_gather_rows, grid, 256, 0, st, A, ld, last, (int64_t)nlast, Ag.p);
-    SSG_LAUNCH(k_centred_norms, (unsigned)ceil_div(nlast, 8), 256, 0, st, Ag.p, (int64_t)nlast, d, ld,
-               (const float*)nullptr, agn.p, (unsigned*)nullptr);
-    Scratch<int32_t> ids((size_t)nlast * K1, st);
-    Scratch<float> dd((size_t)nlast * K1, st);
-    const KnnResult kr = knn_exact(Ag.p, nlast, ld, agn.p, B, nb, ld, b_norm_raw, d, info, 0, K1,
-                                   ids.p, dd.p, st, nullptr);
-    (void)kr;
-    SSG_LAUNCH(k_scatter_drop_self, (unsigned)ceil_div(nlast, 8), 256, 0, st, ids.p, dd.p, K1, last,
-               (int64_t)nlast, self, out_id, out_d2);
+    std::vector<double> kh((size_t)nlast);
+    SSG_CUDA(cudaMemcpyAsync(kh.data(), fbk.p, sizeof(double) * nlast, cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    bool bounded = true;
+    for (double v : kh) bounded = bounded && std::isfinite(v);
+    if (bounded && (int64_t)nlast * nb <= (1ll << 28)) {
+      knn_fallback_rows(A, ld, B, ld, d, nb, self, last, fbk.p, nlast, K, out_id, out_d2, st);
+    } else {
+      const int K1 = K + self;
+      Scratch<float> Ag((size_t)nlast * ld, st), agn((size_t)nlast, st);
+      SSG_LAUNCH(k_gather_rows, grid, 256, 0, st, A, ld, last, (int64_t)nlast, Ag.p);
+      SSG_LAUNCH(k_centred_norms, (unsigned)ceil_div(nlast, 8), 256, 0, st, Ag.p, (int64_t)nlast, d,
+                 ld, (const float*)nullptr, agn.p, (unsigned*)nullptr);
+      Scratch<int32_t> ids((size_t)nlast * K1, st);
+      Scratch<float> dd((size_t)nlast * K1, st);
+      knn_exact(Ag.p, nlast, ld, agn.p, B, nb, ld, b_norm_raw, d, info, 0, K1, ids.p, dd.p, st,
+                nullptr);
+      SSG_LAUNCH(k_scatter_drop_self, (unsigned)ceil_div(nlast, 8), 256, 0, st, ids.p, dd.p, K1,
+                 last, (int64_t)nlast, self, out_id, out_d2);
+    }
     res.exact_rows = nlast;
   }
   return res;

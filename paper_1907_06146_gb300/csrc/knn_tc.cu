@@ -69,8 +69,14 @@ struct TcArgs {
   const int32_t* tile_order;  // per cluster, its first tstride tile indices (null: in order)
   const int32_t* rb_cluster;  // cluster of each block of BM stored query rows
   float* out_thresh;          // nullable: per output row, the KS-th smallest distance kept
+                              // (or, with fewer kept, the final admission bound)
   const int32_t* qid;         // nullable: query row r is base row qid[r] (the self column);
                               // outputs then go to row r
+  const float* tau_in;        // nullable: per stored row, an upper bound of its KS-th
+                              // distance to start the streaming threshold from
+  float tau_relax;            // tau_in is widened by (|tau_in| + |x|^2) tau_relax (0: exact)
+  float* tau_out;             // thresh_only: per stored row, the KS-th distance of its walk
+  int thresh_only;            // 1: no output rows, only tau_out
 };
 
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -303,6 +309,12 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       const int64_t row = rb * BM + row_in_cta;
       const float nx = row < p.na ? p.a_norm[row] : 0.f;
       float tau = INF;
+      if (p.tau_in && row < p.na) {
+        // a bound from a shorter walk over the same columns: every column at or below it
+        // is admitted, so the KS smallest are all kept
+        const float t0 = p.tau_in[row];
+        tau = t0 + (fabsf(t0) + fabsf(nx)) * p.tau_relax;
+      }
       int cnt = 0;
       uint64_t* buf = p.rowbuf + ((size_t)blockIdx.x * BM + row_in_cta) * C;
       const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * p.tstride : nullptr;
@@ -389,14 +401,27 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           const int c1 = select_row<C>(lb, cl, p.KS, 256, 256, &t2);
           if (c1 >= 0) cl = c1;
         }
+        if (p.thresh_only) {
+          // the KS-th distance of this walk (the order of equal distances is irrelevant)
+          if (cl <= 256)
+            compact_row<256>(lb, cl, p.KS, &t2);
+          else
+            compact_row<C>(lb, cl, p.KS, &t2);
+          if (r < p.na && lane == 0) p.tau_out[r] = t2;
+          __syncwarp();
+          continue;
+        }
         map_key_ids(lb, cl, p.perm);
         const int c2 = cl <= 256 ? compact_row<256>(lb, cl, p.KS, &t2)
                                  : compact_row<C>(lb, cl, p.KS, &t2);
+        // the row's last admission bound: with fewer than KS kept (a bound from tau_in that
+        // few columns meet) every column not kept lies above it
+        const float taul = __shfl_sync(0xffffffffu, tau, l);
         if (r >= p.na) continue;
         // the output row, and the base id of the row itself (the self column)
         const int64_t ro = p.qid ? r : (p.perm ? (int64_t)p.perm[r] : r);
         const int32_t sid = p.qid ? p.qid[r] : (int32_t)ro;
-        if (p.out_thresh && lane == 0) p.out_thresh[ro] = t2;
+        if (p.out_thresh && lane == 0) p.out_thresh[ro] = fminf(t2, taul);
         int selfpos = c2;
         if (p.self) {
           for (int e0 = 0; e0 < c2; e0 += 32) {
@@ -586,6 +611,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   a.err = err.p;
   a.out_thresh = ex.out_thresh;
   a.qid = ex.qid;
+  a.tau_in = ex.tau_in;
   if (ordered) {
     a.perm = ord.perm.p;
     a.inv = ord.inv.p;
@@ -593,13 +619,35 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
     a.rb_cluster = ord.rb_cluster.p;
   }
   const size_t smem = tc_smem_bytes(kchunks, stages);
+  auto launch = [&](TcArgs& args) {
+    if (C == 256)
+      launch_tc<256>(maps, args, grid, smem, st);
+    else if (C == 512)
+      launch_tc<512>(maps, args, grid, smem, st);
+    else
+      launch_tc<1024>(maps, args, grid, smem, st);
+  };
+  // Near-first full walks: a first launch over each block's prepass_tiles nearest tiles
+  // only records each row's KS-th distance there, an upper bound of its KS-th distance over
+  // all columns (the same values: the MMAs are the same); the full walk then admits only
+  // columns at or below that bound, so its appends and compactions are few from the start.
+  Scratch<float> tau0;
+  const bool prepass = ordered && max_tiles == 0 && ex.prepass_tiles > 0 &&
+                       a.ntiles > 2 * (int64_t)ex.prepass_tiles;
   if (gemm_timer) gemm_timer->start();
-  if (C == 256)
-    launch_tc<256>(maps, a, grid, smem, st);
-  else if (C == 512)
-    launch_tc<512>(maps, a, grid, smem, st);
-  else
-    launch_tc<1024>(maps, a, grid, smem, st);
+  if (prepass) {
+    tau0.alloc((size_t)na, st);
+    TcArgs a0 = a;
+    a0.nwalk = ex.prepass_tiles;
+    a0.thresh_only = 1;
+    a0.tau_out = tau0.p;
+    a0.out_thresh = nullptr;
+    launch(a0);
+    a.tau_in = tau0.p;
+    // approximate data: widen by far more than the rounding of the threshold test
+    a.tau_relax = approx ? 9.5367431640625e-07f : 0.f;  // 2^-20
+  }
+  launch(a);
   if (gemm_timer) gemm_timer->stop();
   int h = 0;
   SSG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));

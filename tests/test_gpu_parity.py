@@ -149,9 +149,10 @@ def test_knn_bf16_near_first_order_duplicates(ssg):
 
 
 def test_knn_bf16_signed_integers(ssg):
-    """Negative values: the tensor-core path needs 4 d max|x|^2 <= 2^24 (squared distances
-    up to 4 d max|x|^2 must stay exact); within it bf16 is taken and exact, beyond it auto
-    falls back to the fp32 path (still exact) and an explicit bf16 request is refused."""
+    """Negative values: the exact tensor-core GEMM needs 4 d max|x|^2 <= 2^24 (squared
+    distances up to 4 d max|x|^2 must stay exact); within it bf16 is exact by itself, beyond
+    it bf16 values are not exact and the certified path (bounded error, exact re-rank) runs,
+    with the same result as the fp32 path and the oracle."""
     if not _tc(ssg):
         pytest.skip("bf16 tensor-core kNN needs sm_103")
     rng = np.random.default_rng(31)
@@ -165,8 +166,11 @@ def test_knn_bf16_signed_integers(ssg):
     ref_ids, ref_d2 = oracle.knn_rows(beyond, 30)
     np.testing.assert_array_equal(_np(ids), ref_ids)
     np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
-    with pytest.raises(ssg.SSGError):
-        ssg.knn(_cuda(beyond), 30, prec="bf16")
+    ids, d2 = ssg.knn(_cuda(beyond), 30, prec="bf16")
+    np.testing.assert_array_equal(_np(ids), ref_ids)
+    np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
+    ids, d2 = ssg.knn(_cuda(beyond), 30, prec="fp32")
+    np.testing.assert_array_equal(_np(ids), ref_ids)
 
 
 def test_knn_wide_integer_rows_use_fp32(ssg):
