@@ -124,7 +124,7 @@ __host__ __device__ inline double stream_slop(double nx, double t) {
 // Calibration: for each sampled query row t, the number of base rows j (j != sid[t]) whose
 // bf16 distance is at most lim[t].  One block of 256 threads per tile sweep; thread t owns
 // sampled row t (its bf16 values, transposed in shared memory); base rows come through in
-// tiles of TJ.  d <= 128.
+// tiles of TJ.  (d + 3) / 4 * 4 * (256 + 32) floats of shared memory: d <= 128.
 constexpr int CAL_S = 256, CAL_TJ = 32;
 __global__ void __launch_bounds__(CAL_S)
 k_band_count(const float* __restrict__ As, int s, int lda, const float* __restrict__ B, int64_t nb,

@@ -13,17 +13,20 @@
 //               pipeline of 128-column base tiles (B), bf16 with 128-byte swizzle, plus the
 //               16-element augmentation rows with 32-byte swizzle;
 //   warp 1      allocates 512 TMEM columns and issues tcgen05.mma: for every B tile two
-//               128x128 accumulators (the two 128-row halves of A) into one of two TMEM
-//               buffers, so the epilogue drains one buffer while the MMAs fill the other;
+//               128x128 accumulators (the two 128-row halves of A) into one of NBUF = 2
+//               TMEM buffers, so the epilogue drains one buffer while the MMAs fill the
+//               other;
 //   warps 2..9  epilogue, one thread per query row (TMEM lane): tcgen05.ld 64 columns at
 //               a time, their largest accumulator against the row's threshold (a tree of
 //               three-input maxes), and only where some lane passes, the passing values go
 //               to the row's buffer in global scratch (L2); a warp compacts a full buffer
-//               with a register bitonic sort (top-KS, new threshold).  The row's own column
-//               (self) takes one extra slot and is dropped at output.
+//               with a bisection or a register bitonic sort (top-KS, new threshold).  The
+//               row's own column (self) takes one extra slot and is dropped at output.
 // Columns are visited in BN-wide tiles, in id order or (large self-joins) nearest cluster
 // first; in id order "d2 < threshold" also settles equal distances by id, otherwise ties
-// are admitted and settled by the compaction.
+// are admitted and settled by the compaction.  (64-column tiles with four TMEM buffers and
+// twice the TMA stages were measured 1.65x slower: the MMAs then take about as long per
+// instruction while doing half the work.)
 // Every wait on an mbarrier is bounded (about 2 s); a wait that runs out sets an error
 // word, tells the other roles to stop, and the CTA releases its TMEM and exits.
 #include <cuda.h>
@@ -42,6 +45,9 @@ using namespace tc;
 
 constexpr int BM = 256;               // query rows per CTA (two UMMA_M = 128 halves)
 constexpr int BN = 128;               // base columns per pipeline stage (UMMA_N)
+constexpr int API_TILE = 128;         // tile limits are given in 128-point tiles
+constexpr int NBUF = 2;               // TMEM accumulator buffers
+constexpr uint32_t IDESC_N = idesc_bf16(BN);
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + EPI_WARPS * 32;
 constexpr int TMEM_COLS = 512;        // 2 buffers x 2 halves x 128 fp32 columns
@@ -167,8 +173,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
   uint64_t* b_full = bars + 2;
   uint64_t* b_empty = b_full + MAX_STAGES;
   uint64_t* t_full = b_empty + MAX_STAGES;
-  uint64_t* t_empty = t_full + 2;
-  uint32_t* tmem_slot = (uint32_t*)(t_empty + 2);
+  uint64_t* t_empty = t_full + NBUF;
+  uint32_t* tmem_slot = (uint32_t*)(t_empty + NBUF);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -179,7 +185,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       mbar_init(smem_u32(b_full + s), 1);
       mbar_init(smem_u32(b_empty + s), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NBUF; ++b) {
       mbar_init(smem_u32(t_full + b), 1);
       mbar_init(smem_u32(t_empty + b), EPI_WARPS);
     }
@@ -252,8 +258,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         ok = mbar_wait(smem_u32(a_full), rbi & 1, abort_flag);
         if (!ok) break;
         for (int64_t ct = 0; ct < nwalk; ++ct, ++it) {
-          const int b = (int)(it & 1);
-          const uint32_t tph = (uint32_t)((it >> 1) & 1);
+          const int b = (int)(it % NBUF);
+          const uint32_t tph = (uint32_t)((it / NBUF) & 1);
           ok = mbar_wait(smem_u32(t_empty + b), tph ^ 1, abort_flag) &&
                mbar_wait(smem_u32(b_full + s), ph, abort_flag);
           if (!ok) break;
@@ -273,10 +279,11 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
                 const uint64_t ad =
                     adesc0 + (uint64_t)((kc * BM * 128 + h * 128 * 128 + kk * 32) >> 4);
                 const uint64_t bd = bdesc0 + (uint64_t)((kc * BN * 128 + kk * 32) >> 4);
-                umma_bf16(d_tmem, ad, bd, (kc | kk) ? 1u : 0u);
+                umma_bf16_id(d_tmem, ad, bd, IDESC_N, (kc | kk) ? 1u : 0u);
               }
             }
-            umma_bf16(d_tmem, adesc_aug + (uint64_t)((h * 128 * AUG_BYTES) >> 4), bdesc_aug, 1u);
+            umma_bf16_id(d_tmem, adesc_aug + (uint64_t)((h * 128 * AUG_BYTES) >> 4), bdesc_aug,
+                         IDESC_N, 1u);
           }
           umma_commit(smem_u32(b_empty + s));
           umma_commit(smem_u32(t_full + b));
@@ -322,8 +329,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
       for (int64_t i = 0; i < nwalk; ++i, ++it) {
         const int32_t j0 = (int32_t)(tn * BN);
         if (i + 1 < nwalk) tn = tl ? tl[i + 1] : i + 1;
-        const int b = (int)(it & 1);
-        const uint32_t tph = (uint32_t)((it >> 1) & 1);
+        const int b = (int)(it % NBUF);
+        const uint32_t tph = (uint32_t)((it / NBUF) & 1);
         ok = mbar_wait(smem_u32(t_full + b), tph, abort_flag);
         if (!__all_sync(0xffffffffu, ok)) {
           ok = false;
@@ -504,7 +511,8 @@ __global__ void k_aug_ones(__nv_bfloat16* __restrict__ aug) {
 size_t tc_smem_bytes(int kchunks, int stages) {
   return 1024 + (size_t)kchunks * BM * 128 + BM * AUG_BYTES +
          (size_t)stages * (kchunks * BN * 128 + BN * AUG_BYTES) +
-         EPI_WARPS * 32 * 32 * sizeof(float) + sizeof(uint64_t) * (2 + 2 * MAX_STAGES + 4) + 16;
+         EPI_WARPS * 32 * 32 * sizeof(float) + sizeof(uint64_t) * (2 + 2 * MAX_STAGES + 2 * NBUF) +
+         16;
 }
 
 struct TcMaps {
@@ -547,6 +555,8 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   // threshold otherwise falls slowly and many candidates are appended).
   KnnOrder ord;
   Scratch<float> norm_p;
+  // tile limits come in 128-point tiles; the walk counts BN-column tiles
+  max_tiles *= API_TILE / BN;
   // same: the query rows are the base rows (a self-join); with ex.qid the query rows are a
   // gathered subset of the base and only the self column is excluded
   const bool same = self && !ex.qid;
@@ -632,13 +642,13 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   // all columns (the same values: the MMAs are the same); the full walk then admits only
   // columns at or below that bound, so its appends and compactions are few from the start.
   Scratch<float> tau0;
-  const bool prepass = ordered && max_tiles == 0 && ex.prepass_tiles > 0 &&
-                       a.ntiles > 2 * (int64_t)ex.prepass_tiles;
+  const int64_t pre_tiles = (int64_t)ex.prepass_tiles * (API_TILE / BN);
+  const bool prepass = ordered && max_tiles == 0 && pre_tiles > 0 && a.ntiles > 2 * pre_tiles;
   if (gemm_timer) gemm_timer->start();
   if (prepass) {
     tau0.alloc((size_t)na, st);
     TcArgs a0 = a;
-    a0.nwalk = ex.prepass_tiles;
+    a0.nwalk = pre_tiles;
     a0.thresh_only = 1;
     a0.tau_out = tau0.p;
     a0.out_thresh = nullptr;
