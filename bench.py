@@ -166,6 +166,8 @@ def make_workload(name: str, n: int | None, rank: int):
         return synth.sift_like(seed=synth.SEED_SIFT + rank, **kw)
     if name == "small":
         return synth.small(seed=synth.SEED_SMALL + rank, **kw)
+    if name == "gist_like":
+        return synth.gist_like(seed=synth.SEED_GIST + rank, **kw)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -377,20 +379,23 @@ def run_serving_curve(ssg, g, base, w, seconds: float, rates):
                    "L_search uniform in [k, 512]; 4 batch slots"}
 
 
-def run_float_arm(ssg, n, d, K, L, R, ls=64, seed=190706144):
-    """One float index shaped like the many-index batch (a 16-centre Gaussian mixture, the
-    recipe of synth.batched_index): built through the certified bf16 path and through the
-    plain fp32 path (fp32 kNN GEMM, fp32 warp prune); build times, whether the edge sets
-    are identical, and recall@10 at one L_search on 1,000 queries."""
+def run_float_arm(ssg, n, d, K, L, R, ls=64, seed=190706144, w=None, label=None):
+    """One float index built through the certified bf16 path and through the plain fp32
+    path (fp32 kNN GEMM, fp32 warp prune): build times, whether the edge sets are identical,
+    and recall@10 at one L_search on the workload's queries.  Default data: a 16-centre
+    Gaussian mixture shaped like the many-index batch (the recipe of synth.batched_index)."""
     import torch
     from paper_1907_06146_gb300 import synth
-    w = synth.small(n=n, d=d, nq=1000, seed=seed)
+    if w is None:
+        w = synth.small(n=n, d=d, nq=1000, seed=seed)
+    n, d = w.base.shape
     base = torch.from_numpy(w.base).cuda()
     q = torch.from_numpy(w.queries).cuda()
+    nq = w.queries.shape[0]
     nav = synth.nav_ids(n, 10, seed)
     truth, _ = ssg.knn_query(base, q, 10)
-    out = {"workload": f"16-centre Gaussian mixture n={n} d={d} (float32) K={K} L={L} R={R} "
-                       f"alpha=60 nav=10"}
+    out = {"workload": (label or "16-centre Gaussian mixture") +
+                       f" n={n} d={d} (float32) K={K} L={L} R={R} alpha=60 nav=10"}
     graphs = {}
     for arm, kw in (("bf16", {"prec": "auto"}), ("fp32", {"prec": "fp32", "gram_prec": "fp32"})):
         g = ssg.build(base, K, L, R, 60.0, nav=nav, **kw)  # warm-up
@@ -404,7 +409,9 @@ def run_float_arm(ssg, n, d, K, L, R, ls=64, seed=190706144):
                     "gemm_prec_used": st["gemm_prec_used"],
                     "knn_candidates": st["knn_candidates"],
                     "knn_rows_not_certified_by_first_pass": st["n_knn_fallback_rows"],
-                    "recall@10": ssg.recall_hits(ids, truth, 10) / 10000.0, "L_search": ls}
+                    "stages_ms": {k: st[k] for k in ("ms_pool", "ms_prune", "ms_reverse",
+                                                     "ms_connect")},
+                    "recall@10": ssg.recall_hits(ids, truth, 10) / (10.0 * nq), "L_search": ls}
         graphs[arm] = g
     out["edge_sets_identical"] = bool(torch.equal(graphs["bf16"].adj, graphs["fp32"].adj)
                                       and torch.equal(graphs["bf16"].deg, graphs["fp32"].deg))
@@ -624,6 +631,13 @@ def run_gpu(args):
     if rank == 0 and args.float_n > 0:
         float_arm = run_float_arm(ssg, args.float_n, args.float_d, 100, 200, 32)
 
+    wide_arm = None
+    if rank == 0 and args.wide_n > 0 and w.name != "gist_like":
+        # the 960-d GIST-shaped data (SURVEY config 3's shape) at a size both paths finish
+        gw = synth.gist_like(n=args.wide_n, nq=1000)
+        wide_arm = run_float_arm(ssg, 0, 0, gw.K, gw.L, gw.R, ls=64, w=gw,
+                                 label="GIST-shaped softplus mixture, values in [0, 1],")
+
     alg4 = None
     if rank == 0 and args.alg4_tiles > 0:
         # Alg. 4: pools searched on the fly over the cluster-ordered tiles, no kNN graph
@@ -704,7 +718,8 @@ def run_gpu(args):
         "dtype": "bf16" if used_prec == 1 else "f32", "data": "synthetic",
         "config": {"workload": f"{w.name} n={w.n} d={w.d} K={w.K} L={w.L} R={w.R} "
                                f"alpha={w.alpha} nav={w.n_nav} queries={nq}",
-                   "l2": "inputs larger than L2 (base 512 MB)", "gemm_prec": args.prec,
+                   "l2": f"inputs larger than L2 (base {w.base.nbytes // 2**20} MiB)",
+                   "gemm_prec": args.prec,
                    "tune_table": args.tune_table,
                    "parallelism": f"replicas x{ws}"},
         "search": {"qps": qps, "recall@10": float(np.mean(recalls)), "L_search": ls_used,
@@ -726,6 +741,7 @@ def run_gpu(args):
         "serving_deep": serving_deep,
         "fp32_path": fp32_arm,
         "float_mixed": float_arm,
+        "wide_mixed": wide_arm,
         "batched": batched,
         "ablations": ablations,
         "alg4": alg4,
@@ -750,7 +766,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sift_like", choices=["sift_like", "small"])
+    ap.add_argument("--workload", default="sift_like", choices=["sift_like", "small", "gist_like"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--target-recall", type=float, default=0.95)
@@ -783,6 +799,9 @@ def main():
     ap.add_argument("--float-n", type=int, default=200_000,
                     help="points of the float index built through both precisions (0 = skip)")
     ap.add_argument("--float-d", type=int, default=128)
+    ap.add_argument("--wide-n", type=int, default=200_000,
+                    help="points of the 960-d GIST-shaped index built through both precisions "
+                         "(0 = skip)")
     ap.add_argument("--serve-deep", type=int, default=0,
                     help="also build the 96-d L2-normalised workload at this many points with "
                          "search-based pools and serve it (10000000: the 10M serving case)")

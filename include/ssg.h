@@ -54,7 +54,9 @@ typedef enum {
  * kNN GEMM:
  *   FP32  single-precision SIMT GEMM form, top-(K + slack) re-ranked in fp64, each row
  *         certified against the GEMM's error bound (uncertified rows recomputed exhaustively).
- *   BF16  bf16 tcgen05 GEMM with fp32 accumulation (sm_103, d <= 128).  On integer data
+ *   BF16  bf16 tcgen05 GEMM with fp32 accumulation (sm_103, d <= 4096: rows of up to 128
+ *         values stay resident in shared memory, wider rows stream in 64-value chunks
+ *         through 128 x 256 tiles).  On integer data
  *         that bf16 holds exactly the GEMM itself is exact.  On other data the rows are
  *         centred on the column mean before rounding, each row keeps the KS nearest by bf16
  *         distance (KS sized from a seeded sample of rows so that about 99% of rows
@@ -97,7 +99,7 @@ typedef struct {
                                each node's L nearest among the points of the pool_tiles
                                128-point tiles nearest to it in the cluster order (an
                                IVF-style index over k-means clusters of the data, searched
-                               nearest cluster first); needs sm_103 and d <= 128 (EINVAL
+                               nearest cluster first); needs sm_103 and d <= 4096 (EINVAL
                                otherwise).  On data exact in bf16 the selection is exact;
                                on other data the tensor cores select L + slack candidates
                                by bf16 distance and each pool is re-ranked exactly (so a
@@ -194,7 +196,7 @@ ssg_status ssg_nav_ids(int64_t n, int32_t s, uint64_t seed, int32_t* out_host);
 
 /* Exact kNN graph (Alg. 3 line 1, computed exactly): for every i, the K nearest j != i
  * by (d2, id).  knn_id int32 [n][K], knn_d2 float32 [n][K] (d2 rounded to float32).
- * EINVAL if n < 2, d < 1, K < 1, K > n - 1 or K > 768. */
+ * EINVAL if n < 2, d < 1, K < 1, K > n - 1 or K > 700. */
 ssg_status ssg_knn(const float* base, int64_t n, int32_t d, int32_t K, ssg_precision prec,
                    int32_t* knn_id, float* knn_d2, ssg_stream stream);
 

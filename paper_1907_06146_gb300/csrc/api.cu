@@ -267,7 +267,7 @@ static KnnResult knn_any(const Ingested& a, int64_t na, const Ingested& b, int64
                          cudaStream_t st, StageTimer* t_gemm, CertResult* cr) {
   const int path = knn_path(prec, info, d);
   SSG_REQUIRE(prec != SSG_PREC_BF16 || path != 0, SSG_EINVAL,
-              "bf16 distance GEMM needs sm_103 and d <= 128");
+              "bf16 distance GEMM needs sm_103 and d <= 4096");
   KnnResult kr;
   if (path == 1) {
     TcExtra ex;
@@ -549,7 +549,7 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
     const double border = opts.cos_margin_fp64;
     const bool gram_tc = opts.gram_prec != SSG_PREC_FP32 && in.info.bf16_exact;
     SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || kpath != 0, SSG_EINVAL,
-                "bf16 distance GEMM needs sm_103 and d <= 128");
+                "bf16 distance GEMM needs sm_103 and d <= 4096");
     CertResult cert;
     Scratch<int32_t> pool_id((size_t)n * L, st), pool_len((size_t)n, st);
     Scratch<float> pool_d2((size_t)n * L, st);
@@ -560,9 +560,10 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
       const bool tc_any = opts.gemm_prec != SSG_PREC_FP32 && knn_tc_available(d);
       SSG_REQUIRE(tc_any, SSG_EINVAL,
                   "search-based pools (pool_tiles > 0) need the bf16 tensor-core path: sm_103 "
-                  "and d <= 128");
+                  "and d <= 4096");
       SSG_REQUIRE(knn_order_fits(n, 128), SSG_EINVAL, "search-based pools: n too large");
-      SSG_REQUIRE(L <= 895, SSG_EINVAL, "search-based pools: need L <= 895");
+      const int lmax = knn_tc_max_k(d, true);
+      SSG_REQUIRE(L <= lmax, SSG_EINVAL, "search-based pools: need L <= %d for d = %d", lmax, d);
       t_knn.start();
       if (tc) {
         // data exact in bf16: the selection itself is exact
@@ -577,7 +578,8 @@ ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t
       } else {
         // other data: a bf16 selection of L + slack candidates (approximate distances), then
         // each pool ordered from the original vectors as Alg. 3's pools are and cut to L
-        const int Lp = (int)std::min<int64_t>(std::min(L + std::max(8, L / 4), 895), n - 1);
+        const int Lp = (int)std::min<int64_t>(
+            std::min(L + std::max(8, L / 4), knn_tc_max_k(d, true)), n - 1);
         Scratch<int32_t> cid((size_t)n * Lp, st);
         Scratch<float> cd2((size_t)n * Lp, st);
         knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p,

@@ -112,7 +112,7 @@ CheckResult check_pool(const int32_t* pid, const float* pd2, const int32_t* plen
   SSG_CUDA(cudaMemsetAsync(bad.p, 0xff, sizeof(unsigned long long), st));
   if (n > 0) {
     const int grid = (int)std::min<int64_t>(ceil_div(n, 8), 8 * num_sms());
-    SSG_LAUNCH(k_check_pool, grid, 256, 0, st, pid, pd2, plen, n, L, exact, dist_rel_fp32(d),
+    SSG_LAUNCH(k_check_pool, grid, 256, 0, st, pid, pd2, plen, n, L, exact, dist_rel_team8((d + 3) & ~3),
                bad.p);
   }
   const unsigned long long h = read_bad(bad, st);

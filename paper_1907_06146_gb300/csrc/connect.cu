@@ -310,7 +310,7 @@ int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int3
   int32_t* f[2] = {f0.p, f1.p};
   RepairState* S = state.p;
   const int grid = 8 * num_sms();
-  const float rel = dist_rel_fp32(d);
+  const float rel = dist_rel_team8(ld);
   const int small_limit = 4096;
   int64_t repairs = 0;
   for (int r = 0; r < n_nav; ++r) {
@@ -421,7 +421,7 @@ static int64_t connect_run_noalloc(const float* X, int ld, int d, int64_t n, int
   RepairState* S = (RepairState*)(base + OFF_STATE);
   const int64_t nw = ceil_div(n, 32);
   const int grid = 8 * num_sms();
-  const float rel = dist_rel_fp32(d);
+  const float rel = dist_rel_team8(ld);
   const int small_limit = 4096;
   int64_t repairs = 0;
   for (int r = 0; r < n_nav; ++r) {

@@ -46,8 +46,12 @@ void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN,
                        KnnOrder& o, int64_t walk = 0, const float* x_norm = nullptr);
 
 // bf16 tensor-core variant of the exact top-K (only for info.bf16_exact data).
-// True on sm_103 when the shared-memory pipeline fits rows of d values (d <= 128).
+// True on sm_103 for rows of up to 4,096 values: the resident pipeline holds d <= 128, wider
+// rows stream through the K-chunked kernel.
 bool knn_tc_available(int d);
+// Largest K (self-joins; one less than the row buffer's room) the tensor-core kernel takes
+// for rows of d values, for a full walk or a tile-limited one.
+int knn_tc_max_k(int d, bool limited);
 // Optional inputs and outputs of knn_exact_tc.
 struct TcExtra {
   const float* mu = nullptr;          // centre every row on mu [d] before rounding to bf16
@@ -195,5 +199,12 @@ void pad_rows(const float* X, int64_t n, int d, cudaStream_t st, PaddedRows& out
 inline float angle_margin_fp32(int d) { return (float)((2.0 * d + 20.0) * U32 * 1.1); }
 // Relative error bound of an fp32 squared distance summed directly from differences.
 inline float dist_rel_fp32(int d) { return (float)((d + 4.0) * U32 * 1.01); }
+// The same for distances summed by team8_dist over rows of stride ld: each lane adds
+// m = 4 ceil(ld / 32) squares of rounded differences with fused multiply-adds (at most
+// (m + 2) units of roundoff relative to the sum of the squares: one per addition, two for
+// the rounded difference squared), then three pairwise additions join the 8 lanes.
+inline float dist_rel_team8(int ld) {
+  return (float)((4.0 * ((ld + 31) / 32) + 6.0) * U32 * 1.01);
+}
 
 }  // namespace ssg

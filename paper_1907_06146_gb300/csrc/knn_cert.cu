@@ -122,50 +122,60 @@ __host__ __device__ inline double stream_slop(double nx, double t) {
 }
 
 // Calibration: for each sampled query row t, the number of base rows j (j != sid[t]) whose
-// bf16 distance is at most lim[t].  One block of 256 threads per tile sweep; thread t owns
-// sampled row t (its bf16 values, transposed in shared memory); base rows come through in
-// tiles of TJ.  (d + 3) / 4 * 4 * (256 + 32) floats of shared memory: d <= 128.
-constexpr int CAL_S = 256, CAL_TJ = 32;
+// bf16 distance is at most lim[t].  One block of 256 threads walks tiles of CAL_TJ base
+// rows; thread t owns sampled row t.  The dimensions go through in chunks of CAL_DC: the
+// sampled rows' chunk (bf16 values, transposed) and the tile's chunk sit in shared memory
+// (for rows of at most CAL_DC values the sample's chunk is loaded once).
+constexpr int CAL_S = 256, CAL_TJ = 32, CAL_DC = 128;
 __global__ void __launch_bounds__(CAL_S)
 k_band_count(const float* __restrict__ As, int s, int lda, const float* __restrict__ B, int64_t nb,
              int ldb, int d, const float* __restrict__ mu, const float* __restrict__ nac,
              const float* __restrict__ nbc, const double* __restrict__ lim,
              const int32_t* __restrict__ sid, int* __restrict__ count) {
   extern __shared__ __align__(16) float csm[];
-  const int dp = (d + 3) & ~3;
-  float* Qt = csm;                 // [dp][CAL_S]
-  float* Y = Qt + (size_t)dp * CAL_S;  // [CAL_TJ][dp]
+  float* Qt = csm;                        // [CAL_DC][CAL_S]
+  float* Y = Qt + (size_t)CAL_DC * CAL_S; // [CAL_TJ][CAL_DC]
   const int t = threadIdx.x;
-  for (int i = t; i < dp * CAL_S; i += CAL_S) {
-    const int k = i / CAL_S, q = i - k * CAL_S;
-    float v = 0.f;
-    if (q < s && k < d) v = __bfloat162float(__float2bfloat16_rn(__fsub_rn(As[(int64_t)q * lda + k], mu[k])));
-    Qt[i] = v;
-  }
+  const int nchunks = (d + CAL_DC - 1) / CAL_DC;
+  auto load_q = [&](int c0) {
+    for (int i = t; i < CAL_DC * CAL_S; i += CAL_S) {
+      const int k = i / CAL_S, q = i - k * CAL_S;
+      float v = 0.f;
+      if (q < s && c0 + k < d)
+        v = __bfloat162float(__float2bfloat16_rn(__fsub_rn(As[(int64_t)q * lda + c0 + k], mu[c0 + k])));
+      Qt[i] = v;
+    }
+  };
+  if (nchunks == 1) load_q(0);
   const float nq = t < s ? nac[t] : 0.f;
   const double lq = t < s ? lim[t] : -1.0;
   const int32_t me = t < s && sid ? sid[t] : -1;
   int cnt = 0;
   for (int64_t j0 = (int64_t)blockIdx.x * CAL_TJ; j0 < nb; j0 += (int64_t)gridDim.x * CAL_TJ) {
-    __syncthreads();
-    for (int i = t; i < CAL_TJ * dp; i += CAL_S) {
-      const int r = i / dp, k = i - r * dp;
-      const int64_t j = j0 + r;
-      float v = 0.f;
-      if (j < nb && k < d) v = __bfloat162float(__float2bfloat16_rn(__fsub_rn(B[j * ldb + k], mu[k])));
-      Y[i] = v;
-    }
-    __syncthreads();
     float acc[CAL_TJ];
 #pragma unroll
     for (int r = 0; r < CAL_TJ; ++r) acc[r] = 0.f;
-    for (int k = 0; k < dp; k += 4) {
-      const float q0 = Qt[(k + 0) * CAL_S + t], q1 = Qt[(k + 1) * CAL_S + t];
-      const float q2 = Qt[(k + 2) * CAL_S + t], q3 = Qt[(k + 3) * CAL_S + t];
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int c0 = ch * CAL_DC;
+      __syncthreads();
+      if (nchunks > 1) load_q(c0);
+      for (int i = t; i < CAL_TJ * CAL_DC; i += CAL_S) {
+        const int r = i / CAL_DC, k = i - r * CAL_DC;
+        const int64_t j = j0 + r;
+        float v = 0.f;
+        if (j < nb && c0 + k < d)
+          v = __bfloat162float(__float2bfloat16_rn(__fsub_rn(B[j * ldb + c0 + k], mu[c0 + k])));
+        Y[i] = v;
+      }
+      __syncthreads();
+      for (int k = 0; k < CAL_DC; k += 4) {
+        const float q0 = Qt[(k + 0) * CAL_S + t], q1 = Qt[(k + 1) * CAL_S + t];
+        const float q2 = Qt[(k + 2) * CAL_S + t], q3 = Qt[(k + 3) * CAL_S + t];
 #pragma unroll
-      for (int r = 0; r < CAL_TJ; ++r) {
-        const float4 y = *(const float4*)(Y + r * dp + k);
-        acc[r] = fmaf(q0, y.x, fmaf(q1, y.y, fmaf(q2, y.z, fmaf(q3, y.w, acc[r]))));
+        for (int r = 0; r < CAL_TJ; ++r) {
+          const float4 y = *(const float4*)(Y + r * CAL_DC + k);
+          acc[r] = fmaf(q0, y.x, fmaf(q1, y.y, fmaf(q2, y.z, fmaf(q3, y.w, acc[r]))));
+        }
       }
     }
     if (t < s) {
@@ -324,7 +334,7 @@ static int certify(const float* A, const float* B, int ld, int d, const int32_t*
   const size_t smem = (size_t)cap * 16 * wpb;
   ensure_smem((const void*)k_knn_cert, smem);
   SSG_LAUNCH(k_knn_cert, (unsigned)ceil_div(count, wpb), wpb * 32, smem, st, A, B, ld, d, rows, count,
-             cand, KS, thr, nac, ymax2, K, cap, dist_rel_fp32(d), exact_d2 ? 1 : 0, out_id, out_d2, fb,
+             cand, KS, thr, nac, ymax2, K, cap, dist_rel_team8(ld), exact_d2 ? 1 : 0, out_id, out_d2, fb,
              fbk, fbc, n_order);
   return read_count(fbc, st);
 }
@@ -335,7 +345,7 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
                               bool exact_d2, const KnnTune& tune, unsigned long long* n_order,
                               cudaStream_t st, StageTimer* gemm_timer) {
   CertResult res;
-  SSG_REQUIRE(knn_tc_available(d) && d <= 128, SSG_EINTERNAL,
+  SSG_REQUIRE(knn_tc_available(d), SSG_EINTERNAL,
               "certified bf16 kNN: the tensor-core path does not run for d = %d", d);
   const int grid = 8 * num_sms();
   // centre on the base's column mean; centred squared norms and their maximum
@@ -363,7 +373,7 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
   memcpy(&ymax2f, &mbits, 4);
   const double ymax2 = (double)ymax2f;
   const int64_t avail = self ? nb - 1 : nb;
-  const int KS_MAX = 895;  // the largest top-K the tensor-core kernel keeps
+  const int KS_MAX = knn_tc_max_k(d, false);  // the largest top-K the kernel keeps
 
   // KS: the tune.quantile point of the sampled rows' candidate needs, plus 5%
   int KS = std::min<int64_t>(avail, std::max(K + 8, 2 * K));
@@ -378,18 +388,21 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
     SSG_LAUNCH(k_centred_norms, (unsigned)ceil_div(s, 8), 256, 0, st, As.p, (int64_t)s, d, ld,
                (const float*)nullptr, asn.p, (unsigned*)nullptr);
     SSG_LAUNCH(k_gather_vals, (unsigned)ceil_div(s, 256), 256, 0, st, nac, sid.p, (int64_t)s, asc.p);
-    // the sample's exact K-th distance (itself included as a column when self: K + 1)
+    // the sample's exact K-th distance (itself included as a column when self: K + 1),
+    // through this same certified path with the sample as queries and no sizing of its own
     const int Kq = K + self;
     Scratch<int32_t> sids((size_t)s * Kq, st);
     Scratch<float> sd2((size_t)s * Kq, st);
-    knn_exact(As.p, s, ld, asn.p, B, nb, ld, b_norm_raw, d, info, 0, Kq, sids.p, sd2.p, st, nullptr);
+    KnnTune t0 = tune;
+    t0.sample_rows = 0;
+    knn_bf16_certified(As.p, s, ld, asn.p, B, nb, b_norm_raw, d, info, 0, Kq, sids.p, sd2.p, false,
+                       t0, n_order, st, nullptr);
     Scratch<double> lim((size_t)s, st);
     SSG_LAUNCH(k_band_limit, (unsigned)ceil_div(s, 128), 128, 0, st, sd2.p, Kq, Kq - 1, s, asc.p,
                ymax2, d, lim.p);
     Scratch<int> cnt((size_t)s, st);
     SSG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * s, st));
-    const int dp = (d + 3) & ~3;
-    const size_t smem = sizeof(float) * ((size_t)dp * CAL_S + (size_t)CAL_TJ * dp);
+    const size_t smem = sizeof(float) * ((size_t)CAL_DC * CAL_S + (size_t)CAL_TJ * CAL_DC);
     ensure_smem((const void*)k_band_count, smem);
     const unsigned cg = (unsigned)std::min<int64_t>(ceil_div(nb, CAL_TJ), num_sms());
     SSG_LAUNCH(k_band_count, cg, CAL_S, smem, st, As.p, s, ld, B, nb, ld, d, mu.p, asc.p, nbc.p, lim.p,
@@ -429,7 +442,7 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
   // their K-th exact distance so far plus the bound (the band that can hold a true
   // neighbour), up to KS2 columns; a band that fits certifies the row
   if (nfb > 0 && KS < avail) {
-    const int KS2 = (int)std::min<int64_t>(avail, std::max(KS, 640));
+    const int KS2 = (int)std::min<int64_t>(avail, std::min(KS_MAX, std::max(KS, 640)));
     Scratch<float> Ag((size_t)nfb * ld, st), nag((size_t)nfb, st), thr2((size_t)nfb, st),
         tau2((size_t)nfb, st);
     Scratch<int32_t> cid2((size_t)nfb * KS2, st);

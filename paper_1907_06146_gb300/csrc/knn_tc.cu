@@ -152,6 +152,93 @@ __device__ __forceinline__ void map_key_ids(uint64_t* buf, int cnt, const int32_
   __syncwarp();
 }
 
+// Cuts back the row buffers of a warp's 32 rows that the next tile could overflow (count
+// above trig) to the entries at or below their KS-th smallest distance (a full sort only if
+// ties would keep too many).  wbuf: the buffer of lane 0's row; lane l's is wbuf + l C.
+template <int C>
+__device__ __forceinline__ void compact_needed(const TcArgs& p, uint64_t* wbuf, int& cnt,
+                                               float& tau) {
+  unsigned need = __ballot_sync(0xffffffffu, cnt > p.trig);
+  while (need) {
+    const int l = __ffs(need) - 1;
+    need &= need - 1;
+    uint64_t* lb = wbuf + (size_t)l * C;
+    const int cl = __shfl_sync(0xffffffffu, cnt, l);
+    float t2;
+    int c2 = select_row<C>(lb, cl, p.KS, (p.KS + p.trig) / 2, p.trig, &t2);
+    if (c2 < 0) {
+      // too many ties at the threshold: a sort settles them by original id, and the
+      // kept keys go back to stored positions like the ones still to come
+      map_key_ids(lb, cl, p.perm);
+      c2 = compact_row<C>(lb, cl, p.KS, &t2);
+      map_key_ids(lb, c2, p.inv);
+    }
+    if (lane_id() == l) {
+      cnt = c2;
+      tau = t2;
+    }
+  }
+}
+
+// Final compaction of a warp's 32 rows (stored rows r0 .. r0 + 31, buffers as for
+// compact_needed), then their output: the first K keys after dropping the row itself (or,
+// thresh_only, the KS-th distance), and the threshold when asked.
+template <int C>
+__device__ __forceinline__ void finish_rows(const TcArgs& p, uint64_t* wbuf, int64_t r0, int cnt,
+                                            float tau) {
+  const int lane = lane_id();
+  const float INF = __int_as_float(0x7f800000);
+  for (int l = 0; l < 32; ++l) {
+    const int64_t r = r0 + l;
+    uint64_t* lb = wbuf + (size_t)l * C;
+    float t2;
+    int cl = __shfl_sync(0xffffffffu, cnt, l);
+    if (cl > 256 && cl > p.KS) {
+      const int c1 = select_row<C>(lb, cl, p.KS, 256, 256, &t2);
+      if (c1 >= 0) cl = c1;
+    }
+    if (p.thresh_only) {
+      // the KS-th distance of this walk (the order of equal distances is irrelevant)
+      if (cl <= 256)
+        compact_row<256>(lb, cl, p.KS, &t2);
+      else
+        compact_row<C>(lb, cl, p.KS, &t2);
+      if (r < p.na && lane == 0) p.tau_out[r] = t2;
+      __syncwarp();
+      continue;
+    }
+    map_key_ids(lb, cl, p.perm);
+    const int c2 = cl <= 256 ? compact_row<256>(lb, cl, p.KS, &t2)
+                             : compact_row<C>(lb, cl, p.KS, &t2);
+    // the row's last admission bound: with fewer than KS kept (a bound from tau_in that
+    // few columns meet) every column not kept lies above it
+    const float taul = __shfl_sync(0xffffffffu, tau, l);
+    if (r >= p.na) continue;
+    // the output row, and the base id of the row itself (the self column)
+    const int64_t ro = p.qid ? r : (p.perm ? (int64_t)p.perm[r] : r);
+    const int32_t sid = p.qid ? p.qid[r] : (int32_t)ro;
+    if (p.out_thresh && lane == 0) p.out_thresh[ro] = fminf(t2, taul);
+    int selfpos = c2;
+    if (p.self) {
+      for (int e0 = 0; e0 < c2; e0 += 32) {
+        const int e = e0 + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, e < c2 && key_id(lb[e]) == sid);
+        if (m) {
+          selfpos = e0 + __ffs(m) - 1;
+          break;
+        }
+      }
+    }
+    for (int t = lane; t < p.K; t += 32) {
+      const int src = t < selfpos ? t : t + 1;
+      const uint64_t key = src < c2 ? lb[src] : KEY_NONE;
+      p.out_id[ro * p.K + t] = key == KEY_NONE ? -1 : key_id(key);
+      p.out_d2[ro * p.K + t] = key == KEY_NONE ? INF : key_dist(key);
+    }
+    __syncwarp();
+  }
+}
+
 template <int C>
 __global__ void __launch_bounds__(THREADS, 1)
 k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -374,80 +461,260 @@ k_knn_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
           scan64(v0, v1, c);
         }
         // a buffer that the next tile could overflow drops to the entries at or below its
-        // KS-th smallest distance (a full sort only if ties would keep too many)
-        unsigned need = __ballot_sync(0xffffffffu, cnt > p.trig);
-        while (need) {
-          const int l = __ffs(need) - 1;
-          need &= need - 1;
-          uint64_t* lb = p.rowbuf + ((size_t)blockIdx.x * BM + h * 128 + q * 32 + l) * C;
-          const int cl = __shfl_sync(0xffffffffu, cnt, l);
-          float t2;
-          int c2 = select_row<C>(lb, cl, p.KS, (p.KS + p.trig) / 2, p.trig, &t2);
-          if (c2 < 0) {
-            // too many ties at the threshold: a sort settles them by original id, and the
-            // kept keys go back to stored positions like the ones still to come
-            map_key_ids(lb, cl, p.perm);
-            c2 = compact_row<C>(lb, cl, p.KS, &t2);
-            map_key_ids(lb, c2, p.inv);
-          }
-          if (lane == l) {
-            cnt = c2;
-            tau = t2;
-          }
-        }
+        // KS-th smallest distance
+        compact_needed<C>(p, p.rowbuf + ((size_t)blockIdx.x * BM + h * 128 + q * 32) * C, cnt,
+                          tau);
       }
       if (!ok) break;
-      // final compaction of each row of this warp, then output (dropping the row itself)
-      for (int l = 0; l < 32; ++l) {
-        const int rin = h * 128 + q * 32 + l;
-        const int64_t r = rb * BM + rin;
-        uint64_t* lb = p.rowbuf + ((size_t)blockIdx.x * BM + rin) * C;
-        float t2;
-        int cl = __shfl_sync(0xffffffffu, cnt, l);
-        if (cl > 256 && cl > p.KS) {
-          const int c1 = select_row<C>(lb, cl, p.KS, 256, 256, &t2);
-          if (c1 >= 0) cl = c1;
-        }
-        if (p.thresh_only) {
-          // the KS-th distance of this walk (the order of equal distances is irrelevant)
-          if (cl <= 256)
-            compact_row<256>(lb, cl, p.KS, &t2);
-          else
-            compact_row<C>(lb, cl, p.KS, &t2);
-          if (r < p.na && lane == 0) p.tau_out[r] = t2;
-          __syncwarp();
-          continue;
-        }
-        map_key_ids(lb, cl, p.perm);
-        const int c2 = cl <= 256 ? compact_row<256>(lb, cl, p.KS, &t2)
-                                 : compact_row<C>(lb, cl, p.KS, &t2);
-        // the row's last admission bound: with fewer than KS kept (a bound from tau_in that
-        // few columns meet) every column not kept lies above it
-        const float taul = __shfl_sync(0xffffffffu, tau, l);
-        if (r >= p.na) continue;
-        // the output row, and the base id of the row itself (the self column)
-        const int64_t ro = p.qid ? r : (p.perm ? (int64_t)p.perm[r] : r);
-        const int32_t sid = p.qid ? p.qid[r] : (int32_t)ro;
-        if (p.out_thresh && lane == 0) p.out_thresh[ro] = fminf(t2, taul);
-        int selfpos = c2;
-        if (p.self) {
-          for (int e0 = 0; e0 < c2; e0 += 32) {
-            const int e = e0 + lane;
-            const unsigned m = __ballot_sync(0xffffffffu, e < c2 && key_id(lb[e]) == sid);
-            if (m) {
-              selfpos = e0 + __ffs(m) - 1;
-              break;
+      finish_rows<C>(p, p.rowbuf + ((size_t)blockIdx.x * BM + h * 128 + q * 32) * C,
+                     rb * BM + h * 128 + q * 32, cnt, tau);
+    }
+    if (!ok && lane == 0) {
+      atomicOr(p.err, 4);
+      *abort_flag = 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Rows wider than the resident pipeline holds (d > 128): the query rows are streamed with
+// the base tiles, 64 values at a time.  A CTA owns BMW = 128 query rows and walks
+// BNW = 256-column tiles; per tile and 64-wide chunk one stage holds the A chunk (16 KB)
+// and the B chunk (32 KB), and the MMA thread issues four 128 x 256 x 16 MMAs into one of
+// two 256-column TMEM buffers (N = 256: the wider instruction does twice the work of
+// N = 128 for about the same issue time).  The augmentation step (-|y|^2/2 folded into the
+// accumulator) comes last in each tile from a two-slot ring.  Four epilogue warps, one per
+// TMEM lane quadrant, scan the tile's 256 columns of their 32 rows as the resident kernel
+// does; a tile's MMAs take long enough that the handoff between the two buffers is cheap.
+// ---------------------------------------------------------------------------------------
+constexpr int BMW = 128;
+constexpr int BNW = 256;
+constexpr int EPI_W = 4;
+constexpr int THREADS_W = 64 + EPI_W * 32;
+constexpr int STAGES_W = 3;
+constexpr uint32_t IDESC_W = idesc_bf16(BNW);
+constexpr uint32_t A_CHUNK_W = BMW * 128;   // 16 KB
+constexpr uint32_t B_CHUNK_W = BNW * 128;   // 32 KB
+constexpr uint32_t STAGE_W = A_CHUNK_W + B_CHUNK_W;
+
+size_t tcw_smem_bytes() {
+  return 1024 + (size_t)STAGES_W * STAGE_W + 2 * (BNW * AUG_BYTES) + BMW * AUG_BYTES +
+         EPI_W * 32 * 32 * sizeof(float) + sizeof(uint64_t) * (1 + 2 * STAGES_W + 4 + 4) + 16;
+}
+
+template <int C>
+__global__ void __launch_bounds__(THREADS_W, 1)
+k_knn_tc_wide(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmAaug, const __grid_constant__ CUtensorMap tmBaug,
+              TcArgs p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sS = sm;                                        // STAGES_W x [A chunk | B chunk]
+  unsigned char* sBaug = sS + (size_t)STAGES_W * STAGE_W;        // 2 x BNW rows x 32 B
+  unsigned char* sAaug = sBaug + 2 * BNW * AUG_BYTES;            // BMW rows x 32 B
+  float* stash = (float*)(sAaug + BMW * AUG_BYTES);              // 32 floats per epilogue thread
+  uint64_t* bars = (uint64_t*)(stash + EPI_W * 32 * 32);
+  uint64_t* aa_full = bars;
+  uint64_t* s_full = bars + 1;
+  uint64_t* s_empty = s_full + STAGES_W;
+  uint64_t* g_full = s_empty + STAGES_W;   // augmentation ring
+  uint64_t* g_empty = g_full + 2;
+  uint64_t* t_full = g_empty + 2;
+  uint64_t* t_empty = t_full + 2;
+  uint32_t* tmem_slot = (uint32_t*)(t_empty + 2);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const int kc_n = p.kchunks;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(aa_full), 1);
+    for (int s = 0; s < STAGES_W; ++s) {
+      mbar_init(smem_u32(s_full + s), 1);
+      mbar_init(smem_u32(s_empty + s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(g_full + b), 1);
+      mbar_init(smem_u32(g_empty + b), 1);
+      mbar_init(smem_u32(t_full + b), 1);
+      mbar_init(smem_u32(t_empty + b), EPI_W);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int64_t nrb = (p.na + BMW - 1) / BMW;
+  const int64_t nwalk = p.nwalk;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      bool ok = true;
+      mbar_expect_tx(smem_u32(aa_full), BMW * AUG_BYTES);
+      tma_load_2d(smem_u32(sAaug), &tmAaug, smem_u32(aa_full), 0, 0);
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t t = 0;  // tiles so far (augmentation slot t & 1)
+      for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
+        const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * p.tstride : nullptr;
+        int64_t tn = tl ? tl[0] : 0;
+        for (int64_t i = 0; i < nwalk && ok; ++i, ++t) {
+          const int j0 = (int)(tn * BNW);
+          if (i + 1 < nwalk) tn = tl ? tl[i + 1] : i + 1;
+          const int g = (int)(t & 1);
+          ok = mbar_wait(smem_u32(g_empty + g), (uint32_t)(((t >> 1) & 1) ^ 1), abort_flag);
+          if (!ok) break;
+          mbar_expect_tx(smem_u32(g_full + g), BNW * AUG_BYTES);
+          tma_load_2d(smem_u32(sBaug + (size_t)g * BNW * AUG_BYTES), &tmBaug, smem_u32(g_full + g), 0,
+                      j0);
+          for (int kc = 0; kc < kc_n; ++kc) {
+            ok = mbar_wait(smem_u32(s_empty + s), ph ^ 1, abort_flag);
+            if (!ok) break;
+            mbar_expect_tx(smem_u32(s_full + s), STAGE_W);
+            unsigned char* dst = sS + (size_t)s * STAGE_W;
+            tma_load_2d(smem_u32(dst), &tmA, smem_u32(s_full + s), kc * 64, (int)(rb * BMW));
+            tma_load_2d(smem_u32(dst + A_CHUNK_W), &tmB, smem_u32(s_full + s), kc * 64, j0);
+            if (++s == STAGES_W) {
+              s = 0;
+              ph ^= 1;
             }
           }
         }
-        for (int t = lane; t < p.K; t += 32) {
-          const int src = t < selfpos ? t : t + 1;
-          const uint64_t key = src < c2 ? lb[src] : KEY_NONE;
-          p.out_id[ro * p.K + t] = key == KEY_NONE ? -1 : key_id(key);
-          p.out_d2[ro * p.K + t] = key == KEY_NONE ? INF : key_dist(key);
-        }
-        __syncwarp();
       }
+      if (!ok) {
+        atomicOr(p.err, 1);
+        *abort_flag = 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      bool ok = mbar_wait(smem_u32(aa_full), 0, abort_flag);
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t t = 0;
+      const uint64_t adesc_aug = sdesc_sw32(smem_u32(sAaug));
+      for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
+        for (int64_t i = 0; i < nwalk && ok; ++i, ++t) {
+          const int b = (int)(t & 1);
+          const uint32_t tph = (uint32_t)((t >> 1) & 1);
+          ok = mbar_wait(smem_u32(t_empty + b), tph ^ 1, abort_flag);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(b * BNW);
+          for (int kc = 0; kc < kc_n; ++kc) {
+            ok = mbar_wait(smem_u32(s_full + s), ph, abort_flag);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(sS + (size_t)s * STAGE_W);
+            const uint64_t ad0 = sdesc_sw128(sa), bd0 = sdesc_sw128(sa + A_CHUNK_W);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              umma_bf16_id(d_tmem, ad0 + (uint64_t)((kk * 32) >> 4), bd0 + (uint64_t)((kk * 32) >> 4),
+                           IDESC_W, (kc | kk) ? 1u : 0u);
+            umma_commit(smem_u32(s_empty + s));
+            if (++s == STAGES_W) {
+              s = 0;
+              ph ^= 1;
+            }
+          }
+          if (!ok) break;
+          const int g = (int)(t & 1);
+          ok = mbar_wait(smem_u32(g_full + g), (uint32_t)((t >> 1) & 1), abort_flag);
+          if (!ok) break;
+          tc_fence_after();
+          umma_bf16_id(d_tmem, adesc_aug,
+                       sdesc_sw32(smem_u32(sBaug + (size_t)g * BNW * AUG_BYTES)), IDESC_W, 1u);
+          umma_commit(smem_u32(g_empty + g));
+          umma_commit(smem_u32(t_full + b));
+        }
+      }
+      if (!ok) {
+        atomicOr(p.err, 2);
+        *abort_flag = 1;
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: one thread per query row ----------------
+    const int ew = warp - 2;
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const int row_in_cta = q * 32 + lane;
+    float* st = stash + (size_t)(ew * 32 + lane) * 32;
+    const int sw = lane & 7;
+    const bool strict = p.tile_order == nullptr;
+    int64_t t = 0;
+    bool ok = true;
+    const float INF = __int_as_float(0x7f800000);
+    for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
+      const int64_t row = rb * BMW + row_in_cta;
+      const float nx = row < p.na ? p.a_norm[row] : 0.f;
+      float tau = INF;
+      if (p.tau_in && row < p.na) {
+        const float t0 = p.tau_in[row];
+        tau = t0 + (fabsf(t0) + fabsf(nx)) * p.tau_relax;
+      }
+      int cnt = 0;
+      uint64_t* wbuf = p.rowbuf + ((size_t)blockIdx.x * BMW + q * 32) * C;
+      uint64_t* buf = wbuf + (size_t)lane * C;
+      const int32_t* tl = p.tile_order ? p.tile_order + (int64_t)p.rb_cluster[rb] * p.tstride : nullptr;
+      int64_t tn = tl ? tl[0] : 0;
+      for (int64_t i = 0; i < nwalk; ++i, ++t) {
+        const int32_t j0 = (int32_t)(tn * BNW);
+        if (i + 1 < nwalk) tn = tl ? tl[i + 1] : i + 1;
+        const int b = (int)(t & 1);
+        ok = mbar_wait(smem_u32(t_full + b), (uint32_t)((t >> 1) & 1), abort_flag);
+        if (!__all_sync(0xffffffffu, ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BNW);
+        const float thr = 0.5f * (nx - tau);
+        const float ts = strict ? thr : nextafterf(thr, -INF);
+        uint32_t v0[32], v1[32];
+#pragma unroll 1
+        for (int c = 0; c < BNW / 32; c += 2) {
+          tmem_ld32(taddr + (uint32_t)c * 32, v0);
+          tmem_ld32(taddr + (uint32_t)c * 32 + 32, v1);
+          tmem_wait_ld(v0);
+          tmem_dep(v1);
+          if (c + 2 == BNW / 32) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(t_empty + b));
+          }
+          const bool pa = max32(v0) > ts;
+          const bool pb = max32(v1) > ts;
+          if (__any_sync(0xffffffffu, pa || pb)) {
+            if (pa) {
+              stash32(st, sw, v0);
+              cnt = append_stash(st, sw, ts, nx, j0 + c * 32, p.nb, buf, cnt);
+            }
+            if (pb) {
+              stash32(st, sw, v1);
+              cnt = append_stash(st, sw, ts, nx, j0 + c * 32 + 32, p.nb, buf, cnt);
+            }
+            __syncwarp();
+          }
+        }
+        compact_needed<C>(p, wbuf, cnt, tau);
+      }
+      if (!ok) break;
+      finish_rows<C>(p, wbuf, rb * BMW + q * 32, cnt, tau);
     }
     if (!ok && lane == 0) {
       atomicOr(p.err, 4);
@@ -520,10 +787,17 @@ struct TcMaps {
 };
 
 template <int C>
-void launch_tc(const TcMaps& m, TcArgs& a, int grid, size_t smem, cudaStream_t st) {
-  ensure_smem((const void*)k_knn_tc<C>, smem);
-  SSG_LAUNCH(k_knn_tc<C>, grid, THREADS, smem, st, m.a, m.b, m.a_aug, m.b_aug, a);
+void launch_tc(const TcMaps& m, TcArgs& a, int grid, size_t smem, cudaStream_t st, bool wide) {
+  if (wide) {
+    ensure_smem((const void*)k_knn_tc_wide<C>, smem);
+    SSG_LAUNCH(k_knn_tc_wide<C>, grid, THREADS_W, smem, st, m.a, m.b, m.a_aug, m.b_aug, a);
+  } else {
+    ensure_smem((const void*)k_knn_tc<C>, smem);
+    SSG_LAUNCH(k_knn_tc<C>, grid, THREADS, smem, st, m.a, m.b, m.a_aug, m.b_aug, a);
+  }
 }
+
+constexpr int MAX_D_WIDE = 4096;  // rows of up to this many values take the streamed kernel
 
 }  // namespace
 
@@ -537,7 +811,16 @@ bool knn_tc_available(int d) {
     return 0;
   }();
   const int kchunks = ((d + 63) & ~63) / 64;
-  return avail == 1 && d >= 1 && tc_smem_bytes(kchunks, 2) <= 225 * 1024;
+  if (avail != 1 || d < 1) return false;
+  return tc_smem_bytes(kchunks, 2) <= 225 * 1024 ||
+         (d <= MAX_D_WIDE && tcw_smem_bytes() <= 225 * 1024);
+}
+
+int knn_tc_max_k(int d, bool limited) {
+  const int kchunks = ((d + 63) & ~63) / 64;
+  const int bn = tc_smem_bytes(kchunks, 2) <= 225 * 1024 ? BN : BNW;
+  // a row buffer holds 1024 keys: KS + bn (twice KS for a limited walk), KS = K + 1
+  return limited ? (1024 - bn) / 2 - 1 : 1024 - bn - 1;
 }
 
 void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, const float* B,
@@ -548,24 +831,27 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   const int kchunks = dp / 64;
   int stages = MAX_STAGES;
   while (stages > 2 && tc_smem_bytes(kchunks, stages) > 225 * 1024) --stages;
-  SSG_REQUIRE(tc_smem_bytes(kchunks, stages) <= 225 * 1024, SSG_EINVAL,
+  // rows that do not fit the resident pipeline stream through the wide kernel
+  const bool wide = tc_smem_bytes(kchunks, stages) > 225 * 1024;
+  SSG_REQUIRE(!wide || (d <= MAX_D_WIDE && tcw_smem_bytes() <= 225 * 1024), SSG_EINVAL,
               "tensor-core kNN: d = %d is too large for the shared-memory pipeline", d);
+  const int bm = wide ? BMW : BM, bn = wide ? BNW : BN;
   const int KS = self ? K + 1 : K;
   // Near-first column order for large self-joins with a deep top-K (where the streaming
   // threshold otherwise falls slowly and many candidates are appended).
   KnnOrder ord;
   Scratch<float> norm_p;
-  // tile limits come in 128-point tiles; the walk counts BN-column tiles
-  max_tiles *= API_TILE / BN;
+  // tile limits come in 128-point tiles; the walk counts bn-column tiles
+  if (max_tiles > 0) max_tiles = (int)ceil_div((int64_t)max_tiles * API_TILE, bn);
   // same: the query rows are the base rows (a self-join); with ex.qid the query rows are a
   // gathered subset of the base and only the self column is excluded
   const bool same = self && !ex.qid;
-  SSG_REQUIRE(max_tiles == 0 || (same && knn_order_fits(na, BN)), SSG_EINVAL,
+  SSG_REQUIRE(max_tiles == 0 || (same && knn_order_fits(na, bn)), SSG_EINVAL,
               "a tile limit needs a self-join whose cluster order fits");
   const bool ordered =
-      max_tiles > 0 || (same && na >= (1 << 16) && K >= 16 && knn_order_fits(na, BN));
+      max_tiles > 0 || (same && na >= (1 << 16) && K >= 16 && knn_order_fits(na, bn));
   if (ordered) {
-    knn_cluster_order(A, lda, d, na, BM, BN, st, ord, max_tiles,
+    knn_cluster_order(A, lda, d, na, bm, bn, st, ord, max_tiles,
                       ex.order_norm ? ex.order_norm : a_norm);
     norm_p.alloc((size_t)na, st);
   }
@@ -590,23 +876,25 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
              nb, aug_b.p, err.p, approx ? 1 : 0);
   SSG_LAUNCH(k_aug_ones, 1, 256, 0, st, aug_a.p);
   TcMaps maps;
-  maps.a = make_map(ab.p, na, dp, 64, BM, CU_TENSOR_MAP_SWIZZLE_128B);
-  maps.b = make_map(bptr, nb, dp, 64, BN, CU_TENSOR_MAP_SWIZZLE_128B);
-  maps.a_aug = make_map(aug_a.p, BM, AUG, AUG, BM, CU_TENSOR_MAP_SWIZZLE_32B);
-  maps.b_aug = make_map(aug_b.p, nb, AUG, AUG, BN, CU_TENSOR_MAP_SWIZZLE_32B);
-  const int64_t nrb = ceil_div(na, BM);
+  maps.a = make_map(ab.p, na, dp, 64, bm, CU_TENSOR_MAP_SWIZZLE_128B);
+  maps.b = make_map(bptr, nb, dp, 64, bn, CU_TENSOR_MAP_SWIZZLE_128B);
+  maps.a_aug = make_map(aug_a.p, BM, AUG, AUG, bm, CU_TENSOR_MAP_SWIZZLE_32B);
+  maps.b_aug = make_map(aug_b.p, nb, AUG, AUG, bn, CU_TENSOR_MAP_SWIZZLE_32B);
+  const int64_t nrb = ceil_div(na, bm);
   const int grid = (int)std::min<int64_t>(nrb, num_sms());
   // A row buffer holds C keys and is compacted once a tile could overflow it.  A limited
   // walk spends most of its tiles while the threshold is still falling, so it gets room
   // for about KS more keys between compactions.
-  const int need = max_tiles > 0 ? 2 * KS + BN : KS + BN;
+  const int need = max_tiles > 0 ? 2 * KS + bn : KS + bn;
+  SSG_REQUIRE(need <= 1024, SSG_EINVAL, "tensor-core kNN: K = %d is too large for %d-column tiles",
+              K, bn);
   const int C = need <= 256 ? 256 : (need <= 512 ? 512 : 1024);
-  Scratch<uint64_t> rowbuf((size_t)grid * BM * C, st);
+  Scratch<uint64_t> rowbuf((size_t)grid * bm * C, st);
   TcArgs a{};
   a.a_norm = a_norm;
   a.na = na;
   a.nb = nb;
-  a.ntiles = ceil_div(nb, BN);
+  a.ntiles = ceil_div(nb, bn);
   a.nwalk = max_tiles > 0 ? std::min<int64_t>(a.ntiles, max_tiles) : a.ntiles;
   a.tstride = ordered ? ord.tstride : a.ntiles;
   a.kchunks = kchunks;
@@ -614,7 +902,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   a.self = self;
   a.KS = KS;
   a.K = K;
-  a.trig = C - BN;
+  a.trig = C - bn;
   a.rowbuf = rowbuf.p;
   a.out_id = out_id;
   a.out_d2 = out_d2;
@@ -628,21 +916,21 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
     a.tile_order = ord.tile_order.p;
     a.rb_cluster = ord.rb_cluster.p;
   }
-  const size_t smem = tc_smem_bytes(kchunks, stages);
+  const size_t smem = wide ? tcw_smem_bytes() : tc_smem_bytes(kchunks, stages);
   auto launch = [&](TcArgs& args) {
     if (C == 256)
-      launch_tc<256>(maps, args, grid, smem, st);
+      launch_tc<256>(maps, args, grid, smem, st, wide);
     else if (C == 512)
-      launch_tc<512>(maps, args, grid, smem, st);
+      launch_tc<512>(maps, args, grid, smem, st, wide);
     else
-      launch_tc<1024>(maps, args, grid, smem, st);
+      launch_tc<1024>(maps, args, grid, smem, st, wide);
   };
   // Near-first full walks: a first launch over each block's prepass_tiles nearest tiles
   // only records each row's KS-th distance there, an upper bound of its KS-th distance over
   // all columns (the same values: the MMAs are the same); the full walk then admits only
   // columns at or below that bound, so its appends and compactions are few from the start.
   Scratch<float> tau0;
-  const int64_t pre_tiles = (int64_t)ex.prepass_tiles * (API_TILE / BN);
+  const int64_t pre_tiles = ceil_div((int64_t)ex.prepass_tiles * API_TILE, bn);
   const bool prepass = ordered && max_tiles == 0 && pre_tiles > 0 && a.ntiles > 2 * pre_tiles;
   if (gemm_timer) gemm_timer->start();
   if (prepass) {

@@ -155,7 +155,7 @@ void pool_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const
   const size_t smem = per_warp * wpb;
   ensure_smem((const void*)k_pool, smem);
   SSG_LAUNCH(k_pool, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, X8, ld, d, n, knn, K, L, cap,
-             log2h, own_first, exact, dist_rel_fp32(d), pool_id, pool_d2, pool_len, &dctr->order_fp64);
+             log2h, own_first, exact, dist_rel_team8(ld), pool_id, pool_d2, pool_len, &dctr->order_fp64);
 }
 
 void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
@@ -166,7 +166,7 @@ void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int6
   const size_t smem = (size_t)cap * 16 * wpb;
   ensure_smem((const void*)k_pool_cand, smem);
   SSG_LAUNCH(k_pool_cand, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, X8, ld, d, n, cand, KS,
-             L, cap, exact, dist_rel_fp32(d), pool_id, pool_d2, pool_len, &dctr->order_fp64);
+             L, cap, exact, dist_rel_team8(ld), pool_id, pool_d2, pool_len, &dctr->order_fp64);
 }
 
 // ---------------------------------------------------------------------------------------

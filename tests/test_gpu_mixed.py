@@ -145,18 +145,17 @@ def test_batch_shaped_index_equals_oracle(ssg):
     np.testing.assert_array_equal(_np(g.adj), o["adj"])
 
 
-def test_wide_rows_auto_takes_fp32_and_bf16_is_refused(ssg):
-    # d > 128: no tensor-core path; AUTO runs the exact fp32 path, BF16 is an argument error
+def test_wide_rows_through_the_tensor_cores(ssg):
+    # d = 960: the K-chunked tensor-core kernel, certified on these float rows; the plain
+    # fp32 path builds the same graph
     w = synth.gist_like(n=600, nq=0, n_clusters=8)
     nav = synth.nav_ids(w.n, 3, 59)
-    g = ssg.build(_cuda(w.base), 10, 30, 12, 60.0, nav=nav, prec="auto")
-    assert g.stats["gemm_prec_used"] == 0
     o = oracle.build_graph(w.base, 10, 30, 12, 60.0, nav)
-    np.testing.assert_array_equal(_np(g.deg), o["deg"])
-    np.testing.assert_array_equal(_np(g.adj), o["adj"])
-    with pytest.raises(ssg.SSGError) as e:
-        ssg.build(_cuda(w.base), 10, 30, 12, 60.0, nav=nav, prec="bf16")
-    assert e.value.status == 1
+    for prec, used in (("auto", 1), ("bf16", 1), ("fp32", 0)):
+        g = ssg.build(_cuda(w.base), 10, 30, 12, 60.0, nav=nav, prec=prec)
+        assert g.stats["gemm_prec_used"] == used
+        np.testing.assert_array_equal(_np(g.deg), o["deg"])
+        np.testing.assert_array_equal(_np(g.adj), o["adj"])
 
 
 def test_borderline_count_and_fp8_refused(ssg, fl):

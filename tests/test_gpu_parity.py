@@ -173,16 +173,15 @@ def test_knn_bf16_signed_integers(ssg):
     np.testing.assert_array_equal(_np(ids), ref_ids)
 
 
-def test_knn_wide_integer_rows_use_fp32(ssg):
-    """d > 128 does not fit the tensor-core pipeline: auto falls back to the (exact) fp32
-    path and an explicit bf16 request is refused."""
+def test_knn_wide_integer_rows(ssg):
+    """d > 128 streams through the K-chunked tensor-core kernel (exact on these integers);
+    the fp32 path gives the same rows."""
     base = synth.uniform_points(700, 130, 2130, integer=True, hi=100)
-    ids, d2 = ssg.knn(_cuda(base), 50, prec="auto")
     ref_ids, ref_d2 = oracle.knn_rows(base, 50)
-    np.testing.assert_array_equal(_np(ids), ref_ids)
-    np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
-    with pytest.raises(ssg.SSGError):
-        ssg.knn(_cuda(base), 50, prec="bf16")
+    for prec in ("auto", "bf16", "fp32"):
+        ids, d2 = ssg.knn(_cuda(base), 50, prec=prec)
+        np.testing.assert_array_equal(_np(ids), ref_ids)
+        np.testing.assert_array_equal(_np(d2), ref_d2.astype(np.float32))
 
 
 def test_ground_truth_bf16(ssg, intdata):

@@ -1,0 +1,103 @@
+"""Rows wider than 128 values on the tensor cores: the K-chunked kernel that streams the
+query rows with the base tiles (128 x 256 tiles, N = 256 MMAs).  Integer data that bf16
+holds exactly (with every distance exact in fp32) give the exact kNN rows directly; float
+data (the 960-d GIST-shaped set) go through the certified path.  Every result must equal
+the oracle's: kNN ids and distances, ground truth, and a whole build."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_06146_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ssg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_06146_gb300 import build_ext, ssg as S
+    build_ext.build()
+    S.lib()
+    return S
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _np(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,d,K,hi", [(1100, 130, 10, 100), (2100, 192, 50, 60), (777, 256, 100, 40),
+                                      (1500, 960, 30, 10), (300, 4096, 5, 3)])
+def test_wide_integer_rows_exact(ssg, n, d, K, hi):
+    """Ragged sizes (not multiples of the 128-row or 256-column tiles), one to 64 chunks."""
+    base = synth.uniform_points(n, d, 3000 + d, integer=True, hi=hi)
+    ids, d2 = ssg.knn(_cuda(base), K, prec="bf16")
+    oid, od2 = oracle.knn_rows(base, K)
+    np.testing.assert_array_equal(_np(ids), oid)
+    np.testing.assert_array_equal(_np(d2), od2.astype(np.float32))
+
+
+def test_wide_duplicates_settled_by_id(ssg):
+    rng = np.random.default_rng(41)
+    base = rng.integers(0, 8, size=(900, 200)).astype(np.float32)
+    base[rng.choice(900, 300, replace=False)] = base[7]
+    ids, d2 = ssg.knn(_cuda(base), 40, prec="bf16")
+    oid, od2 = oracle.knn_rows(base, 40)
+    np.testing.assert_array_equal(_np(ids), oid)
+    np.testing.assert_array_equal(_np(d2), od2.astype(np.float32))
+
+
+def test_wide_near_first_order(ssg):
+    """70,000 rows: the self-join walks the cluster order (nearest cluster's tiles first)."""
+    w = synth.sift_like(n=70_000, d=160, nq=0, n_clusters=70)
+    base = np.minimum(w.base, 60.0).astype(np.float32)
+    ids, d2 = ssg.knn(_cuda(base), 50, prec="bf16")
+    ids, d2 = _np(ids), _np(d2)
+    rows = np.sort(np.random.default_rng(5).choice(base.shape[0], 150, replace=False))
+    oid, od2 = oracle.knn_rows(base, 50, rows=rows)
+    np.testing.assert_array_equal(ids[rows], oid)
+    np.testing.assert_array_equal(d2[rows], od2.astype(np.float32))
+
+
+def test_wide_float_certified(ssg):
+    w = synth.gist_like(n=2_500, nq=50, n_clusters=10)
+    for prec in ("bf16", "auto"):
+        ids, d2 = ssg.knn(_cuda(w.base), 40, prec=prec)
+        oid, od2 = oracle.knn_rows(w.base, 40)
+        np.testing.assert_array_equal(_np(ids), oid)
+        np.testing.assert_array_equal(_np(d2), od2.astype(np.float32))
+    gi, gd = ssg.knn_query(_cuda(w.base), _cuda(w.queries), 10)
+    oi, od = oracle.knn_queries(w.base, w.queries, 10)
+    np.testing.assert_array_equal(_np(gi), oi)
+    np.testing.assert_array_equal(_np(gd), od.astype(np.float32))
+
+
+def test_wide_build_equals_oracle(ssg):
+    """A GIST-shaped index (960-d, float in [0, 1]): bf16 kNN through the tensor cores,
+    certified, then the exact pools, prune, reverse merge and connectivity."""
+    w = synth.gist_like(n=1_200, nq=60, n_clusters=8)
+    nav = synth.nav_ids(w.n, 4, 61)
+    b = _cuda(w.base)
+    g = ssg.build(b, 30, 80, 20, 60.0, nav=nav)
+    assert g.stats["gemm_prec_used"] == ssg.PREC["bf16"]
+    o = oracle.build_graph(w.base, 30, 80, 20, 60.0, nav)
+    np.testing.assert_array_equal(_np(g.deg), o["deg"])
+    np.testing.assert_array_equal(_np(g.adj), o["adj"])
+    g32 = ssg.build(b, 30, 80, 20, 60.0, nav=nav, prec="fp32")
+    np.testing.assert_array_equal(_np(g32.adj), o["adj"])
+
+
+def test_too_wide_rows_refused_for_bf16(ssg):
+    base = synth.uniform_points(200, 4100, 3999, integer=True, hi=3)
+    ids, d2 = ssg.knn(_cuda(base), 5, prec="auto")
+    oid, od2 = oracle.knn_rows(base, 5)
+    np.testing.assert_array_equal(_np(ids), oid)
+    with pytest.raises(ssg.SSGError):
+        ssg.knn(_cuda(base), 5, prec="bf16")
