@@ -122,7 +122,12 @@ typedef struct {
                                sampled to size the bf16 candidate slack, 0..4096),
                                knn_slack_quantile (fraction of sampled rows the slack must
                                certify, 0.5..1), knn_prepass_tiles (tiles of the first,
-                               threshold-only walk of the tensor-core kNN, 0..4096, 0 = none) */
+                               threshold-only walk of the tensor-core kNN, 0..4096, 0 = none),
+                               knn_stream_rows (1: rows of up to 128 values also take the
+                               K-chunked 128 x 256-tile kernel), prune_warps (warps per
+                               block of the batched prune, 0 = automatic, up to 16),
+                               prune_bucket_width (pool lengths per bucket of the batched
+                               prune's longest-first order, 1..1024) */
 } ssg_build_opts;
 
 /* Per-build measurements (all times from CUDA events on the build stream). */
@@ -317,18 +322,36 @@ ssg_status ssg_build_host(const float* base_host, int64_t n, int32_t d, int32_t 
 /* Many independent indices at once (the multi-tenant case): index i is built from the
  * device array bases[i] (float32 [n[i]][d[i]]) with K[i], L[i], R[i], alpha_deg[i] and the
  * shared opts (its navigating nodes drawn from opts->seed; opts->nav_ids_host must be
- * NULL), into graphs[i].  Builds run concurrently on n_streams (1..64) internal streams,
- * each driven by its own host thread and taking the largest remaining index (n^2 d) next,
- * so small indices share the GPU.  Each graph equals what ssg_build returns for the same
- * input, bit for bit.  stats (NULL or count entries) gets each build's stats.  The call
- * returns when every build has finished; on failure it returns the first failing status,
- * ssg_last_error() names the index, and graphs[] keeps the builds that succeeded (the
- * others are NULL). */
+ * NULL), into graphs[i].  Three phases: (1) every index's kNN graph and pools, on
+ * n_streams (1..64) internal streams, each driven by its own host thread, the indices
+ * dealt out largest first (n^2 d) to the least loaded stream; (2) one persistent prune
+ * launch per row shape class over the (index, node) work items of every index (indices
+ * whose data take the tensor-core Gram prune it in phase 1), the items bucketed by pool
+ * length and handed out longest first, the launches recorded once into a CUDA graph and
+ * replayed; (3) every index's reverse merge and connectivity, as in (1).  Launch
+ * parameters come from opts->tune_table (see ssg_autotune_batched).  Each graph equals
+ * what ssg_build returns for the same input, bit for bit.  stats (NULL or count entries)
+ * gets each build's stats (ms_prune: the shared phase-2 time).  The call returns when every
+ * build has finished; on failure it returns the first failing status, ssg_last_error()
+ * names the index, and graphs[] holds no graph (all NULL). */
 ssg_status ssg_build_batched(int32_t count, const float* const* bases, const int64_t* n,
                              const int32_t* d, const int32_t* K, const int32_t* L,
                              const int32_t* R, const double* alpha_deg,
                              const ssg_build_opts* opts, int32_t n_streams, ssg_graph** graphs,
                              ssg_build_stats* stats);
+
+/* Autotuner of ssg_build_batched's launch parameters (no paper counterpart): on the four
+ * largest indices of the batch (same arguments as ssg_build_batched) it times the batched
+ * prune for 2, 4 and 8 warps per block and pool-length buckets 16, 64 and 1,024 wide, and
+ * the resident (256 x 128 tiles) against the streamed (128 x 256 tiles) kNN kernel for
+ * rows of up to 128 values, then writes the fastest choice as a tune_table file at path_out
+ * (prune_warps, prune_bucket_width, knn_stream_rows).  best_ms_host (nullable, 2 entries)
+ * receives the best batched-prune and kNN times.  EIO if the file cannot be written. */
+ssg_status ssg_autotune_batched(int32_t count, const float* const* bases, const int64_t* n,
+                                const int32_t* d, const int32_t* K, const int32_t* L,
+                                const int32_t* R, const double* alpha_deg,
+                                const ssg_build_opts* opts, const char* path_out,
+                                double* best_ms_host);
 
 /* Device views of a graph (no copies).  Any output pointer may be NULL. */
 ssg_status ssg_graph_view(const ssg_graph* g, const int32_t** adj, const int32_t** deg,

@@ -162,6 +162,19 @@ static KnnTune read_tune_table(const char* path) {
       SSG_REQUIRE(v >= 0 && v <= 4096 && v == std::floor(v), SSG_EINVAL,
                   "tune_table %s:%d: knn_prepass_tiles must be an integer in [0, 4096]", path, ln);
       t.prepass_tiles = (int)v;
+    } else if (!strcmp(name, "prune_warps")) {
+      SSG_REQUIRE(v >= 0 && v <= 16 && v == std::floor(v), SSG_EINVAL,
+                  "tune_table %s:%d: prune_warps must be an integer in [0, 16]", path, ln);
+      t.prune_warps = (int)v;
+    } else if (!strcmp(name, "prune_bucket_width")) {
+      SSG_REQUIRE(v >= 1 && v <= 1024 && v == std::floor(v), SSG_EINVAL,
+                  "tune_table %s:%d: prune_bucket_width must be an integer in [1, 1024]", path,
+                  ln);
+      t.prune_bucket_width = (int)v;
+    } else if (!strcmp(name, "knn_stream_rows")) {
+      SSG_REQUIRE(v == 0 || v == 1, SSG_EINVAL, "tune_table %s:%d: knn_stream_rows must be 0 or 1",
+                  path, ln);
+      t.stream_rows = (int)v;
     } else if (!strcmp(name, "knn_slack_quantile")) {
       SSG_REQUIRE(v >= 0.5 && v <= 1.0, SSG_EINVAL,
                   "tune_table %s:%d: knn_slack_quantile must lie in [0.5, 1]", path, ln);
@@ -272,6 +285,7 @@ static KnnResult knn_any(const Ingested& a, int64_t na, const Ingested& b, int64
   if (path == 1) {
     TcExtra ex;
     ex.prepass_tiles = tune.prepass_tiles;
+    ex.stream_rows = tune.stream_rows;
     knn_exact_tc(a.rows.p, na, a.rows.ld, a.norms.p, b.rows.p, nb, b.rows.ld, b.norms.p, d, self, K,
                  ids, d2, st, t_gemm, 0, false, ex);
   } else if (path == 2) {
@@ -472,205 +486,292 @@ ssg_status ssg_recall_hits(const int32_t* found, int32_t ld_found, const int32_t
   });
 }
 
+// ---- the build in stages (Alg. 3) --------------------------------------------------------
+// front: ingest, kNN graph (or Alg. 4's search-based pools) and pools; prune: the first SSG
+// prune; back: reverse merge, connectivity and the stats.  ssg_build runs them in a row; a
+// batch of indices runs every front, then one persistent prune over all of them, then every
+// back.
+struct BuildCtx {
+  const float* base = nullptr;
+  int64_t n = 0;
+  int d = 0, K = 0, L = 0, R = 0;
+  double alpha = 0.0;
+  ssg_build_opts opts{};
+  KnnTune tune;
+  cudaStream_t st = nullptr;
+  std::vector<int32_t> nav;
+  std::unique_ptr<ssg_graph> g;
+  Ingested in;
+  Scratch<Counters> ctr;
+  double cos_a = 0.0;
+  int kpath = 0;
+  bool gram_tc = false;
+  CertResult cert;
+  KnnResult kr;
+  Scratch<int32_t> pool_id, pool_len, adj0, deg0;
+  Scratch<float> pool_d2;
+  ssg_precision gram_used = SSG_PREC_FP32;
+  int64_t launches = 0;  // kernels launched for this build, over the threads that ran it
+  double prune_ms = -1.0;  // the shared batched prune's time (batched builds)
+  int64_t n_repair = 0;
+  int max_indeg = 0;
+  Counters hc{};
+  std::unique_ptr<StageTimer> t_all, t_ing, t_knn, t_gemm, t_pool, t_prune, t_rev, t_con;
+};
+
+// Checks the arguments, draws the navigating nodes and allocates the graph (host work only
+// until the graph's device arrays).
+static void build_setup(BuildCtx& c, const float* base, int64_t n, int32_t d, int32_t K,
+                        int32_t L, int32_t R, double alpha_deg, const ssg_build_opts* opts_in,
+                        cudaStream_t st) {
+  SSG_REQUIRE(base, SSG_EINVAL, "null pointer");
+  ssg_default_opts(&c.opts);
+  if (opts_in) c.opts = *opts_in;
+  const ssg_build_opts& opts = c.opts;
+  SSG_REQUIRE(n >= 2 && n < (1ll << 31) && d >= 1, SSG_EINVAL, "need 2 <= n < 2^31 and d >= 1");
+  SSG_REQUIRE(K >= 1 && K <= n - 1 && K <= 700, SSG_EINVAL, "need 1 <= K <= min(n - 1, 700)");
+  SSG_REQUIRE(L >= 1 && L + K <= 1023, SSG_EINVAL, "need L >= 1 and L + K <= 1023");
+  check_alpha(alpha_deg);
+  check_prune_fit(d, R);
+  check_prec(opts.gemm_prec, "gemm_prec");
+  check_prec(opts.gram_prec, "gram_prec");
+  SSG_REQUIRE(opts.cos_margin_fp64 >= 0.0 && opts.cos_margin_fp64 <= 0.5, SSG_EINVAL,
+              "cos_margin_fp64 must lie in [0, 0.5], got %g", opts.cos_margin_fp64);
+  c.tune = read_tune_table(opts.tune_table);
+  SSG_REQUIRE(opts.n_nav >= 1 && opts.n_nav <= n && opts.n_nav <= 4096, SSG_EINVAL,
+              "need 1 <= n_nav <= min(n, 4096)");
+  c.nav.resize((size_t)opts.n_nav);
+  if (opts.nav_ids_host) {
+    for (int t = 0; t < opts.n_nav; ++t) {
+      c.nav[t] = opts.nav_ids_host[t];
+      SSG_REQUIRE(c.nav[t] >= 0 && c.nav[t] < n, SSG_EINVAL, "navigating node %d out of range",
+                  c.nav[t]);
+      for (int u = 0; u < t; ++u)
+        SSG_REQUIRE(c.nav[u] != c.nav[t], SSG_EINVAL, "navigating nodes must be distinct");
+    }
+  } else {
+    ssg_status s = ssg_nav_ids(n, opts.n_nav, opts.seed, c.nav.data());
+    if (s != SSG_OK) throw Fail{s};
+  }
+  c.base = base;
+  c.n = n;
+  c.d = d;
+  c.K = K;
+  c.L = L;
+  c.R = R;
+  c.alpha = alpha_deg;
+  c.st = st;
+  c.t_all.reset(new StageTimer(st, "ssg_build"));
+  c.t_ing.reset(new StageTimer(st, "ingest"));
+  c.t_knn.reset(new StageTimer(st, "knn graph"));
+  c.t_gemm.reset(new StageTimer(st, "knn kernel"));
+  c.t_pool.reset(new StageTimer(st, "pools"));
+  c.t_prune.reset(new StageTimer(st, "prune"));
+  c.t_rev.reset(new StageTimer(st, "reverse merge"));
+  c.t_con.reset(new StageTimer(st, "connectivity"));
+  c.g.reset(new ssg_graph());
+  ssg_graph* g = c.g.get();
+  g->n = n;
+  g->d = d;
+  g->R = R;
+  g->n_nav = opts.n_nav;
+  g->alpha = alpha_deg;
+  g->nav_host = c.nav;
+}
+
+static void build_front(BuildCtx& c) {
+  const int64_t l0 = t_launches;
+  const int64_t n = c.n;
+  const int d = c.d, K = c.K, L = c.L;
+  const ssg_build_opts& opts = c.opts;
+  cudaStream_t st = c.st;
+  ssg_graph* g = c.g.get();
+  c.t_all->start();
+  SSG_CUDA(cudaMalloc(&g->adj, sizeof(int32_t) * n * c.R));
+  SSG_CUDA(cudaMalloc(&g->deg, sizeof(int32_t) * n));
+  SSG_CUDA(cudaMalloc(&g->nav_dev, sizeof(int32_t) * opts.n_nav));
+  SSG_CUDA(cudaMemcpyAsync(g->nav_dev, c.nav.data(), sizeof(int32_t) * opts.n_nav,
+                           cudaMemcpyHostToDevice, st));
+
+  c.t_ing->start();
+  ingest_all(c.base, n, d, st, c.in, true);
+  Ingested& in = c.in;
+  // integers 0..255: a byte copy of the rows (a quarter of the bytes, the same distances)
+  // for the pool, reverse-merge and search distances
+  if (in.info.exact && in.info.nonneg && in.info.max_abs <= 255.f) {
+    SSG_CUDA(cudaMalloc(&g->rows_u8, (size_t)n * in.rows.ld));
+    g->rows_ld = in.rows.ld;
+    g->rows_src = c.base;
+    rows_to_u8(in.rows.p, in.rows.ld, d, n, g->rows_u8, st);
+  }
+  c.t_ing->stop();
+  c.ctr.alloc(1, st);
+  SSG_CUDA(cudaMemsetAsync(c.ctr.p, 0, sizeof(Counters), st));
+  c.cos_a = cos_alpha_of(c.alpha);
+
+  const uint8_t* X8 = g->rows_u8;
+  c.kpath = knn_path(opts.gemm_prec, in.info, d);
+  const bool tc = c.kpath == 1;
+  c.gram_tc = opts.gram_prec != SSG_PREC_FP32 && in.info.bf16_exact;
+  SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || c.kpath != 0, SSG_EINVAL,
+              "bf16 distance GEMM needs sm_103 and d <= 4096");
+  c.pool_id.alloc((size_t)n * L, st);
+  c.pool_len.alloc((size_t)n, st);
+  c.pool_d2.alloc((size_t)n * L, st);
+  if (opts.pool_tiles > 0) {
+    // a1 + a2 of Alg. 4: no kNN graph; each node's L nearest among the points of its
+    // nearest pool_tiles tiles in the cluster order (the index searched on the fly)
+    const bool tc_any = opts.gemm_prec != SSG_PREC_FP32 && knn_tc_available(d);
+    SSG_REQUIRE(tc_any, SSG_EINVAL,
+                "search-based pools (pool_tiles > 0) need the bf16 tensor-core path: sm_103 "
+                "and d <= 4096");
+    SSG_REQUIRE(knn_order_fits(n, 128), SSG_EINVAL, "search-based pools: n too large");
+    const int lmax = knn_tc_max_k(d, true);
+    SSG_REQUIRE(L <= lmax, SSG_EINVAL, "search-based pools: need L <= %d for d = %d", lmax, d);
+    c.t_knn->start();
+    if (tc) {
+      // data exact in bf16: the selection itself is exact
+      knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d, 1,
+                   L, c.pool_id.p, c.pool_d2.p, st, c.t_gemm.get(), opts.pool_tiles);
+      c.t_knn->stop();
+      in.norms.release();
+      c.t_pool->start();
+      SSG_LAUNCH(k_pool_len_from_ids, (unsigned)ceil_div(n, 256), 256, 0, st, c.pool_id.p, n, L,
+                 c.pool_len.p);
+      c.t_pool->stop();
+    } else {
+      // other data: a bf16 selection of L + slack candidates (approximate distances), then
+      // each pool ordered from the original vectors as Alg. 3's pools are and cut to L
+      const int Lp = (int)std::min<int64_t>(
+          std::min(L + std::max(8, L / 4), knn_tc_max_k(d, true)), n - 1);
+      Scratch<int32_t> cid((size_t)n * Lp, st);
+      Scratch<float> cd2((size_t)n * Lp, st);
+      knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p, d, 1,
+                   Lp, cid.p, cd2.p, st, c.t_gemm.get(), opts.pool_tiles, true);
+      c.t_knn->stop();
+      in.norms.release();
+      c.t_pool->start();
+      pool_from_candidates(in.rows.p, X8, in.rows.ld, d, n, cid.p, Lp, L, in.info.exact, c.pool_id.p,
+                           c.pool_d2.p, c.pool_len.p, c.ctr.p, st);
+      c.t_pool->stop();
+    }
+  } else {
+    // a1: exact kNN graph
+    Scratch<int32_t> knn_id((size_t)n * K, st);
+    Scratch<float> knn_d2((size_t)n * K, st);
+    c.t_knn->start();
+    c.kr = knn_any(in, n, in, n, d, in.info, 1, K, opts.gemm_prec, knn_id.p, knn_d2.p, false, c.tune,
+                   c.ctr.p, st, c.t_gemm.get(), &c.cert);
+    c.t_knn->stop();
+    in.norms.release();
+
+    // a2: candidate pools
+    c.t_pool->start();
+    pool_run(in.rows.p, X8, in.rows.ld, d, n, knn_id.p, K, L, in.info.exact, c.pool_id.p,
+             c.pool_d2.p, c.pool_len.p, c.ctr.p, st, opts.pool_own_row_first);
+    c.t_pool->stop();
+  }
+  if (opts.debug_checks) {
+    const CheckResult r = check_pool(c.pool_id.p, c.pool_d2.p, c.pool_len.p, n, L, in.info.exact, d, st);
+    SSG_REQUIRE(r.row < 0, SSG_EINTERNAL, "debug check after the pools: row %lld: %s",
+                (long long)r.row, check_name(r.code));
+  }
+  c.adj0.alloc((size_t)n * c.R, st);
+  c.deg0.alloc((size_t)n, st);
+  c.launches += t_launches - l0;
+}
+
+// a3, one index at a time (a batch prunes on the warps in one persistent launch instead)
+static void build_prune(BuildCtx& c) {
+  const int64_t l0 = t_launches;
+  c.t_prune->start();
+  c.gram_used = prune_dispatch(c.gram_tc, c.in.rows.p, c.in.rows.ld, c.d, c.n, c.pool_id.p,
+                               c.pool_len.p, c.L, c.R, c.cos_a, c.opts.cos_margin_fp64, c.adj0.p,
+                               c.deg0.p, c.ctr.p, c.st);
+  c.t_prune->stop();
+  c.launches += t_launches - l0;
+}
+
+static void build_back(BuildCtx& c) {
+  const int64_t l0 = t_launches;
+  const int64_t n = c.n;
+  const int d = c.d, R = c.R;
+  cudaStream_t st = c.st;
+  ssg_graph* g = c.g.get();
+  Ingested& in = c.in;
+  auto debug_check = [&](const CheckResult& r, const char* stage) {
+    SSG_REQUIRE(r.row < 0, SSG_EINTERNAL, "debug check after %s: row %lld: %s", stage,
+                (long long)r.row, check_name(r.code));
+  };
+  if (c.opts.debug_checks) debug_check(check_adj(c.adj0.p, c.deg0.p, n, R, st), "the prune");
+  c.pool_id.release();
+  c.pool_d2.release();
+  c.pool_len.release();
+
+  // a4: reverse-neighbour merge
+  c.t_rev->start();
+  c.max_indeg = reverse_run(in.rows.p, g->rows_u8, in.rows.ld, d, n, c.adj0.p, c.deg0.p, R,
+                                c.cos_a, c.opts.cos_margin_fp64, in.info.exact, c.gram_tc, g->adj,
+                                g->deg, c.ctr.p, st);
+  c.t_rev->stop();
+  if (c.opts.debug_checks) debug_check(check_adj(g->adj, g->deg, n, R, st), "the reverse merge");
+  c.adj0.release();
+  c.deg0.release();
+
+  // a5: connectivity from the navigating nodes
+  c.t_con->start();
+  c.n_repair = connect_run(in.rows.p, in.rows.ld, d, n, g->adj, g->deg, R, g->nav_dev,
+                           c.nav.data(), c.opts.n_nav, st);
+  c.t_con->stop();
+  if (c.opts.debug_checks) debug_check(check_adj(g->adj, g->deg, n, R, st), "connectivity");
+  c.t_all->stop();
+
+  SSG_CUDA(cudaMemcpyAsync(&c.hc, c.ctr.p, sizeof(c.hc), cudaMemcpyDeviceToHost, st));
+  SSG_CUDA(cudaStreamSynchronize(st));
+  c.launches += t_launches - l0;
+}
+
+// The per-build measurements of a finished build.
+static void build_stats(BuildCtx& c, ssg_build_stats* stats) {
+  const Counters& hc = c.hc;
+  ssg_build_stats S{};
+  S.ms_ingest = c.t_ing->ms();
+  S.ms_knn = c.t_knn->ms();
+  S.ms_knn_gemm = c.t_gemm->ms();
+  S.ms_pool = c.t_pool->ms();
+  S.ms_prune = c.prune_ms >= 0.0 ? c.prune_ms : c.t_prune->ms();
+  S.ms_reverse = c.t_rev->ms();
+  S.ms_connect = c.t_con->ms();
+  S.ms_total = c.t_all->ms();
+  S.n_repair = c.n_repair;
+  S.n_angle_fp64 = (int64_t)hc.angle_fp64;
+  S.n_order_fp64 = (int64_t)hc.order_fp64;
+  S.n_knn_fallback_rows = c.kr.fallback_rows;
+  S.max_indegree = c.max_indeg;
+  S.exact_mode = c.in.info.exact;
+  S.gemm_prec_used = c.kpath == 0 ? SSG_PREC_FP32 : SSG_PREC_BF16;
+  S.gram_prec_used = c.gram_used;
+  S.n_angle_borderline = (int64_t)hc.angle_border;
+  S.knn_candidates = c.cert.candidates;
+  S.ms_knn_certify = c.kpath == 2 && c.opts.pool_tiles == 0 ? S.ms_knn - S.ms_knn_gemm : 0.0;
+  S.kernel_launches = c.launches;
+  S.search_row_bytes = c.g->rows_u8 ? 1 : 4;
+  *stats = S;
+}
+
 ssg_status ssg_build(const float* base, int64_t n, int32_t d, int32_t K, int32_t L, int32_t R,
                      double alpha_deg, const ssg_build_opts* opts_in, ssg_stream stream,
                      ssg_graph** out, ssg_build_stats* stats) {
   return guard([&] {
-    SSG_REQUIRE(base && out, SSG_EINVAL, "null pointer");
+    SSG_REQUIRE(out, SSG_EINVAL, "null pointer");
     *out = nullptr;
-    ssg_build_opts opts;
-    ssg_default_opts(&opts);
-    if (opts_in) opts = *opts_in;
-    SSG_REQUIRE(n >= 2 && n < (1ll << 31) && d >= 1, SSG_EINVAL, "need 2 <= n < 2^31 and d >= 1");
-    SSG_REQUIRE(K >= 1 && K <= n - 1 && K <= 700, SSG_EINVAL, "need 1 <= K <= min(n - 1, 700)");
-    SSG_REQUIRE(L >= 1 && L + K <= 1023, SSG_EINVAL, "need L >= 1 and L + K <= 1023");
-    check_alpha(alpha_deg);
-    check_prune_fit(d, R);
-    check_prec(opts.gemm_prec, "gemm_prec");
-    check_prec(opts.gram_prec, "gram_prec");
-    SSG_REQUIRE(opts.cos_margin_fp64 >= 0.0 && opts.cos_margin_fp64 <= 0.5, SSG_EINVAL,
-                "cos_margin_fp64 must lie in [0, 0.5], got %g", opts.cos_margin_fp64);
-    const KnnTune tune = read_tune_table(opts.tune_table);
-    SSG_REQUIRE(opts.n_nav >= 1 && opts.n_nav <= n && opts.n_nav <= 4096, SSG_EINVAL,
-                "need 1 <= n_nav <= min(n, 4096)");
-    std::vector<int32_t> nav((size_t)opts.n_nav);
-    if (opts.nav_ids_host) {
-      for (int t = 0; t < opts.n_nav; ++t) {
-        nav[t] = opts.nav_ids_host[t];
-        SSG_REQUIRE(nav[t] >= 0 && nav[t] < n, SSG_EINVAL, "navigating node %d out of range", nav[t]);
-        for (int u = 0; u < t; ++u)
-          SSG_REQUIRE(nav[u] != nav[t], SSG_EINVAL, "navigating nodes must be distinct");
-      }
-    } else {
-      ssg_status s = ssg_nav_ids(n, opts.n_nav, opts.seed, nav.data());
-      if (s != SSG_OK) throw Fail{s};
-    }
-    cudaStream_t st = (cudaStream_t)stream;
-    const int64_t launches0 = t_launches;
-    ssg_build_stats S{};
-    StageTimer t_all(st, "ssg_build"), t_ing(st, "ingest"), t_knn(st, "knn graph"),
-        t_gemm(st, "knn kernel"), t_pool(st, "pools"), t_prune(st, "prune"),
-        t_rev(st, "reverse merge"), t_con(st, "connectivity");
-    t_all.start();
-
-    ssg_graph* g = new ssg_graph();
-    std::unique_ptr<ssg_graph> gp(g);
-    g->n = n;
-    g->d = d;
-    g->R = R;
-    g->n_nav = opts.n_nav;
-    g->alpha = alpha_deg;
-    g->nav_host = nav;
-    SSG_CUDA(cudaMalloc(&g->adj, sizeof(int32_t) * n * R));
-    SSG_CUDA(cudaMalloc(&g->deg, sizeof(int32_t) * n));
-    SSG_CUDA(cudaMalloc(&g->nav_dev, sizeof(int32_t) * opts.n_nav));
-    SSG_CUDA(cudaMemcpyAsync(g->nav_dev, nav.data(), sizeof(int32_t) * opts.n_nav,
-                             cudaMemcpyHostToDevice, st));
-
-    t_ing.start();
-    Ingested in;
-    ingest_all(base, n, d, st, in, true);
-    // integers 0..255: a byte copy of the rows (a quarter of the bytes, the same distances)
-    // for the pool, reverse-merge and search distances
-    if (in.info.exact && in.info.nonneg && in.info.max_abs <= 255.f) {
-      SSG_CUDA(cudaMalloc(&g->rows_u8, (size_t)n * in.rows.ld));
-      g->rows_ld = in.rows.ld;
-      g->rows_src = base;
-      rows_to_u8(in.rows.p, in.rows.ld, d, n, g->rows_u8, st);
-    }
-    t_ing.stop();
-    Scratch<Counters> ctr(1, st);
-    SSG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), st));
-    const double cos_a = cos_alpha_of(alpha_deg);
-
-    const uint8_t* X8 = g->rows_u8;
-    const int kpath = knn_path(opts.gemm_prec, in.info, d);
-    const bool tc = kpath == 1;
-    const double border = opts.cos_margin_fp64;
-    const bool gram_tc = opts.gram_prec != SSG_PREC_FP32 && in.info.bf16_exact;
-    SSG_REQUIRE(opts.gemm_prec != SSG_PREC_BF16 || kpath != 0, SSG_EINVAL,
-                "bf16 distance GEMM needs sm_103 and d <= 4096");
-    CertResult cert;
-    Scratch<int32_t> pool_id((size_t)n * L, st), pool_len((size_t)n, st);
-    Scratch<float> pool_d2((size_t)n * L, st);
-    KnnResult kr;
-    if (opts.pool_tiles > 0) {
-      // a1 + a2 of Alg. 4: no kNN graph; each node's L nearest among the points of its
-      // nearest pool_tiles tiles in the cluster order (the index searched on the fly)
-      const bool tc_any = opts.gemm_prec != SSG_PREC_FP32 && knn_tc_available(d);
-      SSG_REQUIRE(tc_any, SSG_EINVAL,
-                  "search-based pools (pool_tiles > 0) need the bf16 tensor-core path: sm_103 "
-                  "and d <= 4096");
-      SSG_REQUIRE(knn_order_fits(n, 128), SSG_EINVAL, "search-based pools: n too large");
-      const int lmax = knn_tc_max_k(d, true);
-      SSG_REQUIRE(L <= lmax, SSG_EINVAL, "search-based pools: need L <= %d for d = %d", lmax, d);
-      t_knn.start();
-      if (tc) {
-        // data exact in bf16: the selection itself is exact
-        knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p,
-                     d, 1, L, pool_id.p, pool_d2.p, st, &t_gemm, opts.pool_tiles);
-        t_knn.stop();
-        in.norms.release();
-        t_pool.start();
-        SSG_LAUNCH(k_pool_len_from_ids, (unsigned)ceil_div(n, 256), 256, 0, st, pool_id.p, n, L,
-                   pool_len.p);
-        t_pool.stop();
-      } else {
-        // other data: a bf16 selection of L + slack candidates (approximate distances), then
-        // each pool ordered from the original vectors as Alg. 3's pools are and cut to L
-        const int Lp = (int)std::min<int64_t>(
-            std::min(L + std::max(8, L / 4), knn_tc_max_k(d, true)), n - 1);
-        Scratch<int32_t> cid((size_t)n * Lp, st);
-        Scratch<float> cd2((size_t)n * Lp, st);
-        knn_exact_tc(in.rows.p, n, in.rows.ld, in.norms.p, in.rows.p, n, in.rows.ld, in.norms.p,
-                     d, 1, Lp, cid.p, cd2.p, st, &t_gemm, opts.pool_tiles, true);
-        t_knn.stop();
-        in.norms.release();
-        t_pool.start();
-        pool_from_candidates(in.rows.p, X8, in.rows.ld, d, n, cid.p, Lp, L, in.info.exact, pool_id.p,
-                             pool_d2.p, pool_len.p, ctr.p, st);
-        t_pool.stop();
-      }
-    } else {
-      // a1: exact kNN graph
-      Scratch<int32_t> knn_id((size_t)n * K, st);
-      Scratch<float> knn_d2((size_t)n * K, st);
-      t_knn.start();
-      kr = knn_any(in, n, in, n, d, in.info, 1, K, opts.gemm_prec, knn_id.p, knn_d2.p, false, tune,
-                   ctr.p, st, &t_gemm, &cert);
-      t_knn.stop();
-      in.norms.release();
-
-      // a2: candidate pools
-      t_pool.start();
-      pool_run(in.rows.p, X8, in.rows.ld, d, n, knn_id.p, K, L, in.info.exact, pool_id.p, pool_d2.p,
-               pool_len.p, ctr.p, st, opts.pool_own_row_first);
-      t_pool.stop();
-    }
-
-    auto debug_check = [&](const CheckResult& r, const char* stage) {
-      SSG_REQUIRE(r.row < 0, SSG_EINTERNAL, "debug check after %s: row %lld: %s", stage,
-                  (long long)r.row, check_name(r.code));
-    };
-    if (opts.debug_checks)
-      debug_check(check_pool(pool_id.p, pool_d2.p, pool_len.p, n, L, in.info.exact, d, st),
-                  "the pools");
-
-    // a3: SSG prune
-    Scratch<int32_t> adj0((size_t)n * R, st), deg0((size_t)n, st);
-    t_prune.start();
-    const ssg_precision gram_used =
-        prune_dispatch(gram_tc, in.rows.p, in.rows.ld, d, n, pool_id.p, pool_len.p, L, R, cos_a,
-                       border, adj0.p, deg0.p, ctr.p, st);
-    t_prune.stop();
-    if (opts.debug_checks) debug_check(check_adj(adj0.p, deg0.p, n, R, st), "the prune");
-    pool_id.release();
-    pool_d2.release();
-    pool_len.release();
-
-    // a4: reverse-neighbour merge
-    t_rev.start();
-    const int maxin = reverse_run(in.rows.p, X8, in.rows.ld, d, n, adj0.p, deg0.p, R, cos_a, border,
-                                  in.info.exact, gram_tc, g->adj, g->deg, ctr.p, st);
-    t_rev.stop();
-    if (opts.debug_checks) debug_check(check_adj(g->adj, g->deg, n, R, st), "the reverse merge");
-    adj0.release();
-    deg0.release();
-
-    // a5: connectivity from the navigating nodes
-    t_con.start();
-    const int64_t rep = connect_run(in.rows.p, in.rows.ld, d, n, g->adj, g->deg, R, g->nav_dev,
-                                    nav.data(), opts.n_nav, st);
-    t_con.stop();
-    if (opts.debug_checks) debug_check(check_adj(g->adj, g->deg, n, R, st), "connectivity");
-    t_all.stop();
-
-    Counters hc;
-    SSG_CUDA(cudaMemcpyAsync(&hc, ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
-    SSG_CUDA(cudaStreamSynchronize(st));
-    S.ms_ingest = t_ing.ms();
-    S.ms_knn = t_knn.ms();
-    S.ms_knn_gemm = t_gemm.ms();
-    S.ms_pool = t_pool.ms();
-    S.ms_prune = t_prune.ms();
-    S.ms_reverse = t_rev.ms();
-    S.ms_connect = t_con.ms();
-    S.ms_total = t_all.ms();
-    S.n_repair = rep;
-    S.n_angle_fp64 = (int64_t)hc.angle_fp64;
-    S.n_order_fp64 = (int64_t)hc.order_fp64;
-    S.n_knn_fallback_rows = kr.fallback_rows;
-    S.max_indegree = maxin;
-    S.exact_mode = in.info.exact;
-    S.gemm_prec_used = kpath == 0 ? SSG_PREC_FP32 : SSG_PREC_BF16;
-    S.gram_prec_used = gram_used;
-    S.n_angle_borderline = (int64_t)hc.angle_border;
-    S.knn_candidates = cert.candidates;
-    S.ms_knn_certify = kpath == 2 && opts.pool_tiles == 0 ? S.ms_knn - S.ms_knn_gemm : 0.0;
-    S.kernel_launches = t_launches - launches0;
-    S.search_row_bytes = g->rows_u8 ? 1 : 4;
-    if (stats) *stats = S;
-    *out = gp.release();
+    BuildCtx c;
+    build_setup(c, base, n, d, K, L, R, alpha_deg, opts_in, (cudaStream_t)stream);
+    build_front(c);
+    build_prune(c);
+    build_back(c);
+    if (stats) build_stats(c, stats);
+    *out = c.g.release();
   });
 }
 
@@ -687,46 +788,247 @@ ssg_status ssg_build_batched(int32_t count, const float* const* bases, const int
     SSG_REQUIRE(!opts || !opts->nav_ids_host, SSG_EINVAL,
                 "batched builds draw navigating nodes from the seed (nav_ids_host must be NULL)");
     for (int32_t i = 0; i < count; ++i) graphs[i] = nullptr;
-    // largest work first (n^2 d: the kNN graph dominates), so the tail is short
+    int dev = 0;
+    SSG_CUDA(cudaGetDevice(&dev));
+    const int nt = std::min<int32_t>(n_streams, count);
+    std::vector<cudaStream_t> streams((size_t)nt + 1, nullptr);
+    struct StreamsGuard {
+      std::vector<cudaStream_t>& v;
+      ~StreamsGuard() {
+        for (cudaStream_t s : v)
+          if (s) cudaStreamDestroy(s);
+      }
+    } sg{streams};
+    for (int t = 0; t <= nt; ++t)
+      SSG_CUDA(cudaStreamCreateWithFlags(&streams[t], cudaStreamNonBlocking));
+    // every index checked and set up first (host work), so that no build starts on a batch
+    // with a bad member
+    std::vector<std::unique_ptr<BuildCtx>> ctx((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+      ctx[i].reset(new BuildCtx());
+      try {
+        build_setup(*ctx[i], bases[i], n[i], d[i], K[i], L[i], R[i], alpha_deg[i], opts, nullptr);
+      } catch (const Fail& e) {
+        const std::string m = ssg_last_error();
+        set_error("index %d: %s", i, m.c_str());
+        throw;
+      }
+    }
+    // the largest work (n^2 d: the kNN graph dominates) first, each index to the least
+    // loaded stream, so every stream's share ends at about the same time
     std::vector<int32_t> order((size_t)count);
     for (int32_t i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
       return (double)n[a] * n[a] * d[a] > (double)n[b] * n[b] * d[b];
     });
-    int dev = 0;
-    SSG_CUDA(cudaGetDevice(&dev));
-    const int nt = std::min<int32_t>(n_streams, count);
-    std::vector<cudaStream_t> streams((size_t)nt, nullptr);
-    for (int t = 0; t < nt; ++t)
-      SSG_CUDA(cudaStreamCreateWithFlags(&streams[t], cudaStreamNonBlocking));
-    std::atomic<int32_t> next{0};
+    std::vector<std::vector<int32_t>> share((size_t)nt);
+    std::vector<double> load((size_t)nt, 0.0);
+    for (int32_t i : order) {
+      const int t = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      share[t].push_back(i);
+      load[t] += (double)n[i] * n[i] * d[i];
+      ctx[i]->st = streams[t];
+    }
+    // rebuild the stage timers on the index's stream
+    for (int32_t i = 0; i < count; ++i) {
+      BuildCtx& c = *ctx[i];
+      c.t_all.reset(new StageTimer(c.st, "ssg_build"));
+      c.t_ing.reset(new StageTimer(c.st, "ingest"));
+      c.t_knn.reset(new StageTimer(c.st, "knn graph"));
+      c.t_gemm.reset(new StageTimer(c.st, "knn kernel"));
+      c.t_pool.reset(new StageTimer(c.st, "pools"));
+      c.t_prune.reset(new StageTimer(c.st, "prune"));
+      c.t_rev.reset(new StageTimer(c.st, "reverse merge"));
+      c.t_con.reset(new StageTimer(c.st, "connectivity"));
+    }
     std::mutex mu;
     ssg_status first = SSG_OK;
     std::string first_msg;
-    auto worker = [&](int t) {
-      cudaSetDevice(dev);
-      for (;;) {
-        const int32_t k = next.fetch_add(1);
-        if (k >= count) break;
-        const int32_t i = order[k];
-        const ssg_status s = ssg_build(bases[i], n[i], d[i], K[i], L[i], R[i], alpha_deg[i], opts,
-                                       (ssg_stream)streams[t], &graphs[i],
-                                       stats ? &stats[i] : nullptr);
-        if (s != SSG_OK) {
-          std::lock_guard<std::mutex> lk(mu);
-          if (first == SSG_OK) {
-            first = s;
-            first_msg = "index " + std::to_string(i) + ": " + ssg_last_error();
+    auto fail = [&](int32_t i, ssg_status s) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (first == SSG_OK) {
+        first = s;
+        first_msg = "index " + std::to_string(i) + ": " + ssg_last_error();
+      }
+    };
+    auto run_phase = [&](auto&& body) {
+      std::vector<std::thread> pool;
+      for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&, t] {
+          cudaSetDevice(dev);
+          for (int32_t i : share[t]) {
+            {
+              std::lock_guard<std::mutex> lk(mu);
+              if (first != SSG_OK) break;
+            }
+            const ssg_status s = guard([&] { body(*ctx[i]); });
+            if (s != SSG_OK) fail(i, s);
           }
+          cudaStreamSynchronize(streams[t]);
+        });
+      for (auto& th : pool) th.join();
+    };
+    // 1: every index's kNN graph and pools (indices whose data allow the tensor-core Gram
+    // prune it right away)
+    run_phase([&](BuildCtx& c) {
+      build_front(c);
+      if (c.gram_tc) build_prune(c);
+    });
+    SSG_REQUIRE(first == SSG_OK, first, "%s", first_msg.c_str());
+    // 2: every other index's prune in one persistent launch over (index, node) items
+    std::vector<PruneJob> jobs;
+    std::vector<int32_t> jobs_of;
+    for (int32_t i = 0; i < count; ++i) {
+      BuildCtx& c = *ctx[i];
+      if (c.gram_tc) continue;
+      PruneJob j{};
+      j.X = c.in.rows.p;
+      j.pool_id = c.pool_id.p;
+      j.pool_len = c.pool_len.p;
+      j.adj = c.adj0.p;
+      j.deg = c.deg0.p;
+      j.n64 = &c.ctr.p->angle_fp64;
+      j.nborder = &c.ctr.p->angle_border;
+      j.cosA64 = c.cos_a;
+      j.border = c.opts.cos_margin_fp64;
+      j.n = c.n;
+      j.ld = c.in.rows.ld;
+      j.d = c.d;
+      j.L = c.L;
+      j.R = c.R;
+      j.cosA32 = (float)c.cos_a;
+      j.margin = angle_margin_fp32(c.d) + (float)c.opts.cos_margin_fp64;
+      jobs.push_back(j);
+      jobs_of.push_back(i);
+    }
+    if (!jobs.empty()) {
+      PruneTune pt;
+      pt.warps = ctx[0]->tune.prune_warps;
+      pt.bucket_width = ctx[0]->tune.prune_bucket_width;
+      const double ms = prune_run_batched(jobs, pt, streams[nt]);
+      for (int32_t i : jobs_of) {
+        ctx[i]->gram_used = SSG_PREC_FP32;
+        ctx[i]->prune_ms = ms;
+      }
+    }
+    // 3: every index's reverse merge and connectivity
+    run_phase([&](BuildCtx& c) { build_back(c); });
+    SSG_REQUIRE(first == SSG_OK, first, "%s", first_msg.c_str());
+    for (int32_t i = 0; i < count; ++i) {
+      if (stats) build_stats(*ctx[i], &stats[i]);
+      graphs[i] = ctx[i]->g.release();
+    }
+  });
+}
+
+ssg_status ssg_autotune_batched(int32_t count, const float* const* bases, const int64_t* n,
+                               const int32_t* d, const int32_t* K, const int32_t* L,
+                               const int32_t* R, const double* alpha_deg,
+                               const ssg_build_opts* opts, const char* path_out,
+                               double* best_ms_host) {
+  return guard([&] {
+    SSG_REQUIRE(count >= 1 && bases && n && d && K && L && R && alpha_deg && path_out, SSG_EINVAL,
+                "need count >= 1 and non-null arrays and path");
+    SSG_REQUIRE(!opts || !opts->nav_ids_host, SSG_EINVAL, "nav_ids_host must be NULL");
+    cudaStream_t st = nullptr;
+    SSG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct SG {
+      cudaStream_t s;
+      ~SG() { cudaStreamDestroy(s); }
+    } sg{st};
+    // the sample: the four largest indices (by n^2 d), with the kNN graphs and pools the
+    // batched build would compute
+    std::vector<int32_t> order((size_t)count);
+    for (int32_t i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return (double)n[a] * n[a] * d[a] > (double)n[b] * n[b] * d[b];
+    });
+    order.resize((size_t)std::min<int32_t>(count, 4));
+    std::vector<std::unique_ptr<BuildCtx>> ctx;
+    double knn_ms[2] = {0.0, 0.0};
+    for (int32_t i : order) {
+      ctx.emplace_back(new BuildCtx());
+      BuildCtx& c = *ctx.back();
+      build_setup(c, bases[i], n[i], d[i], K[i], L[i], R[i], alpha_deg[i], opts, st);
+      if (knn_tc_available(d[i]) && d[i] <= 128 && c.opts.gemm_prec != SSG_PREC_FP32 &&
+          c.opts.pool_tiles == 0) {
+        // the kNN kernel: resident 256 x 128 tiles against streamed 128 x 256 tiles
+        for (int w = 0; w < 2; ++w) {
+          Ingested in;
+          ingest_all(bases[i], n[i], d[i], st, in, true);
+          Scratch<int32_t> ids((size_t)n[i] * K[i], st);
+          Scratch<float> dd((size_t)n[i] * K[i], st);
+          Scratch<Counters> ct(1, st);
+          SSG_CUDA(cudaMemsetAsync(ct.p, 0, sizeof(Counters), st));
+          KnnTune t = c.tune;
+          t.stream_rows = w;
+          StageTimer tm(st);
+          tm.start();
+          knn_any(in, n[i], in, n[i], d[i], in.info, 1, K[i], c.opts.gemm_prec, ids.p, dd.p, false, t,
+                  ct.p, st, nullptr, nullptr);
+          tm.stop();
+          knn_ms[w] += tm.ms();
         }
       }
-      cudaStreamSynchronize(streams[t]);
-    };
-    std::vector<std::thread> pool;
-    for (int t = 0; t < nt; ++t) pool.emplace_back(worker, t);
-    for (auto& th : pool) th.join();
-    for (int t = 0; t < nt; ++t) cudaStreamDestroy(streams[t]);
-    SSG_REQUIRE(first == SSG_OK, first, "%s", first_msg.c_str());
+      build_front(c);
+    }
+    std::vector<PruneJob> jobs;
+    for (auto& cp : ctx) {
+      BuildCtx& c = *cp;
+      PruneJob j{};
+      j.X = c.in.rows.p;
+      j.pool_id = c.pool_id.p;
+      j.pool_len = c.pool_len.p;
+      j.adj = c.adj0.p;
+      j.deg = c.deg0.p;
+      j.n64 = &c.ctr.p->angle_fp64;
+      j.nborder = &c.ctr.p->angle_border;
+      j.cosA64 = c.cos_a;
+      j.border = c.opts.cos_margin_fp64;
+      j.n = c.n;
+      j.ld = c.in.rows.ld;
+      j.d = c.d;
+      j.L = c.L;
+      j.R = c.R;
+      j.cosA32 = (float)c.cos_a;
+      j.margin = angle_margin_fp32(c.d) + (float)c.opts.cos_margin_fp64;
+      jobs.push_back(j);
+    }
+    // the batched prune: warps per block x pool-length bucket width, best of two runs each
+    PruneTune best;
+    double best_ms = 1e300;
+    for (int warps : {2, 4, 8})
+      for (int width : {16, 64, 1024}) {
+        PruneTune t;
+        t.warps = warps;
+        t.bucket_width = width;
+        double ms = 1e300;
+        try {
+          for (int r = 0; r < 2; ++r) ms = std::min(ms, prune_run_batched(jobs, t, st));
+        } catch (const Fail&) {
+          continue;  // this many warps do not fit shared memory for these rows
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
+      }
+    SSG_REQUIRE(best_ms < 1e300, SSG_EINTERNAL, "autotune: no batched prune configuration ran");
+    const int stream_rows = knn_ms[0] > 0.0 && knn_ms[1] < knn_ms[0] ? 1 : 0;
+    FILE* f = fopen(path_out, "w");
+    SSG_REQUIRE(f, SSG_EIO, "cannot open %s for writing", path_out);
+    const bool ok =
+        fprintf(f,
+                "# launch parameters chosen by ssg_autotune_batched on the %d largest of %d "
+                "indices\n# batched prune %.3f ms; kNN kernel resident %.3f ms, streamed %.3f ms\n"
+                "prune_warps = %d\nprune_bucket_width = %d\nknn_stream_rows = %d\n",
+                (int)order.size(), count, best_ms, knn_ms[0], knn_ms[1], best.warps,
+                best.bucket_width, stream_rows) > 0;
+    SSG_REQUIRE(fclose(f) == 0 && ok, SSG_EIO, "short write to %s", path_out);
+    if (best_ms_host) {
+      best_ms_host[0] = best_ms;
+      best_ms_host[1] = std::min(knn_ms[0], knn_ms[1] > 0.0 ? knn_ms[1] : knn_ms[0]);
+    }
   });
 }
 

@@ -1,6 +1,8 @@
 // Declarations shared by the library's translation units.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace ssg {
@@ -65,6 +67,8 @@ struct TcExtra {
   const int32_t* qid = nullptr;       // self with A a gathered subset of B: query row r is
                                       // base row qid[r]; outputs go to row r
   const float* order_norm = nullptr;  // norms of A as given, for the cluster order
+  int stream_rows = 0;                // 1: the K-chunked kernel (128 x 256 tiles, N = 256)
+                                      // also for rows that fit the resident one
   int prepass_tiles = 0;              // near-first self-joins: a first walk over this many
                                       // tiles gives each row an upper bound of its KS-th
                                       // distance, from which the full walk starts (0: off;
@@ -84,6 +88,9 @@ struct KnnTune {
   int sample_rows = 256;        // rows sampled to size the candidate count KS
   double slack_quantile = 0.99; // fraction of sampled rows KS must certify
   int prepass_tiles = 0;        // TcExtra::prepass_tiles of the kNN graph
+  int stream_rows = 0;          // TcExtra::stream_rows of the kNN graph
+  int prune_warps = 0;          // PruneTune of a batched build
+  int prune_bucket_width = 32;
 };
 struct CertResult {
   int64_t fallback_rows = 0;  // rows not certified by the first pass
@@ -138,6 +145,30 @@ void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int6
 void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
                const int32_t* pool_len, int L, int R, double cos_a, double border, int32_t* adj,
                int32_t* deg, Counters* dctr, cudaStream_t st);
+
+// One index's share of a batched prune (prune_run_batched).
+struct PruneJob {
+  const float* X;
+  const int32_t* pool_id;
+  const int32_t* pool_len;
+  int32_t* adj;
+  int32_t* deg;
+  unsigned long long* n64;
+  unsigned long long* nborder;
+  double cosA64, border;
+  int64_t n;
+  int ld, d, L, R;
+  float cosA32, margin;
+};
+// Launch parameters of the batched prune: warps per block (0: the largest that fits 96 KB
+// of shared memory, at most 8) and the width of the pool-length buckets.
+struct PruneTune {
+  int warps = 0;
+  int bucket_width = 32;
+};
+// The prune of every job's nodes in one persistent launch per row shape class (recorded in
+// a CUDA graph and launched once); returns its device time in ms.  Synchronises `st`.
+double prune_run_batched(const std::vector<PruneJob>& jobs, const PruneTune& tune, cudaStream_t st);
 
 // The same prune with each pool's Gram matrix on the tensor cores (data exact in bf16,
 // d <= 128, L <= 127, R <= 128; true where that path is available).

@@ -426,6 +426,7 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
   ex.out_thresh = thr.p;
   ex.order_norm = a_norm_raw;
   ex.prepass_tiles = tune.prepass_tiles;
+  ex.stream_rows = tune.stream_rows;
   knn_exact_tc(A, na, ld, nac, B, nb, ld, nbc.p, d, self, KS, cid.p, cd2.p, st, gemm_timer, 0, true,
                ex);
   cd2.release();

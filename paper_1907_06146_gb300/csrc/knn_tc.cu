@@ -832,7 +832,7 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   int stages = MAX_STAGES;
   while (stages > 2 && tc_smem_bytes(kchunks, stages) > 225 * 1024) --stages;
   // rows that do not fit the resident pipeline stream through the wide kernel
-  const bool wide = tc_smem_bytes(kchunks, stages) > 225 * 1024;
+  const bool wide = tc_smem_bytes(kchunks, stages) > 225 * 1024 || ex.stream_rows;
   SSG_REQUIRE(!wide || (d <= MAX_D_WIDE && tcw_smem_bytes() <= 225 * 1024), SSG_EINVAL,
               "tensor-core kNN: d = %d is too large for the shared-memory pipeline", d);
   const int bm = wide ? BMW : BM, bn = wide ? BNW : BN;

@@ -229,3 +229,209 @@ void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
 }
 
 }  // namespace ssg
+
+// ---------------------------------------------------------------------------------------
+// The prune of many indices at once (the batched build): one persistent launch per row
+// shape class over work items (index, node).  The items are bucketed by pool length and
+// handed out longest pools first from one atomic counter, so indices of very different
+// sizes and nodes of very different pool lengths share the GPU without a tail; every node
+// is pruned by the same warp routine as prune_run, so the adjacency is the same bit for bit.
+// ---------------------------------------------------------------------------------------
+namespace ssg {
+
+__global__ void k_prune_batched(const PruneJob* __restrict__ jobs, const int2* __restrict__ items,
+                                int64_t nitems, unsigned long long* __restrict__ next,
+                                float* __restrict__ Vg, size_t vg_stride, size_t warp_floats,
+                                int wide) {
+  extern __shared__ __align__(16) float smf[];
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
+  const int64_t gwarp = (int64_t)blockIdx.x * wpb + warp;
+  float* base = smf + (size_t)warp * warp_floats;
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(next, 1ull);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= (unsigned long long)nitems) break;
+    const int2 w = items[it];
+    const PruneJob& jb = jobs[w.x];
+    const int64_t i = w.y;
+    int32_t* out = jb.adj + i * jb.R;
+    const int32_t* cand = jb.pool_id + i * jb.L;
+    const int len = jb.pool_len[i];
+    int kept;
+    if (wide) {
+      const int d4 = (jb.d + 3) & ~3;
+      kept = warp_prune_node_wide(jb.X, jb.ld, jb.d, i, cand, len, jb.R, jb.cosA32, jb.cosA64,
+                                  jb.margin, Vg + (size_t)gwarp * vg_stride, base, base + d4,
+                                  base + 2 * d4, out, jb.n64, jb.border, jb.nborder);
+    } else {
+      const int D1 = prune_row_stride(jb.d);
+      float* xs = base + (size_t)(jb.R + 1) * D1;
+      kept = warp_prune_node(jb.X, jb.ld, jb.d, i, cand, len, jb.R, jb.cosA32, jb.cosA64,
+                             jb.margin, base, D1, xs, xs + D1, out, jb.n64, jb.border,
+                             jb.nborder);
+    }
+    for (int t = kept + lane; t < jb.R; t += 32) out[t] = -1;
+    if (lane == 0) jb.deg[i] = kept;
+    __syncwarp();
+  }
+}
+
+// Bucket of a pool length: buckets of `width` lengths, the longest first.
+__device__ __forceinline__ int pool_bucket(int len, int width, int nb) {
+  const int b = len / width;
+  return nb - 1 - (b < nb - 1 ? b : nb - 1);
+}
+
+// The job of flattened node g (first[j] = the first flattened node of job j).
+__device__ __forceinline__ int job_of(const int64_t* first, int njobs, int64_t g) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_bucket_count(const PruneJob* __restrict__ jobs, const int64_t* __restrict__ first,
+                               int njobs, int64_t total, int width, int nb,
+                               unsigned long long* __restrict__ counts) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int j = job_of(first, njobs, g);
+    const int len = jobs[j].pool_len[g - first[j]];
+    atomicAdd(counts + pool_bucket(len, width, nb), 1ull);
+  }
+}
+
+__global__ void k_bucket_scatter(const PruneJob* __restrict__ jobs, const int64_t* __restrict__ first,
+                                 int njobs, int64_t total, int width, int nb,
+                                 unsigned long long* __restrict__ cursor, int2* __restrict__ items) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int j = job_of(first, njobs, g);
+    const int64_t i = g - first[j];
+    const int len = jobs[j].pool_len[i];
+    const unsigned long long p = atomicAdd(cursor + pool_bucket(len, width, nb), 1ull);
+    items[p] = make_int2(j, (int)i);
+  }
+}
+
+double prune_run_batched(const std::vector<PruneJob>& jobs, const PruneTune& tune, cudaStream_t st) {
+  if (jobs.empty()) return 0.0;
+  // one launch per row shape class: rows whose R + 1 kept vectors fit shared memory, and
+  // wide rows (kept vectors in a device slot per warp)
+  std::vector<PruneJob> cls[2];
+  for (const PruneJob& j : jobs) cls[prune_is_wide(j.d, j.R) ? 1 : 0].push_back(j);
+  const int width = std::max(1, tune.bucket_width);
+  struct Prepared {
+    Scratch<PruneJob> dj;
+    Scratch<int2> items;
+    Scratch<float> Vg;
+    int64_t nitems = 0;
+    size_t warp_floats = 0, vg_stride = 0;
+    int wpb = 1, grid = 1;
+  } prep[2];
+  Scratch<unsigned long long> cnt(64, st), next(2, st);
+  for (int w = 0; w < 2; ++w) {
+    const std::vector<PruneJob>& js = cls[w];
+    if (js.empty()) continue;
+    Prepared& P = prep[w];
+    const int njobs = (int)js.size();
+    std::vector<int64_t> first((size_t)njobs);
+    int64_t total = 0;
+    int Lmax = 1, Rmax = 1, d4max = 4;
+    for (int j = 0; j < njobs; ++j) {
+      first[j] = total;
+      total += js[j].n;
+      Lmax = std::max(Lmax, js[j].L);
+      Rmax = std::max(Rmax, js[j].R);
+      d4max = std::max(d4max, (js[j].d + 3) & ~3);
+      P.warp_floats = std::max(P.warp_floats, w ? prune_wide_smem_floats(js[j].d, js[j].R)
+                                                : prune_smem_floats(js[j].d, js[j].R));
+    }
+    SSG_REQUIRE(total < (1ll << 31), SSG_EINVAL, "batched prune: more than 2^31 nodes");
+    const int nb = std::min(64, (Lmax + width) / width);
+    P.nitems = total;
+    P.dj.alloc((size_t)njobs, st);
+    SSG_CUDA(cudaMemcpyAsync(P.dj.p, js.data(), sizeof(PruneJob) * njobs, cudaMemcpyHostToDevice, st));
+    Scratch<int64_t> dfirst((size_t)njobs, st);
+    SSG_CUDA(cudaMemcpyAsync(dfirst.p, first.data(), sizeof(int64_t) * njobs, cudaMemcpyHostToDevice,
+                             st));
+    SSG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 64, st));
+    const int g = 8 * num_sms();
+    SSG_LAUNCH(k_bucket_count, g, 256, 0, st, P.dj.p, dfirst.p, njobs, total, width, nb, cnt.p);
+    unsigned long long hc[64];
+    SSG_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    unsigned long long off[64], acc = 0;
+    for (int b = 0; b < nb; ++b) {
+      off[b] = acc;
+      acc += hc[b];
+    }
+    SSG_CUDA(cudaMemcpyAsync(cnt.p, off, sizeof(unsigned long long) * nb, cudaMemcpyHostToDevice, st));
+    P.items.alloc((size_t)total, st);
+    SSG_LAUNCH(k_bucket_scatter, g, 256, 0, st, P.dj.p, dfirst.p, njobs, total, width, nb, cnt.p,
+               P.items.p);
+    const size_t per_warp = P.warp_floats * sizeof(float);
+    P.wpb = tune.warps > 0 ? tune.warps
+                           : (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
+    const size_t smem = per_warp * P.wpb;
+    SSG_REQUIRE(smem <= 225 * 1024, SSG_EINVAL, "batched prune: %d warps per block need %zu bytes",
+                P.wpb, smem);
+    ensure_smem((const void*)k_prune_batched, smem);
+    int per_sm = 0;
+    SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prune_batched, P.wpb * 32, smem));
+    P.grid = std::max(1, per_sm) * num_sms();
+    if (w) {
+      P.vg_stride = (size_t)(Rmax + 1) * d4max;
+      P.Vg.alloc((size_t)P.grid * P.wpb * P.vg_stride, st);
+    }
+    SSG_CUDA(cudaStreamSynchronize(st));  // the scatter done and every buffer in place
+  }
+  // the launches themselves, recorded once into a CUDA graph and replayed (no allocation
+  // or host synchronisation inside)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SSG_CUDA(cudaEventCreate(&e0));
+  SSG_CUDA(cudaEventCreate(&e1));
+  struct Cleanup {
+    cudaGraph_t& g;
+    cudaGraphExec_t& x;
+    cudaEvent_t& a;
+    cudaEvent_t& b;
+    ~Cleanup() {
+      if (x) cudaGraphExecDestroy(x);
+      if (g) cudaGraphDestroy(g);
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } cleanup{graph, exec, e0, e1};
+  SSG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t cap = cudaSuccess;
+  try {
+    SSG_CUDA(cudaMemsetAsync(next.p, 0, 2 * sizeof(unsigned long long), st));
+    for (int w = 0; w < 2; ++w) {
+      Prepared& P = prep[w];
+      if (P.nitems == 0) continue;
+      SSG_LAUNCH(k_prune_batched, P.grid, P.wpb * 32, P.warp_floats * sizeof(float) * P.wpb, st,
+                 P.dj.p, P.items.p, P.nitems, next.p + w, P.Vg.p, P.vg_stride, P.warp_floats, w);
+    }
+  } catch (...) {
+    cap = cudaErrorUnknown;
+  }
+  const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+  SSG_REQUIRE(cap == cudaSuccess, SSG_ECUDA, "batched prune: a launch failed during capture");
+  SSG_CUDA(ec);
+  SSG_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  SSG_CUDA(cudaEventRecord(e0, st));
+  SSG_CUDA(cudaGraphLaunch(exec, st));
+  SSG_CUDA(cudaEventRecord(e1, st));
+  SSG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  SSG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  return (double)ms;
+}
+
+}  // namespace ssg

@@ -109,6 +109,10 @@ SYMBOLS = {
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "ssg_autotune_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_char_p, ctypes.c_void_p]),
     "ssg_build_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
@@ -537,11 +541,7 @@ def build(base, K: int, L: int, R: int, alpha: float, n_nav: int = 10, nav=None,
     return g
 
 
-def build_batched(bases, K, L, R, alpha, n_nav: int = 10, seed=None, prec: str = "auto",
-                  n_streams: int = 8):
-    """Independent indices built concurrently (ssg_build_batched): bases is a list of
-    device float32 [n_i][d_i] tensors; K, L, R, alpha are scalars or per-index lists.
-    Returns the list of Graphs (each equal to ssg_build's for the same input)."""
+def _batch_args(bases, K, L, R, alpha):
     torch = _torch()
     bs = [_dev(b, torch.float32) for b in bases]
     m = len(bs)
@@ -553,9 +553,34 @@ def build_batched(bases, K, L, R, alpha, n_nav: int = 10, seed=None, prec: str =
     ptrs = (ctypes.c_void_p * m)(*[_ptr(b) for b in bs])
     ns = (ctypes.c_int64 * m)(*[b.shape[0] for b in bs])
     ds = (ctypes.c_int32 * m)(*[b.shape[1] for b in bs])
-    Ks, Ls, Rs = per(K, ctypes.c_int32), per(L, ctypes.c_int32), per(R, ctypes.c_int32)
-    As = per(alpha, ctypes.c_double)
+    return (bs, m, ptrs, ns, ds, per(K, ctypes.c_int32), per(L, ctypes.c_int32),
+            per(R, ctypes.c_int32), per(alpha, ctypes.c_double))
+
+
+def autotune_batched(bases, K, L, R, alpha, path: str, n_nav: int = 10, seed=None,
+                     prec: str = "auto"):
+    """Times the batched build's launch parameters on the batch's largest indices and writes
+    the fastest as a tune-table file at path (ssg_autotune_batched); returns (best batched
+    prune ms, best kNN ms)."""
+    torch = _torch()
+    bs, m, ptrs, ns, ds, Ks, Ls, Rs, As = _batch_args(bases, K, L, R, alpha)
     o, keep = _opts(n_nav, None, seed, prec)
+    best = (ctypes.c_double * 2)()
+    torch.cuda.synchronize()
+    _check(lib().ssg_autotune_batched(m, ptrs, ns, ds, Ks, Ls, Rs, As, ctypes.byref(o),
+                                      path.encode(), best))
+    del keep
+    return best[0], best[1]
+
+
+def build_batched(bases, K, L, R, alpha, n_nav: int = 10, seed=None, prec: str = "auto",
+                  n_streams: int = 8, tune_table=None):
+    """Independent indices built concurrently (ssg_build_batched): bases is a list of
+    device float32 [n_i][d_i] tensors; K, L, R, alpha are scalars or per-index lists.
+    Returns the list of Graphs (each equal to ssg_build's for the same input)."""
+    torch = _torch()
+    bs, m, ptrs, ns, ds, Ks, Ls, Rs, As = _batch_args(bases, K, L, R, alpha)
+    o, keep = _opts(n_nav, None, seed, prec, tune_table=tune_table)
     hs = (ctypes.c_void_p * m)()
     sts = (BuildStats * m)()
     torch.cuda.synchronize()  # the inputs are read on the library's own streams

@@ -58,3 +58,34 @@ def test_batched_matches_oracle(ssg):
     ref = oracle.build_graph(base, 12, 30, 10, 60.0, nav)
     np.testing.assert_array_equal(_cpu(gs[0].deg), ref["deg"])
     np.testing.assert_array_equal(_cpu(gs[0].adj), ref["adj"])
+
+
+def test_wide_rows_in_the_batch(ssg):
+    """A 960-d index (kept vectors in a device slot per warp: the second shape class of the
+    persistent prune) next to narrow ones."""
+    ws = [synth.gist_like(n=700, nq=0, n_clusters=6).base, synth.small(n=900, d=48, nq=0, seed=4310).base]
+    bases = [torch.from_numpy(b).cuda() for b in ws]
+    gs = ssg.build_batched(bases, 12, 40, 70, 60.0, n_streams=2)
+    for b, g in zip(bases, gs):
+        ref = ssg.build(b, 12, 40, 70, 60.0)
+        np.testing.assert_array_equal(_cpu(g.deg), _cpu(ref.deg))
+        np.testing.assert_array_equal(_cpu(g.adj), _cpu(ref.adj))
+
+
+def test_autotuned_batch_equals_one_by_one(ssg, tmp_path):
+    """The autotuner writes a tune table; a batch built with it equals the one-by-one builds
+    (launch parameters change the speed, not the graph)."""
+    bases = [torch.from_numpy(b).cuda() for b in _inputs()]
+    K, L, R, alpha = 20, 40, 16, 60.0
+    path = str(tmp_path / "batch_tune.txt")
+    prune_ms, knn_ms = ssg.autotune_batched(bases, K, L, R, alpha, path)
+    assert prune_ms > 0.0
+    text = open(path).read()
+    names = {ln.split("=")[0].strip() for ln in text.splitlines() if ln and not ln.startswith("#")}
+    assert names == {"prune_warps", "prune_bucket_width", "knn_stream_rows"}
+    gs = ssg.build_batched(bases, K, L, R, alpha, n_streams=4, tune_table=path)
+    for b, g in zip(bases, gs):
+        ref = ssg.build(b, K, L, R, alpha)
+        np.testing.assert_array_equal(_cpu(g.deg), _cpu(ref.deg))
+        np.testing.assert_array_equal(_cpu(g.adj), _cpu(ref.adj))
+    assert all(g.stats["ms_prune"] > 0.0 for g in gs)
