@@ -154,6 +154,9 @@ typedef struct {
   double ms_knn_certify;        /* of ms_knn on the certified bf16 path: all but the first
                                    tensor-core pass (centring, sizing KS, re-rank and
                                    certification, the passes over rows that failed) */
+  int64_t n_repair_knn_row;     /* of n_repair, the edges whose node was found in the
+                                   unreached node's own kNN row (same choice as a scan of all
+                                   reached nodes, made without one) */
 } ssg_build_stats;
 
 typedef struct ssg_graph ssg_graph; /* opaque, owned by the library; ssg_free releases it */

@@ -509,11 +509,12 @@ struct BuildCtx {
   CertResult cert;
   KnnResult kr;
   Scratch<int32_t> pool_id, pool_len, adj0, deg0;
+  Scratch<int32_t> knn_id;  // the exact kNN graph, kept for the connectivity repairs
   Scratch<float> pool_d2;
   ssg_precision gram_used = SSG_PREC_FP32;
   int64_t launches = 0;  // kernels launched for this build, over the threads that ran it
   double prune_ms = -1.0;  // the shared batched prune's time (batched builds)
-  int64_t n_repair = 0;
+  int64_t n_repair = 0, n_repair_knn = 0;
   int max_indeg = 0;
   Counters hc{};
   std::unique_ptr<StageTimer> t_all, t_ing, t_knn, t_gemm, t_pool, t_prune, t_rev, t_con;
@@ -657,7 +658,8 @@ static void build_front(BuildCtx& c) {
     }
   } else {
     // a1: exact kNN graph
-    Scratch<int32_t> knn_id((size_t)n * K, st);
+    c.knn_id.alloc((size_t)n * K, st);
+    Scratch<int32_t>& knn_id = c.knn_id;
     Scratch<float> knn_d2((size_t)n * K, st);
     c.t_knn->start();
     c.kr = knn_any(in, n, in, n, d, in.info, 1, K, opts.gemm_prec, knn_id.p, knn_d2.p, false, c.tune,
@@ -721,7 +723,8 @@ static void build_back(BuildCtx& c) {
   // a5: connectivity from the navigating nodes
   c.t_con->start();
   c.n_repair = connect_run(in.rows.p, in.rows.ld, d, n, g->adj, g->deg, R, g->nav_dev,
-                           c.nav.data(), c.opts.n_nav, st);
+                           c.nav.data(), c.opts.n_nav, st, c.knn_id.p, c.knn_id.p ? c.K : 0, &c.n_repair_knn);
+  c.knn_id.release();
   c.t_con->stop();
   if (c.opts.debug_checks) debug_check(check_adj(g->adj, g->deg, n, R, st), "connectivity");
   c.t_all->stop();
@@ -744,6 +747,7 @@ static void build_stats(BuildCtx& c, ssg_build_stats* stats) {
   S.ms_connect = c.t_con->ms();
   S.ms_total = c.t_all->ms();
   S.n_repair = c.n_repair;
+  S.n_repair_knn_row = c.n_repair_knn;
   S.n_angle_fp64 = (int64_t)hc.angle_fp64;
   S.n_order_fp64 = (int64_t)hc.order_fp64;
   S.n_knn_fallback_rows = c.kr.fallback_rows;

@@ -278,6 +278,138 @@ __global__ void k_bfs_small(const int32_t* __restrict__ adj, const int32_t* __re
   }
 }
 
+// Repairs that u's own kNN row settles, back to back in one block.  The row lists u's K
+// nearest nodes in exact (d2, id) order, so when some of them is reached and has a free
+// slot the first such one is the (d2, id)-smallest of all reached nodes with a free slot:
+// the same choice as the exhaustive argmin, without a pass over all n nodes.  Each round:
+// the smallest unreached u (from bitmap word `start` on), the link from the first
+// qualifying row entry, and the traversal from u while its frontier stays within `limit`.
+// Stops with s->u = n when every node is reached, with s->best = -3 when u's row has no
+// qualifying node (the exhaustive path takes u), or with s->bfs_state set when a frontier
+// outgrows the block (the grid-wide traversal finishes it).  *nrep += the repairs made.
+__global__ void __launch_bounds__(1024)
+    k_repair_knn(const int32_t* __restrict__ knn, int K, int32_t* __restrict__ adj,
+                 int32_t* __restrict__ deg, int R, uint32_t* __restrict__ bm, int64_t nw,
+                 int64_t n, int64_t start, int32_t* __restrict__ f0, int32_t* __restrict__ f1,
+                 int limit, RepairState* __restrict__ s, unsigned long long* __restrict__ nrep) {
+  __shared__ unsigned long long su;
+  __shared__ int sv, sfc[2];
+  const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nwarps = blockDim.x >> 5;
+  unsigned long long made = 0;
+  for (;;) {
+    // the smallest unreached id from word `start` on
+    for (;;) {
+      if (tid == 0) su = (unsigned long long)n;
+      __syncthreads();
+      const int64_t w = start + tid;
+      if (w < nw) {
+        uint32_t word = bm[w];
+        if (w == nw - 1 && (n & 31)) word |= ~((1u << (n & 31)) - 1u);
+        if (word != 0xffffffffu) atomicMin(&su, (unsigned long long)(w * 32 + __ffs(~word) - 1));
+      }
+      __syncthreads();
+      const bool stop = su < (unsigned long long)n || start + blockDim.x >= nw;
+      __syncthreads();
+      if (stop) break;
+      start += blockDim.x;
+    }
+    const int64_t u = (int64_t)su;
+    if (u >= n) {
+      if (tid == 0) {
+        s->u = (unsigned long long)n;
+        s->best = INT_MAX;
+        s->bfs_state = -1;
+      }
+      break;
+    }
+    if (warp == 0) {
+      int found = -1;
+      for (int c = 0; c < K; c += 32) {
+        const int t = c + lane;
+        int32_t v = -1;
+        bool ok = false;
+        if (t < K) {
+          v = knn[u * K + t];
+          ok = v >= 0 && ((bm[v >> 5] >> (v & 31)) & 1u) && deg[v] < R;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (bal) {
+          found = __shfl_sync(0xffffffffu, v, __ffs(bal) - 1);
+          break;
+        }
+      }
+      if (lane == 0) sv = found;
+    }
+    __syncthreads();
+    const int v = sv;
+    if (v < 0) {
+      if (tid == 0) {
+        s->u = (unsigned long long)u;
+        s->best = -3;
+        s->bfs_state = -1;
+      }
+      break;
+    }
+    if (tid == 0) {
+      adj[(int64_t)v * R + deg[v]] = (int32_t)u;
+      deg[v] += 1;
+      atomicOr(bm + (u >> 5), 1u << (u & 31));
+      f0[0] = (int32_t)u;
+      sfc[0] = 1;
+      ++made;
+    }
+    __syncthreads();
+    int cur = 0;
+    bool big = false;
+    for (;;) {
+      const int fc = sfc[cur];
+      if (fc == 0) break;
+      if (fc > limit) {
+        big = true;
+        break;
+      }
+      __syncthreads();
+      if (tid == 0) sfc[cur ^ 1] = 0;
+      __syncthreads();
+      const int32_t* fr = cur ? f1 : f0;
+      int32_t* nx = cur ? f0 : f1;
+      for (int w = warp; w < fc; w += nwarps) {
+        const int32_t node = fr[w];
+        const int dg = deg[node];
+        for (int c = 0; c < dg; c += 32) {
+          const int t = c + lane;
+          bool fresh = false;
+          int32_t x = 0;
+          if (t < dg) {
+            x = adj[(int64_t)node * R + t];
+            const uint32_t bit = 1u << (x & 31);
+            fresh = !(atomicOr(bm + (x >> 5), bit) & bit);
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+          int basep = 0;
+          if (lane == 0 && bal) basep = atomicAdd(&sfc[cur ^ 1], __popc(bal));
+          basep = __shfl_sync(0xffffffffu, basep, 0);
+          if (fresh) nx[basep + __popc(bal & lanemask_lt())] = x;
+        }
+      }
+      __syncthreads();
+      cur ^= 1;
+    }
+    if (big) {
+      if (tid == 0) {
+        s->u = (unsigned long long)u;
+        s->best = v;
+        s->fcnt[cur] = sfc[cur];
+        s->bfs_state = cur;
+      }
+      break;
+    }
+    start = u >> 5;
+    __syncthreads();
+  }
+  if (tid == 0 && made) atomicAdd(nrep, made);
+}
+
 // Level-synchronous traversal by the whole grid, starting from frontier buffer `cur`.
 static void bfs_levels(const int32_t* adj, const int32_t* deg, int R, uint32_t* bm, int32_t* f[2],
                        RepairState* s, int cur, cudaStream_t st) {
@@ -296,8 +428,13 @@ static void bfs_levels(const int32_t* adj, const int32_t* deg, int R, uint32_t* 
 
 int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int32_t* deg,
                     int R, const int32_t* nav_dev, const int32_t* nav_host, int n_nav,
-                    cudaStream_t st) {
+                    cudaStream_t st, const int32_t* knn, int K, int64_t* knn_repairs) {
   (void)nav_dev;
+  Scratch<unsigned long long> knn_rep;
+  if (knn) {
+    knn_rep.alloc(1, st);
+    SSG_CUDA(cudaMemsetAsync(knn_rep.p, 0, sizeof(unsigned long long), st));
+  }
   const int64_t nw = ceil_div(n, 32);
   const int cap = 1 << 16;
   Scratch<uint32_t> bm((size_t)nw, st);
@@ -319,6 +456,21 @@ int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int3
     int64_t start = 0;
     bool first = true;
     for (;;) {
+      if (!first && knn) {
+        // the repairs the kNN rows settle, in one launch; the rest below
+        SSG_LAUNCH(k_repair_knn, 1, 1024, 0, st, knn, K, adj, deg, R, bm.p, nw, n, start, f[0], f[1],
+                   small_limit, S, knn_rep.p);
+        RepairState h;
+        SSG_CUDA(cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st));
+        SSG_CUDA(cudaStreamSynchronize(st));
+        if ((int64_t)h.u >= n) break;
+        start = (int64_t)h.u >> 5;
+        if (h.best != -3) {
+          // u is linked and its traversal outgrew the block: the grid finishes it
+          if (h.bfs_state >= 0) bfs_levels(adj, deg, R, bm.p, f, S, h.bfs_state, st);
+          continue;
+        }
+      }
       if (!first) {
         SSG_LAUNCH(k_repair_init, 1, 1, 0, st, S, n);
         SSG_LAUNCH(k_first_unreached, grid, 256, 0, st, bm.p, nw, n, start, &S->u);
@@ -358,6 +510,13 @@ int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int3
       if (h.bfs_state >= 0) bfs_levels(adj, deg, R, bm.p, f, S, h.bfs_state, st);
       first = false;
     }
+  }
+  if (knn) {
+    unsigned long long kr = 0;
+    SSG_CUDA(cudaMemcpyAsync(&kr, knn_rep.p, sizeof(kr), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    repairs += (int64_t)kr;
+    if (knn_repairs) *knn_repairs = (int64_t)kr;
   }
   return repairs;
 }

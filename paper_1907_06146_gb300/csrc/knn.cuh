@@ -184,10 +184,13 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
                 int exact, bool tc, int32_t* adj1, int32_t* deg1, Counters* dctr,
                 cudaStream_t st);
 
-// Connectivity from navigating nodes; returns the number of repair edges.
+// Connectivity from navigating nodes; returns the number of repair edges.  knn (nullable):
+// the exact kNN graph [n][K] in (d2, id) order, which settles most repairs without a pass
+// over all nodes (same result).
 int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int32_t* deg,
                     int R, const int32_t* nav_dev, const int32_t* nav_host, int n_nav,
-                    cudaStream_t st);
+                    cudaStream_t st, const int32_t* knn = nullptr, int K = 0,
+                    int64_t* knn_repairs = nullptr);
 
 // Search-on-Graph.  X: float rows at stride ld; X8 (nullable): the same values as bytes
 // (integers 0..255) at the same stride, read instead of X when given (same results).

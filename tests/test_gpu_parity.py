@@ -356,6 +356,58 @@ def test_connect_many_components(ssg):
     np.testing.assert_array_equal(_np(a), ref[0])
 
 
+def test_build_repairs_by_knn_row_and_by_scan(ssg):
+    """60 tight clusters far apart, K = 8: no kNN row leaves its cluster, so the first
+    repair into a cluster finds no reached node in the unreached node's row and scans all
+    nodes, while repairs inside a reached cluster are settled from the row.  Both routes
+    must give the oracle's graph."""
+    rng = np.random.default_rng(77)
+    centres = rng.normal(size=(60, 8)) * 100.0
+    lab = rng.integers(0, 60, size=2400)
+    base = (centres[lab] + rng.normal(size=(2400, 8))).astype(np.float32)
+    nav = synth.nav_ids(2400, 3, 17)
+    ref = oracle.build_graph(base, 8, 16, 6, 60.0, nav)
+    g = ssg.build(_cuda(base), 8, 16, 6, 60.0, nav=nav)
+    np.testing.assert_array_equal(_np(g.deg), ref["deg"])
+    np.testing.assert_array_equal(_np(g.adj), ref["adj"])
+    st = g.stats
+    assert st["n_repair"] == ref["n_repair"]
+    # replay the repairs on the host: which of them had a qualifying node in u's row
+    knn, _ = oracle.knn_rows(base, 8)
+    adj, deg, n = ref["adj1"].copy(), ref["deg1"].copy(), base.shape[0]
+    by_row = 0
+    for s in nav:
+        reached = _reach(adj, deg, s, np.zeros(n, bool))
+        while not reached.all():
+            u = int(np.argmin(reached))
+            row = [v for v in knn[u] if reached[v] and deg[v] < 6]
+            by_row += bool(row)
+            if row:
+                v = row[0]
+            else:
+                ok = np.flatnonzero(reached & (deg < 6))
+                d2 = ((base[ok].astype(np.float64) - base[u]) ** 2).sum(1)
+                v = int(ok[np.lexsort((ok, d2))[0]])
+            adj[v, deg[v]] = u
+            deg[v] += 1
+            reached = _reach(adj, deg, u, reached)
+    np.testing.assert_array_equal(adj, ref["adj"])
+    assert st["n_repair_knn_row"] == by_row
+    assert 0 < by_row and st["n_repair"] - by_row >= 59
+
+
+def _reach(adj, deg, s, reached):
+    stack = [s]
+    reached[s] = True
+    while stack:
+        x = stack.pop()
+        for y in adj[x, :deg[x]]:
+            if not reached[y]:
+                reached[y] = True
+                stack.append(y)
+    return reached
+
+
 # ---- whole build ---------------------------------------------------------------------------
 @pytest.mark.parametrize("which", ["small", "int"])
 def test_build_end_to_end(ssg, which, small, intdata, small_ref, int_ref):
