@@ -99,12 +99,56 @@ __device__ __forceinline__ void warp_fill_dist_keys_u8(uint64_t* keys, int m,
   __syncwarp();
 }
 
+// fp64 squared distance by all 32 lanes of a warp: lane l takes coordinates l, l + 32, ...;
+// every term is rounded exactly as in dist2_f64 and only the order of the additions
+// differs (a sum per lane, then a shuffle tree).  With non-negative terms both sums lie
+// within (number of additions) x 2^-53 of the exact sum of the terms, so the two values
+// differ by at most fp64_order_rel(d) / 2 relative; GB300's fp64 rate is low enough that
+// the 32-fold shorter chain matters.  Every lane returns the same value.
+__device__ __forceinline__ double warp_dist2_f64(const float* __restrict__ a,
+                                                 const float* __restrict__ b, int d) {
+  const int lane = lane_id();
+  double s = 0.0;
+  for (int t = lane; t < d; t += 32) {
+    const double u = __dsub_rn((double)a[t], (double)b[t]);
+    s = __dadd_rn(s, __dmul_rn(u, u));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+  return s;
+}
+
+// Twice the largest relative gap between warp_dist2_f64 and dist2_f64 of the same pair.
+__host__ __device__ inline double fp64_order_rel(int d) {
+  return 2.0 * (d + (d + 31) / 32 + 6) * 1.1102230246251565e-16 * 1.01;
+}
+
+// Insertion sort of keys[s, e] (with their fp64 distances d64) by (d64, id); one lane.
+__device__ __forceinline__ void sort_run_f64(uint64_t* keys, double* d64, int s, int e) {
+  for (int t = s + 1; t <= e; ++t) {
+    const uint64_t kk = keys[t];
+    const double dv = d64[t];
+    int u = t - 1;
+    while (u >= s && (d64[u] > dv || (d64[u] == dv && (uint32_t)keys[u] > (uint32_t)kk))) {
+      keys[u + 1] = keys[u];
+      d64[u + 1] = d64[u];
+      --u;
+    }
+    keys[u + 1] = kk;
+    d64[u + 1] = dv;
+  }
+}
+
 // keys[0, m) are sorted by their fp32 distances.  The fp32 value of a direct sum of d
 // squared differences lies within a relative `rel` of the exact value, so two entries
 // can be out of their true (d2, id) order only inside a run of neighbours whose fp32
 // values are within that bound of each other.  Every such run that starts before
-// `limit` is re-sorted by (fp64 d2, id).  d64 is scratch for m doubles.
-// Returns the number of runs re-sorted by this lane (sum over lanes = total).
+// `limit` is re-sorted by (fp64 d2, id): the warp computes each fp64 distance together
+// (warp_dist2_f64), and where two of them are too close for that summation order to
+// settle their order the way the coordinate-order sum does, those entries are re-taken in
+// coordinate order (dist2_f64), so the order is always that of the coordinate-order fp64
+// values.  d64 is scratch for m doubles.  Returns the number of runs re-sorted (in lane 0;
+// the other lanes return 0, so a sum over lanes gives the total).
 __device__ __forceinline__ int warp_fix_runs(uint64_t* keys, int m, int limit, double* d64,
                                              const float* __restrict__ X, int ld, int d,
                                              const float* __restrict__ xi, float rel) {
@@ -113,28 +157,41 @@ __device__ __forceinline__ int warp_fix_runs(uint64_t* keys, int m, int limit, d
     float a = key_dist(keys[p]), b = key_dist(keys[p + 1]);
     return (b - a) <= rel * (a + b);
   };
+  const double trel = fp64_order_rel(d);
   int fixed = 0;
   const int smax = m - 1 < limit ? m - 1 : limit;
-  for (int s = lane; s < smax; s += 32) {
-    if (!close(s) || (s > 0 && close(s - 1))) continue;
-    int e = s + 1;
-    while (e + 1 < m && close(e)) ++e;
-    for (int t = s; t <= e; ++t) d64[t] = dist2_f64(xi, X + (int64_t)key_id(keys[t]) * ld, d);
-    for (int t = s + 1; t <= e; ++t) {  // insertion sort of the run by (d64, id)
-      uint64_t kk = keys[t];
-      double dv = d64[t];
-      int u = t - 1;
-      while (u >= s && (d64[u] > dv || (d64[u] == dv && (uint32_t)keys[u] > (uint32_t)kk))) {
-        keys[u + 1] = keys[u];
-        d64[u + 1] = d64[u];
-        --u;
+  for (int b0 = 0; b0 < smax; b0 += 32) {
+    const int s = b0 + lane;
+    const bool start = s < smax && close(s) && !(s > 0 && close(s - 1));
+    unsigned bal = __ballot_sync(0xffffffffu, start);
+    while (bal) {
+      const int s0 = b0 + __ffs(bal) - 1;
+      bal &= bal - 1;
+      int e = s0 + 1;
+      while (e + 1 < m && close(e)) ++e;
+      for (int t = s0; t <= e; ++t) {
+        const double v = warp_dist2_f64(xi, X + (int64_t)key_id(keys[t]) * ld, d);
+        if (lane == 0) d64[t] = v;
       }
-      keys[u + 1] = kk;
-      d64[u + 1] = dv;
+      __syncwarp();
+      if (lane == 0) {
+        sort_run_f64(keys, d64, s0, e);
+        for (int t = s0; t < e;) {
+          if (d64[t + 1] - d64[t] > trel * d64[t + 1]) {
+            ++t;
+            continue;
+          }
+          int u = t + 1;
+          while (u < e && d64[u + 1] - d64[u] <= trel * d64[u + 1]) ++u;
+          for (int q = t; q <= u; ++q) d64[q] = dist2_f64(xi, X + (int64_t)key_id(keys[q]) * ld, d);
+          sort_run_f64(keys, d64, t, u);
+          t = u + 1;
+        }
+        ++fixed;
+      }
+      __syncwarp();
     }
-    ++fixed;
   }
-  __syncwarp();
   return fixed;
 }
 

@@ -146,6 +146,16 @@ void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
                const int32_t* pool_len, int L, int R, double cos_a, double border, int32_t* adj,
                int32_t* deg, Counters* dctr, cudaStream_t st);
 
+// The same prune, one node per thread block, for rows too long for the warp prune to keep
+// its vectors beside the warp (prune_is_wide) and of at most 1,024 values
+// (prune_wide_available): node i's candidates are cand[i * stride + t], t < len[i].
+// blocks_per_sm (0: 2) sets how much shared memory each block takes for kept vectors.
+bool prune_wide_available(int d);
+void prune_run_wide(const float* X, int ld, int d, int64_t n, const int32_t* cand,
+                    const int32_t* len, int stride, int R, double cos_a, double border,
+                    int32_t* adj, int32_t* deg, Counters* dctr, cudaStream_t st,
+                    int blocks_per_sm = 0);
+
 // One index's share of a batched prune (prune_run_batched).
 struct PruneJob {
   const float* X;

@@ -210,6 +210,10 @@ void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
                const int32_t* pool_len, int L, int R, double cos_a, double border, int32_t* adj,
                int32_t* deg, Counters* dctr, cudaStream_t st) {
   const bool wide = prune_is_wide(d, R);
+  if (wide && prune_wide_available(d)) {
+    prune_run_wide(X, ld, d, n, pool_id, pool_len, L, R, cos_a, border, adj, deg, dctr, st);
+    return;
+  }
   const size_t per_warp =
       (wide ? prune_wide_smem_floats(d, R) : prune_smem_floats(d, R)) * sizeof(float);
   int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));

@@ -118,10 +118,13 @@ __global__ void k_reverse_merge(const float* __restrict__ X, const uint8_t* __re
                                 unsigned long long* __restrict__ n_order,
                                 unsigned long long* __restrict__ n_angle, float* __restrict__ Vg,
                                 int32_t* __restrict__ lists, int32_t* __restrict__ list_len,
-                                double border, unsigned long long* __restrict__ n_border) {
+                                int lstride, double border,
+                                unsigned long long* __restrict__ n_border) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
-  const size_t per_warp = (size_t)cap * 20 + merge_prune_bytes(d, R, Vg != nullptr);
+  // merge only (lists != nullptr): no prune state
+  const size_t per_warp =
+      (size_t)cap * 20 + (lists ? 0 : merge_prune_bytes(d, R, Vg != nullptr));
   unsigned char* base = sm_raw + warp * per_warp;
   uint64_t* keys = (uint64_t*)base;
   double* d64 = (double*)(keys + cap);
@@ -173,8 +176,8 @@ __global__ void k_reverse_merge(const float* __restrict__ X, const uint8_t* __re
       if (lane == 0 && f) atomicAdd(n_order, (unsigned long long)f);
     }
     if (lists) {
-      // merge only: the sorted list goes to the tensor-core prune
-      for (int t = lane; t < m; t += 32) lists[j * limit + t] = key_id(keys[t]);
+      // merge only: the sorted list goes to the tensor-core or the block prune
+      for (int t = lane; t < m; t += 32) lists[j * lstride + t] = key_id(keys[t]);
       if (lane == 0) list_len[j] = m;
       __syncwarp();
       continue;
@@ -230,6 +233,42 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
   // Tensor-core path (data exact in bf16): the warps only merge and sort, lists of up to
   // 127 candidates go to the Gram prune, longer ones to the warp prune below.
   const bool use_tc = tc && exact && prune_tc_available(d, 127, R);
+  if (wide && !use_tc && prune_wide_available(d)) {
+    // long rows: the warps merge and sort every list, the block prune prunes them
+    int h[2];
+    SSG_CUDA(cudaMemcpyAsync(h, small.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    const int Lr = R + std::max(h[1], 1);
+    Scratch<int32_t> lists((size_t)n * Lr, st), list_len((size_t)n, st), big((size_t)n, st);
+    const size_t smem_max = 220 * 1024;
+    ensure_smem((const void*)k_reverse_merge, smem_max);
+    int cap1 = 32;
+    while (cap1 < Lr && cap1 < 1024) cap1 *= 2;
+    const int wpb1 = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / ((size_t)cap1 * 20)));
+    SSG_LAUNCH(k_reverse_merge, (unsigned)ceil_div(n, wpb1), wpb1 * 32, (size_t)cap1 * 20 * wpb1, st, X,
+               X8, ld, d, n, adj0, deg0, R, off.p, rev.p, (const int32_t*)nullptr, n, cap1, cap1, exact,
+               rel, (float)cos_a, cos_a, margin, adj1, deg1, big.p, small.p, &dctr->order_fp64,
+               &dctr->angle_fp64, (float*)nullptr, lists.p, list_len.p, Lr, border,
+               &dctr->angle_border);
+    SSG_CUDA(cudaMemcpyAsync(h, small.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    if (h[0] > 0) {
+      int cap_big = cap1;
+      while (cap_big < Lr) cap_big *= 2;
+      SSG_REQUIRE((size_t)cap_big * 20 <= smem_max, SSG_EINTERNAL,
+                  "reverse merge: a node has %d candidates, more than the %zu supported", Lr,
+                  smem_max / 20);
+      Scratch<int> small2(2, st);
+      SSG_CUDA(cudaMemsetAsync(small2.p, 0, sizeof(int) * 2, st));
+      SSG_LAUNCH(k_reverse_merge, (unsigned)std::min<int64_t>(h[0], 8 * num_sms()), 32,
+                 (size_t)cap_big * 20, st, X, X8, ld, d, n, adj0, deg0, R, off.p, rev.p, big.p,
+                 (int64_t)h[0], cap_big, cap_big, exact, rel, (float)cos_a, cos_a, margin, adj1, deg1,
+                 big.p, small2.p, &dctr->order_fp64, &dctr->angle_fp64, (float*)nullptr, lists.p,
+                 list_len.p, Lr, border, &dctr->angle_border);
+    }
+    prune_run_wide(X, ld, d, n, lists.p, list_len.p, Lr, R, cos_a, border, adj1, deg1, dctr, st);
+    return h[1];
+  }
   // warp path: per-warp buffers of cap keys (a power of two, for the sort); lists longer
   // than limit go to the second pass
   const int cap = use_tc ? 128 : 256;
@@ -259,7 +298,7 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
   SSG_LAUNCH(k_reverse_merge, (unsigned)mgrid, wpb * 32, smem, st, X, X8, ld, d, n, adj0, deg0, R, off.p,
              rev.p, (const int32_t*)nullptr, n, cap, limit, exact, rel, (float)cos_a, cos_a, margin, adj1,
              deg1, big.p, small.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p, lists.p, list_len.p,
-             border, &dctr->angle_border);
+             limit, border, &dctr->angle_border);
   if (use_tc)
     prune_run_tc(X, ld, d, n, lists.p, list_len.p, limit, R, cos_a, border, adj1, deg1, dctr, st);
   int h[2];
@@ -281,7 +320,7 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
     SSG_LAUNCH(k_reverse_merge, grid_big, 32, smem_big, st, X, X8, ld, d, n, adj0, deg0, R, off.p, rev.p,
                big.p, (int64_t)h[0], cap_big, cap_big, exact, rel, (float)cos_a, cos_a, margin, adj1, deg1,
                none.p, small2.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p, (int32_t*)nullptr,
-               (int32_t*)nullptr, border, &dctr->angle_border);
+               (int32_t*)nullptr, 0, border, &dctr->angle_border);
   }
   return h[1];
 }

@@ -101,3 +101,69 @@ def test_too_wide_rows_refused_for_bf16(ssg):
     np.testing.assert_array_equal(_np(ids), oid)
     with pytest.raises(ssg.SSGError):
         ssg.knn(_cuda(base), 5, prec="bf16")
+
+
+def test_block_prune_spill_and_ties(ssg):
+    """The block prune of long rows (d = 960, R = 70).  80 repeated rows give zero-length
+    edges and exact distance ties in the pools and the reverse lists.  At 60 degrees about a
+    sixth of the nodes keep more vectors than the block's shared memory holds (the rest
+    live in its device slot); at 35 degrees every node keeps R = 70.  Prune and reverse
+    merge at both angles, the pools and the whole build at 60 must equal the oracle."""
+    w = synth.gist_like(n=900, nq=0, n_clusters=6)
+    base = w.base.copy()
+    rng = np.random.default_rng(43)
+    base[rng.choice(900, 80, replace=False)] = base[rng.choice(900, 80)]
+    nav = synth.nav_ids(900, 3, 67)
+    ref = oracle.build_graph(base, 40, 150, 70, 60.0, nav)
+    b = _cuda(base)
+    pid, _, pl = ssg.pool(b, _cuda(ref["knn_id"]), 150)
+    np.testing.assert_array_equal(_np(pl), ref["pool_len"])
+    np.testing.assert_array_equal(_np(pid), ref["pool_id"])
+    for alpha in (60.0, 35.0):
+        if alpha == 60.0:
+            a0, d0, a1, d1 = ref["adj0"], ref["deg0"], ref["adj1"], ref["deg1"]
+            assert (d0 > 24).mean() > 0.1
+        else:
+            a0, d0 = oracle.prune(base, ref["pool_id"], ref["pool_len"], 70, alpha)
+            a1, d1 = oracle.reverse(base, a0, d0, alpha)[:2]
+            assert (d0 == 70).all()
+        adj0, deg0 = ssg.prune(b, _cuda(ref["pool_id"]), _cuda(ref["pool_len"]), 70, alpha)
+        np.testing.assert_array_equal(_np(deg0), d0)
+        np.testing.assert_array_equal(_np(adj0), a0)
+        adj1, deg1 = ssg.reverse(b, _cuda(a0), _cuda(d0), alpha)
+        np.testing.assert_array_equal(_np(deg1), d1)
+        np.testing.assert_array_equal(_np(adj1), a1)
+    g = ssg.build(b, 40, 150, 70, 60.0, nav=nav)
+    np.testing.assert_array_equal(_np(g.deg), ref["deg"])
+    np.testing.assert_array_equal(_np(g.adj), ref["adj"])
+
+
+def test_block_prune_exact_angles(ssg):
+    """0/1 rows of 400 values with four ones among the first 12 columns: many centred
+    pairs meet at exactly 60 degrees, where the block prune's fp64 cosine is re-taken in
+    coordinate order (an angle of exactly alpha keeps the edge)."""
+    rng = np.random.default_rng(44)
+    base = np.zeros((600, 400), np.float32)
+    for r in range(600):
+        base[r, rng.choice(12, 4, replace=False)] = 1.0
+    base[:, 12:] = rng.integers(0, 2, size=(600, 388)) * (rng.random((600, 388)) < 0.01)
+    knn, _ = oracle.knn_rows(base, 30)
+    pool_id, _, pool_len = oracle.pool(base, knn, 100)
+    for alpha in (60.0, 45.0):
+        a0, d0 = oracle.prune(base, pool_id, pool_len, 70, alpha)
+        a1, d1 = oracle.reverse(base, a0, d0, alpha)[:2]
+        b = _cuda(base)
+        adj0, deg0 = ssg.prune(b, _cuda(pool_id), _cuda(pool_len), 70, alpha)
+        np.testing.assert_array_equal(_np(deg0), d0)
+        np.testing.assert_array_equal(_np(adj0), a0)
+        adj1, deg1 = ssg.reverse(b, _cuda(a0), _cuda(d0), alpha)
+        np.testing.assert_array_equal(_np(deg1), d1)
+        np.testing.assert_array_equal(_np(adj1), a1)
+    # the data do hold pairs at exactly 60 degrees
+    x = base[0]
+    c = base[pool_id[0, :pool_len[0]]] - x
+    g = c @ c.T
+    nrm = np.sqrt(np.diag(g))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        exact = int(np.sum(np.isclose(g / np.outer(nrm, nrm), 0.5, rtol=0, atol=1e-12)))
+    assert exact > 0
