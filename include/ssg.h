@@ -127,7 +127,10 @@ typedef struct {
                                K-chunked 128 x 256-tile kernel), prune_warps (warps per
                                block of the batched prune, 0 = automatic, up to 16),
                                prune_bucket_width (pool lengths per bucket of the batched
-                               prune's longest-first order, 1..1024) */
+                               prune's longest-first order, 1..1024), prune_wide_blocks
+                               (blocks per SM of the block prune of rows of 330 to 1,024
+                               values, 0 = automatic (2), up to 4; fewer blocks hold more
+                               kept vectors in shared memory) */
 } ssg_build_opts;
 
 /* Per-build measurements (all times from CUDA events on the build stream). */

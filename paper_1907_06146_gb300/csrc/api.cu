@@ -108,12 +108,12 @@ __global__ void k_pool_len_from_ids(const int32_t* __restrict__ ids, int64_t n, 
 static ssg_precision prune_dispatch(bool tc_ok, const float* X, int ld, int d, int64_t n,
                                     const int32_t* pool_id, const int32_t* pool_len, int L, int R,
                                     double cos_a, double border, int32_t* adj, int32_t* deg,
-                                    Counters* ctr, cudaStream_t st) {
+                                    Counters* ctr, cudaStream_t st, int wide_blocks = 0) {
   if (tc_ok && prune_tc_available(d, L, R)) {
     prune_run_tc(X, ld, d, n, pool_id, pool_len, L, R, cos_a, border, adj, deg, ctr, st);
     return SSG_PREC_BF16;
   }
-  prune_run(X, ld, d, n, pool_id, pool_len, L, R, cos_a, border, adj, deg, ctr, st);
+  prune_run(X, ld, d, n, pool_id, pool_len, L, R, cos_a, border, adj, deg, ctr, st, wide_blocks);
   return SSG_PREC_FP32;
 }
 
@@ -171,6 +171,10 @@ static KnnTune read_tune_table(const char* path) {
                   "tune_table %s:%d: prune_bucket_width must be an integer in [1, 1024]", path,
                   ln);
       t.prune_bucket_width = (int)v;
+    } else if (!strcmp(name, "prune_wide_blocks")) {
+      SSG_REQUIRE(v >= 0 && v <= 4 && v == std::floor(v), SSG_EINVAL,
+                  "tune_table %s:%d: prune_wide_blocks must be an integer in [0, 4]", path, ln);
+      t.prune_wide_blocks = (int)v;
     } else if (!strcmp(name, "knn_stream_rows")) {
       SSG_REQUIRE(v == 0 || v == 1, SSG_EINVAL, "tune_table %s:%d: knn_stream_rows must be 0 or 1",
                   path, ln);
@@ -689,7 +693,7 @@ static void build_prune(BuildCtx& c) {
   c.t_prune->start();
   c.gram_used = prune_dispatch(c.gram_tc, c.in.rows.p, c.in.rows.ld, c.d, c.n, c.pool_id.p,
                                c.pool_len.p, c.L, c.R, c.cos_a, c.opts.cos_margin_fp64, c.adj0.p,
-                               c.deg0.p, c.ctr.p, c.st);
+                               c.deg0.p, c.ctr.p, c.st, c.tune.prune_wide_blocks);
   c.t_prune->stop();
   c.launches += t_launches - l0;
 }
@@ -714,7 +718,7 @@ static void build_back(BuildCtx& c) {
   c.t_rev->start();
   c.max_indeg = reverse_run(in.rows.p, g->rows_u8, in.rows.ld, d, n, c.adj0.p, c.deg0.p, R,
                                 c.cos_a, c.opts.cos_margin_fp64, in.info.exact, c.gram_tc, g->adj,
-                                g->deg, c.ctr.p, st);
+                                g->deg, c.ctr.p, st, c.tune.prune_wide_blocks);
   c.t_rev->stop();
   if (c.opts.debug_checks) debug_check(check_adj(g->adj, g->deg, n, R, st), "the reverse merge");
   c.adj0.release();

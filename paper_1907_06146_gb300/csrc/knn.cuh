@@ -91,6 +91,7 @@ struct KnnTune {
   int stream_rows = 0;          // TcExtra::stream_rows of the kNN graph
   int prune_warps = 0;          // PruneTune of a batched build
   int prune_bucket_width = 32;
+  int prune_wide_blocks = 0;    // blocks per SM of the block prune of long rows (0: 2)
 };
 struct CertResult {
   int64_t fallback_rows = 0;  // rows not certified by the first pass
@@ -144,7 +145,7 @@ void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int6
 // cosine lies within border are counted in dctr->angle_border.
 void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
                const int32_t* pool_len, int L, int R, double cos_a, double border, int32_t* adj,
-               int32_t* deg, Counters* dctr, cudaStream_t st);
+               int32_t* deg, Counters* dctr, cudaStream_t st, int wide_blocks = 0);
 
 // The same prune, one node per thread block, for rows too long for the warp prune to keep
 // its vectors beside the warp (prune_is_wide) and of at most 1,024 values
@@ -192,7 +193,7 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
 int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
                 const int32_t* adj0, const int32_t* deg0, int R, double cos_a, double border,
                 int exact, bool tc, int32_t* adj1, int32_t* deg1, Counters* dctr,
-                cudaStream_t st);
+                cudaStream_t st, int wide_blocks = 0);
 
 // Connectivity from navigating nodes; returns the number of repair edges.  knn (nullable):
 // the exact kNN graph [n][K] in (d2, id) order, which settles most repairs without a pass

@@ -1,23 +1,28 @@
 // SSG prune (Alg. 2 selection applied to every pool, Alg. 3) of nodes whose rows are long
-// (for example d = 960 with R = 70): one node per thread block.
+// (for example d = 960 with R = 70): one node per thread block of eight warps.
 //
 // The warp prune keeps a node's kept centred vectors beside the warp, which rows this
 // long do not fit, and a warp that then walks its kept vectors one dot product after
-// another waits on memory for each of them.  Here:
-//   * the block's shared memory holds the node's kept centred vectors c_k - x (the first
-//     `cap` of them; the rest go to a device slot of the block, which stays in L2);
-//   * candidate rows arrive through a ring of PF rows filled by asynchronous copies, PF
-//     candidates ahead of the one being tested;
-//   * every warp forms the candidate's centred vector c_j - x in its own registers (lane l
-//     holds float4 columns l, l + 32, ...), so the eight warps test it against disjoint
-//     subsets of the kept vectors at once (two at a time per warp) and stop as soon as one
-//     of them finds a definite conflict; one barrier per candidate joins their verdicts.
+// another waits on memory for each of them.  Here the candidates are taken in windows of
+// eight, one per warp:
+//   1. every warp loads its candidate's row, forms the centred vector c_j - x in its
+//      registers (lane l holds float4 columns l, l + 32, ...) and in the kept-vector slot
+//      it would take if every candidate before it in the window were kept, and tests it
+//      against the node's kept vectors as they stood when the window began (four dot
+//      products at a time, stopping at the first definite conflict);
+//   2. after one barrier, warp 0 settles the window in candidate order: a candidate that
+//      passed step 1 is also tested against the candidates of this window kept before it,
+//      then kept (its vector moved down to the next kept slot) or dropped, until R are
+//      kept.
+// The kept vectors sit in the block's shared memory (the first `cap` of them; the rest in
+// a device slot of the block, which stays in L2).  So the eight warps run eight
+// independent chains of dot products and meet twice per window, not once per candidate.
 // The decisions are those of the warp prune: the fp32 cosine decides outside a margin that
 // bounds its rounding error for any summation order; the rest, and zero-length edges, are
 // re-taken in fp64 from the original vectors.  Those fp64 dot products are summed by the
-// 32 lanes of one warp; where the resulting cosine lies within 1e-10 of cos(alpha) --
-// far more than the two summation orders can move it for any d up to 4,096 -- the three
-// dot products are re-taken in coordinate order, so every decision is the one the
+// 32 lanes of warp 0; where the resulting cosine lies within 1e-10 of cos(alpha) -- far
+// more than the two summation orders can move it for any d up to 4,096 -- the three dot
+// products are re-taken in coordinate order, so every decision is the one the
 // coordinate-order fp64 rule takes.
 #include "common.cuh"
 #include "graph_dev.cuh"
@@ -26,9 +31,8 @@
 namespace ssg {
 namespace {
 
-constexpr int PW_WARPS = 8;
+constexpr int PW_WARPS = 8;                  // = candidates per window
 constexpr int PW_THREADS = PW_WARPS * 32;
-constexpr int PW_PF = 4;                     // candidate rows in flight
 constexpr double PW_TIE_COS = 1e-10;         // fp64 cosines this close to cos(alpha) are
                                              // re-taken in coordinate order
 
@@ -44,7 +48,7 @@ struct WideArgs {
   double cosA64, border;
   int32_t* adj;             // [n][R]
   int32_t* deg;
-  float* Vg;                // block b's kept vectors cap.. R: Vg + b * (R + 1 - cap) * d4
+  float* Vg;                // block b's kept vectors cap .. R + 7: Vg + b * (R + 8 - cap) * d4
   int cap;                  // kept vectors held in shared memory
   unsigned long long* n64;
   unsigned long long* nborder;
@@ -52,21 +56,20 @@ struct WideArgs {
 
 // Byte offsets of the block's shared-memory regions (all multiples of 16).
 struct WideLayout {
-  size_t xs, ring, V, gkk, g64, kid, flags, nlist, total;
+  size_t xs, V, gkk, g64, kid, wmeta, nlist, total;
 };
 __host__ __device__ inline WideLayout wide_layout(int d, int R, int cap) {
   const size_t row = (size_t)((d + 3) & ~3) * 4;
   const size_t R1a = (size_t)((R + 1 + 3) & ~3);
   WideLayout L;
   L.xs = 0;
-  L.ring = L.xs + row;
-  L.V = L.ring + PW_PF * row;
-  L.gkk = L.V + (size_t)cap * row;
-  L.g64 = L.gkk + R1a * 4;
-  L.kid = L.g64 + R1a * 8;
-  L.flags = L.kid + R1a * 4;
-  L.nlist = L.flags + 16 * 4;
-  L.total = L.nlist + 3 * R1a * 4;
+  L.V = L.xs + row;                          // cap kept vectors
+  L.gkk = L.V + (size_t)cap * row;           // [R1a] fp32 |c_k - x|^2
+  L.g64 = L.gkk + R1a * 4;                   // [R1a] fp64 |c_k - x|^2 (< 0: not computed)
+  L.kid = L.g64 + R1a * 8;                   // [R1a] kept ids
+  L.wmeta = L.kid + R1a * 4;                 // per window slot: |v|^2, id, verdict, near count
+  L.nlist = L.wmeta + 4 * PW_WARPS * 4;      // [PW_WARPS][R1a] kept vectors to re-test in fp64
+  L.total = L.nlist + PW_WARPS * R1a * 4;
   return L;
 }
 
@@ -93,6 +96,16 @@ __device__ __forceinline__ float dot4(float4 a, float4 b, float s) {
   return fmaf(a.w, b.w, s);
 }
 
+// fp32 angle test of one pair from its centred dot product g and squared lengths:
+// 2 = definite conflict, 1 = to be re-taken in fp64, 0 = no conflict.
+__device__ __forceinline__ int angle_test32(float g, float gjj, float gk, float cosA32,
+                                            float margin) {
+  if (gjj == 0.f || gk == 0.f) return 1;
+  const float c = g / (sqrtf(gjj) * sqrtf(gk));
+  if (c > cosA32 + margin) return 2;
+  return c >= cosA32 - margin ? 1 : 0;
+}
+
 // NVR: float4 columns of the candidate vector each lane holds (rows of up to 128 NVR values).
 template <int NVR>
 __global__ void __launch_bounds__(PW_THREADS) k_prune_wide(WideArgs a) {
@@ -101,18 +114,21 @@ __global__ void __launch_bounds__(PW_THREADS) k_prune_wide(WideArgs a) {
   const int d4 = (a.d + 3) & ~3, nq4 = d4 >> 2;
   const int R1a = (a.R + 1 + 3) & ~3;
   float* xs = (float*)(smw + Ly.xs);
-  float* ring = (float*)(smw + Ly.ring);
   float* V = (float*)(smw + Ly.V);
   float* gkk = (float*)(smw + Ly.gkk);
   double* g64 = (double*)(smw + Ly.g64);
   int32_t* kid = (int32_t*)(smw + Ly.kid);
-  volatile int* conf = (volatile int*)(smw + Ly.flags);  // [3] by candidate index mod 3
-  int* nnear = (int*)(smw + Ly.flags) + 4;               // [3]
-  volatile int* dec = (volatile int*)(smw + Ly.flags) + 8;  // [3] fp64 verdicts
-  int* nlist = (int*)(smw + Ly.nlist);                   // [3][R1a]
-  float* spill = a.Vg ? a.Vg + (size_t)blockIdx.x * (a.R + 1 - a.cap) * d4 : nullptr;
+  float* wg = (float*)(smw + Ly.wmeta);                  // [8] |v|^2 of the window's vectors
+  int32_t* wid = (int32_t*)(wg + PW_WARPS);              // [8] their ids
+  int* wdead = (int*)(wid + PW_WARPS);                   // [8] definite conflict in step 1
+  int* wnn = wdead + PW_WARPS;                           // [8] fp64 re-tests listed
+  int* nlist = (int*)(smw + Ly.nlist);                   // [8][R1a]
+  float* spill = a.Vg ? a.Vg + (size_t)blockIdx.x * (a.R + PW_WARPS - a.cap) * d4 : nullptr;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned long long n64 = 0, nb = 0;
+  auto kept_row = [&](int k) -> float* {
+    return k < a.cap ? V + (size_t)k * d4 : spill + (size_t)(k - a.cap) * d4;
+  };
 
   for (int64_t i = blockIdx.x; i < a.n; i += gridDim.x) {
     const int len = a.len[i];
@@ -121,162 +137,157 @@ __global__ void __launch_bounds__(PW_THREADS) k_prune_wide(WideArgs a) {
     int32_t* out = a.adj + i * a.R;
     __syncthreads();  // the previous node's readers are done with every buffer
     for (int f = tid; f < nq4; f += PW_THREADS) ((float4*)xs)[f] = __ldg((const float4*)xg + f);
-    if (tid < 3) {
-      conf[tid] = 0;
-      nnear[tid] = 0;
-    }
-    auto prefetch = [&](int t) {
+    __syncthreads();
+    int kept = 0;  // the same in every thread
+    for (int t0 = 0; t0 < len && kept < a.R; t0 += PW_WARPS) {
+      // ---- step 1: warp w takes candidate t0 + w against the kept vectors 0 .. kept-1
+      const int t = t0 + warp;
       if (t < len) {
-        const float4* src = (const float4*)(a.X + (int64_t)cand[t] * a.ld);
-        float* dst = ring + (size_t)(t % PW_PF) * d4;
-        for (int f = tid; f < nq4; f += PW_THREADS) cp_async16(dst + 4 * f, src + f);
-      }
-      cp_async_commit();
-    };
-    for (int t = 0; t < PW_PF; ++t) prefetch(t);
-    cp_async_wait<PW_PF - 1>();
-    __syncthreads();  // xs, the flags and candidate 0's row in place
-
-    int kept = 0;
-    for (int t = 0; t < len && kept < a.R; ++t) {
-      const int s3 = t % 3;
-      const int32_t j = cand[t];
-      const float4* cs4 = (const float4*)(ring + (size_t)(t % PW_PF) * d4);
-      const float4* xs4 = (const float4*)xs;
-      float4 v[NVR];
-      float part = 0.f;
-#pragma unroll
-      for (int r = 0; r < NVR; ++r) {
-        const int f = lane + 32 * r;
-        if (f < nq4) {
-          const float4 c = cs4[f], x = xs4[f];
-          v[r] = make_float4(c.x - x.x, c.y - x.y, c.z - x.z, c.w - x.w);
-        } else {
-          v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        part = dot4(v[r], v[r], part);
-      }
-      const float gjj = warp_sum(part);  // the same value in every warp
-      if (warp == 0) {
-        // the tentative kept row: used from the next candidate on if this one is kept
-        float4* slot = (float4*)(kept < a.cap ? V + (size_t)kept * d4
-                                              : spill + (size_t)(kept - a.cap) * d4);
+        const int32_t j = cand[t];
+        const float4* c4 = (const float4*)(a.X + (int64_t)j * a.ld);
+        const float4* xs4 = (const float4*)xs;
+        float4 v[NVR];
 #pragma unroll
         for (int r = 0; r < NVR; ++r) {
           const int f = lane + 32 * r;
-          if (f < nq4) slot[f] = v[r];
+          v[r] = f < nq4 ? __ldg(c4 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (lane == 0) {
-          gkk[kept] = gjj;
-          kid[kept] = j;
-          g64[kept] = -1.0;  // fp64 norm not computed yet
-          const int s1 = (t + 1) % 3;
-          conf[s1] = 0;
-          nnear[s1] = 0;
-        }
-      }
-      // fp32 tests against the kept vectors k = warp, warp + 8, ... (two at a time)
-      for (int k0 = warp; k0 < kept; k0 += 2 * PW_WARPS) {
-        if (conf[s3]) break;
-        const int k1 = k0 + PW_WARPS;
-        const bool two = k1 < kept;
-        const float4* v0 = (const float4*)(k0 < a.cap ? V + (size_t)k0 * d4
-                                                      : spill + (size_t)(k0 - a.cap) * d4);
-        const float4* v1 = !two ? v0
-                                : (const float4*)(k1 < a.cap ? V + (size_t)k1 * d4
-                                                             : spill + (size_t)(k1 - a.cap) * d4);
-        float g0 = 0.f, g1 = 0.f;
+        float part = 0.f;
+        float4* slot = (float4*)kept_row(kept + warp);
 #pragma unroll
         for (int r = 0; r < NVR; ++r) {
           const int f = lane + 32 * r;
           if (f < nq4) {
-            g0 = dot4(v[r], v0[f], g0);
-            g1 = dot4(v[r], v1[f], g1);
+            const float4 x = xs4[f];
+            v[r] = make_float4(v[r].x - x.x, v[r].y - x.y, v[r].z - x.z, v[r].w - x.w);
+            slot[f] = v[r];
           }
+          part = dot4(v[r], v[r], part);
         }
+        const float gjj = warp_sum(part);
+        int dead = 0, nn = 0;
+        // four kept vectors per round; the four sums are reduced together (lanes 8u .. 8u+7
+        // end up holding dot product u)
+        const int mine = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+        for (int k0 = 0; k0 < kept && !dead; k0 += 4) {
+          const int kn = min(4, kept - k0);
+          const float4* w0 = (const float4*)kept_row(k0);
+          const float4* w1 = kn > 1 ? (const float4*)kept_row(k0 + 1) : w0;
+          const float4* w2 = kn > 2 ? (const float4*)kept_row(k0 + 2) : w0;
+          const float4* w3 = kn > 3 ? (const float4*)kept_row(k0 + 3) : w0;
+          float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          g0 += __shfl_xor_sync(0xffffffffu, g0, o);
-          g1 += __shfl_xor_sync(0xffffffffu, g1, o);
-        }
-        bool definite = false;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          if (q == 1 && !two) break;
-          const int k = q ? k1 : k0;
-          const float g = q ? g1 : g0;
-          const float gk = gkk[k];
-          bool near = gjj == 0.f || gk == 0.f;
-          if (!near) {
-            const float c = g / (sqrtf(gjj) * sqrtf(gk));
-            if (c > a.cosA32 + a.margin)
-              definite = true;
-            else if (c >= a.cosA32 - a.margin)
-              near = true;
+          for (int r = 0; r < NVR; ++r) {
+            const int f = lane + 32 * r;
+            if (f < nq4) {
+              g0 = dot4(v[r], w0[f], g0);
+              g1 = dot4(v[r], w1[f], g1);
+              g2 = dot4(v[r], w2[f], g2);
+              g3 = dot4(v[r], w3[f], g3);
+            }
           }
-          if (near && lane == 0) nlist[s3 * R1a + atomicAdd(&nnear[s3], 1)] = k;
-        }
-        if (definite) {
-          if (lane == 0) conf[s3] = 1;
-          break;
-        }
-      }
-      // the next candidate's row must be in place for every thread after the barrier
-      cp_async_wait<PW_PF - 2>();
-      __syncthreads();
-      bool accept = !conf[s3];
-      const int nn = *(volatile int*)&nnear[s3];
-      if (accept && nn > 0) {
-        if (warp == 0) {
-          int* lst = nlist + s3 * R1a;
-          if (lane == 0) {  // test in kept order, so the counts do not depend on timing
-            for (int u = 1; u < nn; ++u) {
-              const int x = lst[u];
-              int w = u - 1;
-              while (w >= 0 && lst[w] > x) {
-                lst[w + 1] = lst[w];
-                --w;
+          const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+          const float r0 = __shfl_xor_sync(0xffffffffu, hi16 ? g0 : g2, 16);
+          const float r1 = __shfl_xor_sync(0xffffffffu, hi16 ? g1 : g3, 16);
+          const float h0 = (hi16 ? g2 : g0) + r0, h1 = (hi16 ? g3 : g1) + r1;
+          float g = (hi8 ? h1 : h0) + __shfl_xor_sync(0xffffffffu, hi8 ? h0 : h1, 8);
+          g += __shfl_xor_sync(0xffffffffu, g, 4);
+          g += __shfl_xor_sync(0xffffffffu, g, 2);
+          g += __shfl_xor_sync(0xffffffffu, g, 1);
+          const int res = mine < kn ? angle_test32(g, gjj, gkk[k0 + mine], a.cosA32, a.margin) : 0;
+          if (__any_sync(0xffffffffu, res == 2)) {
+            dead = 1;
+          } else {
+            const unsigned nb4 = __ballot_sync(0xffffffffu, res == 1 && (lane & 7) == 0);
+            for (int u = 0; u < 4; ++u)
+              if ((nb4 >> (8 * u)) & 1u) {
+                if (lane == 0) nlist[warp * R1a + nn] = k0 + u;
+                ++nn;
               }
-              lst[w + 1] = x;
-            }
-          }
-          __syncwarp();
-          const float* cj = a.X + (int64_t)j * a.ld;
-          const double gj = warp_cdot_f64(cj, cj, xg, a.d);
-          bool c64 = false;
-          for (int u = 0; u < nn && !c64; ++u) {
-            const int k = lst[u];
-            const float* ck = a.X + (int64_t)kid[k] * a.ld;
-            double gk = g64[k];
-            if (gk < 0.0) {
-              gk = warp_cdot_f64(ck, ck, xg, a.d);
-              __syncwarp();
-              if (lane == 0) g64[k] = gk;
-            }
-            double c = cos_from_gram_f64(warp_cdot_f64(cj, ck, xg, a.d), gj, gk);
-            if (fabs(c - a.cosA64) <= PW_TIE_COS)
-              c = cos_from_gram_f64(centred_dot_f64(cj, ck, xg, a.d), centred_dot_f64(cj, cj, xg, a.d),
-                                    centred_dot_f64(ck, ck, xg, a.d));
-            if (fabs(c - a.cosA64) <= a.border) ++nb;
-            ++n64;
-            if (c > a.cosA64) c64 = true;
-          }
-          __syncwarp();
-          if (lane == 0) {
-            dec[s3] = c64 ? 1 : 0;
-            if (!c64) g64[kept] = gj;
           }
         }
-        __syncthreads();
-        accept = !dec[s3];
+        if (lane == 0) {
+          wg[warp] = gjj;
+          wid[warp] = j;
+          wdead[warp] = dead;
+          wnn[warp] = nn;
+        }
       }
-      if (accept) {
-        if (tid == 0) out[kept] = j;
-        ++kept;
+      __syncthreads();
+      // ---- step 2: warp 0 settles the window in candidate order
+      if (warp == 0) {
+        const int kept0 = kept;
+        const int wend = min(PW_WARPS, len - t0);
+        for (int w = 0; w < wend && kept < a.R; ++w) {
+          if (wdead[w]) continue;
+          const float gjj = wg[w];
+          const int32_t j = wid[w];
+          const float4* vw = (const float4*)kept_row(kept0 + w);
+          // against the vectors kept earlier in this window (their window slots)
+          bool conflict = false;
+          int wnear = 0;  // bit q: kept vector kept0 + q to re-take in fp64
+          for (int q = 0; q < kept - kept0 && !conflict; ++q) {
+            const float4* vu = (const float4*)kept_row(kept0 + q);
+            float g = 0.f;
+            for (int f = lane; f < nq4; f += 32) g = dot4(vw[f], vu[f], g);
+            g = warp_sum(g);
+            const int r = angle_test32(g, gjj, gkk[kept0 + q], a.cosA32, a.margin);
+            if (r == 2) conflict = true;
+            else if (r == 1) wnear |= 1 << q;
+          }
+          if (!conflict && (wnn[w] > 0 || wnear)) {
+            // fp64 re-tests, kept order: first those listed in step 1, then this window's
+            const float* cj = a.X + (int64_t)j * a.ld;
+            const double gj = warp_cdot_f64(cj, cj, xg, a.d);
+            const int nl = wnn[w];
+            for (int u = 0; u < nl + PW_WARPS && !conflict; ++u) {
+              int k;
+              if (u < nl) {
+                k = nlist[w * R1a + u];
+              } else {
+                if (!((wnear >> (u - nl)) & 1)) continue;
+                k = kept0 + (u - nl);
+              }
+              const float* ck = a.X + (int64_t)kid[k] * a.ld;
+              double gk = g64[k];
+              if (gk < 0.0) {
+                gk = warp_cdot_f64(ck, ck, xg, a.d);
+                __syncwarp();
+                if (lane == 0) g64[k] = gk;
+              }
+              double c = cos_from_gram_f64(warp_cdot_f64(cj, ck, xg, a.d), gj, gk);
+              if (fabs(c - a.cosA64) <= PW_TIE_COS)
+                c = cos_from_gram_f64(centred_dot_f64(cj, ck, xg, a.d),
+                                      centred_dot_f64(cj, cj, xg, a.d),
+                                      centred_dot_f64(ck, ck, xg, a.d));
+              if (fabs(c - a.cosA64) <= a.border) ++nb;
+              ++n64;
+              if (c > a.cosA64) conflict = true;
+            }
+            if (!conflict && lane == 0) g64[kept] = gj;
+          } else if (!conflict && lane == 0) {
+            g64[kept] = -1.0;
+          }
+          if (!conflict) {
+            if (kept != kept0 + w) {  // down to the next kept slot (a dropped one's)
+              float4* dst = (float4*)kept_row(kept);
+              for (int f = lane; f < nq4; f += 32) dst[f] = vw[f];
+            }
+            if (lane == 0) {
+              gkk[kept] = gjj;
+              kid[kept] = j;
+              out[kept] = j;
+            }
+            ++kept;
+          }
+          __syncwarp();
+        }
+        if (lane == 0) wdead[0] = kept;  // hand the count to the other warps
       }
-      prefetch(t + PW_PF);  // into the ring slot of candidate t, which every warp has read
+      __syncthreads();
+      kept = wdead[0];
+      __syncthreads();  // every warp has read the count before the next window writes it
     }
-    cp_async_wait<0>();
     for (int t = kept + tid; t < a.R; t += PW_THREADS) out[t] = -1;
     if (tid == 0) a.deg[i] = kept;
   }
@@ -298,7 +309,7 @@ void prune_run_wide(const float* X, int ld, int d, int64_t n, const int32_t* can
   const size_t budget = std::min<size_t>(225 * 1024, (226 * 1024) / bps - 1024);
   const size_t fixed = wide_layout(d, R, 0).total;
   SSG_REQUIRE(fixed + row <= budget, SSG_EINTERNAL, "wide prune: rows of %d values do not fit", d);
-  const int cap = (int)std::min<size_t>((size_t)R + 1, (budget - fixed) / row);
+  const int cap = (int)std::min<size_t>((size_t)R + PW_WARPS, (budget - fixed) / row);
   const size_t smem = wide_layout(d, R, cap).total;
   const void* fn = d4 <= 512 ? (const void*)k_prune_wide<4> : (const void*)k_prune_wide<8>;
   ensure_smem(fn, smem);
@@ -307,7 +318,7 @@ void prune_run_wide(const float* X, int ld, int d, int64_t n, const int32_t* can
   const int64_t grid = std::min<int64_t>(std::max<int64_t>(n, 1),
                                          (int64_t)std::max(1, per_sm) * num_sms());
   Scratch<float> Vg;
-  if (cap < R + 1) Vg.alloc((size_t)grid * (R + 1 - cap) * d4, st);
+  if (cap < R + PW_WARPS) Vg.alloc((size_t)grid * (R + PW_WARPS - cap) * d4, st);
   WideArgs a{X, ld, d, n, cand, len, stride, R, (float)cos_a,
              angle_margin_fp32(d) + (float)border, cos_a, border, adj, deg, Vg.p, cap,
              &dctr->angle_fp64, &dctr->angle_border};

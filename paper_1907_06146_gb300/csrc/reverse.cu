@@ -213,7 +213,7 @@ __global__ void k_max_int(const int* __restrict__ v, int64_t n, int* __restrict_
 int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
                 const int32_t* adj0, const int32_t* deg0, int R, double cos_a, double border,
                 int exact, bool tc, int32_t* adj1, int32_t* deg1, Counters* dctr,
-                cudaStream_t st) {
+                cudaStream_t st, int wide_blocks) {
   const int grid = 8 * num_sms();
   Scratch<int> indeg((size_t)n, st), fill((size_t)n, st), small(2, st);
   SSG_CUDA(cudaMemsetAsync(indeg.p, 0, sizeof(int) * n, st));
@@ -266,7 +266,8 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
                  big.p, small2.p, &dctr->order_fp64, &dctr->angle_fp64, (float*)nullptr, lists.p,
                  list_len.p, Lr, border, &dctr->angle_border);
     }
-    prune_run_wide(X, ld, d, n, lists.p, list_len.p, Lr, R, cos_a, border, adj1, deg1, dctr, st);
+    prune_run_wide(X, ld, d, n, lists.p, list_len.p, Lr, R, cos_a, border, adj1, deg1, dctr, st,
+                   wide_blocks);
     return h[1];
   }
   // warp path: per-warp buffers of cap keys (a power of two, for the sort); lists longer
