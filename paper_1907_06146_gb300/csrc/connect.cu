@@ -141,8 +141,8 @@ __global__ void k_repair_fp32(const float* __restrict__ X, int ld, int64_t n,
     atomicMin(&s->hi_bits, __float_as_uint(best * (1.f + 2.f * rel) + 1e-30f));
 }
 
-// Pass 2: every candidate whose fp32 lower bound does not exceed that upper bound is
-// recomputed in fp64 (coordinate-order sum) into a short list.
+// Pass 2: every candidate whose fp32 lower bound does not exceed that upper bound goes
+// into a short list ...
 __global__ void k_repair_band(const float* __restrict__ X, int ld, int d, int64_t n,
                               const float* __restrict__ d32, float rel, int cap,
                               int32_t* __restrict__ ids, double* __restrict__ dv,
@@ -154,41 +154,30 @@ __global__ void k_repair_band(const float* __restrict__ X, int ld, int d, int64_
        v += (int64_t)gridDim.x * blockDim.x) {
     const float e = d32[v];
     if (e >= 0.f && e * (1.f - 2.f * rel) <= hi) {
-      const double x = dist2_f64(X + v * ld, X + u * ld, d);
       const int p = atomicAdd(&s->band, 1);
-      if (p < cap) {
-        ids[p] = (int32_t)v;
-        dv[p] = x;
-      }
+      if (p < cap) ids[p] = (int32_t)v;
     }
   }
 }
 
-// Pass 3 (one block): the (d2, id)-smallest entry of the list; link it to u and make u the
-// frontier of the next traversal.
-__global__ void k_repair_pick(const int32_t* __restrict__ ids, const double* __restrict__ dv,
-                              int cap, int32_t* __restrict__ adj, int32_t* __restrict__ deg, int R,
-                              uint32_t* __restrict__ bm, int32_t* __restrict__ frontier,
-                              int64_t n, RepairState* __restrict__ s) {
-  __shared__ double bd[32];
-  __shared__ int bi[32];
+// ... whose fp64 distances to u are then summed, one list entry per warp
+// (warp_dist2_f64; k_repair_pick re-takes near-equal ones in coordinate order).
+__global__ void k_repair_band64(const float* __restrict__ X, int ld, int d, int64_t n,
+                                int cap, const int32_t* __restrict__ ids, double* __restrict__ dv,
+                                const RepairState* __restrict__ s) {
   const int64_t u = (int64_t)s->u;
   if (u >= n) return;
-  const int m = s->band;
-  if (m > cap) {
-    if (threadIdx.x == 0) s->best = -2;
-    return;
+  const int m = min(s->band, cap);
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = gw; p < m; p += nwarp) {
+    const double x = warp_dist2_f64(X + (int64_t)ids[p] * ld, X + u * ld, d);
+    if (lane_id() == 0) dv[p] = x;
   }
-  double best = __longlong_as_double(0x7ff0000000000000ll);
-  int bid = INT_MAX;
-  for (int t = threadIdx.x; t < m; t += blockDim.x) {
-    const double x = dv[t];
-    const int v = ids[t];
-    if (x < best || (x == best && v < bid)) {
-      best = x;
-      bid = v;
-    }
-  }
+}
+
+// (d2, id)-smallest over the block (every thread returns it); bd / bi: 32 entries each.
+__device__ __forceinline__ void block_argmin(double& best, int& bid, double* bd, int* bi) {
   for (int o = 16; o > 0; o >>= 1) {
     const double ob = __shfl_xor_sync(0xffffffffu, best, o);
     const int oi = __shfl_xor_sync(0xffffffffu, bid, o);
@@ -198,17 +187,72 @@ __global__ void k_repair_pick(const int32_t* __restrict__ ids, const double* __r
     }
   }
   const int w = threadIdx.x >> 5, lane = lane_id();
+  __syncthreads();
   if (lane == 0) {
     bd[w] = best;
     bi[w] = bid;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int t = 1; t < (int)(blockDim.x >> 5); ++t)
-      if (bd[t] < best || (bd[t] == best && bi[t] < bid)) {
-        best = bd[t];
-        bid = bi[t];
+  for (int t = 0; t < (int)(blockDim.x >> 5); ++t)
+    if (bd[t] < best || (bd[t] == best && bi[t] < bid)) {
+      best = bd[t];
+      bid = bi[t];
+    }
+}
+
+// Pass 3 (one block): the (d2, id)-smallest entry of the list; link it to u and make u the
+// frontier of the next traversal.  Where other entries lie within fp64_order_rel of the
+// smallest warp-summed value, those entries are re-taken in coordinate order, so the
+// choice is the one the coordinate-order fp64 values give.
+__global__ void k_repair_pick(const float* __restrict__ X, int ld, int d,
+                              const int32_t* __restrict__ ids, const double* __restrict__ dv,
+                              int cap, int32_t* __restrict__ adj, int32_t* __restrict__ deg, int R,
+                              uint32_t* __restrict__ bm, int32_t* __restrict__ frontier,
+                              int64_t n, RepairState* __restrict__ s) {
+  __shared__ double bd[32];
+  __shared__ int bi[32];
+  __shared__ int nties;
+  const int64_t u = (int64_t)s->u;
+  if (u >= n) return;
+  const int m = s->band;
+  if (m > cap) {
+    if (threadIdx.x == 0) s->best = -2;
+    return;
+  }
+  const double INF = __longlong_as_double(0x7ff0000000000000ll);
+  double best = INF;
+  int bid = INT_MAX;
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    const double x = dv[t];
+    const int v = ids[t];
+    if (x < best || (x == best && v < bid)) {
+      best = x;
+      bid = v;
+    }
+  }
+  if (threadIdx.x == 0) nties = 0;
+  block_argmin(best, bid, bd, bi);
+  const double lim = best + fp64_order_rel(d) * best;
+  int mine = 0;
+  for (int t = threadIdx.x; t < m; t += blockDim.x) mine += dv[t] <= lim;
+  if (mine) atomicAdd(&nties, mine);
+  __syncthreads();
+  if (nties > 1) {
+    double b2 = INF;
+    int i2 = INT_MAX;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+      if (dv[t] > lim) continue;
+      const int v = ids[t];
+      const double x = dist2_f64(X + (int64_t)v * ld, X + u * ld, d);
+      if (x < b2 || (x == b2 && v < i2)) {
+        b2 = x;
+        i2 = v;
       }
+    }
+    block_argmin(b2, i2, bd, bi);
+    bid = i2;
+  }
+  if (threadIdx.x == 0) {
     s->best = bid;
     if (bid != INT_MAX) {
       adj[(int64_t)bid * R + deg[bid]] = (int32_t)u;
@@ -477,8 +521,10 @@ int64_t connect_run(const float* X, int ld, int d, int64_t n, int32_t* adj, int3
         SSG_LAUNCH(k_repair_fp32, grid, 256, 0, st, X, ld, n, bm.p, deg, R, rel, d32.p, S);
         SSG_LAUNCH(k_repair_band, grid, 256, 0, st, X, ld, d, n, d32.p, rel, cap, band_ids.p,
                    band_d.p, S);
-        SSG_LAUNCH(k_repair_pick, 1, 256, 0, st, band_ids.p, band_d.p, cap, adj, deg, R, bm.p, f[0],
-                   n, S);
+        SSG_LAUNCH(k_repair_band64, 2 * num_sms(), 256, 0, st, X, ld, d, n, cap, band_ids.p,
+                   band_d.p, S);
+        SSG_LAUNCH(k_repair_pick, 1, 256, 0, st, X, ld, d, band_ids.p, band_d.p, cap, adj, deg, R,
+                   bm.p, f[0], n, S);
       }
       SSG_LAUNCH(k_bfs_small, 1, 1024, 0, st, adj, deg, R, bm.p, f[0], f[1], small_limit, S);
       RepairState h;
@@ -596,8 +642,10 @@ static int64_t connect_run_noalloc(const float* X, int ld, int d, int64_t n, int
         SSG_LAUNCH(k_repair_fp32, grid, 256, 0, st, X, ld, n, bm, deg, R, rel, d32, S);
         SSG_LAUNCH(k_repair_band, grid, 256, 0, st, X, ld, d, n, d32, rel, NOALLOC_BAND, band_ids,
                    band_d, S);
-        SSG_LAUNCH(k_repair_pick, 1, 256, 0, st, band_ids, band_d, NOALLOC_BAND, adj, deg, R, bm,
-                   f[0], n, S);
+        SSG_LAUNCH(k_repair_band64, 2 * num_sms(), 256, 0, st, X, ld, d, n, NOALLOC_BAND, band_ids,
+                   band_d, S);
+        SSG_LAUNCH(k_repair_pick, 1, 256, 0, st, X, ld, d, band_ids, band_d, NOALLOC_BAND, adj, deg,
+                   R, bm, f[0], n, S);
       }
       SSG_LAUNCH(k_bfs_small, 1, 1024, 0, st, adj, deg, R, bm, f[0], f[1], small_limit, S);
       RepairState h;

@@ -39,20 +39,69 @@ __device__ __forceinline__ float team8_dist(const float* __restrict__ a,
   return s;
 }
 
+// team8_dist of a against two rows at once (b1 may be invalid): the same sums in the same
+// order as two calls, with twice the loads in flight.
+__device__ __forceinline__ void team8_dist2(const float* __restrict__ a,
+                                            const float* __restrict__ b0,
+                                            const float* __restrict__ b1, int ld4, int tl,
+                                            bool v0, bool v1, float& s0, float& s1) {
+  s0 = 0.f;
+  s1 = 0.f;
+  if (v0) {
+    const float4* a4 = (const float4*)a;
+    const float4* p4 = (const float4*)b0;
+    const float4* q4 = (const float4*)(v1 ? b1 : b0);
+#pragma unroll 4
+    for (int f = tl; f < ld4; f += 8) {
+      const float4 x = __ldg(a4 + f), y = __ldg(p4 + f), z = __ldg(q4 + f);
+      float u;
+      u = x.x - y.x;
+      s0 = fmaf(u, u, s0);
+      u = x.y - y.y;
+      s0 = fmaf(u, u, s0);
+      u = x.z - y.z;
+      s0 = fmaf(u, u, s0);
+      u = x.w - y.w;
+      s0 = fmaf(u, u, s0);
+      u = x.x - z.x;
+      s1 = fmaf(u, u, s1);
+      u = x.y - z.y;
+      s1 = fmaf(u, u, s1);
+      u = x.z - z.z;
+      s1 = fmaf(u, u, s1);
+      u = x.w - z.w;
+      s1 = fmaf(u, u, s1);
+    }
+    if (!v1) s1 = 0.f;
+  }
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 4);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 4);
+}
+
 // keys[t] holds a candidate id in its low 32 bits; replace every key in [0, m) by
-// (fp32 d2(x_i, candidate), id).  xi points at node i's padded row.
+// (fp32 d2(x_i, candidate), id).  xi points at node i's padded row.  Each team of 8 lanes
+// takes two candidates per step (team8_dist2).
 __device__ __forceinline__ void warp_fill_dist_keys(uint64_t* keys, int m,
                                                     const float* __restrict__ X, int ld,
                                                     const float* __restrict__ xi) {
   const int lane = lane_id(), team = lane >> 3, tl = lane & 7;
   const int ld4 = ld >> 2;
-  for (int t0 = 0; t0 < m; t0 += 4) {
-    const int t = t0 + team;
-    const bool valid = t < m;
-    const int32_t id = valid ? key_id(keys[t]) : 0;
-    const float dd = team8_dist(xi, X + (int64_t)id * ld, ld4, tl, valid);
+  for (int t0 = 0; t0 < m; t0 += 8) {
+    const int t = t0 + team, t1 = t + 4;
+    const bool v0 = t < m, v1 = t1 < m;
+    const int32_t id0 = v0 ? key_id(keys[t]) : 0;
+    const int32_t id1 = v1 ? key_id(keys[t1]) : 0;
+    float d0, d1;
+    team8_dist2(xi, X + (int64_t)id0 * ld, X + (int64_t)id1 * ld, ld4, tl, v0, v1, d0, d1);
     __syncwarp();
-    if (valid && tl == 0) keys[t] = make_key(dd, id);
+    if (tl == 0) {
+      if (v0) keys[t] = make_key(d0, id0);
+      if (v1) keys[t1] = make_key(d1, id1);
+    }
   }
   __syncwarp();
 }
