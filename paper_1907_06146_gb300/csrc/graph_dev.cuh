@@ -39,58 +39,75 @@ __device__ __forceinline__ float team8_dist(const float* __restrict__ a,
   return s;
 }
 
-// team8_dist of a against two rows at once (b1 may be invalid): the same sums in the same
-// order as two calls, with twice the loads in flight.
+// s + x with the rounding error of the sum added to c (Knuth's two-sum: s + x = t + err
+// exactly).  The _rn intrinsics keep the compiler from fusing or reordering these steps.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = __fadd_rn(s, x);
+  const float z = __fsub_rn(t, s);
+  c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
+  s = t;
+}
+
+// Squared distances of a to two rows at once (b1 may be invalid) by a team of 8 lanes, with
+// compensated sums: each rounded difference u is squared exactly (u*u = p + e with e from a
+// fused multiply-add), the p are added with two-sum and every error term is kept in a
+// second accumulator, also across the team's three shuffle levels.  The result lies within
+// dist_rel_team8c(ld) of the exact squared distance (the rounding of the differences,
+// then one rounding of the final sum), some forty times tighter than a plain fp32 sum of
+// 960 terms, so that far fewer neighbouring distances need an fp64 re-sort.  On integer
+// data below 2^24 every term and sum is exact and the value is that of a plain sum.
 __device__ __forceinline__ void team8_dist2(const float* __restrict__ a,
                                             const float* __restrict__ b0,
                                             const float* __restrict__ b1, int ld4, int tl,
-                                            bool v0, bool v1, float& s0, float& s1) {
-  s0 = 0.f;
-  s1 = 0.f;
+                                            bool v0, bool v1, float& r0, float& r1) {
+  float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
   if (v0) {
     const float4* a4 = (const float4*)a;
     const float4* p4 = (const float4*)b0;
     const float4* q4 = (const float4*)(v1 ? b1 : b0);
-#pragma unroll 4
+#pragma unroll 2
     for (int f = tl; f < ld4; f += 8) {
       const float4 x = __ldg(a4 + f), y = __ldg(p4 + f), z = __ldg(q4 + f);
-      float u;
-      u = x.x - y.x;
-      s0 = fmaf(u, u, s0);
-      u = x.y - y.y;
-      s0 = fmaf(u, u, s0);
-      u = x.z - y.z;
-      s0 = fmaf(u, u, s0);
-      u = x.w - y.w;
-      s0 = fmaf(u, u, s0);
-      u = x.x - z.x;
-      s1 = fmaf(u, u, s1);
-      u = x.y - z.y;
-      s1 = fmaf(u, u, s1);
-      u = x.z - z.z;
-      s1 = fmaf(u, u, s1);
-      u = x.w - z.w;
-      s1 = fmaf(u, u, s1);
+      const float ux[4] = {__fsub_rn(x.x, y.x), __fsub_rn(x.y, y.y), __fsub_rn(x.z, y.z),
+                           __fsub_rn(x.w, y.w)};
+      const float uz[4] = {__fsub_rn(x.x, z.x), __fsub_rn(x.y, z.y), __fsub_rn(x.z, z.z),
+                           __fsub_rn(x.w, z.w)};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float p = __fmul_rn(ux[e], ux[e]);
+        c0 = __fadd_rn(c0, fmaf(ux[e], ux[e], -p));
+        two_sum_acc(s0, c0, p);
+        const float q = __fmul_rn(uz[e], uz[e]);
+        c1 = __fadd_rn(c1, fmaf(uz[e], uz[e], -q));
+        two_sum_acc(s1, c1, q);
+      }
     }
-    if (!v1) s1 = 0.f;
+    if (!v1) s1 = c1 = 0.f;
   }
-  s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-  s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-  s0 += __shfl_xor_sync(0xffffffffu, s0, 4);
-  s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-  s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-  s1 += __shfl_xor_sync(0xffffffffu, s1, 4);
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const float os0 = __shfl_xor_sync(0xffffffffu, s0, o), oc0 = __shfl_xor_sync(0xffffffffu, c0, o);
+    const float os1 = __shfl_xor_sync(0xffffffffu, s1, o), oc1 = __shfl_xor_sync(0xffffffffu, c1, o);
+    c0 = __fadd_rn(c0, oc0);
+    two_sum_acc(s0, c0, os0);
+    c1 = __fadd_rn(c1, oc1);
+    two_sum_acc(s1, c1, os1);
+  }
+  r0 = __fadd_rn(s0, c0);
+  r1 = __fadd_rn(s1, c1);
 }
 
-// keys[t] holds a candidate id in its low 32 bits; replace every key in [0, m) by
-// (fp32 d2(x_i, candidate), id).  xi points at node i's padded row.  Each team of 8 lanes
-// takes two candidates per step (team8_dist2).
-__device__ __forceinline__ void warp_fill_dist_keys(uint64_t* keys, int m,
-                                                    const float* __restrict__ X, int ld,
-                                                    const float* __restrict__ xi) {
+// keys[t] holds a candidate id in its low 32 bits; replace the keys of steps t0 = first,
+// first + stride, ... (eight keys t0 .. t0 + 7 per step, below m) by (fp32 d2(x_i,
+// candidate), id).  xi points at node i's padded row.  Each team of 8 lanes takes two
+// candidates per step (team8_dist2).
+__device__ __forceinline__ void warp_fill_dist_keys_steps(uint64_t* keys, int m,
+                                                          const float* __restrict__ X, int ld,
+                                                          const float* __restrict__ xi,
+                                                          int first, int stride) {
   const int lane = lane_id(), team = lane >> 3, tl = lane & 7;
   const int ld4 = ld >> 2;
-  for (int t0 = 0; t0 < m; t0 += 8) {
+  for (int t0 = first; t0 < m; t0 += stride) {
     const int t = t0 + team, t1 = t + 4;
     const bool v0 = t < m, v1 = t1 < m;
     const int32_t id0 = v0 ? key_id(keys[t]) : 0;
@@ -104,6 +121,13 @@ __device__ __forceinline__ void warp_fill_dist_keys(uint64_t* keys, int m,
     }
   }
   __syncwarp();
+}
+
+// Every key in [0, m), by one warp.
+__device__ __forceinline__ void warp_fill_dist_keys(uint64_t* keys, int m,
+                                                    const float* __restrict__ X, int ld,
+                                                    const float* __restrict__ xi) {
+  warp_fill_dist_keys_steps(keys, m, X, ld, xi, 0, 8);
 }
 
 // Byte rows (integers 0..255, ld bytes per row, a multiple of 4): the squared distance of

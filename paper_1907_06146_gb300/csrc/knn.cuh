@@ -251,5 +251,12 @@ inline float dist_rel_fp32(int d) { return (float)((d + 4.0) * U32 * 1.01); }
 inline float dist_rel_team8(int ld) {
   return (float)((4.0 * ((ld + 31) / 32) + 6.0) * U32 * 1.01);
 }
+// The same for the compensated sums of team8_dist2 (warp_fill_dist_keys): 2u + u^2 from
+// the rounded differences, u from the final rounding, and second-order terms in the error
+// accumulator, at most (4 m^2 + 8 m + 1) u^2 with m = 4 ceil(ld / 32) terms per lane.
+inline float dist_rel_team8c(int ld) {
+  const double m = 4.0 * ((ld + 31) / 32);
+  return (float)((3.0 + (4.0 * m * m + 8.0 * m + 2.0) * U32) * U32 * 1.01);
+}
 
 }  // namespace ssg

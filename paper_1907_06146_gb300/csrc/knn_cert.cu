@@ -334,7 +334,7 @@ static int certify(const float* A, const float* B, int ld, int d, const int32_t*
   const size_t smem = (size_t)cap * 16 * wpb;
   ensure_smem((const void*)k_knn_cert, smem);
   SSG_LAUNCH(k_knn_cert, (unsigned)ceil_div(count, wpb), wpb * 32, smem, st, A, B, ld, d, rows, count,
-             cand, KS, thr, nac, ymax2, K, cap, dist_rel_team8(ld), exact_d2 ? 1 : 0, out_id, out_d2, fb,
+             cand, KS, thr, nac, ymax2, K, cap, dist_rel_team8c(ld), exact_d2 ? 1 : 0, out_id, out_d2, fb,
              fbk, fbc, n_order);
   return read_count(fbc, st);
 }

@@ -64,23 +64,13 @@ __device__ __forceinline__ void pool_finish(uint64_t* keys, int m, int L, int ex
   if (lane == 0) pool_len[i] = keep;
 }
 
-__global__ void k_pool(const float* __restrict__ X, const uint8_t* __restrict__ X8, int ld, int d,
-                       int64_t n,
-                       const int32_t* __restrict__ knn, int K, int L, int cap, int log2h,
-                       int own_first, int exact, float rel, int32_t* __restrict__ pool_id,
-                       float* __restrict__ pool_d2, int32_t* __restrict__ pool_len,
-                       unsigned long long* __restrict__ n_order) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
-  const int hcap = 1 << log2h;
-  const size_t per_warp = (size_t)cap * 8 + (size_t)hcap * 4;
-  uint64_t* keys = (uint64_t*)(sm_raw + warp * per_warp);
-  int32_t* hset = (int32_t*)(keys + cap);
-  const int64_t i = (int64_t)blockIdx.x * wpb + warp;
-  if (i >= n) return;
-
-  for (int t = lane; t < hcap; t += 32) hset[t] = -1;
-  __syncwarp();
+// Node i's candidate ids, in the order of Alg. 3's loop (or its own-row-first reading),
+// repeats and i itself dropped, into keys[0, m); returns m.  One warp; hset (1 << log2h
+// entries) must hold -1 everywhere.
+__device__ __forceinline__ int warp_collect_pool(int64_t i, const int32_t* __restrict__ knn,
+                                                 int K, int L, int own_first, int log2h,
+                                                 int32_t* hset, uint64_t* keys) {
+  const int lane = lane_id();
   int m = 0;
   if (own_first) {
     // the node's own row whole, then its neighbours' rows while the pool holds < L ids
@@ -114,8 +104,81 @@ __global__ void k_pool(const float* __restrict__ X, const uint8_t* __restrict__ 
     }
   }
   __syncwarp();
+  return m;
+}
+
+__global__ void k_pool(const float* __restrict__ X, const uint8_t* __restrict__ X8, int ld, int d,
+                       int64_t n,
+                       const int32_t* __restrict__ knn, int K, int L, int cap, int log2h,
+                       int own_first, int exact, float rel, int32_t* __restrict__ pool_id,
+                       float* __restrict__ pool_d2, int32_t* __restrict__ pool_len,
+                       unsigned long long* __restrict__ n_order) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
+  const int hcap = 1 << log2h;
+  const size_t per_warp = (size_t)cap * 8 + (size_t)hcap * 4;
+  uint64_t* keys = (uint64_t*)(sm_raw + warp * per_warp);
+  int32_t* hset = (int32_t*)(keys + cap);
+  const int64_t i = (int64_t)blockIdx.x * wpb + warp;
+  if (i >= n) return;
+
+  for (int t = lane; t < hcap; t += 32) hset[t] = -1;
+  __syncwarp();
+  const int m = warp_collect_pool(i, knn, K, L, own_first, log2h, hset, keys);
+  __syncwarp();
   pool_finish(keys, m, L, exact, (double*)hset, X, X8, ld, d, i, rel, pool_id, pool_d2, pool_len,
               n_order);
+}
+
+// The same pools for nodes with long rows (above 256 values), one node per block of eight
+// warps: at these widths the distances (some L rows of d floats per node) are nearly all
+// of the work, and a warp per node with its key and hash buffers beside it leaves the SM
+// with too few warps to cover the row loads.  Warp 0 gathers the ids exactly as k_pool
+// does, the eight warps share the distances, the block sorts, warp 0 re-sorts near-equal
+// runs; the pool is k_pool's, entry for entry.
+constexpr int POOLW_WARPS = 8;
+__global__ void __launch_bounds__(POOLW_WARPS * 32)
+    k_pool_wide(const float* __restrict__ X, int ld, int d, int64_t n,
+                const int32_t* __restrict__ knn, int K, int L, int cap, int log2h, int own_first,
+                int exact, float rel, int32_t* __restrict__ pool_id, float* __restrict__ pool_d2,
+                int32_t* __restrict__ pool_len, unsigned long long* __restrict__ n_order) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ int s_m;
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const int hcap = 1 << log2h;
+  uint64_t* keys = (uint64_t*)sm_raw;
+  int32_t* hset = (int32_t*)(keys + cap);
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    __syncthreads();  // the previous node's readers are done
+    for (int t = threadIdx.x; t < hcap; t += blockDim.x) hset[t] = -1;
+    __syncthreads();
+    if (warp == 0) {
+      const int m0 = warp_collect_pool(i, knn, K, L, own_first, log2h, hset, keys);
+      if (lane == 0) s_m = m0;
+    }
+    __syncthreads();
+    const int m = s_m;
+    const float* xi = X + i * ld;
+    warp_fill_dist_keys_steps(keys, m, X, ld, xi, 8 * warp, 8 * POOLW_WARPS);
+    int mp = 1;
+    while (mp < m) mp <<= 1;
+    for (int t = m + threadIdx.x; t < mp; t += blockDim.x) keys[t] = KEY_NONE;
+    __syncthreads();
+    block_sort_keys(keys, mp);
+    const int keep = m < L ? m : L;
+    if (warp == 0 && !exact && m > 1) {
+      int f = warp_fix_runs(keys, m, keep, (double*)hset, X, ld, d, xi, rel);
+      for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+      if (lane == 0 && f) atomicAdd(n_order, (unsigned long long)f);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+      const bool v = t < keep;
+      pool_id[i * L + t] = v ? key_id(keys[t]) : -1;
+      pool_d2[i * L + t] = v ? key_dist(keys[t]) : __int_as_float(0x7f800000);
+    }
+    if (threadIdx.x == 0) pool_len[i] = keep;
+  }
 }
 
 // Pools from given candidates: row i's pool is the L nearest of its KS candidate ids
@@ -151,11 +214,24 @@ void pool_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const
   int log2h = 0;
   while ((1 << log2h) < 2 * cap) ++log2h;
   const size_t per_warp = (size_t)cap * 8 + ((size_t)1 << log2h) * 4;
+  if (!X8 && ((d + 3) & ~3) > 256) {
+    // long float rows: a block per node
+    ensure_smem((const void*)k_pool_wide, per_warp);
+    int per_sm = 0;
+    SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pool_wide, POOLW_WARPS * 32,
+                                                           per_warp));
+    const int64_t grid = std::min<int64_t>(std::max<int64_t>(n, 1),
+                                           (int64_t)std::max(1, per_sm) * num_sms());
+    SSG_LAUNCH(k_pool_wide, (unsigned)grid, POOLW_WARPS * 32, per_warp, st, X, ld, d, n, knn, K, L,
+               cap, log2h, own_first, exact, dist_rel_team8c(ld), pool_id, pool_d2, pool_len,
+               &dctr->order_fp64);
+    return;
+  }
   int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
   const size_t smem = per_warp * wpb;
   ensure_smem((const void*)k_pool, smem);
   SSG_LAUNCH(k_pool, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, X8, ld, d, n, knn, K, L, cap,
-             log2h, own_first, exact, dist_rel_team8(ld), pool_id, pool_d2, pool_len, &dctr->order_fp64);
+             log2h, own_first, exact, dist_rel_team8c(ld), pool_id, pool_d2, pool_len, &dctr->order_fp64);
 }
 
 void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
@@ -166,7 +242,7 @@ void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int6
   const size_t smem = (size_t)cap * 16 * wpb;
   ensure_smem((const void*)k_pool_cand, smem);
   SSG_LAUNCH(k_pool_cand, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, X8, ld, d, n, cand, KS,
-             L, cap, exact, dist_rel_team8(ld), pool_id, pool_d2, pool_len, &dctr->order_fp64);
+             L, cap, exact, dist_rel_team8c(ld), pool_id, pool_d2, pool_len, &dctr->order_fp64);
 }
 
 // ---------------------------------------------------------------------------------------

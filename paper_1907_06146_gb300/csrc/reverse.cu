@@ -228,7 +228,7 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
 
   const bool wide = prune_is_wide(d, R);
   const size_t prune_bytes = merge_prune_bytes(d, R, wide);
-  const float rel = dist_rel_team8(ld), margin = angle_margin_fp32(d) + (float)border;
+  const float rel = dist_rel_team8c(ld), margin = angle_margin_fp32(d) + (float)border;
   const int d4 = (d + 3) & ~3;
   // Tensor-core path (data exact in bf16): the warps only merge and sort, lists of up to
   // 127 candidates go to the Gram prune, longer ones to the warp prune below.
