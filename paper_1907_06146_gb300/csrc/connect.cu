@@ -27,13 +27,19 @@ __global__ void k_mark(uint32_t* __restrict__ bm, int32_t* __restrict__ frontier
   *fcount = 1;
 }
 
-__global__ void k_bfs_level(const int32_t* __restrict__ adj, const int32_t* __restrict__ deg, int R,
-                            uint32_t* __restrict__ bm, const int32_t* __restrict__ frontier,
-                            const int* __restrict__ fcount, int32_t* __restrict__ next,
-                            int* __restrict__ ncount) {
+// Level l of the grid-wide traversal launched in batches (no host round trip per level):
+// the frontier size is lvl[l % 3], the next one is counted in lvl[(l + 1) % 3], and
+// lvl[(l + 2) % 3] (level l - 1's input, level l + 1's output) is cleared for the next
+// launch.  A level whose frontier is empty does nothing.
+__global__ void k_bfs_level_ring(const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
+                                 int R, uint32_t* __restrict__ bm,
+                                 const int32_t* __restrict__ frontier, int32_t* __restrict__ next,
+                                 int* __restrict__ lvl, int l) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) lvl[(l + 2) % 3] = 0;
   const int lane = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int fc = *fcount;
+  const int fc = lvl[l % 3];
+  int* ncount = lvl + (l + 1) % 3;
   for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < fc;
        w += nwarps) {
     const int32_t node = frontier[w];
@@ -54,6 +60,11 @@ __global__ void k_bfs_level(const int32_t* __restrict__ adj, const int32_t* __re
       if (fresh) next[basep + __popc(bal & lanemask_lt())] = v;
     }
   }
+}
+
+__global__ void k_ring_init(int* __restrict__ lvl, const int* __restrict__ fcount) {
+  lvl[0] = *fcount;
+  lvl[1] = 0;
 }
 
 __global__ void k_first_unreached(const uint32_t* __restrict__ bm, int64_t nw, int64_t n,
@@ -106,6 +117,7 @@ struct RepairState {
   int best;              // chosen v (INT_MAX: none; -2: band overflow)
   int fcnt[2];           // frontier sizes
   int bfs_state;         // -1 traversal finished, else index of the frontier still to expand
+  int lvl[3];            // frontier sizes of the batched traversal, by level mod 3
 };
 
 __global__ void k_repair_init(RepairState* __restrict__ s, int64_t n) {
@@ -454,19 +466,23 @@ __global__ void __launch_bounds__(1024)
   if (tid == 0 && made) atomicAdd(nrep, made);
 }
 
-// Level-synchronous traversal by the whole grid, starting from frontier buffer `cur`.
+// Level-synchronous traversal by the whole grid, starting from frontier buffer `cur`: the
+// levels are launched in batches (4, 8, 16, then 32 at a time) and the host reads the
+// next frontier's size once per batch.
 static void bfs_levels(const int32_t* adj, const int32_t* deg, int R, uint32_t* bm, int32_t* f[2],
                        RepairState* s, int cur, cudaStream_t st) {
   const int grid = 4 * num_sms();
+  SSG_LAUNCH(k_ring_init, 1, 1, 0, st, s->lvl, &s->fcnt[cur]);
+  int l = 0, batch = 4;
   for (;;) {
-    SSG_CUDA(cudaMemsetAsync(&s->fcnt[cur ^ 1], 0, sizeof(int), st));
-    SSG_LAUNCH(k_bfs_level, grid, 256, 0, st, adj, deg, R, bm, f[cur], &s->fcnt[cur], f[cur ^ 1],
-               &s->fcnt[cur ^ 1]);
+    for (int b = 0; b < batch; ++b, ++l)
+      SSG_LAUNCH(k_bfs_level_ring, grid, 256, 0, st, adj, deg, R, bm, f[(cur + l) & 1],
+                 f[(cur + l + 1) & 1], s->lvl, l);
     int h = 0;
-    SSG_CUDA(cudaMemcpyAsync(&h, &s->fcnt[cur ^ 1], sizeof(int), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaMemcpyAsync(&h, &s->lvl[l % 3], sizeof(int), cudaMemcpyDeviceToHost, st));
     SSG_CUDA(cudaStreamSynchronize(st));
-    cur ^= 1;
     if (h == 0) break;
+    batch = std::min(2 * batch, 32);
   }
 }
 
