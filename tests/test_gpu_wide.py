@@ -105,9 +105,9 @@ def test_too_wide_rows_refused_for_bf16(ssg):
 
 def test_block_prune_spill_and_ties(ssg):
     """The block prune of long rows (d = 960, R = 70).  80 repeated rows give zero-length
-    edges and exact distance ties in the pools and the reverse lists.  At 60 degrees about a
-    sixth of the nodes keep more vectors than the block's shared memory holds (the rest
-    live in its device slot); at 35 degrees every node keeps R = 70.  Prune and reverse
+    edges and exact distance ties in the pools and the reverse lists.  At 60 degrees a few
+    percent of the nodes keep more than 24 vectors, more than the block's shared memory
+    holds (the rest live in its device slot); at 35 degrees nearly every node keeps R = 70.  Prune and reverse
     merge at both angles, the pools and the whole build at 60 must equal the oracle."""
     w = synth.gist_like(n=900, nq=0, n_clusters=6)
     base = w.base.copy()
@@ -122,11 +122,11 @@ def test_block_prune_spill_and_ties(ssg):
     for alpha in (60.0, 35.0):
         if alpha == 60.0:
             a0, d0, a1, d1 = ref["adj0"], ref["deg0"], ref["adj1"], ref["deg1"]
-            assert (d0 > 24).mean() > 0.1
+            assert (d0 > 24).mean() > 0.02
         else:
             a0, d0 = oracle.prune(base, ref["pool_id"], ref["pool_len"], 70, alpha)
             a1, d1 = oracle.reverse(base, a0, d0, alpha)[:2]
-            assert (d0 == 70).all()
+            assert (d0 == 70).mean() > 0.9
         adj0, deg0 = ssg.prune(b, _cuda(ref["pool_id"]), _cuda(ref["pool_len"]), 70, alpha)
         np.testing.assert_array_equal(_np(deg0), d0)
         np.testing.assert_array_equal(_np(adj0), a0)
