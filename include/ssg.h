@@ -63,7 +63,12 @@ typedef enum {
  *         certify), the candidates are re-ranked in fp64, and a row is certified when its
  *         K-th exact distance lies below the KS-th bf16 distance minus the rigorous bound
  *         |d2_bf16 - d2| <= (2^-7 + ..) |x - mu| max_y |y - mu| + ..; every other row is
- *         recomputed exhaustively (counted in ssg_build_stats.n_knn_fallback_rows).
+ *         recomputed exhaustively (counted in ssg_build_stats.n_knn_fallback_rows).  Where
+ *         that band would need more than 768 candidates (high intrinsic dimension, as in
+ *         the GIST-shaped data), every value goes in as a bf16 pair hi + lo (three products
+ *         per coordinate, K three times as long, error about 3 * 2^-16 |x| |y| plus the
+ *         fp32 accumulation), for rows of up to 1,344 values
+ *         (ssg_build_stats.knn_bf16_pairs).
  *         EINVAL where the tensor-core path does not run.
  *   AUTO  BF16 where the tensor-core path runs, FP32 otherwise (the default).
  *   BF16_RERANK  the same as BF16 (an older name of the mode).
@@ -127,7 +132,10 @@ typedef struct {
                                K-chunked 128 x 256-tile kernel), prune_warps (warps per
                                block of the batched prune, 0 = automatic, up to 16),
                                prune_bucket_width (pool lengths per bucket of the batched
-                               prune's longest-first order, 1..1024), prune_wide_blocks
+                               prune's longest-first order, 1..1024), knn_bf16_pairs (the
+                               certified bf16 kNN's operands as bf16 pairs: 1 always, 0
+                               never, -1 = automatic: where the sized single-bf16 band
+                               needs more than 768 candidates), prune_wide_blocks
                                (blocks per SM of the block prune of rows of 330 to 1,024
                                values, 0 = automatic (2), up to 4; fewer blocks hold more
                                kept vectors in shared memory) */
@@ -160,6 +168,9 @@ typedef struct {
   int64_t n_repair_knn_row;     /* of n_repair, the edges whose node was found in the
                                    unreached node's own kNN row (same choice as a scan of all
                                    reached nodes, made without one) */
+  int32_t knn_bf16_pairs;       /* 1 if the certified bf16 kNN sent every value as a bf16
+                                   pair (hi + lo, three products per coordinate) because a
+                                   single bf16's error band was too wide for these data */
 } ssg_build_stats;
 
 typedef struct ssg_graph ssg_graph; /* opaque, owned by the library; ssg_free releases it */

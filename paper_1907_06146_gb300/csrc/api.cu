@@ -171,6 +171,10 @@ static KnnTune read_tune_table(const char* path) {
                   "tune_table %s:%d: prune_bucket_width must be an integer in [1, 1024]", path,
                   ln);
       t.prune_bucket_width = (int)v;
+    } else if (!strcmp(name, "knn_bf16_pairs")) {
+      SSG_REQUIRE(v >= -1 && v <= 1 && v == std::floor(v), SSG_EINVAL,
+                  "tune_table %s:%d: knn_bf16_pairs must be -1, 0 or 1", path, ln);
+      t.bf16_pairs = (int)v;
     } else if (!strcmp(name, "prune_wide_blocks")) {
       SSG_REQUIRE(v >= 0 && v <= 4 && v == std::floor(v), SSG_EINVAL,
                   "tune_table %s:%d: prune_wide_blocks must be an integer in [0, 4]", path, ln);
@@ -752,6 +756,7 @@ static void build_stats(BuildCtx& c, ssg_build_stats* stats) {
   S.ms_total = c.t_all->ms();
   S.n_repair = c.n_repair;
   S.n_repair_knn_row = c.n_repair_knn;
+  S.knn_bf16_pairs = c.cert.pairs;
   S.n_angle_fp64 = (int64_t)hc.angle_fp64;
   S.n_order_fp64 = (int64_t)hc.order_fp64;
   S.n_knn_fallback_rows = c.kr.fallback_rows;

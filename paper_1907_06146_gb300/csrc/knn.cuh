@@ -69,6 +69,11 @@ struct TcExtra {
   const float* order_norm = nullptr;  // norms of A as given, for the cluster order
   int stream_rows = 0;                // 1: the K-chunked kernel (128 x 256 tiles, N = 256)
                                       // also for rows that fit the resident one
+  int pairs = 0;                      // 1: each centred value v goes in as the bf16 pair
+                                      // hi = bf16(v), lo = bf16(v - hi); A rows are laid out
+                                      // [hi | hi | lo] and B rows [hi | lo | hi] (each part
+                                      // padded to 64 values), so one accumulator sums
+                                      // hi.hi + hi.lo + lo.hi (K three times as long)
   int prepass_tiles = 0;              // near-first self-joins: a first walk over this many
                                       // tiles gives each row an upper bound of its KS-th
                                       // distance, from which the full walk starts (0: off;
@@ -92,12 +97,15 @@ struct KnnTune {
   int prune_warps = 0;          // PruneTune of a batched build
   int prune_bucket_width = 32;
   int prune_wide_blocks = 0;    // blocks per SM of the block prune of long rows (0: 2)
+  int bf16_pairs = -1;          // certified kNN operands as bf16 pairs: 1 always, 0 never,
+                                // -1 where the sized single-bf16 band is too wide
 };
 struct CertResult {
   int64_t fallback_rows = 0;  // rows not certified by the first pass
   int64_t pass2_rows = 0;     // rows that took the second tensor-core pass
   int64_t exact_rows = 0;     // rows recomputed on the exact fp32 path
   int candidates = 0;         // KS of the first pass
+  int pairs = 0;              // 1: the operands went to the tensor cores as bf16 pairs
 };
 
 struct Counters {

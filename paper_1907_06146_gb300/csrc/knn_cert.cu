@@ -103,14 +103,21 @@ __global__ void k_gather_vals(const float* __restrict__ v, const int32_t* __rest
 //  - the final fused multiply-add and the fp32 centring (x - mu rounded once per value):
 //    4.2 u32 (|x| + |y|)^2 together.
 // Every factor 2 on the dot product terms comes from d2 = |x|^2 + |y|^2 - 2 x.y.
-__host__ __device__ inline double bf16_dist_bound(double nx, double ymax2, int d) {
+// With bf16 pairs (pairs = 1: v = hi + lo + r, hi = bf16(v), lo = bf16(v - hi), so |r| <=
+// u^2 |v| and |lo| <= u (1 + u) |v|) the products hi.hi + hi.lo + lo.hi miss x.y by at most
+// (3u^2 + 2u^3 + 2u^4) |x| |y| (the product of the two pairs, less lo.lo), the accumulation
+// runs over 3 dp + 16 terms of total magnitude at most (1 + u)^2 (1 + 2u) |x| |y|, and the
+// other terms are unchanged.
+__host__ __device__ inline double bf16_dist_bound(double nx, double ymax2, int d, int pairs) {
   const double u = 1.0 / 256.0, u32 = 5.9604644775390625e-08;
-  const double g = (double)((((d + 63) / 64) * 64) + 16) * 2.384185791015625e-07;
+  const int dp = ((d + 63) / 64) * 64;
+  const double g = (double)((pairs ? 3 * dp : dp) + 16) * 2.384185791015625e-07;
   const double ax = sqrt(fmax(nx, 0.0) * (1.0 + (d + 2) * u32));
   const double ay = sqrt(fmax(ymax2, 0.0) * (1.0 + (d + 2) * u32));
   const double s = ax + ay;
-  const double e = 2.0 * (2.0 * u + u * u) * ax * ay +
-                   2.0 * g * ((1.0 + u) * (1.0 + u) * ax * ay + 0.5 * ay * ay) +
+  const double prod = pairs ? 3.0 * u * u + 2.0 * u * u * u + 2.0 * u * u * u * u : 2.0 * u + u * u;
+  const double mag = pairs ? (1.0 + u) * (1.0 + u) * (1.0 + 2.0 * u) : (1.0 + u) * (1.0 + u);
+  const double e = 2.0 * prod * ax * ay + 2.0 * g * (mag * ax * ay + 0.5 * ay * ay) +
                    4.0e-9 * ay * ay + (d + 2) * u32 * (ax * ax + ay * ay) + 4.2 * u32 * s * s;
   return e * 1.05;
 }
@@ -127,6 +134,9 @@ __host__ __device__ inline double stream_slop(double nx, double t) {
 // sampled rows' chunk (bf16 values, transposed) and the tile's chunk sit in shared memory
 // (for rows of at most CAL_DC values the sample's chunk is loaded once).
 constexpr int CAL_S = 256, CAL_TJ = 32, CAL_DC = 128;
+// RAW: the centred values unrounded (fp32 distances; used to size KS for bf16 pairs, whose
+// error is far below the band's width)
+template <bool RAW>
 __global__ void __launch_bounds__(CAL_S)
 k_band_count(const float* __restrict__ As, int s, int lda, const float* __restrict__ B, int64_t nb,
              int ldb, int d, const float* __restrict__ mu, const float* __restrict__ nac,
@@ -141,8 +151,10 @@ k_band_count(const float* __restrict__ As, int s, int lda, const float* __restri
     for (int i = t; i < CAL_DC * CAL_S; i += CAL_S) {
       const int k = i / CAL_S, q = i - k * CAL_S;
       float v = 0.f;
-      if (q < s && c0 + k < d)
-        v = __bfloat162float(__float2bfloat16_rn(__fsub_rn(As[(int64_t)q * lda + c0 + k], mu[c0 + k])));
+      if (q < s && c0 + k < d) {
+        v = __fsub_rn(As[(int64_t)q * lda + c0 + k], mu[c0 + k]);
+        if (!RAW) v = __bfloat162float(__float2bfloat16_rn(v));
+      }
       Qt[i] = v;
     }
   };
@@ -163,8 +175,10 @@ k_band_count(const float* __restrict__ As, int s, int lda, const float* __restri
         const int r = i / CAL_DC, k = i - r * CAL_DC;
         const int64_t j = j0 + r;
         float v = 0.f;
-        if (j < nb && c0 + k < d)
-          v = __bfloat162float(__float2bfloat16_rn(__fsub_rn(B[j * ldb + c0 + k], mu[c0 + k])));
+        if (j < nb && c0 + k < d) {
+          v = __fsub_rn(B[j * ldb + c0 + k], mu[c0 + k]);
+          if (!RAW) v = __bfloat162float(__float2bfloat16_rn(v));
+        }
         Y[i] = v;
       }
       __syncthreads();
@@ -193,10 +207,11 @@ k_band_count(const float* __restrict__ As, int s, int lda, const float* __restri
 // lim[t] = the sampled row's exact K-th distance plus the bound (kth: [s][ld] rows of the
 // exact kNN of the sample, the K-th distance in column col).
 __global__ void k_band_limit(const float* __restrict__ d2, int ld, int col, int s,
-                             const float* __restrict__ nac, double ymax2, int d,
-                             double* __restrict__ lim) {
+                             const float* __restrict__ nac, double ymax2, int d, int pairs,
+                             double widen, double* __restrict__ lim) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < s) lim[t] = (double)d2[(int64_t)t * ld + col] + bf16_dist_bound(nac[t], ymax2, d);
+  if (t < s)
+    lim[t] = (double)d2[(int64_t)t * ld + col] + widen * bf16_dist_bound(nac[t], ymax2, d, pairs);
 }
 
 // Exact order of each row's candidates and its certificate.  One warp per row r (rows:
@@ -209,8 +224,9 @@ __global__ void k_band_limit(const float* __restrict__ d2, int ld, int col, int 
 __global__ void k_knn_cert(const float* __restrict__ A, const float* __restrict__ B, int ld, int d,
                            const int32_t* __restrict__ rows, int64_t count,
                            const int32_t* __restrict__ cand, int KS, const float* __restrict__ thr,
-                           const float* __restrict__ nac, double ymax2, int K, int cap, float rel,
-                           int exact_d2, int32_t* __restrict__ out_id, float* __restrict__ out_d2,
+                           const float* __restrict__ nac, double ymax2, int pairs, int K, int cap,
+                           float rel, int exact_d2, int32_t* __restrict__ out_id,
+                           float* __restrict__ out_d2,
                            int32_t* __restrict__ fb, double* __restrict__ fb_kth,
                            int* __restrict__ fb_count, unsigned long long* __restrict__ n_order) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -259,7 +275,7 @@ __global__ void k_knn_cert(const float* __restrict__ A, const float* __restrict_
       kth = (double)key_dist(keys[K - 1]) * (1.0 + 1.01 * (double)rel) + 1e-30;
       if (!ok) {
         const double nx = (double)nac[row];
-        ok = kth < (double)t - stream_slop(nx, t) - bf16_dist_bound(nx, ymax2, d);
+        ok = kth < (double)t - stream_slop(nx, t) - bf16_dist_bound(nx, ymax2, d, pairs);
       }
     }
     if (!ok) {
@@ -305,11 +321,11 @@ __global__ void k_scatter_drop_self(const int32_t* __restrict__ ids, const float
 // candidates may exceed the old one by up to twice that), so that every column that can be
 // a true neighbour is admitted and a band that fits certifies against it.
 __global__ void k_band_start(const double* __restrict__ kth, const float* __restrict__ nag, int m,
-                             double ymax2, int d, float* __restrict__ tau) {
+                             double ymax2, int d, int pairs, float* __restrict__ tau) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m) return;
   const double nx = (double)nag[t];
-  const double b = kth[t] + bf16_dist_bound(nx, ymax2, d);
+  const double b = kth[t] + bf16_dist_bound(nx, ymax2, d, pairs);
   const double rel = (d + 4.0) * 5.9604644775390625e-08 * 1.01;
   const double v = b + 3.0 * stream_slop(nx, b) + 4.0 * rel * fabs(b) + 1e-30;
   tau[t] = isfinite(v) ? (float)v * (1.f + 1e-6f) : __int_as_float(0x7f800000);
@@ -325,7 +341,7 @@ static int read_count(const int* p, cudaStream_t st) {
 // One certification launch (k_knn_cert) over count rows; returns the rows that failed.
 static int certify(const float* A, const float* B, int ld, int d, const int32_t* rows, int64_t count,
                    const int32_t* cand, int KS, const float* thr, const float* nac, double ymax2,
-                   int K, bool exact_d2, int32_t* out_id, float* out_d2, int32_t* fb, double* fbk,
+                   int pairs, int K, bool exact_d2, int32_t* out_id, float* out_d2, int32_t* fb, double* fbk,
                    int* fbc, unsigned long long* n_order, cudaStream_t st) {
   SSG_CUDA(cudaMemsetAsync(fbc, 0, sizeof(int), st));
   if (count == 0) return 0;
@@ -334,7 +350,8 @@ static int certify(const float* A, const float* B, int ld, int d, const int32_t*
   const size_t smem = (size_t)cap * 16 * wpb;
   ensure_smem((const void*)k_knn_cert, smem);
   SSG_LAUNCH(k_knn_cert, (unsigned)ceil_div(count, wpb), wpb * 32, smem, st, A, B, ld, d, rows, count,
-             cand, KS, thr, nac, ymax2, K, cap, dist_rel_team8c(ld), exact_d2 ? 1 : 0, out_id, out_d2, fb,
+             cand, KS, thr, nac, ymax2, pairs, K, cap, dist_rel_team8c(ld), exact_d2 ? 1 : 0, out_id,
+             out_d2, fb,
              fbk, fbc, n_order);
   return read_count(fbc, st);
 }
@@ -373,7 +390,10 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
   memcpy(&ymax2f, &mbits, 4);
   const double ymax2 = (double)ymax2f;
   const int64_t avail = self ? nb - 1 : nb;
-  const int KS_MAX = knn_tc_max_k(d, false);  // the largest top-K the kernel keeps
+  const int dp = (d + 63) & ~63;
+  // bf16 pairs triple the rows the tensor cores see; they run where that width fits
+  const bool pairs_ok = knn_tc_available(3 * dp);
+  int pairs = tune.bf16_pairs == 1 && pairs_ok ? 1 : 0;
 
   // KS: the tune.quantile point of the sampled rows' candidate needs, plus 5%
   int KS = std::min<int64_t>(avail, std::max(K + 8, 2 * K));
@@ -390,33 +410,57 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
     SSG_LAUNCH(k_gather_vals, (unsigned)ceil_div(s, 256), 256, 0, st, nac, sid.p, (int64_t)s, asc.p);
     // the sample's exact K-th distance (itself included as a column when self: K + 1),
     // through this same certified path with the sample as queries and no sizing of its own
+    // (bf16 pairs where they run: their narrow band certifies most sample rows at once)
     const int Kq = K + self;
     Scratch<int32_t> sids((size_t)s * Kq, st);
     Scratch<float> sd2((size_t)s * Kq, st);
     KnnTune t0 = tune;
     t0.sample_rows = 0;
+    t0.bf16_pairs = pairs_ok ? 1 : 0;
     knn_bf16_certified(As.p, s, ld, asn.p, B, nb, b_norm_raw, d, info, 0, Kq, sids.p, sd2.p, false,
                        t0, n_order, st, nullptr);
     Scratch<double> lim((size_t)s, st);
-    SSG_LAUNCH(k_band_limit, (unsigned)ceil_div(s, 128), 128, 0, st, sd2.p, Kq, Kq - 1, s, asc.p,
-               ymax2, d, lim.p);
     Scratch<int> cnt((size_t)s, st);
-    SSG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * s, st));
     const size_t smem = sizeof(float) * ((size_t)CAL_DC * CAL_S + (size_t)CAL_TJ * CAL_DC);
-    ensure_smem((const void*)k_band_count, smem);
+    ensure_smem((const void*)k_band_count<false>, smem);
+    ensure_smem((const void*)k_band_count<true>, smem);
     const unsigned cg = (unsigned)std::min<int64_t>(ceil_div(nb, CAL_TJ), num_sms());
-    SSG_LAUNCH(k_band_count, cg, CAL_S, smem, st, As.p, s, ld, B, nb, ld, d, mu.p, asc.p, nbc.p, lim.p,
-               self ? (const int32_t*)sid.p : nullptr, cnt.p);
-    std::vector<int> h((size_t)s);
-    SSG_CUDA(cudaMemcpyAsync(h.data(), cnt.p, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
-    SSG_CUDA(cudaStreamSynchronize(st));
-    std::sort(h.begin(), h.end());
-    const int qi = std::min(s - 1, (int)std::ceil(tune.slack_quantile * s) - 1);
-    const int need = (int)std::ceil(h[std::max(qi, 0)] * 1.05) + 8;
+    // columns a row's first pass must keep: single bf16, those whose bf16 distance lies
+    // within the bound of the exact K-th; bf16 pairs (whose error is far below the band),
+    // those whose fp32 distance lies within twice their bound
+    auto need_for = [&](int pr) -> int {
+      SSG_LAUNCH(k_band_limit, (unsigned)ceil_div(s, 128), 128, 0, st, sd2.p, Kq, Kq - 1, s, asc.p,
+                 ymax2, d, pr, pr ? 2.0 : 1.0, lim.p);
+      SSG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * s, st));
+      const int32_t* me = self ? (const int32_t*)sid.p : nullptr;
+      if (pr)
+        SSG_LAUNCH(k_band_count<true>, cg, CAL_S, smem, st, As.p, s, ld, B, nb, ld, d, mu.p, asc.p,
+                   nbc.p, lim.p, me, cnt.p);
+      else
+        SSG_LAUNCH(k_band_count<false>, cg, CAL_S, smem, st, As.p, s, ld, B, nb, ld, d, mu.p, asc.p,
+                   nbc.p, lim.p, me, cnt.p);
+      std::vector<int> h((size_t)s);
+      SSG_CUDA(cudaMemcpyAsync(h.data(), cnt.p, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
+      SSG_CUDA(cudaStreamSynchronize(st));
+      std::sort(h.begin(), h.end());
+      const int qi = std::min(s - 1, (int)std::ceil(tune.slack_quantile * s) - 1);
+      return (int)std::ceil(h[std::max(qi, 0)] * 1.05) + 8;
+    };
+    int need = need_for(pairs);
+    // single bf16 too coarse for these data (its band would need more candidates than
+    // PAIRS_AT, or than the kernel keeps): bf16 pairs, three products per coordinate
+    constexpr int PAIRS_AT = 768;
+    if (!pairs && pairs_ok && tune.bf16_pairs < 0 &&
+        (need > PAIRS_AT || need > knn_tc_max_k(d, false))) {
+      pairs = 1;
+      need = need_for(1);
+    }
     KS = (int)std::min<int64_t>(avail, std::max(K + 8, need));
   }
+  const int KS_MAX = knn_tc_max_k(pairs ? 3 * dp : d, false);  // the largest top-K kept
   KS = std::min(KS, KS_MAX);
   res.candidates = KS;
+  res.pairs = pairs;
 
   // pass 1: every row
   Scratch<int32_t> cid((size_t)na * KS, st);
@@ -427,13 +471,14 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
   ex.order_norm = a_norm_raw;
   ex.prepass_tiles = tune.prepass_tiles;
   ex.stream_rows = tune.stream_rows;
+  ex.pairs = pairs;
   knn_exact_tc(A, na, ld, nac, B, nb, ld, nbc.p, d, self, KS, cid.p, cd2.p, st, gemm_timer, 0, true,
                ex);
   cd2.release();
   Scratch<int32_t> fb((size_t)na, st), fb2((size_t)na, st);
   Scratch<double> fbk((size_t)na, st);
   Scratch<int> fbc(1, st);
-  int nfb = certify(A, B, ld, d, nullptr, na, cid.p, KS, thr.p, nac, ymax2, K, exact_d2, out_id,
+  int nfb = certify(A, B, ld, d, nullptr, na, cid.p, KS, thr.p, nac, ymax2, pairs, K, exact_d2, out_id,
                     out_d2, fb.p, fbk.p, fbc.p, n_order, st);
   cid.release();
   res.fallback_rows = nfb;
@@ -451,15 +496,16 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
     SSG_LAUNCH(k_gather_rows, grid, 256, 0, st, A, ld, fb.p, (int64_t)nfb, Ag.p);
     SSG_LAUNCH(k_gather_vals, (unsigned)ceil_div(nfb, 256), 256, 0, st, nac, fb.p, (int64_t)nfb, nag.p);
     SSG_LAUNCH(k_band_start, (unsigned)ceil_div(nfb, 128), 128, 0, st, fbk.p, nag.p, nfb, ymax2, d,
-               tau2.p);
+               pairs, tau2.p);
     TcExtra ex2;
     ex2.mu = mu.p;
     ex2.out_thresh = thr2.p;
     ex2.qid = self ? fb.p : nullptr;
     ex2.tau_in = tau2.p;
+    ex2.pairs = pairs;
     knn_exact_tc(Ag.p, nfb, ld, nag.p, B, nb, ld, nbc.p, d, self, KS2, cid2.p, cd22.p, st, nullptr, 0,
                  true, ex2);
-    nlast = certify(Ag.p, B, ld, d, fb.p, nfb, cid2.p, KS2, thr2.p, nac, ymax2, K, exact_d2, out_id,
+    nlast = certify(Ag.p, B, ld, d, fb.p, nfb, cid2.p, KS2, thr2.p, nac, ymax2, pairs, K, exact_d2, out_id,
                     out_d2, fb2.p, fbk.p, fbc.p, n_order, st);
     last = fb2.p;
     res.pass2_rows = nfb;

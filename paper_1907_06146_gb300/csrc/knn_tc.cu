@@ -731,20 +731,26 @@ k_knn_tc_wide(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 
 // bf16 copy with rows padded to dp; with perm, stored row r holds row perm[r] (and its norm);
 // with mu, the rows are centred first (x - mu rounded to fp32, then to bf16).
+// Rows of width dp (pairs = 0) or of three parts of width dp (pairs = 1: [hi | hi | lo],
+// pairs = 2: [hi | lo | hi], hi = bf16(v), lo = bf16(v - hi), v the centred value).
 __global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int d, int ld,
                           __nv_bfloat16* __restrict__ Y, int dp, const int32_t* __restrict__ perm,
                           const float* __restrict__ norm_in, float* __restrict__ norm_out,
-                          const float* __restrict__ mu) {
-  const int64_t total = n * (int64_t)dp;
+                          const float* __restrict__ mu, int pairs) {
+  const int w = pairs ? 3 * dp : dp;
+  const int64_t total = n * (int64_t)w;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / dp;
-    const int c = (int)(i - r * dp);
+    const int64_t r = i / w;
+    const int cw = (int)(i - r * w);
+    const int part = cw / dp, c = cw - part * dp;
     const int64_t src = perm ? (int64_t)perm[r] : r;
     float v = c < d ? X[src * ld + c] : 0.f;
     if (mu && c < d) v = __fsub_rn(v, mu[c]);
-    Y[i] = __float2bfloat16_rn(v);
-    if (norm_out && c == 0) norm_out[r] = norm_in[src];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const bool low = (pairs == 1 && part == 2) || (pairs == 2 && part == 1);
+    Y[i] = low ? __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(hi))) : hi;
+    if (norm_out && cw == 0) norm_out[r] = norm_in[src];
   }
 }
 
@@ -828,12 +834,13 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
                   int32_t* out_id, float* out_d2, cudaStream_t st, StageTimer* gemm_timer,
                   int max_tiles, bool approx, const TcExtra& ex) {
   const int dp = (d + 63) & ~63;
-  const int kchunks = dp / 64;
+  const int dpe = ex.pairs ? 3 * dp : dp;  // row width the tensor cores see
+  const int kchunks = dpe / 64;
   int stages = MAX_STAGES;
   while (stages > 2 && tc_smem_bytes(kchunks, stages) > 225 * 1024) --stages;
   // rows that do not fit the resident pipeline stream through the wide kernel
   const bool wide = tc_smem_bytes(kchunks, stages) > 225 * 1024 || ex.stream_rows;
-  SSG_REQUIRE(!wide || (d <= MAX_D_WIDE && tcw_smem_bytes() <= 225 * 1024), SSG_EINVAL,
+  SSG_REQUIRE(!wide || (dpe <= MAX_D_WIDE && tcw_smem_bytes() <= 225 * 1024), SSG_EINVAL,
               "tensor-core kNN: d = %d is too large for the shared-memory pipeline", d);
   const int bm = wide ? BMW : BM, bn = wide ? BNW : BN;
   const int KS = self ? K + 1 : K;
@@ -855,18 +862,20 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
                       ex.order_norm ? ex.order_norm : a_norm);
     norm_p.alloc((size_t)na, st);
   }
-  Scratch<__nv_bfloat16> ab((size_t)na * dp, st);
+  Scratch<__nv_bfloat16> ab((size_t)na * dpe, st);
   Scratch<__nv_bfloat16> bb;
   const int cgrid = 8 * num_sms();
   SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, A, na, d, lda, ab.p, dp,
              ordered ? (const int32_t*)ord.perm.p : nullptr, a_norm, ordered ? norm_p.p : nullptr,
-             ex.mu);
+             ex.mu, ex.pairs ? 1 : 0);
   if (ordered) a_norm = b_norm = norm_p.p;
   const __nv_bfloat16* bptr = ab.p;
-  if (!same) {
-    bb.alloc((size_t)nb * dp, st);
-    SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, B, nb, d, ldb, bb.p, dp, (const int32_t*)nullptr,
-               (const float*)nullptr, (float*)nullptr, ex.mu);
+  if (!same || ex.pairs) {
+    // bf16 pairs: the base side has its own layout (in the self-join's stored order)
+    bb.alloc((size_t)nb * dpe, st);
+    SSG_LAUNCH(k_to_bf16, cgrid, 256, 0, st, B, nb, d, ldb, bb.p, dp,
+               same && ordered ? (const int32_t*)ord.perm.p : nullptr, (const float*)nullptr,
+               (float*)nullptr, ex.mu, ex.pairs ? 2 : 0);
     bptr = bb.p;
   }
   Scratch<__nv_bfloat16> aug_b((size_t)nb * AUG, st), aug_a((size_t)BM * AUG, st);
@@ -876,8 +885,8 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
              nb, aug_b.p, err.p, approx ? 1 : 0);
   SSG_LAUNCH(k_aug_ones, 1, 256, 0, st, aug_a.p);
   TcMaps maps;
-  maps.a = make_map(ab.p, na, dp, 64, bm, CU_TENSOR_MAP_SWIZZLE_128B);
-  maps.b = make_map(bptr, nb, dp, 64, bn, CU_TENSOR_MAP_SWIZZLE_128B);
+  maps.a = make_map(ab.p, na, dpe, 64, bm, CU_TENSOR_MAP_SWIZZLE_128B);
+  maps.b = make_map(bptr, nb, dpe, 64, bn, CU_TENSOR_MAP_SWIZZLE_128B);
   maps.a_aug = make_map(aug_a.p, BM, AUG, AUG, bm, CU_TENSOR_MAP_SWIZZLE_32B);
   maps.b_aug = make_map(aug_b.p, nb, AUG, AUG, bn, CU_TENSOR_MAP_SWIZZLE_32B);
   const int64_t nrb = ceil_div(na, bm);

@@ -46,7 +46,8 @@ class BuildStats(ctypes.Structure):
                 ("gemm_prec_used", ctypes.c_int32), ("ms_knn_gemm", ctypes.c_double),
                 ("search_row_bytes", ctypes.c_int32), ("gram_prec_used", ctypes.c_int32),
                 ("n_angle_borderline", ctypes.c_int64), ("knn_candidates", ctypes.c_int32),
-                ("ms_knn_certify", ctypes.c_double), ("n_repair_knn_row", ctypes.c_int64)]
+                ("ms_knn_certify", ctypes.c_double), ("n_repair_knn_row", ctypes.c_int64),
+                ("knn_bf16_pairs", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

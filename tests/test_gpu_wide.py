@@ -167,3 +167,48 @@ def test_block_prune_exact_angles(ssg):
     with np.errstate(divide="ignore", invalid="ignore"):
         exact = int(np.sum(np.isclose(g / np.outer(nrm, nrm), 0.5, rtol=0, atol=1e-12)))
     assert exact > 0
+
+
+def _tune(text):
+    import os
+    import tempfile
+    f = tempfile.NamedTemporaryFile("w", suffix=".txt", delete=False)
+    f.write(text)
+    f.close()
+    return f.name
+
+
+def test_bf16_pairs_forced_equal_oracle(ssg):
+    """knn_bf16_pairs = 1: every value goes to the tensor cores as a bf16 pair (hi + lo,
+    three products per coordinate); the graph of 960-d and 64-d float rows equals the
+    oracle's."""
+    import os
+    path = _tune("knn_bf16_pairs = 1\n")
+    try:
+        for w, K, L, R in ((synth.gist_like(n=1_500, nq=0, n_clusters=10), 30, 120, 40),
+                           (synth.small(n=3_000, d=64, nq=0, seed=77), 20, 60, 24)):
+            nav = synth.nav_ids(w.n, 3, 71)
+            g = ssg.build(_cuda(w.base), K, L, R, 60.0, nav=nav, prec="bf16", tune_table=path)
+            assert g.stats["knn_bf16_pairs"] == 1
+            o = oracle.build_graph(w.base, K, L, R, 60.0, nav)
+            np.testing.assert_array_equal(_np(g.deg), o["deg"])
+            np.testing.assert_array_equal(_np(g.adj), o["adj"])
+    finally:
+        os.unlink(path)
+
+
+def test_bf16_pairs_chosen_where_the_band_is_wide(ssg):
+    """200,000 GIST-shaped rows (local intrinsic dimension about 40): a single bf16's band
+    holds over a thousand candidates, so the build switches to bf16 pairs by itself; the
+    kNN rows of 40 sampled nodes equal the oracle's, and the candidate count stays small."""
+    w = synth.gist_like(n=200_000, nq=0)
+    b = _cuda(w.base)
+    g = ssg.build(b, 100, 300, 70, 60.0, n_nav=4)
+    st = g.stats
+    assert st["knn_bf16_pairs"] == 1
+    assert st["knn_candidates"] < 700
+    ids, d2 = ssg.knn(b, 100)
+    rows = np.sort(np.random.default_rng(9).choice(w.n, 40, replace=False))
+    oid, od2 = oracle.knn_rows(w.base, 100, rows=rows)
+    np.testing.assert_array_equal(_np(ids)[rows], oid)
+    np.testing.assert_array_equal(_np(d2)[rows], od2.astype(np.float32))
