@@ -215,15 +215,19 @@ __global__ void k_band_limit(const float* __restrict__ d2, int ld, int col, int 
 }
 
 // Exact order of each row's candidates and its certificate.  One warp per row r (rows:
-// compact index -> row id, null = identity): the candidates cand[r][0, KS) (-1 padded) get
-// fp32 distances from the original rows, are sorted by (d2, id), and runs of near-equal
-// values up to position K are re-sorted in fp64; the first K go to row rows[r] of the
-// output (d2 in fp64 rounded to float when exact_d2, else the fp32 value).  The row is
-// certified when the K-th exact distance (bounded above through the fp32 value) lies below
-// thr[r] - slop - E; otherwise it is listed in fb (with that bound) for another pass.
+// compact index -> row id, null = identity).  Of the candidates cand[r][0, KS) (-1
+// padded) only those whose tensor-core distance cd2 lies within 2 E (plus the rounding of
+// that value) of the K-th smallest one can be among the K nearest: K candidates lie at
+// most at that K-th value plus E, any other candidate at least 2 E further minus E.  Those
+// get fp32 distances from the original rows, are sorted by (d2, id), and runs of
+// near-equal values up to position K are re-sorted in fp64; the first K go to row rows[r]
+// of the output (d2 in fp64 rounded to float when exact_d2, else the fp32 value).  The row
+// is certified when the K-th exact distance (bounded above through the fp32 value) lies
+// below thr[r] - slop - E; otherwise it is listed in fb (with that bound) for another pass.
 __global__ void k_knn_cert(const float* __restrict__ A, const float* __restrict__ B, int ld, int d,
                            const int32_t* __restrict__ rows, int64_t count,
-                           const int32_t* __restrict__ cand, int KS, const float* __restrict__ thr,
+                           const int32_t* __restrict__ cand, const float* __restrict__ cd2, int KS,
+                           const float* __restrict__ thr,
                            const float* __restrict__ nac, double ymax2, int pairs, int K, int cap,
                            float rel, int exact_d2, int32_t* __restrict__ out_id,
                            float* __restrict__ out_d2,
@@ -243,12 +247,33 @@ __global__ void k_knn_cert(const float* __restrict__ A, const float* __restrict_
     const int32_t id = t < KS ? cand[r * KS + t] : -1;
     const bool v = id >= 0;
     const unsigned bal = __ballot_sync(0xffffffffu, v);
-    if (v) keys[m + __popc(bal & lanemask_lt())] = (uint64_t)(uint32_t)id;
+    if (v) keys[m + __popc(bal & lanemask_lt())] = make_key(cd2[r * KS + t], id);
     m += __popc(bal);
   }
   __syncwarp();
-  warp_fill_dist_keys(keys, m, B, ld, xi);
   int mp = 1;
+  while (mp < m) mp <<= 1;
+  for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
+  __syncwarp();
+  if (m > K) {
+    // keep the candidates that can be among the K nearest (by their tensor-core distance)
+    warp_sort_keys(keys, mp);
+    const double nx = (double)nac[row];
+    const double aK = (double)key_dist(keys[K - 1]);
+    const double lim = aK + 2.0 * bf16_dist_bound(nx, ymax2, d, pairs) + stream_slop(nx, aK);
+    int keep = K;
+    for (int c = K; c < m; c += 32) {
+      const int t = c + lane;
+      const unsigned bal = __ballot_sync(0xffffffffu, t < m && (double)key_dist(keys[t]) <= lim);
+      keep += __popc(bal);
+      if (bal != 0xffffffffu) break;
+    }
+    m = keep;
+  }
+  for (int t = lane; t < m; t += 32) keys[t] = (uint64_t)(uint32_t)key_id(keys[t]);
+  __syncwarp();
+  warp_fill_dist_keys(keys, m, B, ld, xi);
+  mp = 1;
   while (mp < m) mp <<= 1;
   for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
   __syncwarp();
@@ -340,7 +365,7 @@ static int read_count(const int* p, cudaStream_t st) {
 
 // One certification launch (k_knn_cert) over count rows; returns the rows that failed.
 static int certify(const float* A, const float* B, int ld, int d, const int32_t* rows, int64_t count,
-                   const int32_t* cand, int KS, const float* thr, const float* nac, double ymax2,
+                   const int32_t* cand, const float* cd2, int KS, const float* thr, const float* nac, double ymax2,
                    int pairs, int K, bool exact_d2, int32_t* out_id, float* out_d2, int32_t* fb, double* fbk,
                    int* fbc, unsigned long long* n_order, cudaStream_t st) {
   SSG_CUDA(cudaMemsetAsync(fbc, 0, sizeof(int), st));
@@ -350,7 +375,7 @@ static int certify(const float* A, const float* B, int ld, int d, const int32_t*
   const size_t smem = (size_t)cap * 16 * wpb;
   ensure_smem((const void*)k_knn_cert, smem);
   SSG_LAUNCH(k_knn_cert, (unsigned)ceil_div(count, wpb), wpb * 32, smem, st, A, B, ld, d, rows, count,
-             cand, KS, thr, nac, ymax2, pairs, K, cap, dist_rel_team8c(ld), exact_d2 ? 1 : 0, out_id,
+             cand, cd2, KS, thr, nac, ymax2, pairs, K, cap, dist_rel_team8c(ld), exact_d2 ? 1 : 0, out_id,
              out_d2, fb,
              fbk, fbc, n_order);
   return read_count(fbc, st);
@@ -474,13 +499,13 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
   ex.pairs = pairs;
   knn_exact_tc(A, na, ld, nac, B, nb, ld, nbc.p, d, self, KS, cid.p, cd2.p, st, gemm_timer, 0, true,
                ex);
-  cd2.release();
   Scratch<int32_t> fb((size_t)na, st), fb2((size_t)na, st);
   Scratch<double> fbk((size_t)na, st);
   Scratch<int> fbc(1, st);
-  int nfb = certify(A, B, ld, d, nullptr, na, cid.p, KS, thr.p, nac, ymax2, pairs, K, exact_d2, out_id,
+  int nfb = certify(A, B, ld, d, nullptr, na, cid.p, cd2.p, KS, thr.p, nac, ymax2, pairs, K, exact_d2, out_id,
                     out_d2, fb.p, fbk.p, fbc.p, n_order, st);
   cid.release();
+  cd2.release();
   res.fallback_rows = nfb;
   int nlast = nfb;
   const int32_t* last = fb.p;
@@ -505,7 +530,7 @@ CertResult knn_bf16_certified(const float* A, int64_t na, int ld, const float* a
     ex2.pairs = pairs;
     knn_exact_tc(Ag.p, nfb, ld, nag.p, B, nb, ld, nbc.p, d, self, KS2, cid2.p, cd22.p, st, nullptr, 0,
                  true, ex2);
-    nlast = certify(Ag.p, B, ld, d, fb.p, nfb, cid2.p, KS2, thr2.p, nac, ymax2, pairs, K, exact_d2, out_id,
+    nlast = certify(Ag.p, B, ld, d, fb.p, nfb, cid2.p, cd22.p, KS2, thr2.p, nac, ymax2, pairs, K, exact_d2, out_id,
                     out_d2, fb2.p, fbk.p, fbc.p, n_order, st);
     last = fb2.p;
     res.pass2_rows = nfb;
