@@ -409,6 +409,7 @@ def run_float_arm(ssg, n, d, K, L, R, ls=64, seed=190706144, w=None, label=None)
                     "gemm_prec_used": st["gemm_prec_used"],
                     "knn_candidates": st["knn_candidates"],
                     "knn_rows_not_certified_by_first_pass": st["n_knn_fallback_rows"],
+                    "knn_bf16_pairs": st["knn_bf16_pairs"],
                     "stages_ms": {k: st[k] for k in ("ms_pool", "ms_prune", "ms_reverse",
                                                      "ms_connect")},
                     "recall@10": ssg.recall_hits(ids, truth, 10) / (10.0 * nq), "L_search": ls}
@@ -746,7 +747,8 @@ def run_gpu(args):
         "ablations": ablations,
         "alg4": alg4,
         "counters": {k: st0[k] for k in ("n_repair", "n_angle_fp64", "n_order_fp64",
-                                         "n_knn_fallback_rows", "max_indegree", "exact_mode")},
+                                         "n_knn_fallback_rows", "max_indegree", "exact_mode",
+                                         "knn_candidates", "knn_bf16_pairs")},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                      "peak_source": peak_note, "algorithmic": "2 n (n-1) d flop per launch"},
