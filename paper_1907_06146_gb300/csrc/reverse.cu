@@ -274,7 +274,8 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
   // than limit go to the second pass
   const int cap = use_tc ? 128 : 256;
   const int limit = use_tc ? 127 : cap;
-  const size_t per_warp = (size_t)cap * 20 + prune_bytes;
+  // merge-only warps (the tensor-core path) keep no prune state
+  const size_t per_warp = (size_t)cap * 20 + (use_tc ? 0 : prune_bytes);
   SSG_REQUIRE((cap & (cap - 1)) == 0 && (cap * 20) % 16 == 0 && limit <= cap, SSG_EINTERNAL,
               "reverse merge: bad buffer layout (cap %d, limit %d)", cap, limit);
   const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
