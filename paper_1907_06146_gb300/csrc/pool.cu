@@ -110,13 +110,14 @@ __device__ __forceinline__ int warp_collect_pool(int64_t i, const int32_t* __res
 __global__ void k_pool(const float* __restrict__ X, const uint8_t* __restrict__ X8, int ld, int d,
                        int64_t n,
                        const int32_t* __restrict__ knn, int K, int L, int cap, int log2h,
-                       int own_first, int exact, float rel, int32_t* __restrict__ pool_id,
+                       int hbytes, int own_first, int exact, float rel,
+                       int32_t* __restrict__ pool_id,
                        float* __restrict__ pool_d2, int32_t* __restrict__ pool_len,
                        unsigned long long* __restrict__ n_order) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
   const int hcap = 1 << log2h;
-  const size_t per_warp = (size_t)cap * 8 + (size_t)hcap * 4;
+  const size_t per_warp = (size_t)cap * 8 + (size_t)hbytes;
   uint64_t* keys = (uint64_t*)(sm_raw + warp * per_warp);
   int32_t* hset = (int32_t*)(keys + cap);
   const int64_t i = (int64_t)blockIdx.x * wpb + warp;
@@ -211,9 +212,14 @@ void pool_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const
               int K, int L, int exact, int32_t* pool_id, float* pool_d2, int32_t* pool_len,
               Counters* dctr, cudaStream_t st, int own_first) {
   const int cap = next_pow2(L + K + 1);
+  // after the keys: the id hash set (load factor at most 0.6), reused as the fp64 scratch of
+  // the run re-sorts (one double per pool entry)
+  const int mmax = L + K + 1;
   int log2h = 0;
-  while ((1 << log2h) < 2 * cap) ++log2h;
-  const size_t per_warp = (size_t)cap * 8 + ((size_t)1 << log2h) * 4;
+  while ((1 << log2h) * 3 < 5 * mmax) ++log2h;
+  const size_t hbytes =
+      ((std::max<size_t>(((size_t)1 << log2h) * 4, (size_t)mmax * 8) + 15) / 16) * 16;
+  const size_t per_warp = (size_t)cap * 8 + hbytes;
   if (!X8 && ((d + 3) & ~3) > 256) {
     // long float rows: a block per node
     ensure_smem((const void*)k_pool_wide, per_warp);
@@ -231,7 +237,8 @@ void pool_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n, const
   const size_t smem = per_warp * wpb;
   ensure_smem((const void*)k_pool, smem);
   SSG_LAUNCH(k_pool, (unsigned)ceil_div(n, wpb), wpb * 32, smem, st, X, X8, ld, d, n, knn, K, L, cap,
-             log2h, own_first, exact, dist_rel_team8c(ld), pool_id, pool_d2, pool_len, &dctr->order_fp64);
+             log2h, (int)hbytes, own_first, exact, dist_rel_team8c(ld), pool_id, pool_d2, pool_len,
+             &dctr->order_fp64);
 }
 
 void pool_from_candidates(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
