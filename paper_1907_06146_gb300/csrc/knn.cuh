@@ -160,6 +160,11 @@ void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
 // (prune_wide_available): node i's candidates are cand[i * stride + t], t < len[i].
 // blocks_per_sm (0: 2) sets how much shared memory each block takes for kept vectors.
 bool prune_wide_available(int d);
+// Whether prune_run takes the block prune: rows too long for the warp prune, and rows of
+// 96 or more values, where the block prune was measured faster (200,000 16-centre float
+// points, L = 200, R = 32: d = 96 29.3 -> 27.0 ms, 128 45.9 -> 26.8, 256 131.4 -> 27.8;
+// d = 64 19.8 -> 27.9 and d = 32 10.1 -> 29.6 stay with the warp prune).
+bool prune_block_preferred(int d, int R);
 void prune_run_wide(const float* X, int ld, int d, int64_t n, const int32_t* cand,
                     const int32_t* len, int stride, int R, double cos_a, double border,
                     int32_t* adj, int32_t* deg, Counters* dctr, cudaStream_t st,

@@ -293,7 +293,7 @@ void prune_run(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
                const int32_t* pool_len, int L, int R, double cos_a, double border, int32_t* adj,
                int32_t* deg, Counters* dctr, cudaStream_t st, int wide_blocks) {
   const bool wide = prune_is_wide(d, R);
-  if (wide && prune_wide_available(d)) {
+  if (prune_block_preferred(d, R)) {
     prune_run_wide(X, ld, d, n, pool_id, pool_len, L, R, cos_a, border, adj, deg, dctr, st,
                    wide_blocks);
     return;

@@ -299,6 +299,10 @@ __global__ void __launch_bounds__(PW_THREADS) k_prune_wide(WideArgs a) {
 
 bool prune_wide_available(int d) { return ((d + 3) & ~3) <= 1024; }
 
+bool prune_block_preferred(int d, int R) {
+  return prune_wide_available(d) && (prune_is_wide(d, R) || ((d + 3) & ~3) >= 96);
+}
+
 void prune_run_wide(const float* X, int ld, int d, int64_t n, const int32_t* cand,
                     const int32_t* len, int stride, int R, double cos_a, double border,
                     int32_t* adj, int32_t* deg, Counters* dctr, cudaStream_t st, int blocks_per_sm) {
