@@ -194,6 +194,20 @@ struct PruneTune {
 // a CUDA graph and launched once); returns its device time in ms.  Synchronises `st`.
 double prune_run_batched(const std::vector<PruneJob>& jobs, const PruneTune& tune, cudaStream_t st);
 
+// The block prune over the work items of jobs that prune_block_preferred picks: the job
+// table (each job's kept-vector capacity in shared memory), the spill slots and the launch
+// shape, prepared before a stream capture; the launch itself allocates nothing.
+struct WideBatchPlan {
+  Scratch<unsigned char> jobs;
+  Scratch<float> Vg;
+  size_t vg_stride = 0, smem = 0;
+  int grid = 0, nvr = 8;
+};
+void prune_wide_batched_prepare(const std::vector<PruneJob>& js, WideBatchPlan& plan,
+                                cudaStream_t st);
+void prune_wide_batched_launch(const WideBatchPlan& plan, const int2* items, int64_t nitems,
+                               unsigned long long* next, cudaStream_t st);
+
 // The same prune with each pool's Gram matrix on the tensor cores (data exact in bf16,
 // d <= 128, L <= 127, R <= 128; true where that path is available).
 bool prune_tc_available(int d, int L, int R);

@@ -407,10 +407,12 @@ __global__ void k_bucket_scatter(const PruneJob* __restrict__ jobs, const int64_
 
 double prune_run_batched(const std::vector<PruneJob>& jobs, const PruneTune& tune, cudaStream_t st) {
   if (jobs.empty()) return 0.0;
-  // one launch per row shape class: rows whose R + 1 kept vectors fit shared memory, and
-  // wide rows (kept vectors in a device slot per warp)
-  std::vector<PruneJob> cls[2];
-  for (const PruneJob& j : jobs) cls[prune_is_wide(j.d, j.R) ? 1 : 0].push_back(j);
+  // one launch per row shape class: rows the warp prune takes with its R + 1 kept vectors
+  // in shared memory, rows it takes with them in a device slot per warp (wider than 1,024
+  // values), and rows the block prune takes (prune_block_preferred: 96 values and more)
+  std::vector<PruneJob> cls[3];
+  for (const PruneJob& j : jobs)
+    cls[prune_block_preferred(j.d, j.R) ? 2 : (prune_is_wide(j.d, j.R) ? 1 : 0)].push_back(j);
   const int width = std::max(1, tune.bucket_width);
   struct Prepared {
     Scratch<PruneJob> dj;
@@ -419,9 +421,10 @@ double prune_run_batched(const std::vector<PruneJob>& jobs, const PruneTune& tun
     int64_t nitems = 0;
     size_t warp_floats = 0, vg_stride = 0;
     int wpb = 1, grid = 1;
-  } prep[2];
-  Scratch<unsigned long long> cnt(64, st), next(2, st);
-  for (int w = 0; w < 2; ++w) {
+  } prep[3];
+  WideBatchPlan plan;
+  Scratch<unsigned long long> cnt(64, st), next(3, st);
+  for (int w = 0; w < 3; ++w) {
     const std::vector<PruneJob>& js = cls[w];
     if (js.empty()) continue;
     Prepared& P = prep[w];
@@ -435,8 +438,8 @@ double prune_run_batched(const std::vector<PruneJob>& jobs, const PruneTune& tun
       Lmax = std::max(Lmax, js[j].L);
       Rmax = std::max(Rmax, js[j].R);
       d4max = std::max(d4max, (js[j].d + 3) & ~3);
-      P.warp_floats = std::max(P.warp_floats, w ? prune_wide_smem_floats(js[j].d, js[j].R)
-                                                : prune_smem_floats(js[j].d, js[j].R));
+      P.warp_floats = std::max(P.warp_floats, w == 1 ? prune_wide_smem_floats(js[j].d, js[j].R)
+                                                     : prune_smem_floats(js[j].d, js[j].R));
     }
     SSG_REQUIRE(total < (1ll << 31), SSG_EINVAL, "batched prune: more than 2^31 nodes");
     const int nb = std::min(64, (Lmax + width) / width);
@@ -461,6 +464,10 @@ double prune_run_batched(const std::vector<PruneJob>& jobs, const PruneTune& tun
     P.items.alloc((size_t)total, st);
     SSG_LAUNCH(k_bucket_scatter, g, 256, 0, st, P.dj.p, dfirst.p, njobs, total, width, nb, cnt.p,
                P.items.p);
+    if (w == 2) {
+      prune_wide_batched_prepare(js, plan, st);
+      continue;
+    }
     const size_t per_warp = P.warp_floats * sizeof(float);
     P.wpb = tune.warps > 0 ? tune.warps
                            : (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
@@ -499,10 +506,14 @@ double prune_run_batched(const std::vector<PruneJob>& jobs, const PruneTune& tun
   SSG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   cudaError_t cap = cudaSuccess;
   try {
-    SSG_CUDA(cudaMemsetAsync(next.p, 0, 2 * sizeof(unsigned long long), st));
-    for (int w = 0; w < 2; ++w) {
+    SSG_CUDA(cudaMemsetAsync(next.p, 0, 3 * sizeof(unsigned long long), st));
+    for (int w = 0; w < 3; ++w) {
       Prepared& P = prep[w];
       if (P.nitems == 0) continue;
+      if (w == 2) {
+        prune_wide_batched_launch(plan, P.items.p, P.nitems, next.p + 2, st);
+        continue;
+      }
       SSG_LAUNCH(k_prune_batched, P.grid, P.wpb * 32, P.warp_floats * sizeof(float) * P.wpb, st,
                  P.dj.p, P.items.p, P.nitems, next.p + w, P.Vg.p, P.vg_stride, P.warp_floats, w);
     }

@@ -106,10 +106,13 @@ __device__ __forceinline__ int angle_test32(float g, float gjj, float gk, float 
   return c >= cosA32 - margin ? 1 : 0;
 }
 
-// NVR: float4 columns of the candidate vector each lane holds (rows of up to 128 NVR values).
+// One node i of a (a.len, a.cand, ...) by the whole block.  NVR: float4 columns of the
+// candidate vector each lane holds (rows of up to 128 NVR values).  spill: this block's
+// device slot for kept vectors beyond a.cap.  n64 / nb: this thread's fp64 re-test counts.
 template <int NVR>
-__global__ void __launch_bounds__(PW_THREADS) k_prune_wide(WideArgs a) {
-  extern __shared__ __align__(16) unsigned char smw[];
+__device__ __forceinline__ void block_prune_node(const WideArgs& a, int64_t i, unsigned char* smw,
+                                                 float* spill, unsigned long long& n64,
+                                                 unsigned long long& nb) {
   const WideLayout Ly = wide_layout(a.d, a.R, a.cap);
   const int d4 = (a.d + 3) & ~3, nq4 = d4 >> 2;
   const int R1a = (a.R + 1 + 3) & ~3;
@@ -123,14 +126,11 @@ __global__ void __launch_bounds__(PW_THREADS) k_prune_wide(WideArgs a) {
   int* wdead = (int*)(wid + PW_WARPS);                   // [8] definite conflict in step 1
   int* wnn = wdead + PW_WARPS;                           // [8] fp64 re-tests listed
   int* nlist = (int*)(smw + Ly.nlist);                   // [8][R1a]
-  float* spill = a.Vg ? a.Vg + (size_t)blockIdx.x * (a.R + PW_WARPS - a.cap) * d4 : nullptr;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  unsigned long long n64 = 0, nb = 0;
   auto kept_row = [&](int k) -> float* {
     return k < a.cap ? V + (size_t)k * d4 : spill + (size_t)(k - a.cap) * d4;
   };
-
-  for (int64_t i = blockIdx.x; i < a.n; i += gridDim.x) {
+  {
     const int len = a.len[i];
     const int32_t* cand = a.cand + i * a.stride;
     const float* xg = a.X + i * a.ld;
@@ -291,8 +291,43 @@ __global__ void __launch_bounds__(PW_THREADS) k_prune_wide(WideArgs a) {
     for (int t = kept + tid; t < a.R; t += PW_THREADS) out[t] = -1;
     if (tid == 0) a.deg[i] = kept;
   }
-  if (lane == 0 && n64) atomicAdd(a.n64, n64);
-  if (lane == 0 && nb) atomicAdd(a.nborder, nb);
+}
+
+template <int NVR>
+__global__ void __launch_bounds__(PW_THREADS) k_prune_wide(WideArgs a) {
+  extern __shared__ __align__(16) unsigned char smw[];
+  const int d4 = (a.d + 3) & ~3;
+  float* spill = a.Vg ? a.Vg + (size_t)blockIdx.x * (a.R + PW_WARPS - a.cap) * d4 : nullptr;
+  unsigned long long n64 = 0, nb = 0;
+  for (int64_t i = blockIdx.x; i < a.n; i += gridDim.x)
+    block_prune_node<NVR>(a, i, smw, spill, n64, nb);
+  if ((threadIdx.x & 31) == 0 && n64) atomicAdd(a.n64, n64);
+  if ((threadIdx.x & 31) == 0 && nb) atomicAdd(a.nborder, nb);
+}
+
+// The same over the (index, node) work items of a batch, handed out from one counter in
+// the order of items (longest pools first); each block's spill slot holds vg_stride floats.
+template <int NVR>
+__global__ void __launch_bounds__(PW_THREADS)
+    k_prune_wide_batched(const WideArgs* __restrict__ jobs, const int2* __restrict__ items,
+                         int64_t nitems, unsigned long long* __restrict__ next,
+                         float* __restrict__ Vg, size_t vg_stride) {
+  extern __shared__ __align__(16) unsigned char smw[];
+  __shared__ unsigned long long s_it;
+  float* spill = Vg ? Vg + (size_t)blockIdx.x * vg_stride : nullptr;
+  for (;;) {
+    __syncthreads();  // every thread has read the previous item
+    if (threadIdx.x == 0) s_it = atomicAdd(next, 1ull);
+    __syncthreads();
+    const unsigned long long it = s_it;
+    if (it >= (unsigned long long)nitems) break;
+    const int2 w = items[it];
+    const WideArgs a = jobs[w.x];
+    unsigned long long n64 = 0, nb = 0;
+    block_prune_node<NVR>(a, w.y, smw, spill, n64, nb);
+    if ((threadIdx.x & 31) == 0 && n64) atomicAdd(a.n64, n64);
+    if ((threadIdx.x & 31) == 0 && nb) atomicAdd(a.nborder, nb);
+  }
 }
 
 }  // namespace
@@ -303,14 +338,64 @@ bool prune_block_preferred(int d, int R) {
   return prune_wide_available(d) && (prune_is_wide(d, R) || ((d + 3) & ~3) >= 96);
 }
 
+// Shared memory a block of the block prune takes at blocks_per_sm blocks per SM.
+static size_t wide_budget(int blocks_per_sm) {
+  const int bps = blocks_per_sm > 0 ? blocks_per_sm : 2;
+  return std::min<size_t>(225 * 1024, (226 * 1024) / bps - 1024);
+}
+
+void prune_wide_batched_prepare(const std::vector<PruneJob>& js, WideBatchPlan& plan,
+                                cudaStream_t st) {
+  const size_t budget = wide_budget(0);
+  std::vector<WideArgs> h(js.size());
+  int d4max = 4;
+  for (size_t j = 0; j < js.size(); ++j) {
+    const PruneJob& p = js[j];
+    SSG_REQUIRE(prune_wide_available(p.d), SSG_EINTERNAL, "batched block prune: rows of %d values",
+                p.d);
+    const int d4 = (p.d + 3) & ~3;
+    const size_t row = (size_t)d4 * 4, fixed = wide_layout(p.d, p.R, 0).total;
+    SSG_REQUIRE(fixed + row <= budget, SSG_EINTERNAL, "batched block prune: rows of %d values",
+                p.d);
+    const int cap = (int)std::min<size_t>((size_t)p.R + PW_WARPS, (budget - fixed) / row);
+    h[j] = WideArgs{p.X, p.ld, p.d, p.n, p.pool_id, p.pool_len, p.L, p.R, p.cosA32, p.margin,
+                    p.cosA64, p.border, p.adj, p.deg, nullptr, cap, p.n64, p.nborder};
+    plan.smem = std::max(plan.smem, wide_layout(p.d, p.R, cap).total);
+    plan.vg_stride = std::max(plan.vg_stride, (size_t)(p.R + PW_WARPS - cap) * d4);
+    d4max = std::max(d4max, d4);
+  }
+  plan.nvr = d4max <= 512 ? 4 : 8;
+  const void* fn = plan.nvr == 4 ? (const void*)k_prune_wide_batched<4>
+                                 : (const void*)k_prune_wide_batched<8>;
+  ensure_smem(fn, plan.smem);
+  int per_sm = 0;
+  SSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PW_THREADS, plan.smem));
+  plan.grid = std::max(1, per_sm) * num_sms();
+  plan.jobs.alloc(sizeof(WideArgs) * h.size(), st);
+  SSG_CUDA(cudaMemcpyAsync(plan.jobs.p, h.data(), sizeof(WideArgs) * h.size(),
+                           cudaMemcpyHostToDevice, st));
+  if (plan.vg_stride) plan.Vg.alloc((size_t)plan.grid * plan.vg_stride, st);
+  SSG_CUDA(cudaStreamSynchronize(st));  // the host table is released on return
+}
+
+void prune_wide_batched_launch(const WideBatchPlan& plan, const int2* items, int64_t nitems,
+                               unsigned long long* next, cudaStream_t st) {
+  const WideArgs* jobs = (const WideArgs*)plan.jobs.p;
+  if (plan.nvr == 4)
+    SSG_LAUNCH(k_prune_wide_batched<4>, plan.grid, PW_THREADS, plan.smem, st, jobs, items, nitems,
+               next, plan.Vg.p, plan.vg_stride);
+  else
+    SSG_LAUNCH(k_prune_wide_batched<8>, plan.grid, PW_THREADS, plan.smem, st, jobs, items, nitems,
+               next, plan.Vg.p, plan.vg_stride);
+}
+
 void prune_run_wide(const float* X, int ld, int d, int64_t n, const int32_t* cand,
                     const int32_t* len, int stride, int R, double cos_a, double border,
                     int32_t* adj, int32_t* deg, Counters* dctr, cudaStream_t st, int blocks_per_sm) {
   SSG_REQUIRE(prune_wide_available(d), SSG_EINTERNAL, "wide prune: rows of %d values", d);
   const int d4 = (d + 3) & ~3;
   const size_t row = (size_t)d4 * 4;
-  const int bps = blocks_per_sm > 0 ? blocks_per_sm : 2;
-  const size_t budget = std::min<size_t>(225 * 1024, (226 * 1024) / bps - 1024);
+  const size_t budget = wide_budget(blocks_per_sm);
   const size_t fixed = wide_layout(d, R, 0).total;
   SSG_REQUIRE(fixed + row <= budget, SSG_EINTERNAL, "wide prune: rows of %d values do not fit", d);
   const int cap = (int)std::min<size_t>((size_t)R + PW_WARPS, (budget - fixed) / row);
