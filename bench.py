@@ -639,6 +639,14 @@ def run_gpu(args):
         wide_arm = run_float_arm(ssg, 0, 0, gw.K, gw.L, gw.R, ls=64, w=gw,
                                  label="GIST-shaped softplus mixture, values in [0, 1],")
 
+    # the optional arms run by default on the SIFT-shaped headline workload
+    headline = w.name == "sift_like"
+    if args.alg4_tiles is None:
+        args.alg4_tiles = 128 if headline else 0
+    if args.batched is None:
+        args.batched = 16 if headline else 0
+    if args.ablations is None:
+        args.ablations = headline
     alg4 = None
     if rank == 0 and args.alg4_tiles > 0:
         # Alg. 4: pools searched on the fly over the cluster-ordered tiles, no kNN graph
@@ -782,14 +790,18 @@ def main():
     ap.add_argument("--cpu-nodes-1core", type=int, default=48,
                     help="nodes the cpu_baseline samples on one host core")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batched", type=int, default=0,
+    ap.add_argument("--batched", type=int, default=None,
                     help="also build this many independent indices (log-uniform 10k-500k points, "
-                         "d in {64,96,128,256}), batched and one by one")
+                         "d in {64,96,128,256}), batched and one by one (default: 16 on the "
+                         "SIFT-shaped workload, else 0)")
     ap.add_argument("--batched-streams", type=int, default=8)
-    ap.add_argument("--alg4-tiles", type=int, default=0,
-                    help="also build with Alg. 4's search-based pools over this many tiles")
-    ap.add_argument("--ablations", action="store_true",
-                    help="also run the alpha sweep, exact-SSG overlap and edge-time scaling")
+    ap.add_argument("--alg4-tiles", type=int, default=None,
+                    help="also build with Alg. 4's search-based pools over this many tiles "
+                         "(default: 128 on the SIFT-shaped workload, else 0)")
+    ap.add_argument("--ablations", dest="ablations", action="store_true", default=None,
+                    help="also run the alpha sweep, exact-SSG overlap and edge-time scaling "
+                         "(default on the SIFT-shaped workload)")
+    ap.add_argument("--no-ablations", dest="ablations", action="store_false")
     ap.add_argument("--no-fp32-arm", dest="fp32_arm", action="store_false",
                     help="skip the one plain-FP32 build reported beside the mixed-precision path")
     ap.add_argument("--serve-seconds", type=float, default=1.5,
