@@ -71,9 +71,9 @@ struct TcExtra {
                                       // also for rows that fit the resident one
   int pairs = 0;                      // 1: each centred value v goes in as the bf16 pair
                                       // hi = bf16(v), lo = bf16(v - hi); A rows are laid out
-                                      // [hi | hi | lo] and B rows [hi | lo | hi] (each part
+                                      // [hi | lo | hi] and B rows [lo | hi | hi] (each part
                                       // padded to 64 values), so one accumulator sums
-                                      // hi.hi + hi.lo + lo.hi (K three times as long)
+                                      // hi.lo + lo.hi, then hi.hi (K three times as long)
   int prepass_tiles = 0;              // near-first self-joins: a first walk over this many
                                       // tiles gives each row an upper bound of its KS-th
                                       // distance, from which the full walk starts (0: off;

@@ -105,18 +105,20 @@ __global__ void k_gather_vals(const float* __restrict__ v, const int32_t* __rest
 // Every factor 2 on the dot product terms comes from d2 = |x|^2 + |y|^2 - 2 x.y.
 // With bf16 pairs (pairs = 1: v = hi + lo + r, hi = bf16(v), lo = bf16(v - hi), so |r| <=
 // u^2 |v| and |lo| <= u (1 + u) |v|) the products hi.hi + hi.lo + lo.hi miss x.y by at most
-// (3u^2 + 2u^3 + 2u^4) |x| |y| (the product of the two pairs, less lo.lo), the accumulation
-// runs over 3 dp + 16 terms of total magnitude at most (1 + u)^2 (1 + 2u) |x| |y|, and the
-// other terms are unchanged.
+// (3u^2 + 2u^3 + 2u^4) |x| |y| (the product of the two pairs, less lo.lo).  The accumulation
+// error is charged, as above, at 2^-22 of the running sum's magnitude per added term; the
+// 2 dp cross terms come first (the MMAs run in K order), while that sum is below
+// 2u (1 + u)^2 |x| |y|, so all 3 dp + 16 terms together cost no more than dp + 16 terms of
+// total magnitude (1 + u)^2 (1 + 6u) |x| |y|: the g of a single bf16 with that magnitude.
 __host__ __device__ inline double bf16_dist_bound(double nx, double ymax2, int d, int pairs) {
   const double u = 1.0 / 256.0, u32 = 5.9604644775390625e-08;
   const int dp = ((d + 63) / 64) * 64;
-  const double g = (double)((pairs ? 3 * dp : dp) + 16) * 2.384185791015625e-07;
+  const double g = (double)(dp + 16) * 2.384185791015625e-07;
   const double ax = sqrt(fmax(nx, 0.0) * (1.0 + (d + 2) * u32));
   const double ay = sqrt(fmax(ymax2, 0.0) * (1.0 + (d + 2) * u32));
   const double s = ax + ay;
   const double prod = pairs ? 3.0 * u * u + 2.0 * u * u * u + 2.0 * u * u * u * u : 2.0 * u + u * u;
-  const double mag = pairs ? (1.0 + u) * (1.0 + u) * (1.0 + 2.0 * u) : (1.0 + u) * (1.0 + u);
+  const double mag = pairs ? (1.0 + u) * (1.0 + u) * (1.0 + 6.0 * u) : (1.0 + u) * (1.0 + u);
   const double e = 2.0 * prod * ax * ay + 2.0 * g * (mag * ax * ay + 0.5 * ay * ay) +
                    4.0e-9 * ay * ay + (d + 2) * u32 * (ax * ax + ay * ay) + 4.2 * u32 * s * s;
   return e * 1.05;

@@ -731,8 +731,9 @@ k_knn_tc_wide(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 
 // bf16 copy with rows padded to dp; with perm, stored row r holds row perm[r] (and its norm);
 // with mu, the rows are centred first (x - mu rounded to fp32, then to bf16).
-// Rows of width dp (pairs = 0) or of three parts of width dp (pairs = 1: [hi | hi | lo],
-// pairs = 2: [hi | lo | hi], hi = bf16(v), lo = bf16(v - hi), v the centred value).
+// Rows of width dp (pairs = 0) or of three parts of width dp (pairs = 1: [hi | lo | hi],
+// pairs = 2: [lo | hi | hi], hi = bf16(v), lo = bf16(v - hi), v the centred value), so
+// that the accumulator takes the small products hi.lo and lo.hi before hi.hi.
 __global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int d, int ld,
                           __nv_bfloat16* __restrict__ Y, int dp, const int32_t* __restrict__ perm,
                           const float* __restrict__ norm_in, float* __restrict__ norm_out,
@@ -748,7 +749,7 @@ __global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int d, int ld,
     float v = c < d ? X[src * ld + c] : 0.f;
     if (mu && c < d) v = __fsub_rn(v, mu[c]);
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const bool low = (pairs == 1 && part == 2) || (pairs == 2 && part == 1);
+    const bool low = (pairs == 1 && part == 1) || (pairs == 2 && part == 0);
     Y[i] = low ? __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(hi))) : hi;
     if (norm_out && cw == 0) norm_out[r] = norm_in[src];
   }
