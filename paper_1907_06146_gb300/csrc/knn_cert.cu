@@ -95,9 +95,10 @@ __global__ void k_gather_vals(const float* __restrict__ v, const int32_t* __rest
 //  - bf16 rounding (8 significant bits, unit roundoff u = 2^-8) of both operands:
 //    |x~ y~ - x y| <= (2u + u^2) |x y| per product, summed <= (2u + u^2) |x| |y|;
 //  - the tensor cores' fp32 accumulation of the dp + 16 terms (the augmentation step adds
-//    16): taken as (dp + 16) 2^-22 times the sum of the terms' magnitudes, four times the
-//    error of a sequentially rounded fp32 sum and above any truncating alignment of groups
-//    of 16 terms;
+//    16, last): each added term charged at 2^-22 of the running sum's magnitude, four
+//    times the error of a sequentially rounded fp32 sum and above any truncating alignment
+//    of groups of 16 terms; the dp data terms run below (1 + u)^2 |x| |y|, the 16
+//    augmentation terms below that plus (1 + 2u) |y|^2 / 2;
 //  - the four bf16 parts of -|y|^2/2 (their sum misses it by at most 2^-28 |y|^2);
 //  - the fp32 squared norms ((d + 2) u32 |.|^2 each) and |x|, |y| taken from them;
 //  - the final fused multiply-add and the fp32 centring (x - mu rounded once per value):
@@ -108,19 +109,20 @@ __global__ void k_gather_vals(const float* __restrict__ v, const int32_t* __rest
 // (3u^2 + 2u^3 + 2u^4) |x| |y| (the product of the two pairs, less lo.lo).  The accumulation
 // error is charged, as above, at 2^-22 of the running sum's magnitude per added term; the
 // 2 dp cross terms come first (the MMAs run in K order), while that sum is below
-// 2u (1 + u)^2 |x| |y|, so all 3 dp + 16 terms together cost no more than dp + 16 terms of
-// total magnitude (1 + u)^2 (1 + 6u) |x| |y|: the g of a single bf16 with that magnitude.
+// 2u (1 + u)^2 |x| |y|, so the 3 dp data terms together cost no more than dp terms at a
+// running sum of (1 + u)^2 (1 + 6u) |x| |y|, as for a single bf16 with that magnitude.
 __host__ __device__ inline double bf16_dist_bound(double nx, double ymax2, int d, int pairs) {
   const double u = 1.0 / 256.0, u32 = 5.9604644775390625e-08;
   const int dp = ((d + 63) / 64) * 64;
-  const double g = (double)(dp + 16) * 2.384185791015625e-07;
+  const double g = 2.384185791015625e-07;  // 2^-22 per added term
   const double ax = sqrt(fmax(nx, 0.0) * (1.0 + (d + 2) * u32));
   const double ay = sqrt(fmax(ymax2, 0.0) * (1.0 + (d + 2) * u32));
   const double s = ax + ay;
   const double prod = pairs ? 3.0 * u * u + 2.0 * u * u * u + 2.0 * u * u * u * u : 2.0 * u + u * u;
   const double mag = pairs ? (1.0 + u) * (1.0 + u) * (1.0 + 6.0 * u) : (1.0 + u) * (1.0 + u);
-  const double e = 2.0 * prod * ax * ay + 2.0 * g * (mag * ax * ay + 0.5 * ay * ay) +
-                   4.0e-9 * ay * ay + (d + 2) * u32 * (ax * ax + ay * ay) + 4.2 * u32 * s * s;
+  const double acc = g * ((dp + 16) * mag * ax * ay + 16.0 * 0.5 * (1.0 + 2.0 * u) * ay * ay);
+  const double e = 2.0 * prod * ax * ay + 2.0 * acc + 4.0e-9 * ay * ay +
+                   (d + 2) * u32 * (ax * ax + ay * ay) + 4.2 * u32 * s * s;
   return e * 1.05;
 }
 
