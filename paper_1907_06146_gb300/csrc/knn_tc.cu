@@ -856,8 +856,12 @@ void knn_exact_tc(const float* A, int64_t na, int lda, const float* a_norm, cons
   const bool same = self && !ex.qid;
   SSG_REQUIRE(max_tiles == 0 || (same && knn_order_fits(na, bn)), SSG_EINVAL,
               "a tile limit needs a self-join whose cluster order fits");
+  // (not for the K-chunked kernel: its tiles are long enough that the appends a slowly
+  // falling threshold costs matter less than L2 reuse, which needs every CTA to walk the
+  // columns in the same order: 200,000 x 960 with bf16 pairs, 270 -> 227 ms, the
+  // near-first walks kept DRAM 78% busy at a 34% L2 hit rate)
   const bool ordered =
-      max_tiles > 0 || (same && na >= (1 << 16) && K >= 16 && knn_order_fits(na, bn));
+      max_tiles > 0 || (!wide && same && na >= (1 << 16) && K >= 16 && knn_order_fits(na, bn));
   if (ordered) {
     knn_cluster_order(A, lda, d, na, bm, bn, st, ord, max_tiles,
                       ex.order_norm ? ex.order_norm : a_norm);

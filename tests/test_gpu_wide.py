@@ -54,8 +54,10 @@ def test_wide_duplicates_settled_by_id(ssg):
     np.testing.assert_array_equal(_np(d2), od2.astype(np.float32))
 
 
-def test_wide_near_first_order(ssg):
-    """70,000 rows: the self-join walks the cluster order (nearest cluster's tiles first)."""
+def test_wide_large_self_join(ssg):
+    """70,000 rows of 160 values: a self-join large enough that the resident kernel would
+    walk the cluster order; the K-chunked kernel walks every row block's columns in the same
+    order (for L2 reuse), with many compactions while the thresholds fall."""
     w = synth.sift_like(n=70_000, d=160, nq=0, n_clusters=70)
     base = np.minimum(w.base, 60.0).astype(np.float32)
     ids, d2 = ssg.knn(_cuda(base), 50, prec="bf16")
