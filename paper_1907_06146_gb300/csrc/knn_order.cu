@@ -250,10 +250,13 @@ bool knn_order_fits(int64_t n, int BN) {
 void knn_cluster_order(const float* X, int ld, int d, int64_t n, int BM, int BN, cudaStream_t st,
                        KnnOrder& o, int64_t walk, const float* x_norm) {
   SSG_REQUIRE(knn_order_fits(n, BN), SSG_EINTERNAL, "cluster order: too many column tiles");
-  // About 2,048 rows per cluster.  A full walk only needs the near tiles first, so a few
-  // hundred clusters do; a limited walk (Alg. 4) takes its pools from the first tiles
-  // alone, so the clusters stay that small up to 8,192 of them.
-  const int ncl = (int)std::max<int64_t>(16, std::min<int64_t>(walk > 0 ? 8192 : 512, n / 2048));
+  // A full walk only needs the near tiles first: about 4,096 rows per cluster, up to 512
+  // clusters (1M x 128, K = 200: 341 ms for the kNN graph against 347 with 2,048 rows,
+  // 344 with 8,192, and more the smaller the clusters: 504 ms with 256 rows).  A limited
+  // walk (Alg. 4) takes its pools from the first tiles alone, so its clusters stay at about
+  // 2,048 rows, up to 8,192 of them.
+  const int ncl = (int)std::max<int64_t>(
+      16, walk > 0 ? std::min<int64_t>(8192, n / 2048) : std::min<int64_t>(512, n / 4096));
   const int dc = (d + 3) & ~3;
   o.ncl = ncl;
   o.ntiles = (n + BN - 1) / BN;
