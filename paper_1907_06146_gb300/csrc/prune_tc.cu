@@ -6,22 +6,30 @@
 // H = C C^T in TMEM.  Every product and partial sum is an integer below 2^24, so H is
 // exact, and so is every centred dot product the angle rule needs:
 //     G_jk = (c_j - x).(c_k - x) = H_jk - H_j0 - H_k0 + H_00,   G_jj = d2(x, c_j).
-// All pairs are tested at once: bit k of row j says whether cos(j, k) = G_jk / sqrt(G_jj
-// G_kk) > cos(alpha) (0 for a zero-length edge).  The fp32 cosine decides where it is more
-// than 16 units of roundoff (plus the reporting band) from cos(alpha) (its inputs are
-// exact, its error a few units); otherwise the bit is taken in fp64 from the same exact integers with the operations of
-// the definition, which reproduces the double-precision rule bit for bit.  The selection
-// in candidate order (keep c_j unless it conflicts with a kept c_k, stop at R) is then a
-// scan over these bit rows.
+// c_j and c_k conflict when cos(j, k) = G_jk / sqrt(G_jj G_kk) > cos(alpha); a zero-length
+// edge conflicts with every other exactly when 0 > cos(alpha).  The fp32 cosine decides
+// where it is more than 16 units of roundoff (plus the reporting band) from cos(alpha) (its
+// inputs are exact, its error a few units); otherwise the test is taken in fp64 from the
+// same exact integers with the operations of the definition, which reproduces the
+// double-precision rule bit for bit.
 //
-// Persistent kernel, one CTA per SM, 13 warps:
+// Only the tests the greedy selection needs are made (c_j against the candidates kept
+// before it, in candidate order, until R are kept).  The lower triangle of H goes from TMEM
+// to a shared-memory slot, row i at i(i+1)/2 (32 consecutive rows start in 32 different
+// banks, so a column read across rows is conflict-free, as is a read along a row).  A
+// selection warp then takes the candidates in blocks of 32, one per lane: each lane tests
+// its candidate against the candidates kept in earlier blocks (a conflict with any of them
+// rejects it, whatever the order), and the block's survivors are settled one by one, the
+// lanes testing the candidates kept before them in the block.
+//
+// Persistent kernel, one CTA per SM:
 //   warp 0       gathers the node and candidate rows (gather4, 4 rows per TMA) into one
 //                of GSLOTS shared-memory tiles;
 //   warp 1       allocates 512 TMEM columns and issues the Gram UMMAs into one of 4 TMEM
 //                buffers;
-//   warps 2..9   conflict bits: two warps per TMEM lane quadrant (one row per lane), each
-//                taking every other 32-column chunk left of the diagonal;
-//   warps 10..12 select: each takes every third node.
+//   warps 2..5   copy the lower triangle of H into the node's slot, one TMEM lane quadrant
+//                (32 rows) each;
+//   warps 6..    select, one warp per slot, warp s taking every nsel-th node.
 // Every wait is bounded (about 2 s); a wait that runs out sets an error word, tells the
 // other roles to stop, and the CTA releases its TMEM and exits.
 #include "common.cuh"
@@ -35,19 +43,21 @@ using namespace tc;
 
 constexpr int PT_ROWS = 128;                  // the node and up to 127 candidates
 constexpr int GSLOTS = 3;                     // gather tiles
-constexpr int SEL_WARPS = 3;
-constexpr int MSLOTS = 6;                     // conflict-bit slots (a multiple of SEL_WARPS)
-constexpr int GRAM_WARPS = 8;
-constexpr int THREADS_P = (2 + GRAM_WARPS + SEL_WARPS) * 32;
+constexpr int COPY_WARPS = 4;                 // one per TMEM lane quadrant
+constexpr int MAX_SEL = 8;                    // selection warps (and slots) at most
+constexpr int FIRST_SEL = 2 + COPY_WARPS;
+constexpr int THREADS_MAX = (FIRST_SEL + MAX_SEL) * 32;
 constexpr int TMEM_COLS_P = 512;              // 4 buffers of 128 fp32 columns
-constexpr int MSLOT_BYTES = PT_ROWS * 4 * 4;  // 4 words of conflict bits per row
-constexpr int XCH_FLOATS = 4 * PT_ROWS;       // per node: H_i0, H_ii, d2(x, c_i), 1/sqrt
+constexpr int SMEM_CAP = 225 * 1024;
+constexpr int SEL_F4 = PT_ROWS + 32;         // per selection warp: kept list + block rows
 
 struct PtArgs {
   const int32_t* pool_id;
   const int32_t* pool_len;
   int64_t n;
   int L, R, kchunks;
+  int nsel;                     // selection warps = slots
+  int slot_floats;              // floats of one slot (the lower triangle of the longest pool)
   float cosA32, margin;
   double cosA64;
   int32_t* adj;
@@ -58,26 +68,51 @@ struct PtArgs {
   unsigned long long* nborder;
 };
 
-__global__ void __launch_bounds__(THREADS_P, 1)
+// Offset of row i of a packed lower triangle.
+__device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
+
+// The angle rule for a pair of candidates: g their exact centred dot product, dj and dk
+// their exact squared lengths, rj and rk the reciprocal lengths (0 for a zero length).
+struct AngleRule {
+  float hi, lo;
+  double cosA64, border;
+  bool zc;                      // the rule for a zero-length edge
+  unsigned long long n64, nb;
+
+  // The fp32 decision; band: the cosine is too close to cos(alpha), the fp64 rule decides.
+  __device__ __forceinline__ bool fast(float g, float dj, float dk, float rj, float rk,
+                                       bool& band) const {
+    const float cs = g * rj * rk;
+    const bool zero = (dj == 0.f) | (dk == 0.f);
+    band = !zero & (cs >= lo) & (cs <= hi);
+    return zero ? zc : cs > hi;
+  }
+  // The double-precision rule on the same exact integers.
+  __device__ __forceinline__ bool exact(float g, float dj, float dk) {
+    const double c64 = cos_from_gram_f64((double)g, (double)dj, (double)dk);
+    ++n64;
+    if (fabs(c64 - cosA64) <= border) ++nb;
+    return c64 > cosA64;
+  }
+};
+
+__global__ void __launch_bounds__(THREADS_MAX, 1)
 k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t g_bytes = (uint32_t)p.kchunks * PT_ROWS * 128;
+  const int nsel = p.nsel;
   unsigned char* sG = sm;                                            // GSLOTS gather tiles
-  uint32_t* sM = (uint32_t*)(sG + (size_t)GSLOTS * g_bytes);         // MSLOTS x [128][4] bits
-  float* xch = (float*)(sM + (size_t)MSLOTS * PT_ROWS * 4);         // [2][4][128]
-  uint32_t* xz = (uint32_t*)(xch + 2 * XCH_FLOATS);                  // [2][4] zero-edge bits
-  float* stash = (float*)(xz + 8);                                   // 32 floats per thread
-  uint64_t* bars = (uint64_t*)(stash + GRAM_WARPS * 32 * 32);
+  float* sP = (float*)(sG + (size_t)GSLOTS * g_bytes);               // nsel slots
+  float4* sK = (float4*)(sP + (size_t)nsel * p.slot_floats);          // nsel x SEL_F4
+  uint64_t* bars = (uint64_t*)(sK + (size_t)nsel * SEL_F4);
   uint64_t* g_full = bars;
   uint64_t* g_empty = g_full + GSLOTS;
   uint64_t* t_full = g_empty + GSLOTS;
   uint64_t* t_empty = t_full + 4;
-  uint64_t* m_full = t_empty + 4;
-  uint64_t* m_empty = m_full + MSLOTS;
-  uint64_t* ex1 = m_empty + MSLOTS;
-  uint64_t* ex2 = ex1 + 2;
-  uint32_t* tmem_slot = (uint32_t*)(ex2 + 2);
+  uint64_t* d_full = t_empty + 4;
+  uint64_t* d_empty = d_full + MAX_SEL;
+  uint32_t* tmem_slot = (uint32_t*)(d_empty + MAX_SEL);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -88,15 +123,11 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
     }
     for (int b = 0; b < 4; ++b) {
       mbar_init(smem_u32(t_full + b), 1);
-      mbar_init(smem_u32(t_empty + b), GRAM_WARPS);
+      mbar_init(smem_u32(t_empty + b), COPY_WARPS);
     }
-    for (int u = 0; u < MSLOTS; ++u) {
-      mbar_init(smem_u32(m_full + u), GRAM_WARPS);
-      mbar_init(smem_u32(m_empty + u), 1);
-    }
-    for (int k = 0; k < 2; ++k) {
-      mbar_init(smem_u32(ex1 + k), GRAM_WARPS);
-      mbar_init(smem_u32(ex2 + k), GRAM_WARPS);
+    for (int s = 0; s < nsel; ++s) {
+      mbar_init(smem_u32(d_full + s), COPY_WARPS);
+      mbar_init(smem_u32(d_empty + s), 1);
     }
     *abort_flag = 0;
     fence_barrier_init();
@@ -113,26 +144,48 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
 
   if (warp == 0) {
     // ---------------- gather producer ----------------
+    // a node's length and candidate ids are loaded one node ahead, so that their latency
+    // overlaps the wait for a free tile
+    const int L = p.L;
     int s = 0;
     uint32_t ph = 0;
     bool ok = true;
-    for (int64_t x = blockIdx.x; x < n && ok; x += gridDim.x) {
+    int64_t x = blockIdx.x;
+    int len = 0, yr[4] = {0, 0, 0, 0};
+    if (x < n) {
+      len = p.pool_len[x];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = lane * 4 + e;  // row 0 is the node, row r the candidate r - 1
+        if (r >= 1 && r <= L) yr[e] = p.pool_id[x * L + r - 1];
+      }
+    }
+    for (; x < n && ok; x += gridDim.x) {
+      const int lc = min(len, PT_ROWS - 1);
+      int y[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = lane * 4 + e;
+        y[e] = (r == 0 || r > lc) ? (int)x : yr[e];
+      }
+      const int64_t xn = x + gridDim.x;
+      if (xn < n) {
+        len = p.pool_len[xn];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = lane * 4 + e;
+          if (r >= 1 && r <= L) yr[e] = p.pool_id[xn * L + r - 1];
+        }
+      }
       ok = mbar_wait(smem_u32(g_empty + s), ph ^ 1, abort_flag);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
         break;
       }
-      const int len = min(p.pool_len[x], PT_ROWS - 1);
-      const int ng4 = (len + 1 + 3) >> 2;
+      const int ng4 = (lc + 1 + 3) >> 2;
       if (lane == 0) mbar_expect_tx(smem_u32(g_full + s), (uint32_t)ng4 * 4 * 128 * p.kchunks);
       __syncwarp();
       if (lane < ng4) {
-        int y[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int r = lane * 4 + e;  // row 0 is the node, row r the candidate r - 1
-          y[e] = (r == 0 || r > len) ? (int)x : p.pool_id[x * p.L + r - 1];
-        }
         unsigned char* dst = sG + (size_t)s * g_bytes + (size_t)lane * 4 * 128;
         for (int kc = 0; kc < p.kchunks; ++kc)
           tma_gather4(smem_u32(dst + (size_t)kc * PT_ROWS * 128), &tmX, smem_u32(g_full + s),
@@ -184,200 +237,205 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
       }
     }
     __syncwarp();
-  } else if (warp < 2 + GRAM_WARPS) {
-    // ---------------- conflict bits: TMEM -> shared-memory bit rows ----------------
+  } else if (warp < FIRST_SEL) {
+    // ---------------- TMEM -> packed lower triangle in the node's slot ----------------
     const int q = warp & 3;                  // TMEM lane quadrant
-    const int hh = (warp - 2) >> 2;          // which of the quadrant's two warps
     const int i = q * 32 + lane;             // row: 0 the node, i the candidate i - 1
-    float* st = stash + (size_t)((warp - 2) * 32 + lane) * 32;
-    const bool zc = 0.0 > p.cosA64;          // the rule for a zero-length edge
-    const float hi = p.cosA32 + p.margin, lo = p.cosA32 - p.margin;
-    int b = 0, u = 0, k = 0;
-    uint32_t tph = 0, uph = 0;
+    int b = 0, s = 0;
+    uint32_t tph = 0, sph = 0;
     bool ok = true;
-    unsigned long long fp64_tests = 0, borderline = 0;
-    for (int64_t x = blockIdx.x; x < n; x += gridDim.x, ++k) {
-      const int nrows = min(p.pool_len[x], PT_ROWS - 1) + 1;
-      ok = mbar_wait(smem_u32(t_full + b), tph, abort_flag);
+    int len = blockIdx.x < n ? p.pool_len[blockIdx.x] : 0;   // one node ahead
+    for (int64_t x = blockIdx.x; x < n; x += gridDim.x) {
+      const int nrows = min(len, PT_ROWS - 1) + 1;
+      if (x + gridDim.x < n) len = p.pool_len[x + gridDim.x];
+      ok = mbar_wait(smem_u32(t_full + b), tph, abort_flag) &&
+           mbar_wait(smem_u32(d_empty + s), sph ^ 1, abort_flag);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 128);
-      float* xa = xch + (k & 1) * XCH_FLOATS;  // H_i0
-      float* xh = xa + PT_ROWS;                // H_ii
-      float* xd = xh + PT_ROWS;                // G_ii = d2(x, c_i)
-      float* xr = xd + PT_ROWS;                // 1 / sqrt(G_ii)
-      uint32_t* zq = xz + (k & 1) * 4;         // zero-length edges, one word per quadrant
-      uint32_t v[32];
-      tmem_ld32(taddr, v);
-      tmem_wait_ld(v);
-      const float ai = __uint_as_float(v[0]);
-      if (q != 0) {
-        tmem_ld32(taddr + (uint32_t)(q * 32), v);
-        tmem_wait_ld(v);
-      }
-      float hii = 0.f;
+      if (q * 32 < nrows) {
+        float* row = sP + (size_t)s * p.slot_floats + (i < nrows ? tri(i) : 0);
+        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 128);
+        for (int c = 0; c <= q; ++c) {
+          uint32_t v[32];
+          tmem_ld32(taddr + (uint32_t)(c * 32), v);
+          tmem_wait_ld(v);
+          if (i < nrows) {
 #pragma unroll
-      for (int e = 0; e < 32; ++e)
-        if (e == lane) hii = __uint_as_float(v[e]);
-      if (hh == 0) {
-        xa[i] = ai;
-        xh[i] = hii;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(ex1 + (k & 1)));
-      ok = mbar_wait(smem_u32(ex1 + (k & 1)), (uint32_t)((k >> 1) & 1), abort_flag);
-      if (!__all_sync(0xffffffffu, ok)) {
-        ok = false;
-        break;
-      }
-      const float h00 = xa[0];
-      const float dgi = (hii - 2.f * ai) + h00;  // exact: integers below 2^24
-      const float ri = dgi > 0.f ? __frsqrt_rn(dgi) : 0.f;
-      const uint32_t zb = __ballot_sync(0xffffffffu, dgi == 0.f);
-      if (hh == 0) {
-        xd[i] = dgi;
-        xr[i] = ri;
-        if (lane == 0) zq[q] = zb;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(ex2 + (k & 1)));
-      ok = mbar_wait(smem_u32(ex2 + (k & 1)), (uint32_t)((k >> 1) & 1), abort_flag) &&
-           mbar_wait(smem_u32(m_empty + u), uph ^ 1, abort_flag);
-      if (!__all_sync(0xffffffffu, ok)) {
-        ok = false;
-        break;
-      }
-      const float t2 = h00 - ai;
-      const bool row_ok = i >= 1 && i < nrows;
-      const bool zero_i = dgi == 0.f;
-      uint32_t* mrow = sM + ((size_t)u * PT_ROWS + i) * 4;
-      for (int c = hh; c <= q && c * 32 < nrows; c += 2) {
-        tmem_ld32(taddr + (uint32_t)(c * 32), v);
-        tmem_wait_ld(v);
-        // columns j = 32c + e with 1 <= j < i
-        const int lo_e = c == 0 ? 1 : 0;
-        const int hi_e = i - c * 32;  // exclusive
-        uint32_t valid = 0;
-        if (row_ok && hi_e > lo_e)
-          valid = (hi_e >= 32 ? 0xffffffffu : ((1u << hi_e) - 1u)) & ~((1u << lo_e) - 1u);
-        uint32_t cf = 0, bd = 0;
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          const int j = c * 32 + e;
-          const float g = (__uint_as_float(v[e]) - xa[j]) + t2;  // exact centred dot product
-          const float cs = g * ri * xr[j];
-          cf |= (cs > hi ? 1u : 0u) << e;
-          bd |= (cs >= lo && cs <= hi ? 1u : 0u) << e;
-        }
-        const uint32_t zcol = zq[c];
-        if (zero_i) {
-          cf = zc ? valid : 0u;
-          bd = 0u;
-        } else {
-          cf = ((cf & ~zcol) | (zc ? zcol : 0u)) & valid;
-          bd &= valid & ~zcol;
-        }
-        if (bd) {
-          // near cos(alpha): the double-precision rule on the same exact integers
-#pragma unroll
-          for (int kq = 0; kq < 8; ++kq)
-            *(float4*)(st + 4 * kq) = make_float4(__uint_as_float(v[4 * kq]), __uint_as_float(v[4 * kq + 1]),
-                                                  __uint_as_float(v[4 * kq + 2]), __uint_as_float(v[4 * kq + 3]));
-          while (bd) {
-            const int e = __ffs(bd) - 1;
-            bd &= bd - 1;
-            const int j = c * 32 + e;
-            const float g = (st[e] - xa[j]) + t2;
-            const double c64 = cos_from_gram_f64((double)g, (double)dgi, (double)xd[j]);
-            if (c64 > p.cosA64) cf |= 1u << e;
-            if (fabs(c64 - p.cosA64) <= p.border) ++borderline;
-            ++fp64_tests;
+            for (int e = 0; e < 32; ++e)
+              if (c * 32 + e <= i) row[c * 32 + e] = __uint_as_float(v[e]);
           }
         }
-        mrow[c] = cf;
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(smem_u32(t_empty + b));
-        mbar_arrive(smem_u32(m_full + u));
+        mbar_arrive(smem_u32(d_full + s));
       }
       if (++b == 4) {
         b = 0;
         tph ^= 1;
       }
-      if (++u == MSLOTS) {
-        u = 0;
-        uph ^= 1;
+      if (++s == nsel) {
+        s = 0;
+        sph ^= 1;
       }
     }
-    if (fp64_tests) atomicAdd(p.n64, fp64_tests);
-    if (borderline) atomicAdd(p.nborder, borderline);
     if (!ok && lane == 0) {
       atomicOr(p.err, 4);
       *abort_flag = 1;
     }
-  } else {
-    // ---------------- selection: candidate order over the bit rows ----------------
-    const int sw = warp - 2 - GRAM_WARPS;
-    int u = sw;
-    uint32_t uph = 0;
+  } else if (warp < FIRST_SEL + nsel) {
+    // ---------------- selection in candidate order ----------------
+    const int w = warp - FIRST_SEL;
+    const float* P = sP + (size_t)w * p.slot_floats;
+    float4* S = sK + (size_t)w * SEL_F4;     // kept: H_k0, G_kk, 1/sqrt(G_kk), row k
+    float4* T4 = S + PT_ROWS;                // the block's rows: H_j0, G_jj, 1/sqrt(G_jj)
+    AngleRule at{p.cosA32 + p.margin, p.cosA32 - p.margin, p.cosA64, p.border, 0.0 > p.cosA64,
+                 0ull, 0ull};
+    const int R = p.R, L = p.L;
+    const unsigned lt = lanemask_lt();
+    const int64_t step = (int64_t)nsel * gridDim.x;
+    uint32_t ph = 0;
     bool ok = true;
-    const int R = p.R;
-    for (int64_t x = blockIdx.x + (int64_t)sw * gridDim.x; x < n;
-         x += (int64_t)SEL_WARPS * gridDim.x) {
-      ok = mbar_wait(smem_u32(m_full + u), uph, abort_flag);
+    int64_t x = blockIdx.x + (int64_t)w * gridDim.x;
+    int len = x < n ? p.pool_len[x] : 0;     // one node ahead
+    for (; x < n; x += step) {
+      const int nrows = min(len, PT_ROWS - 1) + 1;
+      // the candidate ids (for the output) and the next length load during the wait
+      const int32_t* cand = p.pool_id + x * L;
+      int cid[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) cid[u] = u * 32 + lane < nrows - 1 ? cand[u * 32 + lane] : -1;
+      if (x + step < n) len = p.pool_len[x + step];
+      ok = mbar_wait(smem_u32(d_full + w), ph, abort_flag);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
         break;
       }
-      const int nrows = min(p.pool_len[x], PT_ROWS - 1) + 1;
-      const uint32_t* mrows = sM + (size_t)u * PT_ROWS * 4;
-      // bit j of K: candidate j - 1 kept
-      uint32_t K0 = 0, K1 = 0, K2 = 0, K3 = 0;
+      ph ^= 1;
+      const float h00 = P[0];
       int kept = 0;
-      if (lane == 0) {
-        for (int i = 1; i < nrows && kept < R; ++i) {
-          const uint4 m = *(const uint4*)(mrows + (size_t)i * 4);
-          if (((m.x & K0) | (m.y & K1) | (m.z & K2) | (m.w & K3)) == 0u) {
-            const uint32_t bit = 1u << (i & 31);
-            const int w = i >> 5;
-            K0 |= w == 0 ? bit : 0u;
-            K1 |= w == 1 ? bit : 0u;
-            K2 |= w == 2 ? bit : 0u;
-            K3 |= w == 3 ? bit : 0u;
-            ++kept;
+      for (int b0 = 0; b0 < nrows && kept < R; b0 += 32) {
+        // lane: candidate j = b0 + lane
+        const int j = b0 + lane;
+        const bool valid = j >= 1 && j < nrows;
+        const int jc = valid ? j : 0;          // last column of row j
+        const int tj = tri(jc);
+        const float aj = P[tj];                                  // H_j0
+        const float dj = valid ? (P[tj + jc] - 2.f * aj) + h00 : 0.f;  // G_jj, exact
+        const float rj = dj > 0.f ? __frsqrt_rn(dj) : 0.f;
+        const float t0j = h00 - aj;
+        // 1. against the candidates kept in earlier blocks (one conflict rejects)
+        bool out = !valid;
+        for (int m0 = 0; m0 < kept; m0 += 4) {
+          if (!__any_sync(0xffffffffu, !out)) break;
+          float4 s4[4];
+          float h[4];
+          bool bd[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) s4[u] = S[min(m0 + u, kept - 1)];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) h[u] = P[tj + min(__float_as_int(s4[u].w), jc)];
+          bool hit = false, band_any = false;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const bool act = m0 + u < kept;
+            const bool c = at.fast((h[u] - s4[u].x) + t0j, dj, s4[u].y, rj, s4[u].z, bd[u]);
+            hit |= act & c;
+            bd[u] &= act;
+            band_any |= bd[u];
+          }
+          out |= hit;
+          band_any &= !out;
+          if (__any_sync(0xffffffffu, band_any) && band_any) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (bd[u] && !out) out = at.exact((h[u] - s4[u].x) + t0j, dj, s4[u].y);
           }
         }
-      }
-      K0 = __shfl_sync(0xffffffffu, K0, 0);
-      K1 = __shfl_sync(0xffffffffu, K1, 0);
-      K2 = __shfl_sync(0xffffffffu, K2, 0);
-      K3 = __shfl_sync(0xffffffffu, K3, 0);
-      kept = __shfl_sync(0xffffffffu, kept, 0);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(m_empty + u));
-      const int32_t* cand = p.pool_id + x * p.L;
-      int32_t* out = p.adj + x * R;
-      const unsigned lt = lanemask_lt();
-      const uint32_t Kw[4] = {K0, K1, K2, K3};
-      int base = 0;
+        const uint32_t alive = __ballot_sync(0xffffffffu, !out);
+        if (alive != 0u) {
+          // 2. conflicts among the block's survivors: bit e of M (lane j) says survivor
+          //    b0 + e (e < lane) conflicts with c_j
+          T4[lane] = make_float4(aj, dj, rj, 0.f);
+          __syncwarp();
+          const bool me = !out;
+          uint32_t M = 0, Mb = 0, rest = alive;
+          while (rest != 0u) {
+            int ee[4];
 #pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        if ((Kw[w] >> lane) & 1u) out[base + __popc(Kw[w] & lt)] = cand[w * 32 + lane - 1];
-        base += __popc(Kw[w]);
+            for (int u = 0; u < 4; ++u) {
+              ee[u] = rest ? __ffs(rest) - 1 : 31;
+              rest &= rest - 1u;
+            }
+            float4 k4[4];
+            float h[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k4[u] = T4[ee[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) h[u] = P[tj + min(b0 + ee[u], jc)];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              bool band;
+              const bool c = at.fast((h[u] - k4[u].x) + t0j, dj, k4[u].y, rj, k4[u].z, band);
+              const bool act = me & (lane > ee[u]) & ((alive >> ee[u]) & 1u);
+              M |= (act & c) ? 1u << ee[u] : 0u;
+              Mb |= (act & band) ? 1u << ee[u] : 0u;
+            }
+          }
+          if (__any_sync(0xffffffffu, Mb != 0u)) {
+            while (Mb != 0u) {
+              const int e = __ffs(Mb) - 1;
+              Mb &= Mb - 1u;
+              const float4 k4 = T4[e];
+              if (at.exact((P[tj + b0 + e] - k4.x) + t0j, dj, k4.y)) M |= 1u << e;
+            }
+          }
+          // 3. the greedy over the survivors in order (every lane takes the same steps)
+          uint32_t kb = 0, rest2 = alive & (alive - 1u);
+          int kn = kept;
+          int e = __ffs(alive) - 1;
+          uint32_t me_m = __shfl_sync(0xffffffffu, M, e);
+          while (e >= 0 && kn < R) {
+            const int en = rest2 ? __ffs(rest2) - 1 : -1;
+            rest2 &= rest2 - 1u;
+            const uint32_t mn = __shfl_sync(0xffffffffu, M, en & 31);
+            if ((me_m & kb) == 0u) {
+              kb |= 1u << e;
+              ++kn;
+            }
+            e = en;
+            me_m = mn;
+          }
+          // 4. the block's kept candidates join the kept list in order
+          if ((kb >> lane) & 1u) S[kept + __popc(kb & lt)] = make_float4(aj, dj, rj, __int_as_float(j));
+          kept = kn;
+        }
+        __syncwarp();
       }
-      for (int e = kept + lane; e < R; e += 32) out[e] = -1;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(d_empty + w));   // the slot is read
+      int32_t* outp = p.adj + x * R;
+      for (int m0 = 0; m0 < R; m0 += 32) {
+        const int m = m0 + lane;
+        const int r = m < kept ? __float_as_int(S[m].w) - 1 : 0;   // candidate r
+        int v = -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int t = __shfl_sync(0xffffffffu, cid[u], r & 31);
+          if ((r >> 5) == u) v = t;
+        }
+        if (m < R) outp[m] = m < kept ? v : -1;
+      }
       if (lane == 0) p.deg[x] = kept;
-      u += SEL_WARPS;
-      if (u >= MSLOTS) {
-        u -= MSLOTS;
-        uph ^= 1;
-      }
+      __syncwarp();
     }
+    if (at.n64) atomicAdd(p.n64, at.n64);
+    if (at.nb) atomicAdd(p.nborder, at.nb);
     if (!ok && lane == 0) {
       atomicOr(p.err, 8);
       *abort_flag = 1;
@@ -403,11 +461,28 @@ __global__ void k_rows_bf16(const float* __restrict__ X, int64_t n, int d, int l
   }
 }
 
-size_t prune_tc_smem(int kchunks) {
-  return 1024 + (size_t)GSLOTS * kchunks * PT_ROWS * 128 + (size_t)MSLOTS * MSLOT_BYTES +
-         2 * XCH_FLOATS * sizeof(float) + 8 * sizeof(uint32_t) +
-         (size_t)GRAM_WARPS * 32 * 32 * sizeof(float) +
-         sizeof(uint64_t) * (2 * GSLOTS + 8 + 2 * MSLOTS + 4) + 16;
+// Floats of one slot: the packed lower triangle of the longest pool's 1 + L rows.
+int prune_tc_slot_floats(int L) {
+  const int rows = std::min(L, PT_ROWS - 1) + 1;
+  return ((rows * (rows + 1) / 2) + 3) & ~3;
+}
+
+size_t prune_tc_fixed_smem(int kchunks) {
+  return 1024 + (size_t)GSLOTS * kchunks * PT_ROWS * 128 +
+         sizeof(uint64_t) * (2 * GSLOTS + 8 + 2 * MAX_SEL) + 16;
+}
+
+// Selection warps (and slots) that fit beside the gather tiles, at most MAX_SEL.
+int prune_tc_nsel(int kchunks, int L) {
+  const size_t fixed = prune_tc_fixed_smem(kchunks);
+  if (fixed >= (size_t)SMEM_CAP) return 0;
+  const size_t per = (size_t)prune_tc_slot_floats(L) * sizeof(float) + SEL_F4 * sizeof(float4);
+  return (int)std::min<size_t>(MAX_SEL, ((size_t)SMEM_CAP - fixed) / per);
+}
+
+size_t prune_tc_smem(int kchunks, int L, int nsel) {
+  return prune_tc_fixed_smem(kchunks) +
+         (size_t)nsel * ((size_t)prune_tc_slot_floats(L) * sizeof(float) + SEL_F4 * sizeof(float4));
 }
 
 }  // namespace
@@ -415,7 +490,7 @@ size_t prune_tc_smem(int kchunks) {
 bool prune_tc_available(int d, int L, int R) {
   const int kchunks = (d + 63) / 64;
   return knn_tc_available(d) && kchunks <= 2 && L >= 1 && L <= PT_ROWS - 1 && R >= 1 &&
-         R <= 128 && prune_tc_smem(kchunks) <= 225 * 1024;
+         R <= PT_ROWS && prune_tc_nsel(kchunks, L) >= 2;
 }
 
 void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
@@ -435,6 +510,8 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
   a.L = L;
   a.R = R;
   a.kchunks = kchunks;
+  a.nsel = prune_tc_nsel(kchunks, L);
+  a.slot_floats = prune_tc_slot_floats(L);
   a.cosA32 = (float)cos_a;
   a.cosA64 = cos_a;
   a.margin = (float)(16.0 * U32 + border);
@@ -444,10 +521,12 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
   a.border = border;
   a.nborder = &dctr->angle_border;
   a.err = err.p;
-  const size_t smem = prune_tc_smem(kchunks);
+  SSG_REQUIRE(a.nsel >= 2 && a.nsel <= MAX_SEL, SSG_EINTERNAL,
+              "tensor-core prune: %d selection slots for pools of %d", a.nsel, L);
+  const size_t smem = prune_tc_smem(kchunks, L, a.nsel);
   ensure_smem((const void*)k_prune_tc, smem);
   const int grid = (int)std::min<int64_t>(n, num_sms());
-  SSG_LAUNCH(k_prune_tc, grid, THREADS_P, smem, st, mx, a);
+  SSG_LAUNCH(k_prune_tc, grid, (FIRST_SEL + a.nsel) * 32, smem, st, mx, a);
   int h = 0;
   SSG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
