@@ -1,10 +1,10 @@
 // SSG prune (Alg. 2 selection applied to every pool, Alg. 3) with the pool's Gram matrix
 // on the 5th-generation tensor cores, for integer data that bf16 holds exactly.
 //
-// For node x with candidates c_1..c_m (m <= 127) the 128 rows [x, c_1, .., c_m, ..] are
-// gathered into shared memory (TMA gather4, 128-byte swizzle) and one 128x128xd UMMA gives
-// H = C C^T in TMEM.  Every product and partial sum is an integer below 2^24, so H is
-// exact, and so is every centred dot product the angle rule needs:
+// For node x with candidates c_1..c_m (m <= 127) the rows [x, c_1, .., c_m] are copied
+// into shared memory in the tensor cores' operand layout (128-byte swizzle) and one
+// 128x128xd UMMA gives H = C C^T in TMEM.  Every product and partial sum is an integer
+// below 2^24, so H is exact, and so is every centred dot product the angle rule needs:
 //     G_jk = (c_j - x).(c_k - x) = H_jk - H_j0 - H_k0 + H_00,   G_jj = d2(x, c_j).
 // c_j and c_k conflict when cos(j, k) = G_jk / sqrt(G_jj G_kk) > cos(alpha); a zero-length
 // edge conflicts with every other exactly when 0 > cos(alpha).  The fp32 cosine decides
@@ -19,17 +19,17 @@
 // banks, so a column read across rows is conflict-free, as is a read along a row).  A
 // selection warp then takes the candidates in blocks of 32, one per lane: each lane tests
 // its candidate against the candidates kept in earlier blocks (a conflict with any of them
-// rejects it, whatever the order), and the block's survivors are settled one by one, the
-// lanes testing the candidates kept before them in the block.
+// rejects it, whatever the order); then each survivor is tested against the block's earlier
+// survivors at once (a bitmask per lane), and the greedy runs over those bitmasks.
 //
 // Persistent kernel, one CTA per SM:
-//   warp 0       gathers the node and candidate rows (gather4, 4 rows per TMA) into one
-//                of GSLOTS shared-memory tiles;
-//   warp 1       allocates 512 TMEM columns and issues the Gram UMMAs into one of 4 TMEM
+//   warps 0..2   load the rows of every third node into their tile (16-byte cp.async
+//                copies);
+//   warp 3       allocates 512 TMEM columns and issues the Gram UMMAs into one of 4 TMEM
 //                buffers;
-//   warps 2..5   copy the lower triangle of H into the node's slot, one TMEM lane quadrant
+//   warps 4..7   copy the lower triangle of H into the node's slot, one TMEM lane quadrant
 //                (32 rows) each;
-//   warps 6..    select, one warp per slot, warp s taking every nsel-th node.
+//   warps 8..    select, one warp per slot, warp s taking every nsel-th node.
 // Every wait is bounded (about 2 s); a wait that runs out sets an error word, tells the
 // other roles to stop, and the CTA releases its TMEM and exits.
 #include "common.cuh"
@@ -42,16 +42,19 @@ namespace {
 using namespace tc;
 
 constexpr int PT_ROWS = 128;                  // the node and up to 127 candidates
-constexpr int GSLOTS = 3;                     // gather tiles
+constexpr int GSLOTS = 3;                     // gather tiles, one loader warp each
+constexpr int MMA_WARP = GSLOTS;
 constexpr int COPY_WARPS = 4;                 // one per TMEM lane quadrant
+constexpr int FIRST_COPY = MMA_WARP + 1;
 constexpr int MAX_SEL = 8;                    // selection warps (and slots) at most
-constexpr int FIRST_SEL = 2 + COPY_WARPS;
+constexpr int FIRST_SEL = FIRST_COPY + COPY_WARPS;
 constexpr int THREADS_MAX = (FIRST_SEL + MAX_SEL) * 32;
 constexpr int TMEM_COLS_P = 512;              // 4 buffers of 128 fp32 columns
 constexpr int SMEM_CAP = 225 * 1024;
 constexpr int SEL_F4 = PT_ROWS + 32;         // per selection warp: kept list + block rows
 
 struct PtArgs {
+  const __nv_bfloat16* xb;      // the rows in bf16, dp = 64 kchunks values each
   const int32_t* pool_id;
   const int32_t* pool_len;
   int64_t n;
@@ -97,7 +100,7 @@ struct AngleRule {
 };
 
 __global__ void __launch_bounds__(THREADS_MAX, 1)
-k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
+k_prune_tc(PtArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t g_bytes = (uint32_t)p.kchunks * PT_ROWS * 128;
@@ -132,7 +135,7 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
     *abort_flag = 0;
     fence_barrier_init();
   }
-  if (warp == 1) {
+  if (warp == MMA_WARP) {
     tmem_alloc(smem_u32(tmem_slot), TMEM_COLS_P);
     tmem_relinquish();
   }
@@ -142,65 +145,68 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
   const uint32_t tmem_base = *tmem_slot;
   const int64_t n = p.n;
 
-  if (warp == 0) {
-    // ---------------- gather producer ----------------
-    // a node's length and candidate ids are loaded one node ahead, so that their latency
-    // overlaps the wait for a free tile
-    const int L = p.L;
-    int s = 0;
+  if (warp < GSLOTS) {
+    // ---------------- loader of tile s = warp: every GSLOTS-th node ----------------
+    // 16-byte cp.async copies straight into the UMMA operand layout (K-major, 128-byte
+    // swizzle: row r of a 64-column chunk at (r / 8) 1024 + (r % 8) 128 bytes, its 16-byte
+    // piece c at (c ^ (r % 8)) 16); the warp waits for its copies, makes them visible to
+    // the tensor cores' proxy and signals the tile.  A node's length and candidate ids load
+    // one node ahead.
+    const int s = warp, L = p.L, dp = p.kchunks * 64;
+    const int vpr = p.kchunks * 8;              // 16-byte pieces per row
+    const int rpi = 32 / vpr;                   // rows per warp step
+    const int sub = lane / vpr, v = lane % vpr, kc = v >> 3, c = v & 7;
+    unsigned char* tile = sG + (size_t)s * g_bytes + (size_t)kc * PT_ROWS * 128;
+    const int64_t step = (int64_t)GSLOTS * gridDim.x;
     uint32_t ph = 0;
     bool ok = true;
-    int64_t x = blockIdx.x;
-    int len = 0, yr[4] = {0, 0, 0, 0};
-    if (x < n) {
-      len = p.pool_len[x];
+    int64_t x = blockIdx.x + (int64_t)s * gridDim.x;
+    int len = 0, ids[4];
+    auto fetch = [&](int64_t xx) {
+      len = p.pool_len[xx];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int r = lane * 4 + e;  // row 0 is the node, row r the candidate r - 1
-        if (r >= 1 && r <= L) yr[e] = p.pool_id[x * L + r - 1];
+      for (int u = 0; u < 4; ++u) {
+        const int r = u * 32 + lane;            // row 0 is the node, row r the candidate r - 1
+        ids[u] = (r >= 1 && r <= L) ? p.pool_id[xx * L + r - 1] : (int)xx;
       }
-    }
-    for (; x < n && ok; x += gridDim.x) {
+    };
+    if (x < n) fetch(x);
+    for (; x < n; x += step) {
       const int lc = min(len, PT_ROWS - 1);
-      int y[4];
+      int cur[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int r = lane * 4 + e;
-        y[e] = (r == 0 || r > lc) ? (int)x : yr[e];
-      }
-      const int64_t xn = x + gridDim.x;
-      if (xn < n) {
-        len = p.pool_len[xn];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int r = lane * 4 + e;
-          if (r >= 1 && r <= L) yr[e] = p.pool_id[xn * L + r - 1];
-        }
-      }
+      for (int u = 0; u < 4; ++u) cur[u] = u * 32 + lane > lc ? (int)x : ids[u];
+      if (x + step < n) fetch(x + step);
       ok = mbar_wait(smem_u32(g_empty + s), ph ^ 1, abort_flag);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
         break;
       }
-      const int ng4 = (lc + 1 + 3) >> 2;
-      if (lane == 0) mbar_expect_tx(smem_u32(g_full + s), (uint32_t)ng4 * 4 * 128 * p.kchunks);
+      ph ^= 1;
+      const int nrows = lc + 1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u * 32 >= nrows) break;
+        for (int r0 = u * 32; r0 < min(nrows, u * 32 + 32); r0 += rpi) {
+          const int r = r0 + sub;
+          const int id = __shfl_sync(0xffffffffu, cur[u], r & 31);
+          if (r < nrows) {
+            const __nv_bfloat16* src = p.xb + (size_t)id * dp + kc * 64 + c * 8;
+            const uint32_t dst = smem_u32(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+          }
+        }
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane < ng4) {
-        unsigned char* dst = sG + (size_t)s * g_bytes + (size_t)lane * 4 * 128;
-        for (int kc = 0; kc < p.kchunks; ++kc)
-          tma_gather4(smem_u32(dst + (size_t)kc * PT_ROWS * 128), &tmX, smem_u32(g_full + s),
-                      kc * 64, y[0], y[1], y[2], y[3]);
-      }
-      if (++s == GSLOTS) {
-        s = 0;
-        ph ^= 1;
-      }
+      if (lane == 0) mbar_arrive(smem_u32(g_full + s));
     }
     if (!ok && lane == 0) {
       atomicOr(p.err, 1);
       *abort_flag = 1;
     }
-  } else if (warp == 1) {
+  } else if (warp == MMA_WARP) {
     // ---------------- Gram MMA issuer ----------------
     if (lane == 0) {
       int s = 0, b = 0;
@@ -443,7 +449,7 @@ k_prune_tc(const __grid_constant__ CUtensorMap tmX, PtArgs p) {
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) {
+  if (warp == MMA_WARP) {
     tc_fence_after();
     tmem_dealloc(tmem_base, TMEM_COLS_P);
   }
@@ -500,10 +506,10 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
   const int kchunks = dp / 64;
   Scratch<__nv_bfloat16> xb((size_t)n * dp, st);
   SSG_LAUNCH(k_rows_bf16, 8 * num_sms(), 256, 0, st, X, n, d, ld, xb.p, dp);
-  const CUtensorMap mx = make_map(xb.p, n, dp, 64, 1, CU_TENSOR_MAP_SWIZZLE_128B);
   Scratch<int> err(1, st);
   SSG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
   PtArgs a{};
+  a.xb = xb.p;
   a.pool_id = pool_id;
   a.pool_len = pool_len;
   a.n = n;
@@ -526,7 +532,7 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
   const size_t smem = prune_tc_smem(kchunks, L, a.nsel);
   ensure_smem((const void*)k_prune_tc, smem);
   const int grid = (int)std::min<int64_t>(n, num_sms());
-  SSG_LAUNCH(k_prune_tc, grid, (FIRST_SEL + a.nsel) * 32, smem, st, mx, a);
+  SSG_LAUNCH(k_prune_tc, grid, (FIRST_SEL + a.nsel) * 32, smem, st, a);
   int h = 0;
   SSG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
