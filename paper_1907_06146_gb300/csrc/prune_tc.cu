@@ -20,7 +20,8 @@
 // selection warp then takes the candidates in blocks of 32, one per lane: each lane tests
 // its candidate against the candidates kept in earlier blocks (a conflict with any of them
 // rejects it, whatever the order); then each survivor is tested against the block's earlier
-// survivors at once (a bitmask per lane), and the greedy runs over those bitmasks.
+// survivors at once (a bitmask per lane), and the greedy runs over those bitmasks in rounds
+// (a survivor is kept once every earlier survivor it conflicts with is rejected).
 //
 // Persistent kernel, one CTA per SM:
 //   warps 0..2   load the rows of every third node into their tile (16-byte cp.async
@@ -401,25 +402,21 @@ k_prune_tc(PtArgs p) {
               if (at.exact((P[tj + b0 + e] - k4.x) + t0j, dj, k4.y)) M |= 1u << e;
             }
           }
-          // 3. the greedy over the survivors in order (every lane takes the same steps)
-          uint32_t kb = 0, rest2 = alive & (alive - 1u);
-          int kn = kept;
-          int e = __ffs(alive) - 1;
-          uint32_t me_m = __shfl_sync(0xffffffffu, M, e);
-          while (e >= 0 && kn < R) {
-            const int en = rest2 ? __ffs(rest2) - 1 : -1;
-            rest2 &= rest2 - 1u;
-            const uint32_t mn = __shfl_sync(0xffffffffu, M, en & 31);
-            if ((me_m & kb) == 0u) {
-              kb |= 1u << e;
-              ++kn;
-            }
-            e = en;
-            me_m = mn;
+          // 3. the greedy over the survivors in order, in rounds: a survivor whose earlier
+          //    conflicting survivors are all rejected is kept, one with a kept one rejected
+          uint32_t U = alive, K = 0;
+          while (U != 0u) {
+            const bool und = (U >> lane) & 1u;
+            const uint32_t bk = __ballot_sync(0xffffffffu, und && (M & (K | U)) == 0u);
+            const uint32_t br = __ballot_sync(0xffffffffu, und && (M & K) != 0u);
+            K |= bk;
+            U &= ~(bk | br);
           }
+          // stop at R: the first R - kept of them in order
+          while (__popc(K) > R - kept) K &= ~(1u << (31 - __clz(K)));
           // 4. the block's kept candidates join the kept list in order
-          if ((kb >> lane) & 1u) S[kept + __popc(kb & lt)] = make_float4(aj, dj, rj, __int_as_float(j));
-          kept = kn;
+          if ((K >> lane) & 1u) S[kept + __popc(K & lt)] = make_float4(aj, dj, rj, __int_as_float(j));
+          kept += __popc(K);
         }
         __syncwarp();
       }
