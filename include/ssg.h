@@ -15,7 +15,10 @@
  *    enqueue their kernels on it and return; ssg_build and ssg_connect synchronise the
  *    stream at stage boundaries to read sizes.
  *  - Scratch memory is taken from the CUDA stream-ordered allocator on `stream` and
- *    released before the call returns (in stream order).
+ *    released before the call returns (in stream order).  At its first scratch
+ *    allocation on a device the library sets that device's default pool to keep up to
+ *    an eighth of the device memory reserved across synchronisations (the pool's release
+ *    threshold), so that the stages of a build do not map their scratch afresh each time.
  *  - Errors come back as an ssg_status; nothing is thrown across the ABI.  After a
  *    non-OK status, ssg_last_error() gives a message for the calling thread.  EINVAL
  *    means an argument is out of range and nothing was enqueued.

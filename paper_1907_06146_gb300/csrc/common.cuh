@@ -71,6 +71,28 @@ struct Fail {
   } while (0)
 
 // Stream-ordered scratch buffer, released in stream order when it leaves scope.
+// Scratch comes from the current device's default stream-ordered pool.  With the pool's
+// default release threshold (0) every stream synchronisation hands its free memory back
+// to the driver, and the next allocation maps it again; a build synchronises at its stage
+// boundaries, so the pool keeps up to an eighth of the device memory between them
+// (once per device, at its first scratch allocation).
+inline void keep_pool_memory() {
+  static std::mutex mu;
+  static std::unordered_map<int, bool> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  done[dev] = true;
+  cudaMemPool_t pool;
+  size_t free_b = 0, total_b = 0;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess ||
+      cudaMemGetInfo(&free_b, &total_b) != cudaSuccess)
+    return;
+  uint64_t keep = (uint64_t)total_b / 8;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+}
+
 template <typename T>
 struct Scratch {
   T* p = nullptr;
@@ -87,6 +109,7 @@ struct Scratch {
       set_error("scratch allocation of %zu bytes failed: injected", n * sizeof(T));
       throw Fail{SSG_ENOMEM};
     }
+    keep_pool_memory();
     cudaError_t e = cudaMallocAsync((void**)&p, n * sizeof(T), st);
     if (e != cudaSuccess) {
       p = nullptr;

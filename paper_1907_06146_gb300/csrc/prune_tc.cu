@@ -154,9 +154,9 @@ k_prune_tc(PtArgs p) {
     // the tensor cores' proxy and signals the tile.  A node's length and candidate ids load
     // one node ahead.
     const int s = warp, L = p.L, dp = p.kchunks * 64;
-    const int vpr = p.kchunks * 8;              // 16-byte pieces per row
-    const int rpi = 32 / vpr;                   // rows per warp step
-    const int sub = lane / vpr, v = lane % vpr, kc = v >> 3, c = v & 7;
+    const int lpr = p.kchunks * 4;              // lanes per row, two 16-byte pieces each
+    const int rpi = 32 / lpr;                   // rows per warp step
+    const int sub = lane / lpr, v = (lane % lpr) * 2, kc = v >> 3, c = v & 7;
     unsigned char* tile = sG + (size_t)s * g_bytes + (size_t)kc * PT_ROWS * 128;
     const int64_t step = (int64_t)GSLOTS * gridDim.x;
     uint32_t ph = 0;
@@ -193,8 +193,11 @@ k_prune_tc(PtArgs p) {
           const int id = __shfl_sync(0xffffffffu, cur[u], r & 31);
           if (r < nrows) {
             const __nv_bfloat16* src = p.xb + (size_t)id * dp + kc * 64 + c * 8;
-            const uint32_t dst = smem_u32(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+            const uint32_t dst = smem_u32(tile + (r >> 3) * 1024 + (r & 7) * 128);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + ((c ^ (r & 7)) << 4)),
+                         "l"(src) : "memory");
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (((c + 1) ^ (r & 7)) << 4)),
+                         "l"(src + 8) : "memory");
           }
         }
       }
