@@ -155,11 +155,54 @@ __device__ __forceinline__ float team8_dist_u8(const uint8_t* __restrict__ a,
   return (float)s;
 }
 
-// warp_fill_dist_keys from byte rows (X8 [n][ld] bytes, xi8 node i's row).
+// warp_fill_dist_keys from byte rows (X8 [n][ld] bytes, xi8 node i's row).  Rows of at
+// most 128 bytes in 16-byte pieces (ld a multiple of 16) take one piece per team lane and
+// four candidates per team at a time, so that a lane has four row loads in flight; other
+// widths go a word at a time.  The sums are integers (exact in int32, and in fp32 below
+// 2^24), so the order does not change the value.
 __device__ __forceinline__ void warp_fill_dist_keys_u8(uint64_t* keys, int m,
                                                        const uint8_t* __restrict__ X8, int ld,
                                                        const uint8_t* __restrict__ xi8) {
   const int lane = lane_id(), team = lane >> 3, tl = lane & 7;
+  if ((ld & 15) == 0 && ld <= 128) {
+    const bool has = tl < (ld >> 4);
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    const uint4 a = has ? __ldg((const uint4*)xi8 + tl) : zero;
+    const unsigned aa = __dp4a(a.w, a.w, __dp4a(a.z, a.z, __dp4a(a.y, a.y, __dp4a(a.x, a.x, 0u))));
+    for (int t0 = 0; t0 < m; t0 += 16) {
+      int id[4];
+      bool val[4];
+      uint4 y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + u * 4 + team;
+        val[u] = t < m;
+        id[u] = val[u] ? key_id(keys[t]) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        y[u] = (val[u] && has) ? __ldg((const uint4*)(X8 + (int64_t)id[u] * ld) + tl) : zero;
+      int s[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned bb = __dp4a(y[u].w, y[u].w, __dp4a(y[u].z, y[u].z,
+                            __dp4a(y[u].y, y[u].y, __dp4a(y[u].x, y[u].x, 0u))));
+        const unsigned ab = __dp4a(a.w, y[u].w, __dp4a(a.z, y[u].z,
+                            __dp4a(a.y, y[u].y, __dp4a(a.x, y[u].x, 0u))));
+        s[u] = (int)aa + (int)bb - 2 * (int)ab;
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (val[u] && tl == 0) keys[t0 + u * 4 + team] = make_key((float)s[u], id[u]);
+    }
+    __syncwarp();
+    return;
+  }
   const int ldw = ld >> 2;
   for (int t0 = 0; t0 < m; t0 += 4) {
     const int t = t0 + team;
