@@ -262,6 +262,41 @@ __device__ __forceinline__ void warp_sort_keys(uint64_t* a, int m) {
   }
 }
 
+// The same network for larger m (the pools' 256 keys): each compare-exchange step takes
+// the m / 2 pairs (i, i + j), i with bit j clear, four per lane at a time -- all loads,
+// then the exchanges (the pairs are disjoint) -- at the cost of more registers.
+__device__ __forceinline__ void warp_sort_keys_wide(uint64_t* a, int m) {
+  const int lane = lane_id(), half = m >> 1;
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int lj = 31 - __clz(j);
+      for (int q0 = 0; q0 < half; q0 += 128) {
+        int ii[4];
+        bool act[4];
+        uint64_t x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + u * 32 + lane;
+          act[u] = q < half;
+          ii[u] = ((q >> lj) << (lj + 1)) | (q & (j - 1));
+          if (act[u]) {
+            x[u] = a[ii[u]];
+            y[u] = a[ii[u] + j];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (act[u] && (x[u] > y[u]) == ((ii[u] & k) == 0)) {
+            a[ii[u]] = y[u];
+            a[ii[u] + j] = x[u];
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // Same for a whole thread block (blockDim.x threads).
 __device__ __forceinline__ void block_sort_keys(uint64_t* a, int m) {
   for (int k = 2; k <= m; k <<= 1) {

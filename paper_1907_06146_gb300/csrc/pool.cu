@@ -49,7 +49,7 @@ __device__ __forceinline__ void pool_finish(uint64_t* keys, int m, int L, int ex
   while (mp < m) mp <<= 1;
   for (int t = m + lane; t < mp; t += 32) keys[t] = KEY_NONE;
   __syncwarp();
-  warp_sort_keys(keys, mp);
+  warp_sort_keys_wide(keys, mp);
   const int keep = m < L ? m : L;
   if (!exact && m > 1) {
     int f = warp_fix_runs(keys, m, keep, d64, X, ld, d, xi, rel);
