@@ -279,6 +279,38 @@ def test_prune_integer_duplicates_full_tile(ssg):
         np.testing.assert_array_equal(_np(adj), ref[0])
 
 
+def test_prune_tensor_core_exact_angles_ragged_pools(ssg):
+    """0/1 rows of 64 values with four ones among the first 12 columns: many centred pairs
+    meet at exactly 60 degrees, where the tensor-core prune's fp64 re-test decides (an
+    angle of exactly alpha keeps the edge), both against the candidates kept in earlier
+    blocks of 32 and among a block's survivors.  Pool lengths are cut at random (0 to 127
+    candidates), so that empty pools and every block boundary occur; repeated rows give
+    zero-length edges (conflicts above 90 degrees); R = 3 stops inside the first block."""
+    rng = np.random.default_rng(45)
+    n, d = 3000, 64
+    base = np.zeros((n, d), np.float32)
+    for r in range(n):
+        base[r, rng.choice(12, 4, replace=False)] = 1.0
+    base[:, 12:] = (rng.random((n, d - 12)) < 0.02).astype(np.float32)
+    knn, _ = oracle.knn_rows(base, 60)
+    pid, _, pl = oracle.pool(base, knn, 127)
+    pl = np.minimum(pl, rng.integers(0, 128, size=n)).astype(np.int32)
+    pid = np.where(np.arange(127)[None, :] < pl[:, None], pid, -1).astype(np.int32)
+    assert (pl == 0).any() and (pl == 127).any()
+    for alpha, R in ((60.0, 70), (60.0, 3), (45.0, 128), (100.0, 20)):
+        ref = oracle.prune(base, pid, pl, R, alpha)
+        adj, deg = ssg.prune(_cuda(base), _cuda(pid), _cuda(pl), R, alpha)
+        np.testing.assert_array_equal(_np(deg), ref[1])
+        np.testing.assert_array_equal(_np(adj), ref[0])
+    # the data do hold centred pairs at exactly 60 degrees
+    i = int(np.argmax(pl))
+    c = base[pid[i, :pl[i]]] - base[i]
+    g = c.astype(np.float64) @ c.T.astype(np.float64)
+    nrm = np.sqrt(np.diag(g))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        assert int(np.sum(np.isclose(g / np.outer(nrm, nrm), 0.5, rtol=0, atol=1e-12))) > 0
+
+
 # ---- a4: reverse merge -------------------------------------------------------------------
 @pytest.mark.parametrize("which", ["small", "int"])
 def test_reverse(ssg, which, small, intdata, small_ref, int_ref):
