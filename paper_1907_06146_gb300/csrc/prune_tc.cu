@@ -51,8 +51,7 @@ constexpr int MAX_SEL = 8;                    // selection warps (and slots) at 
 constexpr int FIRST_SEL = FIRST_COPY + COPY_WARPS;
 constexpr int THREADS_MAX = (FIRST_SEL + MAX_SEL) * 32;
 constexpr int TMEM_COLS_P = 512;              // 4 buffers of 128 fp32 columns
-constexpr int SMEM_CAP = 225 * 1024;
-constexpr int SEL_F4 = PT_ROWS + 32;         // per selection warp: kept list + block rows
+constexpr int SMEM_CAP = 227 * 1024;          // the opt-in limit of one CTA
 
 struct PtArgs {
   const __nv_bfloat16* xb;      // the rows in bf16, dp = 64 kchunks values each
@@ -62,6 +61,7 @@ struct PtArgs {
   int L, R, kchunks;
   int nsel;                     // selection warps = slots
   int slot_floats;              // floats of one slot (the lower triangle of the longest pool)
+  int sel_f4;                   // float4s per selection warp: the kept list (R) + a block's rows (32)
   float cosA32, margin;
   double cosA64;
   int32_t* adj;
@@ -108,8 +108,8 @@ k_prune_tc(PtArgs p) {
   const int nsel = p.nsel;
   unsigned char* sG = sm;                                            // GSLOTS gather tiles
   float* sP = (float*)(sG + (size_t)GSLOTS * g_bytes);               // nsel slots
-  float4* sK = (float4*)(sP + (size_t)nsel * p.slot_floats);          // nsel x SEL_F4
-  uint64_t* bars = (uint64_t*)(sK + (size_t)nsel * SEL_F4);
+  float4* sK = (float4*)(sP + (size_t)nsel * p.slot_floats);          // nsel x sel_f4
+  uint64_t* bars = (uint64_t*)(sK + (size_t)nsel * p.sel_f4);
   uint64_t* g_full = bars;
   uint64_t* g_empty = g_full + GSLOTS;
   uint64_t* t_full = g_empty + GSLOTS;
@@ -302,8 +302,8 @@ k_prune_tc(PtArgs p) {
     // ---------------- selection in candidate order ----------------
     const int w = warp - FIRST_SEL;
     const float* P = sP + (size_t)w * p.slot_floats;
-    float4* S = sK + (size_t)w * SEL_F4;     // kept: H_k0, G_kk, 1/sqrt(G_kk), row k
-    float4* T4 = S + PT_ROWS;                // the block's rows: H_j0, G_jj, 1/sqrt(G_jj)
+    float4* S = sK + (size_t)w * p.sel_f4;   // kept: H_k0, G_kk, 1/sqrt(G_kk), row k
+    float4* T4 = S + p.R;                    // the block's rows: H_j0, G_jj, 1/sqrt(G_jj)
     AngleRule at{p.cosA32 + p.margin, p.cosA32 - p.margin, p.cosA64, p.border, 0.0 > p.cosA64,
                  0ull, 0ull};
     const int R = p.R, L = p.L;
@@ -479,16 +479,20 @@ size_t prune_tc_fixed_smem(int kchunks) {
 }
 
 // Selection warps (and slots) that fit beside the gather tiles, at most MAX_SEL.
-int prune_tc_nsel(int kchunks, int L) {
+int prune_tc_sel_f4(int R) { return R + 32; }
+
+int prune_tc_nsel(int kchunks, int L, int R) {
   const size_t fixed = prune_tc_fixed_smem(kchunks);
   if (fixed >= (size_t)SMEM_CAP) return 0;
-  const size_t per = (size_t)prune_tc_slot_floats(L) * sizeof(float) + SEL_F4 * sizeof(float4);
+  const size_t per = (size_t)prune_tc_slot_floats(L) * sizeof(float) +
+                     (size_t)prune_tc_sel_f4(R) * sizeof(float4);
   return (int)std::min<size_t>(MAX_SEL, ((size_t)SMEM_CAP - fixed) / per);
 }
 
-size_t prune_tc_smem(int kchunks, int L, int nsel) {
+size_t prune_tc_smem(int kchunks, int L, int R, int nsel) {
   return prune_tc_fixed_smem(kchunks) +
-         (size_t)nsel * ((size_t)prune_tc_slot_floats(L) * sizeof(float) + SEL_F4 * sizeof(float4));
+         (size_t)nsel * ((size_t)prune_tc_slot_floats(L) * sizeof(float) +
+                         (size_t)prune_tc_sel_f4(R) * sizeof(float4));
 }
 
 }  // namespace
@@ -496,7 +500,7 @@ size_t prune_tc_smem(int kchunks, int L, int nsel) {
 bool prune_tc_available(int d, int L, int R) {
   const int kchunks = (d + 63) / 64;
   return knn_tc_available(d) && kchunks <= 2 && L >= 1 && L <= PT_ROWS - 1 && R >= 1 &&
-         R <= PT_ROWS && prune_tc_nsel(kchunks, L) >= 2;
+         R <= PT_ROWS && prune_tc_nsel(kchunks, L, R) >= 2;
 }
 
 void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
@@ -516,7 +520,8 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
   a.L = L;
   a.R = R;
   a.kchunks = kchunks;
-  a.nsel = prune_tc_nsel(kchunks, L);
+  a.nsel = prune_tc_nsel(kchunks, L, R);
+  a.sel_f4 = prune_tc_sel_f4(R);
   a.slot_floats = prune_tc_slot_floats(L);
   a.cosA32 = (float)cos_a;
   a.cosA64 = cos_a;
@@ -529,7 +534,7 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
   a.err = err.p;
   SSG_REQUIRE(a.nsel >= 2 && a.nsel <= MAX_SEL, SSG_EINTERNAL,
               "tensor-core prune: %d selection slots for pools of %d", a.nsel, L);
-  const size_t smem = prune_tc_smem(kchunks, L, a.nsel);
+  const size_t smem = prune_tc_smem(kchunks, L, R, a.nsel);
   ensure_smem((const void*)k_prune_tc, smem);
   const int grid = (int)std::min<int64_t>(n, num_sms());
   SSG_LAUNCH(k_prune_tc, grid, (FIRST_SEL + a.nsel) * 32, smem, st, a);
