@@ -209,11 +209,13 @@ void prune_wide_batched_launch(const WideBatchPlan& plan, const int2* items, int
                                unsigned long long* next, cudaStream_t st);
 
 // The same prune with each pool's Gram matrix on the tensor cores (data exact in bf16,
-// d <= 128, L <= 127, R <= 128; true where that path is available).
+// d <= 128, L <= 127, R <= 128; true where that path is available).  split: pools of up to
+// 63 candidates go to a launch of their own with smaller slots (for pools whose lengths
+// vary widely, like the reverse merge's lists).
 bool prune_tc_available(int d, int L, int R);
 void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
                   const int32_t* pool_len, int L, int R, double cos_a, double border,
-                  int32_t* adj, int32_t* deg, Counters* dctr, cudaStream_t st);
+                  int32_t* adj, int32_t* deg, Counters* dctr, cudaStream_t st, bool split = false);
 
 // Reverse-neighbour merge; returns the largest in-degree.  tc: the prune of lists of up to
 // 127 candidates on the tensor cores where the data allow it.  X8 as for pool_run.

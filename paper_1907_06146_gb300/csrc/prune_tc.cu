@@ -57,7 +57,8 @@ struct PtArgs {
   const __nv_bfloat16* xb;      // the rows in bf16, dp = 64 kchunks values each
   const int32_t* pool_id;
   const int32_t* pool_len;
-  int64_t n;
+  const int32_t* items;         // nullable: the nodes to prune (else 0 .. n - 1)
+  int64_t n;                    // nodes to prune (items' length)
   int L, R, kchunks;
   int nsel;                     // selection warps = slots
   int slot_floats;              // floats of one slot (the lower triangle of the longest pool)
@@ -145,6 +146,7 @@ k_prune_tc(PtArgs p) {
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int64_t n = p.n;
+  auto node = [&](int64_t t) -> int64_t { return p.items ? (int64_t)p.items[t] : t; };
 
   if (warp < GSLOTS) {
     // ---------------- loader of tile s = warp: every GSLOTS-th node ----------------
@@ -161,9 +163,10 @@ k_prune_tc(PtArgs p) {
     const int64_t step = (int64_t)GSLOTS * gridDim.x;
     uint32_t ph = 0;
     bool ok = true;
-    int64_t x = blockIdx.x + (int64_t)s * gridDim.x;
+    int64_t t = blockIdx.x + (int64_t)s * gridDim.x;
     int len = 0, ids[4];
-    auto fetch = [&](int64_t xx) {
+    auto fetch = [&](int64_t tt) {
+      const int64_t xx = node(tt);
       len = p.pool_len[xx];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -171,13 +174,14 @@ k_prune_tc(PtArgs p) {
         ids[u] = (r >= 1 && r <= L) ? p.pool_id[xx * L + r - 1] : (int)xx;
       }
     };
-    if (x < n) fetch(x);
-    for (; x < n; x += step) {
+    if (t < n) fetch(t);
+    for (; t < n; t += step) {
+      const int64_t x = node(t);
       const int lc = min(len, PT_ROWS - 1);
       int cur[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) cur[u] = u * 32 + lane > lc ? (int)x : ids[u];
-      if (x + step < n) fetch(x + step);
+      if (t + step < n) fetch(t + step);
       ok = mbar_wait(smem_u32(g_empty + s), ph ^ 1, abort_flag);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
@@ -254,10 +258,10 @@ k_prune_tc(PtArgs p) {
     int b = 0, s = 0;
     uint32_t tph = 0, sph = 0;
     bool ok = true;
-    int len = blockIdx.x < n ? p.pool_len[blockIdx.x] : 0;   // one node ahead
-    for (int64_t x = blockIdx.x; x < n; x += gridDim.x) {
+    int len = blockIdx.x < n ? p.pool_len[node(blockIdx.x)] : 0;   // one node ahead
+    for (int64_t t = blockIdx.x; t < n; t += gridDim.x) {
       const int nrows = min(len, PT_ROWS - 1) + 1;
-      if (x + gridDim.x < n) len = p.pool_len[x + gridDim.x];
+      if (t + gridDim.x < n) len = p.pool_len[node(t + gridDim.x)];
       ok = mbar_wait(smem_u32(t_full + b), tph, abort_flag) &&
            mbar_wait(smem_u32(d_empty + s), sph ^ 1, abort_flag);
       if (!__all_sync(0xffffffffu, ok)) {
@@ -311,16 +315,17 @@ k_prune_tc(PtArgs p) {
     const int64_t step = (int64_t)nsel * gridDim.x;
     uint32_t ph = 0;
     bool ok = true;
-    int64_t x = blockIdx.x + (int64_t)w * gridDim.x;
-    int len = x < n ? p.pool_len[x] : 0;     // one node ahead
-    for (; x < n; x += step) {
+    int64_t t = blockIdx.x + (int64_t)w * gridDim.x;
+    int len = t < n ? p.pool_len[node(t)] : 0;   // one node ahead
+    for (; t < n; t += step) {
+      const int64_t x = node(t);
       const int nrows = min(len, PT_ROWS - 1) + 1;
       // the candidate ids (for the output) and the next length load during the wait
       const int32_t* cand = p.pool_id + x * L;
       int cid[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) cid[u] = u * 32 + lane < nrows - 1 ? cand[u * 32 + lane] : -1;
-      if (x + step < n) len = p.pool_len[x + step];
+      if (t + step < n) len = p.pool_len[node(t + step)];
       ok = mbar_wait(smem_u32(d_full + w), ph, abort_flag);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
@@ -503,26 +508,27 @@ bool prune_tc_available(int d, int L, int R) {
          R <= PT_ROWS && prune_tc_nsel(kchunks, L, R) >= 2;
 }
 
-void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
-                  const int32_t* pool_len, int L, int R, double cos_a, double border,
-                  int32_t* adj, int32_t* deg, Counters* dctr, cudaStream_t st) {
-  const int dp = (d + 63) & ~63;
-  const int kchunks = dp / 64;
-  Scratch<__nv_bfloat16> xb((size_t)n * dp, st);
-  SSG_LAUNCH(k_rows_bf16, 8 * num_sms(), 256, 0, st, X, n, d, ld, xb.p, dp);
-  Scratch<int> err(1, st);
-  SSG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+namespace {
+
+// One launch over `items` (null: nodes 0 .. nitems - 1), slots sized for pools of up to
+// Lrows candidates (pool rows L apart).
+void launch_prune_tc(const __nv_bfloat16* xb, int kchunks, const int32_t* items, int64_t nitems,
+                     const int32_t* pool_id, const int32_t* pool_len, int L, int Lrows, int R,
+                     double cos_a, double border, int32_t* adj, int32_t* deg, Counters* dctr,
+                     int* err, cudaStream_t st) {
+  if (nitems <= 0) return;
   PtArgs a{};
-  a.xb = xb.p;
+  a.xb = xb;
   a.pool_id = pool_id;
   a.pool_len = pool_len;
-  a.n = n;
+  a.items = items;
+  a.n = nitems;
   a.L = L;
   a.R = R;
   a.kchunks = kchunks;
-  a.nsel = prune_tc_nsel(kchunks, L, R);
+  a.nsel = prune_tc_nsel(kchunks, Lrows, R);
   a.sel_f4 = prune_tc_sel_f4(R);
-  a.slot_floats = prune_tc_slot_floats(L);
+  a.slot_floats = prune_tc_slot_floats(Lrows);
   a.cosA32 = (float)cos_a;
   a.cosA64 = cos_a;
   a.margin = (float)(16.0 * U32 + border);
@@ -531,18 +537,79 @@ void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_
   a.n64 = &dctr->angle_fp64;
   a.border = border;
   a.nborder = &dctr->angle_border;
-  a.err = err.p;
+  a.err = err;
   SSG_REQUIRE(a.nsel >= 2 && a.nsel <= MAX_SEL, SSG_EINTERNAL,
-              "tensor-core prune: %d selection slots for pools of %d", a.nsel, L);
-  const size_t smem = prune_tc_smem(kchunks, L, R, a.nsel);
+              "tensor-core prune: %d selection slots for pools of %d", a.nsel, Lrows);
+  const size_t smem = prune_tc_smem(kchunks, Lrows, R, a.nsel);
   ensure_smem((const void*)k_prune_tc, smem);
-  const int grid = (int)std::min<int64_t>(n, num_sms());
+  const int grid = (int)std::min<int64_t>(nitems, num_sms());
   SSG_LAUNCH(k_prune_tc, grid, (FIRST_SEL + a.nsel) * 32, smem, st, a);
+}
+
+// Nodes with at most `thr` candidates to short_ids, the rest to long_ids (counts[0], [1]);
+// a warp takes one slot per list with one atomic.
+__global__ void k_split_by_len(const int32_t* __restrict__ len, int64_t n, int thr,
+                               int32_t* __restrict__ short_ids, int32_t* __restrict__ long_ids,
+                               int* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool in = i < n;
+    const bool sh = in && len[i] <= thr;
+    const unsigned bs = __ballot_sync(0xffffffffu, sh), bl = __ballot_sync(0xffffffffu, in && !sh);
+    int s0 = 0, l0 = 0;
+    if (lane == 0) {
+      if (bs) s0 = atomicAdd(counts, __popc(bs));
+      if (bl) l0 = atomicAdd(counts + 1, __popc(bl));
+    }
+    s0 = __shfl_sync(0xffffffffu, s0, 0);
+    l0 = __shfl_sync(0xffffffffu, l0, 0);
+    const unsigned lt = lanemask_lt();
+    if (sh) short_ids[s0 + __popc(bs & lt)] = (int32_t)i;
+    else if (in) long_ids[l0 + __popc(bl & lt)] = (int32_t)i;
+  }
+}
+
+void check_prune_err(const int* err, cudaStream_t st) {
   int h = 0;
-  SSG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SSG_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
   if (h != 0) note_device_status(SSG_ETIMEOUT);
   SSG_REQUIRE(h == 0, SSG_ETIMEOUT, "tensor-core prune: a pipeline wait timed out (code %d)", h);
+}
+
+}  // namespace
+
+void prune_run_tc(const float* X, int ld, int d, int64_t n, const int32_t* pool_id,
+                  const int32_t* pool_len, int L, int R, double cos_a, double border,
+                  int32_t* adj, int32_t* deg, Counters* dctr, cudaStream_t st, bool split) {
+  const int dp = (d + 63) & ~63;
+  const int kchunks = dp / 64;
+  Scratch<__nv_bfloat16> xb((size_t)n * dp, st);
+  SSG_LAUNCH(k_rows_bf16, 8 * num_sms(), 256, 0, st, X, n, d, ld, xb.p, dp);
+  Scratch<int> err(3, st);
+  SSG_CUDA(cudaMemsetAsync(err.p, 0, 3 * sizeof(int), st));
+  constexpr int SHORT = 63;   // pools of up to 63 candidates: slots a third the size
+  if (!split || L <= SHORT) {
+    launch_prune_tc(xb.p, kchunks, nullptr, n, pool_id, pool_len, L, L, R, cos_a, border, adj,
+                    deg, dctr, err.p, st);
+  } else {
+    // short pools (most merged reverse lists) get small slots and more selection warps
+    Scratch<int32_t> ids((size_t)2 * n, st);
+    SSG_LAUNCH(k_split_by_len, 4 * num_sms(), 256, 0, st, pool_len, n, SHORT, ids.p, ids.p + n,
+               err.p + 1);
+    int cnt[2] = {0, 0};
+    SSG_CUDA(cudaMemcpyAsync(cnt, err.p + 1, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    SSG_CUDA(cudaStreamSynchronize(st));
+    SSG_REQUIRE(cnt[0] >= 0 && cnt[1] >= 0 && (int64_t)cnt[0] + cnt[1] == n, SSG_EINTERNAL,
+                "tensor-core prune: split %d + %d of %lld pools", cnt[0], cnt[1], (long long)n);
+    launch_prune_tc(xb.p, kchunks, ids.p, cnt[0], pool_id, pool_len, L, SHORT, R, cos_a, border,
+                    adj, deg, dctr, err.p, st);
+    launch_prune_tc(xb.p, kchunks, ids.p + n, cnt[1], pool_id, pool_len, L, L, R, cos_a, border,
+                    adj, deg, dctr, err.p, st);
+  }
+  check_prune_err(err.p, st);
 }
 
 }  // namespace ssg

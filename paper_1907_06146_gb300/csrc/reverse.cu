@@ -305,7 +305,8 @@ int reverse_run(const float* X, const uint8_t* X8, int ld, int d, int64_t n,
              deg1, big.p, small.p, &dctr->order_fp64, &dctr->angle_fp64, Vg.p, lists.p, list_len.p,
              limit, border, &dctr->angle_border);
   if (use_tc)
-    prune_run_tc(X, ld, d, n, lists.p, list_len.p, limit, R, cos_a, border, adj1, deg1, dctr, st);
+    prune_run_tc(X, ld, d, n, lists.p, list_len.p, limit, R, cos_a, border, adj1, deg1, dctr, st,
+                 true);
   int h[2];
   SSG_CUDA(cudaMemcpyAsync(h, small.p, sizeof(h), cudaMemcpyDeviceToHost, st));
   SSG_CUDA(cudaStreamSynchronize(st));
